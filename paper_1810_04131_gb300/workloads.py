@@ -1,0 +1,239 @@
+"""Seeded synthetic particle configurations (inputs only).
+
+This module draws particle systems: centres, orientations and semi-axes,
+with a minimum surface gap between particles. It holds none of the method's
+arithmetic (no discretisation, no kernel, no solve), so both the CUDA path
+and the FP64 oracle read their inputs from here.
+
+The paper measures on randomly generated, non-overlapping unit disks in a
+square box (Section 6.3, Table 2) and on Janus ellipses (Section 2.1). The
+named workloads below follow that recipe with the sizes of the benchmark
+configurations:
+
+  * ``disks8``    8 unit disks in a 20x20 box, gap >= 0.5, 16x16 nodes, rho=1, QBX order 8.
+  * ``disks512``  512 unit disks in a 200x200 box, gap >= 0.3, 16x16 nodes, rho=1, QBX order 10.
+  * ``ellipses512`` 512 ellipses 1.0x0.5 in a 200x200 box, gap >= 0.2, 16x16 nodes, QBX order 10.
+  * ``disks8192`` 8192 unit disks in an 800x800 box, gap >= 0.3, 16x16 nodes.
+  * ``stream``    seeded request stream (Poisson arrivals, log-uniform sizes).
+
+A particle row is ``(shape, cx, cy, phi, A, B)`` with shape 0 = disk and
+1 = ellipse; A is the semi-axis along the director d = (cos phi, sin phi)
+and B the one across it (A = B = radius for a disk).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SHAPE_DISK = 0
+SHAPE_ELLIPSE = 1
+
+# label kinds (Dirichlet data generators); values match the C header
+LABEL_TANH = 0     # f = (1 + tanh(param * cos(theta - phi))) / 2
+LABEL_SINP = 1     # f = 1 - sin^param(theta - phi)          (Eq. JanusBC)
+LABEL_COS = 2      # f = (1 + cos(theta - phi)) / 2          (the analytic test of Eq. true_soln)
+LABEL_CUSTOM = 3
+
+
+def _boundary_samples(p, m=4096):
+    """Dense boundary points of one particle row (for gap checks only)."""
+    t = np.linspace(0.0, 2.0 * np.pi, m, endpoint=False)
+    c, s = math.cos(p[3]), math.sin(p[3])
+    u = p[4] * np.cos(t)
+    v = p[5] * np.sin(t)
+    return np.stack([p[1] + c * u - s * v, p[2] + s * u + c * v], axis=1)
+
+
+def _gap(p, q):
+    """Minimum distance between two particle boundaries (disks exact, ellipses sampled)."""
+    d = math.hypot(p[1] - q[1], p[2] - q[2])
+    if p[0] == SHAPE_DISK and q[0] == SHAPE_DISK:
+        return d - p[4] - q[4]
+    # conservative pre-check: bounding circles already far apart
+    ra, rb = max(p[4], p[5]), max(q[4], q[5])
+    if d - ra - rb > 0.0:
+        lo = d - ra - rb
+        if lo >= 1.0:  # far beyond any gap used here; exact value not needed
+            return lo
+    a = _boundary_samples(p)
+    b = _boundary_samples(q)
+    diff = a[:, None, :] - b[None, ::4, :]
+    return float(np.sqrt((diff ** 2).sum(-1)).min())
+
+
+def make_particles(n, box, gap, seed, shape=SHAPE_DISK, A=1.0, B=1.0,
+                   shapes=None, max_tries=2_000_000):
+    """Rejection-sample ``n`` non-overlapping particles in ``[0, box]^2``.
+
+    Centres are uniform in ``[R, box - R]^2`` (R = max semi-axis) and a
+    candidate is accepted when its surface gap to every accepted particle is
+    at least ``gap``; orientations are uniform in ``[0, 2 pi)``. ``shapes``
+    optionally gives a per-particle shape list (0 disk / 1 ellipse).
+    Returns a float64 array of shape (n, 6).
+    """
+    rng = np.random.default_rng(seed)
+    out = np.zeros((n, 6))
+    R = max(A, B)
+    cell = 2.0 * R + gap
+    grid = {}
+    k = 0
+    tries = 0
+    while k < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place %d particles (placed %d)" % (n, k))
+        cx, cy = rng.uniform(R, box - R, size=2)
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        sh = shape if shapes is None else shapes[k]
+        a_, b_ = (A, B) if sh == SHAPE_ELLIPSE else (A, A)
+        cand = np.array([sh, cx, cy, phi, a_, b_])
+        gx, gy = int(cx // cell), int(cy // cell)
+        ok = True
+        for ix in range(gx - 1, gx + 2):
+            for iy in range(gy - 1, gy + 2):
+                for j in grid.get((ix, iy), ()):
+                    if _gap(cand, out[j]) < gap:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            out[k] = cand
+            grid.setdefault((gx, gy), []).append(k)
+            k += 1
+    return out
+
+
+def off_surface_targets(particles, nt, box, min_dist, seed):
+    """``nt`` seeded targets uniform in ``[0, box]^2``, outside every particle
+    and at least ``min_dist`` from every boundary."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    samples = [_boundary_samples(p) for p in particles]
+    while len(pts) < nt:
+        t = rng.uniform(0.0, box, size=2)
+        ok = True
+        for p, s in zip(particles, samples):
+            d = math.hypot(t[0] - p[1], t[1] - p[2])
+            if d > max(p[4], p[5]) + min_dist + 0.01:
+                continue
+            # inside test in the particle frame, then sampled distance
+            c, sn = math.cos(p[3]), math.sin(p[3])
+            u = c * (t[0] - p[1]) + sn * (t[1] - p[2])
+            v = -sn * (t[0] - p[1]) + c * (t[1] - p[2])
+            if (u / p[4]) ** 2 + (v / p[5]) ** 2 <= 1.0:
+                ok = False
+                break
+            if np.sqrt(((s - t) ** 2).sum(-1)).min() < min_dist:
+                ok = False
+                break
+        if ok:
+            pts.append(t)
+    return np.array(pts)
+
+
+@dataclass
+class Workload:
+    """A named synthetic system: particles plus the numerical parameters."""
+    name: str
+    particles: np.ndarray
+    rho: float
+    n_panels: int = 16
+    n_gl: int = 16
+    qbx_order: int = 10
+    gmres_tol: float = 1e-10
+    label_kind: int = LABEL_TANH
+    label_param: float = 10.0
+    box: float = 0.0
+    targets: np.ndarray | None = None
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_particles(self):
+        return int(self.particles.shape[0])
+
+    @property
+    def n_nodes(self):
+        return self.n_particles * self.n_panels * self.n_gl
+
+
+def disks8():
+    """8 unit disks, 20x20 box, gap 0.5, N = 2048, rho = 1, QBX order 8."""
+    p = make_particles(8, 20.0, 0.5, seed=1)
+    t = off_surface_targets(p, 1000, 20.0, 0.25, seed=2)
+    return Workload("disks8", p, rho=1.0, qbx_order=8, box=20.0, targets=t)
+
+
+def disks512():
+    """512 unit disks, 200x200 box, gap 0.3, N = 131072, rho = 1, QBX order 10."""
+    p = make_particles(512, 200.0, 0.3, seed=3)
+    return Workload("disks512", p, rho=1.0, qbx_order=10, box=200.0)
+
+
+def ellipses512(rho=1.0):
+    """512 ellipses 1.0x0.5, 200x200 box, gap 0.2, N = 131072, QBX order 10."""
+    p = make_particles(512, 200.0, 0.2, seed=4, shape=SHAPE_ELLIPSE, A=1.0, B=0.5)
+    return Workload("ellipses512_rho%g" % rho, p, rho=rho, qbx_order=10, box=200.0)
+
+
+def disks8192():
+    """8192 unit disks, 800x800 box, gap 0.3, N = 2,097,152, rho = 1."""
+    p = make_particles(8192, 800.0, 0.3, seed=5)
+    return Workload("disks8192", p, rho=1.0, qbx_order=10, box=800.0)
+
+
+def small_system(n, seed, shape=SHAPE_DISK, n_panels=8, n_gl=16, rho=1.0,
+                 qbx_order=10, gap=0.5, A=1.0, B=1.0):
+    """A small seeded system for parity tests (box scaled to ~4% area fraction)."""
+    R = max(A, B)
+    box = max(4.0 * R + gap, math.sqrt(n * math.pi * R * R / 0.04))
+    p = make_particles(n, box, gap, seed=seed, shape=shape, A=A, B=B)
+    return Workload("small%d_s%d" % (n, seed), p, rho=rho, n_panels=n_panels,
+                    n_gl=n_gl, qbx_order=qbx_order, box=box)
+
+
+def request_stream(n_requests=2000, seed=6, rate=None, np_min=4, np_max=2048,
+                   pan_min=8, pan_max=32, rhos=(0.5, 1.0, 2.0), gap=0.3):
+    """Seeded serving stream: Poisson arrivals, log-uniform particle counts,
+    panels per particle uniform in [pan_min, pan_max], disk/ellipse 50/50,
+    rho from ``rhos``, box side 200*sqrt(Np/512) (about 4% area fraction).
+
+    Returns a list of dicts with the request parameters; the particles are
+    drawn lazily by ``materialise_request`` so that a long stream stays cheap.
+    """
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for i in range(n_requests):
+        if rate:
+            t += rng.exponential(1.0 / rate)
+        npart = int(round(math.exp(rng.uniform(math.log(np_min), math.log(np_max)))))
+        npan = int(rng.integers(pan_min, pan_max + 1))
+        shape = int(rng.integers(0, 2))
+        rho = float(rhos[int(rng.integers(0, len(rhos)))])
+        box = max(8.0, 200.0 * math.sqrt(npart / 512.0))
+        reqs.append(dict(id=i, arrival=t, n_particles=npart, n_panels=npan,
+                         shape=shape, rho=rho, box=box, gap=gap,
+                         seed=int(rng.integers(0, 2 ** 31 - 1))))
+    return reqs
+
+
+def materialise_request(r):
+    """Draw the particles of one stream request."""
+    A, B = (1.0, 0.5) if r["shape"] == SHAPE_ELLIPSE else (1.0, 1.0)
+    p = make_particles(r["n_particles"], r["box"], r["gap"], seed=r["seed"],
+                       shape=r["shape"], A=A, B=B)
+    return Workload("req%d" % r["id"], p, rho=r["rho"], n_panels=r["n_panels"],
+                    qbx_order=10, box=r["box"])
+
+
+WORKLOADS = {
+    "disks8": disks8,
+    "disks512": disks512,
+    "ellipses512": ellipses512,
+    "disks8192": disks8192,
+}

@@ -1,0 +1,381 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an identity, brute-force adaptive quadrature, an invariant, or a value
+the paper prints. Together they cover every step of the oracle (geometry,
+far kernel, QBX expansion, jump, solve, gradient, stress, force, torque,
+potential) so that a dropped term, a wrong sign or index or a transposed
+operand fails at least one of them (``test_planted_mistakes_are_caught``).
+"""
+import json
+import warnings
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+import scipy.special as sp
+
+from oracle import yk_oracle as yo
+from paper_1810_04131_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _disk(R=1.0, phi=0.0, cx=0.0, cy=0.0):
+    return np.array([[W.SHAPE_DISK, cx, cy, phi, R, R]])
+
+
+# --------------------------------------------------------------------------
+# geometry
+# --------------------------------------------------------------------------
+
+def test_geometry_weights_sum_to_perimeter():
+    """Sum of weights = perimeter: 2 pi R for a disk, 4 A E(1 - B^2/A^2)
+    for an ellipse (complete elliptic integral, scipy ellipe)."""
+    g = yo.make_geometry(_disk(1.7), 16, 16)
+    assert abs(g.w.sum() - 2 * math.pi * 1.7) < 1e-13
+    A, B = 1.0, 0.5
+    p = np.array([[W.SHAPE_ELLIPSE, 3.0, -1.0, 0.7, A, B]])
+    g = yo.make_geometry(p, 16, 16)
+    assert abs(g.w.sum() - 4 * A * sp.ellipe(1 - (B / A) ** 2)) < 1e-12
+    # normals: unit, orthogonal to the tangent, pointing away from the centre
+    assert np.allclose(np.hypot(g.nu[:, 0], g.nu[:, 1]), 1.0, atol=1e-15)
+    assert np.allclose((g.nu * g.tau).sum(1), 0.0, atol=1e-15)
+    assert ((g.nu * (g.x - p[0, 1:3])).sum(1) > 0).all()
+    # panel arclengths sum to the perimeter
+    assert abs(g.h.sum() - g.w.sum()) < 1e-12
+
+
+def test_janus_labels():
+    """Eq. JanusBC with theta measured from the director; the tanh and
+    cosine generators at the tail (theta = 0) and head (theta = pi)."""
+    p = _disk(1.0, phi=0.9)
+    g = yo.make_geometry(p, 16, 16)
+    th = np.arctan2(g.x[:, 1], g.x[:, 0]) - 0.9
+    assert np.allclose(yo.label(g, 1, 2), 1 - np.sin(th) ** 2, atol=1e-14)
+    assert np.allclose(yo.label(g, 2), 0.5 * (1 + np.cos(th)), atol=1e-14)
+    assert np.allclose(yo.label(g, 0, 10.0), 0.5 * (1 + np.tanh(10 * np.cos(th))), atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# kernel and expansion identities
+# --------------------------------------------------------------------------
+
+def test_graf_addition_yukawa():
+    """K0(|x-y|/rho) = sum_n K_n(|y-c|/rho) I_n(|x-c|/rho) e^{in(theta_x - phi_y)}
+    for |x - c| < |y - c| (Eq. graf-addition through K0(z) = i pi/2 H0(iz))."""
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        rho = rng.uniform(0.2, 5)
+        c = rng.normal(size=2)
+        r, s = rng.uniform(0.01, 0.4), rng.uniform(0.8, 2.0)
+        tx, ty = rng.uniform(0, 2 * np.pi, 2)
+        x = c + r * np.array([np.cos(tx), np.sin(tx)])
+        y = c + s * np.array([np.cos(ty), np.sin(ty)])
+        n = np.arange(-60, 61)
+        series = (sp.kv(n, s / rho) * sp.iv(n, r / rho) * np.exp(1j * n * (tx - ty))).sum()
+        assert abs(series - sp.k0(np.hypot(*(x - y)) / rho)) < 1e-13 * abs(series)
+
+
+def test_dl_kernel_is_normal_derivative_of_green():
+    """dl_kernel = dG/dnu_y and dl_kernel_grad = grad_x of it (central
+    differences of Eq. Gfunc)."""
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        rho = rng.uniform(0.3, 3)
+        x, y = rng.normal(size=2), rng.normal(size=2) + 2
+        a = rng.uniform(0, 2 * np.pi)
+        nu = np.array([np.cos(a), np.sin(a)])
+        h = 1e-5
+        fd = (yo.green(x, y + h * nu, rho) - yo.green(x, y - h * nu, rho)) / (2 * h)
+        k = yo.dl_kernel(x[None], y[None], nu[None], rho)[0]
+        assert abs(fd - k) < 1e-9 * max(1.0, abs(k))
+        gr = yo.dl_kernel_grad(x[None], y[None], nu[None], rho)[0]
+        for d in range(2):
+            e = np.zeros(2)
+            e[d] = h
+            fd = (yo.dl_kernel((x + e)[None], y[None], nu[None], rho)[0]
+                  - yo.dl_kernel((x - e)[None], y[None], nu[None], rho)[0]) / (2 * h)
+            assert abs(fd - gr[d]) < 1e-8 * max(1.0, abs(gr[d]))
+
+
+@pytest.mark.parametrize("rho", [0.25, 1.0, 4.0])
+def test_circle_eigenvalues(rho):
+    """On a circle of radius R the exterior limit of D maps cos(n theta) to
+    z I_n'(z) K_n(z) cos(n theta) with z = R/rho (Eq. djump with the
+    separable Yukawa potentials), and its normal derivative to
+    z I_n'(z) K_n'(z)/rho cos(n theta). Pins the far kernel, the QBX
+    expansion, the one-sided jump and the normal-derivative row."""
+    R = 1.3
+    o = yo.Oracle(_disk(R, phi=0.4), 16, 16, rho, yo.QBXParams(order=10))
+    g = o.geom
+    th = np.arctan2(g.x[:, 1], g.x[:, 0])
+    rows = list(range(3, g.n, 11))
+    z = R / rho
+    for n in (0, 1, 2, 3, 6):
+        for trig in (np.cos, np.sin):
+            sig = trig(n * th)
+            y, yn = o.apply_rows(sig, rows, want_grad=True)
+            lam = z * sp.ivp(n, z) * sp.kv(n, z)
+            lamn = z * sp.ivp(n, z) * sp.kvp(n, z) / rho
+            assert np.abs(y - lam * sig[rows]).max() < 3e-11
+            assert np.abs(yn - lamn * sig[rows]).max() < 1e-7 * max(1.0, abs(lamn))
+
+
+def _true_soln(X, rho, a=1.0):
+    """Eq. true_soln: the exterior solution for the unit disk with f = (1 + cos theta)/2."""
+    r = np.hypot(X[:, 0], X[:, 1])
+    th = np.arctan2(X[:, 1], X[:, 0])
+    u = 0.5 * (sp.k0(r / rho) / sp.k0(a / rho) + sp.k1(r / rho) / sp.k1(a / rho) * np.cos(th))
+    ur = 0.5 * (sp.kvp(0, r / rho) / sp.k0(a / rho)
+                + sp.kvp(1, r / rho) / sp.k1(a / rho) * np.cos(th)) / rho
+    ut = -0.5 * sp.k1(r / rho) / sp.k1(a / rho) * np.sin(th) / r
+    return u, ur, ut
+
+
+@pytest.mark.parametrize("rho", [0.25, 1.0, 4.0])
+def test_single_disk_analytic(rho):
+    """Section S2.2: the single Janus disk against Eq. true_soln: field at
+    off-surface targets, u_nu and u_tau on the boundary, the stress
+    integrand, and zero net force and torque (Eq. net for one particle)."""
+    o = yo.Oracle(_disk(), 16, 16, rho, yo.QBXParams(order=10))
+    res = yo.solve_dense(o, yo.label(o.geom, 2))
+    ang = np.linspace(0, 2 * np.pi, 37)[:-1]
+    T = np.concatenate([np.stack([r * np.cos(ang), r * np.sin(ang)], 1) for r in (1.3, 2.0, 4.0)])
+    ue, _, _ = _true_soln(T, rho)
+    assert np.abs(o.potential(res["sigma"], T) - ue).max() < 1e-11
+    _, ur, ut = _true_soln(o.geom.x, rho)
+    assert np.abs(res["un"] - ur).max() < 1e-8
+    assert np.abs(o.tangential_derivative(yo.label(o.geom, 2)) - ut).max() < 1e-12
+    assert np.abs(res["F"]).max() < 1e-8
+    assert abs(res["tau"][0]) < 1e-9
+
+
+def _green_setup(n=3, seed=11, shape=W.SHAPE_ELLIPSE, box=None):
+    wl = W.small_system(n, seed, shape=shape, n_panels=16, A=1.0, B=0.5 if shape else 1.0)
+    if box is not None:  # a tight cluster, so that the particles feel each other
+        wl.particles = W.make_particles(n, box, 0.3, seed=seed, shape=shape, A=1.0,
+                                        B=0.5 if shape else 1.0)
+        wl.box = box
+    rng = np.random.default_rng(seed)
+    q = rng.normal(size=n)
+    src = wl.particles[:, 1:3] + 0.2 * rng.normal(size=(n, 2))
+
+    def u(X):
+        return sum(q[k] * sp.k0(np.hypot(X[:, 0] - src[k, 0], X[:, 1] - src[k, 1]))
+                   for k in range(n)) / (2 * np.pi)
+
+    def grad(X):
+        gsum = 0.0
+        for k in range(n):
+            d = X - src[k]
+            r = np.hypot(d[:, 0], d[:, 1])
+            gsum = gsum - q[k] * (sp.k1(r) / r)[:, None] * d
+        return gsum / (2 * np.pi)
+
+    return wl, u, grad
+
+
+def test_green_identity_ellipses():
+    """A field radiated by point sources inside the particles solves the
+    exterior BVP with its own trace as data: solving Eq. (bie) with
+    f = sum q_k G(., x_k) must reproduce that field off the surface
+    (Eq. intrep) and its normal and tangential derivatives on it."""
+    wl, u, grad = _green_setup()
+    o = yo.Oracle(wl.particles, 16, 16, 1.0, yo.QBXParams(order=10))
+    f = u(o.geom.x)
+    res = yo.solve_dense(o, f)
+    T = W.off_surface_targets(wl.particles, 100, wl.box, 0.25, 3)
+    assert np.abs(o.potential(res["sigma"], T) - u(T)).max() < 1e-11
+    ge = grad(o.geom.x)
+    assert np.abs(res["un"] - (ge * o.geom.nu).sum(1)).max() < 1e-8
+    assert np.abs(o.tangential_derivative(f) - (ge * o.geom.tau).sum(1)).max() < 1e-6
+
+
+def test_forces_from_exact_field():
+    """Eqs. stress and force_torque evaluated on the exact Green field: the
+    oracle's F, tau (from its own u_nu) match the same boundary integrals
+    of the exact field, integrated on a 4x finer panel grid."""
+    wl, u, grad = _green_setup(box=5.0)
+    o = yo.Oracle(wl.particles, 16, 16, 1.0, yo.QBXParams(order=10))
+    f = u(o.geom.x)
+    res = yo.solve_dense(o, f)
+    fine = yo.make_geometry(wl.particles, 64, 16)
+    ge = grad(fine.x)
+    un = (ge * fine.nu).sum(1)
+    ut = (ge * fine.tau).sum(1)
+    uf = u(fine.x)
+    # T.nu = gamma [u^2/rho + rho (|grad u|^2) ] nu - 2 gamma rho grad u (grad u . nu), rho = gamma = 1
+    Tn = (uf ** 2 + 0.5 * 2 * (un ** 2 + ut ** 2))[:, None] * fine.nu - 2 * ge * un[:, None]
+    wT = fine.w[:, None] * Tn
+    F = np.zeros((wl.n_particles, 2))
+    np.add.at(F, fine.part, wT)
+    t0 = np.zeros(wl.n_particles)
+    np.add.at(t0, fine.part, fine.x[:, 0] * wT[:, 1] - fine.x[:, 1] * wT[:, 0])
+    # the net forces nearly cancel, so compare against the integrand's size
+    scale = np.zeros(wl.n_particles)
+    np.add.at(scale, fine.part, fine.w * np.hypot(Tn[:, 0], Tn[:, 1]))
+    assert np.abs(F).max() > 1e-2 * scale.max()
+    assert (np.abs(res["F"] - F).max(1) < 1e-8 * scale).all()
+    assert (np.abs(res["tau0"] - t0) < 1e-7 * scale).all()
+
+
+def test_brute_force_principal_value():
+    """Tiny input (two particles): the discrete (1/2 I + D) sigma against
+    1/2 sigma(x) + p.v. integral of Eq. djump by adaptive quadrature in the
+    curve parameter. The kernel is bounded on a smooth curve, so the
+    principal value is an ordinary integral, split at the target."""
+    parts = np.array([[W.SHAPE_ELLIPSE, 0.0, 0.0, 0.3, 1.0, 0.6],
+                      [W.SHAPE_DISK, 2.9, 0.4, 1.1, 0.8, 0.8]])
+    rho = 0.8
+    o = yo.Oracle(parts, 16, 16, rho, yo.QBXParams(order=10))
+    g = o.geom
+
+    def sig_fn(pi, t):
+        return np.cos(2 * t) + 0.3 * np.sin(t) + 0.5 * pi
+
+    sig = sig_fn(g.part, g.t)
+    rows = [0, 10, 74, 128, 200, 260, 400, 510]
+    y = o.apply_rows(sig, rows)
+    for a, i in enumerate(rows):
+        xi = g.x[i]
+        tot = 0.5 * sig[i]
+        for pi, p in enumerate(parts):
+            def integrand(t, pi=pi, p=p):
+                x, dx = yo.curve(p, np.array([t]))
+                spd = np.hypot(dx[0, 0], dx[0, 1])
+                nu = np.array([dx[0, 1], -dx[0, 0]]) / spd
+                if np.hypot(*(x[0] - xi)) < 1e-12:
+                    return 0.0
+                return yo.dl_kernel(xi[None], x, nu[None], rho)[0] * sig_fn(pi, t) * spd
+            t0 = g.t[i] if pi == g.part[i] else 0.0
+            for lo, hi in ((t0 - np.pi, t0), (t0, t0 + np.pi)):
+                val, _ = si.quad(integrand, lo, hi, limit=400, epsabs=1e-15, epsrel=1e-14)
+                tot += val
+        assert abs(y[a] - tot) < 2e-11
+
+
+def test_gmres_matches_direct_solve():
+    """Plain GMRES (Algorithm 1, GMRES step) converges to the direct
+    solution of the discrete system within its tolerance."""
+    wl = W.small_system(4, 5, n_panels=8)
+    o = yo.Oracle(wl.particles, 8, 16, 1.0, yo.QBXParams(order=10))
+    A = o.dense()
+    f = yo.label(o.geom, 0, 10.0)
+    s = np.linalg.solve(A, f)
+    x, it, rel = yo.Oracle.gmres(lambda v: A @ v, f, tol=1e-12)
+    assert rel <= 1e-12 and it < 60
+    assert np.linalg.norm(x - s) < 1e-10 * np.linalg.norm(s)
+    assert np.linalg.norm(A @ x - f) <= 1.01e-12 * np.linalg.norm(f)
+
+
+def test_net_force_and_torque_vanish():
+    """Eq. net: sum_i F_i = 0 and sum_i tau0_i = 0 (about the origin) for a
+    multi-particle system; smooth data so that the discrete sums vanish to
+    discretisation accuracy. (The scalar torques about the centres,
+    Eq. scalar-torque, need not sum to zero.)"""
+    wl = W.small_system(4, 7, shape=W.SHAPE_ELLIPSE, n_panels=16, A=1.0, B=0.5, gap=0.4)
+    o = yo.Oracle(wl.particles, 16, 16, 1.0, yo.QBXParams(order=10))
+    res = yo.solve_dense(o, yo.label(o.geom, 1, 2))
+    Fmax = np.abs(res["F"]).max()
+    assert Fmax > 1e-3
+    assert np.abs(res["F"].sum(0)).max() < 1e-8 * Fmax
+    assert abs(res["tau0"].sum()) < 1e-8 * max(Fmax, np.abs(res["tau0"]).max())
+
+
+def test_max_principle_and_refinement():
+    """0 <= u <= 1 in the water for data in [0, 1] (max principle of the
+    screened Laplace BVP, Section 4), and spectral convergence of the
+    density under panel refinement (16 -> 32 -> 64 panels) for the tanh
+    label on one disk."""
+    sig = {}
+    for npan in (16, 32, 64):
+        o = yo.Oracle(_disk(), npan, 16, 1.0, yo.QBXParams(order=10))
+        f = yo.label(o.geom, 0, 10.0)
+        res = yo.solve_dense(o, f, want_grad=False)
+        sig[npan] = (o, res["sigma"])
+    o16, s16 = sig[16]
+    ang = np.linspace(0, 2 * np.pi, 73)[:-1]
+    T = np.concatenate([np.stack([r * np.cos(ang), r * np.sin(ang)], 1) for r in (1.25, 1.6, 3.0)])
+    u = {k: v[0].potential(v[1], T) for k, v in sig.items()}
+    assert u[16].min() > -1e-6 and u[16].max() < 1 + 1e-6
+    e16 = np.abs(u[16] - u[64]).max()
+    e32 = np.abs(u[32] - u[64]).max()
+    assert e32 < 1e-2 * e16 and e32 < 1e-8
+
+
+def test_table1_single_disk_loose():
+    """Table 1 (printed values, golden file): at the paper's discretisation
+    (7 nodes per panel, rho = 4) the oracle's l_inf field error stays
+    within 10x of the printed error for QBX orders 6 and 8. The paper's
+    GIGAQBX differs from the near-panel expansion used here (its FMM floor
+    is 1e-8), so this pin is loose by design."""
+    gold = json.load(open(os.path.join(GOLDEN, "table1_single_disk.json")))
+    rho = gold["rho"]
+    xs = np.linspace(-2.5, 2.5, 200)
+    X, Y = np.meshgrid(xs, xs)
+    T = np.stack([X.ravel(), Y.ravel()], 1)
+    T = T[np.hypot(T[:, 0], T[:, 1]) > 1.5][::5]
+    ue, _, _ = _true_soln(T, rho)
+    for p in (6, 8):
+        for k, npan in enumerate(gold["n_panels"][:3]):
+            o = yo.Oracle(_disk(), npan, gold["n_gl"], rho,
+                          yo.QBXParams(order=p, r_factor=0.25, oversample=8))
+            s = np.linalg.solve(o.dense(), yo.label(o.geom, 2))
+            err = np.abs(o.potential(s, T) - ue).max()
+            assert err < 10 * gold["linf_error"][str(p)][k] + 1e-12, (p, npan, err)
+
+
+# --------------------------------------------------------------------------
+# the pins catch planted mistakes
+# --------------------------------------------------------------------------
+
+def _circle_ok(mod):
+    rho = 0.7
+    z = 1.0 / rho
+    o = mod.Oracle(_disk(1.0, 0.2), 16, 16, rho, mod.QBXParams(order=10))
+    th = np.arctan2(o.geom.x[:, 1], o.geom.x[:, 0])
+    rows = list(range(0, o.geom.n, 23))
+    for n in (0, 2):
+        sig = np.cos(n * th)
+        y, yn = o.apply_rows(sig, rows, want_grad=True)
+        lam = z * sp.ivp(n, z) * sp.kv(n, z)
+        lamn = z * sp.ivp(n, z) * sp.kvp(n, z) / rho
+        if np.abs(y - lam * sig[rows]).max() > 1e-9 or np.abs(yn - lamn * sig[rows]).max() > 1e-6:
+            return False
+    return True
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plant plausible mistakes in the oracle (on the CPU) and check that the
+    circle-eigenvalue pin notices each of them."""
+    assert _circle_ok(yo)
+    orig_kernel = yo.dl_kernel
+    orig_qbx = yo.Oracle.qbx_eval
+    orig_centre = yo.Oracle.qbx_centre
+    orig_near = yo.near_panels
+
+    mutations = {
+        "kernel sign": lambda: monkeypatch.setattr(
+            yo, "dl_kernel", lambda x, y, n, r: -orig_kernel(x, y, n, r)),
+        "kernel rho factor": lambda: monkeypatch.setattr(
+            yo, "dl_kernel", lambda x, y, n, r: orig_kernel(x, y, n, r) * r),
+        "interior centre": lambda: monkeypatch.setattr(
+            yo.Oracle, "qbx_centre",
+            lambda self, i: (2 * self.geom.x[i] - orig_centre(self, i)[0], orig_centre(self, i)[1])),
+        "no neighbour panels": lambda: monkeypatch.setattr(
+            yo, "near_panels", lambda g, i, w: orig_near(g, i, 0)),
+        "qbx halved": lambda: monkeypatch.setattr(
+            yo.Oracle, "qbx_eval",
+            lambda self, i, s, want_grad=False: tuple(0.5 * v for v in orig_qbx(self, i, s, True))
+            if want_grad else 0.5 * orig_qbx(self, i, s)),
+    }
+    for name, plant in mutations.items():
+        plant()
+        assert not _circle_ok(yo), name
+        monkeypatch.undo()
+    assert _circle_ok(yo)
