@@ -1,0 +1,349 @@
+"""Benchmark: Yukawa-QBX solves per second (mixed precision vs FP64) on the
+512-disk system (N = 131,072 nodes), with the far-field P2P kernel's
+roofline, an end-to-end host-buffer measurement, and the FP64 oracle timed
+on the host cores.
+
+One step = one solve of Eq. (bie) plus forces and torques for the 512 unit
+disks (200 x 200 box, gap >= 0.3, 16 panels x 16 nodes, rho = 1, QBX order
+10, tolerance 1e-10): re-discretise the particles, label, mixed-precision
+GMRES with FP64 iterative refinement, FP64-accurate normal derivative,
+force/torque reduction. Inputs are resident on the device; L2 is flushed
+between steps (a 256 MiB write) outside the timed events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank solves its own replica (independent
+systems; no collective on the data path), value = all ranks' solves / the
+slowest rank's time ("scaling": "weak").
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Yukawa-QBX solves/s mixed vs FP64 @1e-9 rel err; P2P %FMA peak; p50/p99 latency"
+WORKLOAD = "disks512"
+# FP32 operations per far-field pair in the P2P inner loop (FMA counted as 2,
+# each MUFU op as 1): 2 sub, |d|^2 (3), 1/z' (1), z' (1), s (2), K1 poly
+# degree 7 (14), exp2 (1), z'^{-1/2} (1), (d.g) (3), 4 products (4), accumulate (1)
+FLOPS_PER_PAIR = 34
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-solve", type=int, default=1, help="time one plain FP64 solve")
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--cpu-rows", type=int, default=384)
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rows_timing(wl, nrows, want_grad=False):
+    """Seconds per operator row of the FP64 oracle on a sample of rows."""
+    from oracle import yk_oracle as yo
+    o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+    rng = np.random.default_rng(0)
+    sig = yo.label(o.geom, 0, 10.0)
+    rows = np.sort(rng.choice(o.geom.n, nrows, replace=False))
+    o.apply_rows(sig, rows[:2], want_grad=want_grad)  # warm caches
+    t0 = time.perf_counter()
+    o.apply_rows(sig, rows, want_grad=want_grad)
+    return (time.perf_counter() - t0) / nrows
+
+
+def oracle_gmres_iters():
+    """Iterations of the oracle's own GMRES (tol 1e-10) on the 8-disk system,
+    used as the iteration count of the CPU solve-time model."""
+    from oracle import yk_oracle as yo
+    from paper_1810_04131_gb300 import workloads as W
+    wl = W.small_system(8, 1, n_panels=16, rho=1.0)
+    o = yo.Oracle(wl.particles, 16, 16, 1.0, yo.QBXParams(order=10))
+    A = o.dense()
+    f = yo.label(o.geom, 0, 10.0)
+    _, it, _ = yo.Oracle.gmres(lambda v: A @ v, f, tol=1e-10)
+    return it
+
+
+def cpu_solve_rate(wl, nrows, iters):
+    """Oracle solves/s on the host, from a timed sample of rows: one solve =
+    (iters + 1) value matvecs + one gradient pass, each N rows."""
+    t_val = oracle_rows_timing(wl, nrows)
+    t_grad = oracle_rows_timing(wl, max(8, nrows // 4), want_grad=True)
+    t_solve = wl.n_nodes * ((iters + 1) * t_val + t_grad)
+    return 1.0 / t_solve, t_val, t_grad
+
+
+def run_reference(args):
+    """The oracle arm: FP64 CPU oracle timed on the host cores, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1810_04131_gb300 import workloads as W
+    wl = W.disks512()
+    iters = oracle_gmres_iters()
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, t_val, t_grad = cpu_solve_rate(wl, 64, iters)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    sample = ("per step: 64 value rows + 16 gradient rows of the 512-disk operator "
+              "(N=131072), solve = N x ((iters+1) value rows + 1 gradient row), iters=%d "
+              "from the oracle's own GMRES on an 8-disk system" % iters)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_particles": 512, "n_nodes": wl.n_nodes,
+                      "rho": 1.0, "qbx_order": 10, "gmres_tol": 1e-10},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1810_04131_gb300 import workloads as W
+    from paper_1810_04131_gb300 import yk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = yk.Context(local, stream.cuda_stream)
+
+    wl = W.disks512()
+    parts = wl.particles
+    if world > 1 and rank > 0:  # an independent replica per rank
+        parts = W.make_particles(512, 200.0, 0.3, seed=1000 + rank)
+    prm = yk.params_for(wl, precision=yk.YK_MIXED)
+    g = yk.Geometry(ctx, parts, prm)
+    n, npart = g.n, g.n_particles
+    f = torch.zeros(n, dtype=torch.float64, device=dev)
+    sig = torch.zeros(n, dtype=torch.float64, device=dev)
+    F = torch.zeros((npart, 2), dtype=torch.float64, device=dev)
+    tau = torch.zeros(npart, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    infos = []
+
+    def step():
+        g.yk_update_geometry(parts)
+        g.yk_label(yk.YK_LABEL_TANH, 10.0, out=f)
+        _, info = g.yk_solve(f, out=sig)
+        g.yk_forces_torques(sig, f, F=F, tau=tau, want_net=False)
+        infos.append(info)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = yk.yk_kernel_launches()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = yk.yk_kernel_launches() - launches0
+    clk = clocks.stop()
+    t_local = total_ms / 1e3
+    if dist:
+        t = torch.tensor([t_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    else:
+        t_max = t_local
+    value = world * args.steps / t_max
+    info = infos[-1]
+    sig_mixed = sig.clone()
+
+    # ---- the dominant kernel: FP32 far-field P2P (k_p2p_f32) -------------
+    # yk_matvec(YK_MIXED) = k_p2p_f32 + k_assemble (near rows); timed with
+    # CUDA events on the bench stream, back to back on the solved density.
+    y = torch.zeros_like(sig)
+    reps = 10
+    g.yk_matvec(sig, yk.YK_MIXED, out=y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.yk_matvec(sig, yk.YK_MIXED, out=y)
+    e1.record(stream)
+    e1.synchronize()
+    t_p2p = e0.elapsed_time(e1) / 1e3 / reps
+    pairs = n * (n - 3 * 16)
+    achieved = pairs * FLOPS_PER_PAIR / t_p2p / 1e12
+    peak = SMS * FP32_LANES * 2 * 2.070e9 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_p2p_f32 (+k_assemble)", "pairs_per_s": pairs / t_p2p,
+                "flops_per_pair": FLOPS_PER_PAIR,
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max SM clock"}
+
+    # ---- plain FP64 path: one matvec and (optionally) one full solve -------
+    fp64 = {}
+    e0.record(stream)
+    g.yk_matvec(sig, yk.YK_FP64, out=y)
+    e1.record(stream)
+    e1.synchronize()
+    fp64["matvec_ms"] = e0.elapsed_time(e1)
+    fp64["matvec_mixed_ms"] = t_p2p * 1e3
+    if args.fp64_solve and rank == 0:
+        prm64 = yk.params_for(wl, precision=yk.YK_FP64)
+        g64 = yk.Geometry(ctx, parts, prm64)
+        f64 = torch.zeros_like(f)
+        s64 = torch.zeros_like(sig)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g64.yk_update_geometry(parts)
+        g64.yk_label(yk.YK_LABEL_TANH, 10.0, out=f64)
+        _, info64 = g64.yk_solve(f64, out=s64)
+        g64.yk_forces_torques(s64, f64, want_net=False)
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64.update(solves_per_s=1.0 / t64, solve_s=t64, iterations=info64["iterations"],
+                    rel_residual=info64["rel_residual"])
+        fp64["mixed_speedup"] = value / world / fp64["solves_per_s"]
+        fp64["sigma_rel_diff_mixed_vs_fp64"] = float(
+            torch.linalg.norm(sig_mixed - s64) / torch.linalg.norm(s64))
+        g64.close()
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    f_h = np.zeros(n)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.yk_update_geometry(parts)
+        g.yk_label(yk.YK_LABEL_TANH, 10.0, out=f_h)
+        s_h, F_h, tau_h, _ = g.yk_solve_forces(f_h)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": e2e_steps / t_e2e, "unit": "solves/s",
+           "h2d_bytes_per_step": int(parts.shape[0] * 48 + n * 8),
+           "d2h_bytes_per_step": int(n * 8 * 2 + npart * 24)}
+
+    # ---- FP64 oracle on the host cores (bounded sample) ---------------------
+    cpu = None
+    if args.cpu_baseline and rank == 0:
+        iters = oracle_gmres_iters()
+        v, t_val, t_grad = cpu_solve_rate(wl, args.cpu_rows, iters)
+        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "%d value rows + %d gradient rows of the 512-disk operator timed "
+                         "(%.1f ms/row, %.1f ms/gradient row); solve = N x ((iters+1) rows + "
+                         "1 gradient row), iters=%d from the oracle's GMRES on 8 disks"
+                         % (args.cpu_rows, max(8, args.cpu_rows // 4), t_val * 1e3,
+                            t_grad * 1e3, iters)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "n_particles": 512, "n_nodes": n, "rho": 1.0,
+                          "qbx_order": 10, "gmres_tol": 1e-10, "precision": "mixed",
+                          "farfield": "dense", "l2": "flushed (256 MiB write) between steps",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "solve": {"iterations": info["iterations"], "refinements": info["refinements"],
+                         "rel_residual": info["rel_residual"],
+                         "matvecs_fp32": info["matvecs_fp32"],
+                         "matvecs_fp64": info["matvecs_fp64"]},
+               "fp64": fp64, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+               "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(out))
+    g.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

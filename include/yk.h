@@ -1,0 +1,241 @@
+/*
+ * yk.h - C ABI of a GB300 (sm_103a) solver for the exterior screened-Laplace
+ * (Yukawa) Dirichlet problem on the boundaries of rigid planar Janus
+ * particles, and the hydrophobic forces and torques it induces
+ * (Fu, Ryham, Kloeckner, Wala, Jiang, Young, arXiv 1810.04131).
+ *
+ * Problem (Section 1, Eq. SL): -rho^2 Lap u + u = 0 in the water region,
+ * u = f on the particle boundaries, u -> 0 at infinity. The solution is
+ * represented as a double-layer potential u = D[sigma] (Eq. intrep) with
+ * kernel dG/dnu_y, G = K0(|x-y|/rho)/(2 pi) (Eqs. Gfunc, double-layer-def);
+ * sigma solves the second-kind equation 1/2 sigma + D sigma = f (Eq. bie).
+ * Discretisation: composite Gauss-Legendre panels (Nystrom) with one-sided
+ * exterior QBX on the target's own panel and its neighbours (Section 5).
+ * Forces and torques are the boundary integrals of the hydrophobic stress
+ * (Eqs. stress, force_torque, scalar-torque).
+ *
+ * Conventions for every call:
+ *   - Return value: YK_OK (0) or a negative YK_ERR_* code; yk_strerror()
+ *     gives a message. No call aborts, traps or exits.
+ *   - Array arguments are caller-owned. Each may be a host pointer or a
+ *     CUDA device pointer (decided per pointer by cudaPointerGetAttributes);
+ *     host arrays are staged through library-owned device buffers, so a call
+ *     with host arrays includes the host<->device copies.
+ *   - Arrays are dense, C-contiguous, FP64 unless stated. Node arrays have
+ *     length N = n_particles * n_panels * n_gl, ordered particle-major, then
+ *     panel, then Gauss-Legendre node. Point arrays are interleaved (x, y).
+ *   - All work is enqueued on the context's CUDA stream; calls that return
+ *     host-visible results synchronise that stream before returning.
+ *   - Opaque handles are owned by the library and released by yk_destroy*.
+ *   - A context and the geometries made from it are not thread-safe: use
+ *     one host thread per context.
+ */
+#ifndef YK_H
+#define YK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define YK_OK                  0
+#define YK_ERR_ARG            -1  /* bad argument (null, size, range)          */
+#define YK_ERR_BAD_GEOMETRY   -2  /* particles overlap or touch               */
+#define YK_ERR_NO_MEMORY      -3  /* device or host allocation failed         */
+#define YK_ERR_NOT_CONVERGED  -4  /* solver stopped above tolerance; outputs
+                                     still written with the achieved residual */
+#define YK_ERR_TIMEOUT        -5  /* a bounded device wait gave up            */
+#define YK_ERR_CUDA           -6  /* a CUDA runtime call failed               */
+#define YK_ERR_NOT_FOUND      -7  /* unknown request id                       */
+#define YK_ERR_BUSY           -8  /* serving queue full                        */
+
+/* ---- enumerations --------------------------------------------------------- */
+#define YK_SHAPE_DISK     0
+#define YK_SHAPE_ELLIPSE  1
+
+#define YK_FP64   0   /* every step in FP64                                   */
+#define YK_MIXED  1   /* FP32 far-field evaluation with FP64 accumulation inside
+                         an FP64 iterative-refinement outer solve              */
+
+#define YK_FARFIELD_DENSE  0  /* every far source pair evaluated              */
+
+/* Dirichlet data generators; theta is the polar angle of x - a_i measured
+ * from the director d_i = (cos phi_i, sin phi_i) (Section 2.1).           */
+#define YK_LABEL_TANH    0   /* f = (1 + tanh(param cos theta)) / 2            */
+#define YK_LABEL_SINP    1   /* f = 1 - sin^param theta, Eq. JanusBC           */
+#define YK_LABEL_COS     2   /* f = (1 + cos theta) / 2 (Eq. true_soln data)   */
+#define YK_LABEL_CUSTOM  3   /* f supplied by the caller                       */
+
+/* serving request status */
+#define YK_REQ_QUEUED   0
+#define YK_REQ_RUNNING  1
+#define YK_REQ_DONE     2
+#define YK_REQ_FAILED   3
+
+/* ---- data types ----------------------------------------------------------- */
+typedef struct yk_ctx yk_ctx;
+typedef struct yk_geom yk_geom;
+
+/* One rigid particle (Section 2.1): boundary x(t) = (cx, cy) +
+ * R(phi) (A cos t, B sin t), t in [0, 2 pi); A is the semi-axis along the
+ * director. A disk has A = B = radius.                                      */
+typedef struct {
+    int32_t shape;      /* YK_SHAPE_DISK or YK_SHAPE_ELLIPSE                  */
+    int32_t pad_;
+    double cx, cy;      /* centre a_i                                        */
+    double phi;         /* orientation theta_i of the director d_i           */
+    double A, B;        /* semi-axes                                         */
+} yk_particle;
+
+/* Numerical parameters. yk_default_params() fills the defaults given here. */
+typedef struct {
+    double rho;            /* screening length (Eq. SL); default 1            */
+    double gamma;          /* interfacial tension (Eq. main); default 1       */
+    int32_t n_panels;      /* panels per particle; default 16                 */
+    int32_t n_gl;          /* Gauss-Legendre nodes per panel, 2..32; default 16 */
+    int32_t qbx_order;     /* QBX order p, terms |n| <= p, 1..24; default 10  */
+    int32_t oversample;    /* QBX sub-panels per near panel; default 8        */
+    double qbx_r_factor;   /* expansion radius r = factor * panel arclength; 1/8 */
+    int32_t near_width;    /* near panels on each side of the target's; default 1 */
+    int32_t gmres_restart; /* Krylov basis size m; default 100                */
+    int32_t max_iter;      /* total GMRES iterations (all restarts); default 300 */
+    int32_t precision;     /* YK_FP64 or YK_MIXED; default YK_MIXED            */
+    double gmres_tol;      /* relative residual ||f - A sigma|| / ||f||; 1e-10 */
+    double inner_tol;      /* YK_MIXED: inner (FP32) GMRES tolerance; 1e-6     */
+    int32_t max_refine;    /* YK_MIXED: refinement steps; default 8            */
+    int32_t farfield;      /* YK_FARFIELD_DENSE                                */
+    double split_tol;      /* YK_MIXED residual/gradient: a source particle is
+                              evaluated in FP32 only where its FP32 error bound
+                              is below split_tol * max|sigma|; default 1e-16   */
+} yk_params;
+
+/* Solve statistics (all host memory). */
+typedef struct {
+    int32_t iterations;      /* GMRES iterations (inner ones for YK_MIXED)    */
+    int32_t refinements;     /* outer refinement steps (YK_MIXED) or 0        */
+    double rel_residual;     /* final ||f - A sigma|| / ||f|| in FP64         */
+    int32_t matvecs_fp64;    /* FP64-accurate operator applications           */
+    int32_t matvecs_fp32;    /* FP32 far-field operator applications          */
+} yk_solve_info;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Fill *p with the defaults documented in yk_params. Never fails for p != NULL. */
+int yk_default_params(yk_params* p);
+
+/* Create a context on CUDA device `device`, enqueuing all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream). The
+ * stream is borrowed, not owned. Errors: YK_ERR_ARG, YK_ERR_CUDA.        */
+int yk_create(yk_ctx** ctx, int device, void* cuda_stream);
+int yk_destroy(yk_ctx* ctx);
+
+/* ---- geometry (Section 2.1; Section 5: discretisation and QBX set-up) ----- */
+
+/* Discretise n_particles particles with parameters *prm: nodes, normals,
+ * weights (composite Gauss-Legendre panels), per-panel arclength, the QBX
+ * near-correction rows (value and normal derivative; one block per distinct
+ * particle shape, since the rows of a rigid body do not depend on its
+ * position or orientation), and the solver workspace. The particle array
+ * is host memory and is copied.
+ * Errors: YK_ERR_ARG (sizes/parameters out of range), YK_ERR_BAD_GEOMETRY
+ * (two particles' bounding circles overlap: the disks-and-ellipses
+ * configurations used here keep a positive surface gap), YK_ERR_NO_MEMORY. */
+int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particles,
+                       const yk_params* prm, yk_geom** out);
+int yk_destroy_geometry(yk_geom* g);
+
+/* Move the particles of an existing geometry (Algorithm 1, position and
+ * orientation update followed by re-discretisation): same count, same
+ * shapes and semi-axes, new centres and orientations (host array). Nodes,
+ * normals and weights are recomputed; the QBX near rows are kept, because
+ * a rigid particle's rows do not depend on its position or orientation.
+ * Errors: YK_ERR_ARG (count or shapes differ, non-finite values). The
+ * overlap check of yk_create_geometry is not repeated.                   */
+int yk_update_geometry(yk_geom* g, const yk_particle* particles, int n_particles);
+
+/* N = n_particles * n_panels * n_gl (host int64). */
+int yk_num_nodes(const yk_geom* g, int64_t* n);
+
+/* Copy node positions xy (N x 2), unit normals nrm (N x 2, out of the
+ * particle), and weights w (N). Any output may be NULL.                   */
+int yk_nodes(const yk_geom* g, double* xy, double* nrm, double* w);
+
+/* Dirichlet data f at the nodes (Eq. JanusBC and variants): kind is one of
+ * YK_LABEL_*; param is the tanh steepness or the sin exponent. For
+ * YK_LABEL_CUSTOM f_custom (N) is copied to f_out. f_out has length N.    */
+int yk_label(yk_geom* g, int kind, double param, const double* f_custom, double* f_out);
+
+/* y = (1/2 I + D) sigma (Eq. bie), both of length N. precision YK_FP64:
+ * every pair in FP64. YK_MIXED: FP32 far field with FP64 accumulation
+ * (the inner operator of the mixed solver, accurate to about 1e-6).       */
+int yk_matvec(yk_geom* g, const double* sigma, double* y, int precision);
+
+/* Normal derivative u_nu = nu . grad D[sigma] on the boundary, exterior
+ * limit (Algorithm 1, step computing grad u), length N. precision YK_FP64
+ * or YK_MIXED (precision-split: FP64 where FP32 would exceed split_tol). */
+int yk_normal_derivative(yk_geom* g, const double* sigma, double* u_nu, int precision);
+
+/* Solve 1/2 sigma + D sigma = f (Eq. bie) by restarted GMRES (YK_FP64) or
+ * FP64 iterative refinement over FP32-operator GMRES (YK_MIXED), as set in
+ * the geometry's parameters. sigma0 (N, nullable) is an initial guess
+ * (warm start); sigma (N) receives the solution; info (host, nullable)
+ * receives statistics. Returns YK_ERR_NOT_CONVERGED if the tolerance was
+ * not reached (sigma then holds the last iterate).                        */
+int yk_solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
+             yk_solve_info* info);
+
+/* Forces F (n_particles x 2) and scalar torques tau (n_particles) about the
+ * particle centres (Eqs. force_torque, stress, scalar-torque) from the
+ * density sigma and the data f, using u_nu from yk_normal_derivative (in
+ * the geometry's precision mode) and u_tau = df/ds by per-panel spectral
+ * differentiation. net (3, nullable) receives sum F_x, sum F_y and
+ * sum tau0 (torque about the origin), which vanish by Eq. net.            */
+int yk_forces_torques(yk_geom* g, const double* sigma, const double* f,
+                      double* F, double* tau, double* net);
+
+/* u = D[sigma] (Eq. intrep) at nt off-surface targets (nt x 2) by plain
+ * quadrature, FP64. Targets must lie in the water at least about one panel
+ * length from every boundary for full accuracy. u has length nt.          */
+int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets,
+                      int64_t nt, double* u);
+
+/* Convenience: label + solve + forces for one configuration. */
+int yk_solve_forces(yk_geom* g, const double* f, double* sigma, double* F,
+                    double* tau, yk_solve_info* info);
+
+/* ---- serving (continuous batching of independent configurations) --------- */
+
+/* Queue one configuration (particles copied from host memory) to be solved
+ * with the tanh/sin/cos label kind and parameter given, in parameters *prm.
+ * The request is admitted when device memory allows, batched with the
+ * others in flight, and its results are kept until yk_poll collects them.
+ * Errors: YK_ERR_ARG, YK_ERR_BUSY (queue full).                           */
+int yk_submit(yk_ctx* ctx, const yk_particle* particles, int n_particles,
+              const yk_params* prm, int label_kind, double label_param,
+              uint64_t* request_id);
+
+/* Advance the serving loop and report request `id`. status receives a
+ * YK_REQ_* value. When DONE, the outputs (host arrays, each nullable) are
+ * written: sigma (N), F (2 n_particles), tau (n_particles), info, and
+ * latency_ms (submit to completion); the request is then released.
+ * Errors: YK_ERR_NOT_FOUND.                                                */
+int yk_poll(yk_ctx* ctx, uint64_t id, int* status, double* sigma, double* F,
+            double* tau, yk_solve_info* info, double* latency_ms);
+
+/* Run the serving loop until every queued request is done (or a request
+ * failed). Returns the first error met, or YK_OK.                          */
+int yk_drain(yk_ctx* ctx);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts), for accounting in benchmarks. Library-specific; the
+ * paper has no counterpart.                                               */
+int yk_kernel_launches(uint64_t* count);
+
+const char* yk_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* YK_H */

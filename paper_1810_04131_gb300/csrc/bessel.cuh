@@ -1,0 +1,148 @@
+// Device modified Bessel functions for the Yukawa kernel G = K0(r/rho)/(2 pi)
+// (Eq. Gfunc) and its QBX expansions (Section 5, Graf addition for K_n, I_n).
+//
+// K0, K1 (FP64 and FP32):
+//   z <= 2  ascending series, DLMF 10.25.2 and 10.31.1 (coefficients in
+//           bessel_tables.h, generated from exact rationals);
+//   z > 2   K_nu(z) = exp(-z) z^{-1/2} P_nu(t), t = 2/z, with P_nu a
+//           project-fitted polynomial (gen_bessel_tables.py, Chebyshev
+//           interpolation of exp(z) sqrt(z) K_nu(z), checked to 2.2e-16 in FP64
+//           and 1e-7 in FP32).
+// K_n for n >= 2: forward recurrence K_{n+1} = K_{n-1} + (2n/z) K_n
+// (DLMF 10.29.1), stable for K. I_n: ascending series DLMF 10.25.2.
+#pragma once
+#include "bessel_tables.h"
+
+namespace yk {
+
+template <int NT>
+__device__ __forceinline__ double horner(const double (&c)[NT], double s) {
+    double acc = c[NT - 1];
+#pragma unroll
+    for (int k = NT - 2; k >= 0; --k) acc = fma(acc, s, c[k]);
+    return acc;
+}
+
+template <int NT>
+__device__ __forceinline__ float hornerf(const float (&c)[NT], float s) {
+    float acc = c[NT - 1];
+#pragma unroll
+    for (int k = NT - 2; k >= 0; --k) acc = fmaf(acc, s, c[k]);
+    return acc;
+}
+
+// ---- FP64 ------------------------------------------------------------------
+
+// K0 and K1 for z <= 2 (series).
+__device__ __forceinline__ void k01_series(double z, double& k0, double& k1) {
+    const double q = 0.25 * z * z;
+    double si0 = YK_S_I0[YK_SERIES_TERMS - 1], si1 = YK_S_I1[YK_SERIES_TERMS - 1];
+    double sk0 = YK_S_K0[YK_SERIES_TERMS - 1], sk1 = YK_S_K1[YK_SERIES_TERMS - 1];
+#pragma unroll
+    for (int k = YK_SERIES_TERMS - 2; k >= 0; --k) {
+        si0 = fma(si0, q, YK_S_I0[k]);
+        si1 = fma(si1, q, YK_S_I1[k]);
+        sk0 = fma(sk0, q, YK_S_K0[k]);
+        sk1 = fma(sk1, q, YK_S_K1[k]);
+    }
+    const double lg = log(0.5 * z);
+    k0 = -(lg + YK_EULER_GAMMA) * si0 + sk0;  // the k = 0 coefficient H_0 is zero
+    k1 = 1.0 / z + lg * (0.5 * z) * si1 - 0.25 * z * sk1;
+}
+
+// K1 alone for z <= 2 (series).
+__device__ __forceinline__ double k1_series(double z) {
+    const double q = 0.25 * z * z;
+    double si1 = YK_S_I1[YK_SERIES_TERMS - 1], sk1 = YK_S_K1[YK_SERIES_TERMS - 1];
+#pragma unroll
+    for (int k = YK_SERIES_TERMS - 2; k >= 0; --k) {
+        si1 = fma(si1, q, YK_S_I1[k]);
+        sk1 = fma(sk1, q, YK_S_K1[k]);
+    }
+    return 1.0 / z + log(0.5 * z) * (0.5 * z) * si1 - 0.25 * z * sk1;
+}
+
+// exp(z) sqrt(z) K_nu(z) for z > 2, nu = 0, 1 (polynomial in t = 2/z).
+__device__ __forceinline__ double p1_large(double t) {
+    if (t <= 0.25) return horner(YK_P1_FAR, 8.0 * t - 1.0);
+    return horner(YK_P1_MID, (2.0 * t - 1.25) * (1.0 / 0.75));
+}
+__device__ __forceinline__ double p0_large(double t) {
+    if (t <= 0.25) return horner(YK_P0_FAR, 8.0 * t - 1.0);
+    return horner(YK_P0_MID, (2.0 * t - 1.25) * (1.0 / 0.75));
+}
+
+// K1(z), z > 0.
+__device__ __forceinline__ double k1(double z) {
+    if (z <= 2.0) return k1_series(z);
+    return exp(-z) * p1_large(2.0 / z) * rsqrt(z);
+}
+
+// K0(z), K1(z), z > 0.
+__device__ __forceinline__ void k01(double z, double& k0, double& k1) {
+    if (z <= 2.0) {
+        k01_series(z, k0, k1);
+        return;
+    }
+    const double t = 2.0 / z;
+    const double e = exp(-z) * rsqrt(z);
+    k0 = e * p0_large(t);
+    k1 = e * p1_large(t);
+}
+
+// I_n(z) for n = 0..nmax (ascending series, DLMF 10.25.2); small to moderate z.
+__device__ inline double bessel_i_series(int n, double z) {
+    const double q = 0.25 * z * z;
+    double term = 1.0;
+    for (int k = 1; k <= n; ++k) term *= (0.5 * z) / k;  // (z/2)^n / n!
+    double sum = term;
+    for (int k = 1; k < 200; ++k) {
+        term *= q / ((double)k * (double)(n + k));
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+// ---- FP32 ------------------------------------------------------------------
+
+// K1(z) in FP32; rinv_rho2 = t = 2/z supplied by the caller (it has 1/r).
+__device__ __forceinline__ float k1f(float z, float t) {
+    if (z > 2.0f) {
+        return __expf(-z) * hornerf(YK_P1_F32, 2.0f * t - 1.0f) * sqrtf(0.5f * t);
+    }
+    const float q = 0.25f * z * z;
+    float si1 = YK_S_I1_F32[YK_SERIES_TERMS_F32 - 1], sk1 = YK_S_K1_F32[YK_SERIES_TERMS_F32 - 1];
+#pragma unroll
+    for (int k = YK_SERIES_TERMS_F32 - 2; k >= 0; --k) {
+        si1 = fmaf(si1, q, YK_S_I1_F32[k]);
+        sk1 = fmaf(sk1, q, YK_S_K1_F32[k]);
+    }
+    return 0.5f * t + logf(0.5f * z) * (0.5f * z) * si1 - 0.25f * z * sk1;
+}
+
+// K0, K1 in FP32.
+__device__ __forceinline__ void k01f(float z, float t, float& k0, float& k1) {
+    if (z > 2.0f) {
+        const float e = __expf(-z) * sqrtf(0.5f * t);
+        const float s = 2.0f * t - 1.0f;
+        k0 = e * hornerf(YK_P0_F32, s);
+        k1 = e * hornerf(YK_P1_F32, s);
+        return;
+    }
+    const float q = 0.25f * z * z;
+    float si0 = YK_S_I0_F32[YK_SERIES_TERMS_F32 - 1], si1 = YK_S_I1_F32[YK_SERIES_TERMS_F32 - 1];
+    float sk0 = YK_S_K0_F32[YK_SERIES_TERMS_F32 - 1], sk1 = YK_S_K1_F32[YK_SERIES_TERMS_F32 - 1];
+#pragma unroll
+    for (int k = YK_SERIES_TERMS_F32 - 2; k >= 0; --k) {
+        si0 = fmaf(si0, q, YK_S_I0_F32[k]);
+        si1 = fmaf(si1, q, YK_S_I1_F32[k]);
+        sk0 = fmaf(sk0, q, YK_S_K0_F32[k]);
+        sk1 = fmaf(sk1, q, YK_S_K1_F32[k]);
+    }
+    const float lg = logf(0.5f * z);
+    k0 = -(lg + (float)YK_EULER_GAMMA) * si0 + sk0;
+    k1 = 0.5f * t + lg * (0.5f * z) * si1 - 0.25f * z * sk1;
+}
+
+}  // namespace yk

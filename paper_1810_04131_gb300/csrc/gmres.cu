@@ -1,0 +1,357 @@
+// Device GMRES for 1/2 sigma + D sigma = f (Eq. bie; Algorithm 1, GMRES
+// step) and the mixed-precision iterative refinement around it.
+//
+// GMRES: Arnoldi with classical Gram-Schmidt applied twice (CGS2) on an
+// FP64 Krylov basis, Givens rotations on the Hessenberg matrix, restart
+// after m steps. Every vector operation, the rotations and the small
+// triangular solve run on the device; the host reads one residual estimate
+// per iteration to decide whether to stop.
+//
+// Mixed: sigma <- sigma + GMRES_32(r), r = f - A_64 sigma, where A_32 is
+// the FP32-far-field operator (accurate to about 1e-6) and A_64 the
+// FP64-accurate precision-split operator; stops when ||r|| <= tol ||f||.
+#include <math.h>
+
+#include <algorithm>
+
+#include "yk_internal.cuh"
+
+namespace yk {
+
+constexpr int DOT_TPB = 256;
+
+// part[k * nblk + b] = sum over block b's slice of V[k][i] * w[i]
+__global__ void k_dots(const double* __restrict__ V, int64_t n, const double* __restrict__ w,
+                       double* __restrict__ part) {
+    const int k = blockIdx.y;
+    const double* v = V + (int64_t)k * n;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)DOT_TPB + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * DOT_TPB)
+        acc = fma(v[i], w[i], acc);
+    __shared__ double red[DOT_TPB];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = DOT_TPB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_reduce_parts(int nvec, int nblk, const double* __restrict__ part,
+                               double* __restrict__ out) {
+    for (int k = threadIdx.x; k < nvec; k += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[k * nblk + b];
+        out[k] = s;
+    }
+}
+
+// w -= sum_k V[k] h[k]
+__global__ void k_sub_proj(double* __restrict__ w, const double* __restrict__ V, int64_t n,
+                           int nvec, const double* __restrict__ h) {
+    __shared__ double hs[1024];
+    for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = h[k];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i];
+    for (int k = 0; k < nvec; ++k) acc = fma(-V[(int64_t)k * n + i], hs[k], acc);
+    w[i] = acc;
+}
+
+// One Arnoldi column: H[:, j] = h1 + h2, H[j+1, j] = ||w||, previous
+// rotations, a new rotation, and the residual estimate |g[j+1]|.
+// status[0] = residual estimate, status[1] = ||w|| (before normalisation).
+__global__ void k_arnoldi_col(int j, int ldh, double* H, const double* h1, const double* h2,
+                              const double* wn2, double* cs, double* sn, double* g,
+                              double* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double* col = H + (int64_t)j * ldh;
+    for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];
+    const double hn = sqrt(fmax(wn2[0], 0.0));
+    col[j + 1] = hn;
+    status[1] = hn;
+    for (int k = 0; k < j; ++k) {
+        const double a = col[k], b = col[k + 1];
+        col[k] = cs[k] * a + sn[k] * b;
+        col[k + 1] = -sn[k] * a + cs[k] * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double den = hypot(a, b);
+    double c = 1.0, s = 0.0;
+    if (den > 0.0) {
+        c = a / den;
+        s = b / den;
+    }
+    col[j] = den;
+    col[j + 1] = 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    status[0] = fabs(g[j + 1]);
+}
+
+// dst = src / s[0]  (s[0] > 0), or dst = src * scale when s == nullptr
+__global__ void k_scale(double* dst, const double* src, int64_t n, const double* s,
+                        double scale) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double f = s ? 1.0 / s[0] : scale;
+    dst[i] = src[i] * f;
+}
+
+// Start a cycle: g = (beta, 0, ...), status[1] = beta.
+__global__ void k_init_cycle(int m, const double* bn2, double* g, double* status) {
+    if (threadIdx.x != 0) return;
+    const double beta = sqrt(fmax(bn2[0], 0.0));
+    for (int k = 0; k <= m; ++k) g[k] = 0.0;
+    g[0] = beta;
+    status[1] = beta;
+    status[0] = beta;
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k), back substitution (k+1 unknowns)
+__global__ void k_tri_solve(int k1, int ldh, const double* H, const double* g, double* y) {
+    if (threadIdx.x != 0) return;
+    for (int r = k1 - 1; r >= 0; --r) {
+        double s = g[r];
+        for (int c = r + 1; c < k1; ++c) s -= H[(int64_t)c * ldh + r] * y[c];
+        y[r] = s / H[(int64_t)r * ldh + r];
+    }
+}
+
+// x += sum_k V[k] y[k]
+__global__ void k_add_basis(double* __restrict__ x, const double* __restrict__ V, int64_t n,
+                            int k1, const double* __restrict__ y) {
+    __shared__ double ys[1024];
+    for (int k = threadIdx.x; k < k1; k += blockDim.x) ys[k] = y[k];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = x[i];
+    for (int k = 0; k < k1; ++k) acc = fma(V[(int64_t)k * n + i], ys[k], acc);
+    x[i] = acc;
+}
+
+// z = a - b
+__global__ void k_sub(double* z, const double* a, const double* b, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) z[i] = a[i] - b[i];
+}
+
+// x += d
+__global__ void k_axpy1(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] += d[i];
+}
+
+// ---------------------------------------------------------------------------
+
+int alloc_workspace(yk_geom* g) {
+    Workspace& w = g->ws;
+    const int64_t n = g->n;
+    const int m = g->prm.gmres_restart;
+    w.m = m;
+    const int nct = ceil_div(n, 256);
+    int nchunk = std::max(1, std::min(g->np, ceil_div(152 * 32, nct)));
+    const int ppc = ceil_div(g->np, nchunk);
+    w.nchunk = ceil_div(g->np, ppc);
+    w.dot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(296, (n + 2047) / 2048));
+    YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n));
+    YK_TRY(dev_alloc((void**)&w.V, sizeof(double) * (m + 1) * n));
+    YK_TRY(dev_alloc((void**)&w.H, sizeof(double) * (m + 1) * m));
+    YK_TRY(dev_alloc((void**)&w.gvec, sizeof(double) * (m + 1)));
+    YK_TRY(dev_alloc((void**)&w.cs, sizeof(double) * m));
+    YK_TRY(dev_alloc((void**)&w.sn, sizeof(double) * m));
+    YK_TRY(dev_alloc((void**)&w.hbuf, sizeof(double) * 2 * (m + 2)));
+    YK_TRY(dev_alloc((void**)&w.ybuf, sizeof(double) * (m + 1)));
+    YK_TRY(dev_alloc((void**)&w.dotpart, sizeof(double) * (m + 2) * w.dot_blocks));
+    YK_TRY(dev_alloc((void**)&w.status, sizeof(double) * 8));
+    for (int k = 0; k < 6; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n));
+    YK_TRY_CUDA(cudaMallocHost((void**)&w.h_status, sizeof(double) * 8));
+    return YK_OK;
+}
+
+void free_workspace(yk_geom* g) {
+    Workspace& w = g->ws;
+    dev_free(w.partial);
+    dev_free(w.V);
+    dev_free(w.H);
+    dev_free(w.gvec);
+    dev_free(w.cs);
+    dev_free(w.sn);
+    dev_free(w.hbuf);
+    dev_free(w.ybuf);
+    dev_free(w.dotpart);
+    dev_free(w.status);
+    for (int k = 0; k < 6; ++k) dev_free(w.vec[k]);
+    if (w.h_status) cudaFreeHost(w.h_status);
+    w = Workspace{};
+}
+
+// out[0..nvec) = V[0..nvec)^T w
+static void dots(yk_geom* g, const double* V, int nvec, const double* w, double* out) {
+    cudaStream_t st = g->ctx->stream;
+    dim3 grid(g->ws.dot_blocks, nvec);
+    YK_LAUNCH(k_dots, grid, DOT_TPB, 0, st, V, g->n, w, g->ws.dotpart);
+    YK_LAUNCH(k_reduce_parts, 1, 128, 0, st, nvec, g->ws.dot_blocks, g->ws.dotpart, out);
+}
+
+static int read_status(yk_geom* g, double* s0, double* s1) {
+    cudaStream_t st = g->ctx->stream;
+    YK_TRY_CUDA(cudaMemcpyAsync(g->ws.h_status, g->ws.status, 2 * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+    YK_TRY_CUDA(cudaStreamSynchronize(st));
+    *s0 = g->ws.h_status[0];
+    *s1 = g->ws.h_status[1];
+    return YK_OK;
+}
+
+// GMRES on A(prec) x = b with initial guess x (x_zero: x is taken as 0).
+// Stops when the residual estimate <= tol_abs. Returns iterations used.
+static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero, double tol_abs,
+                 int max_iter, int* iters_out, double* res_out, int* matvecs) {
+    Workspace& w = g->ws;
+    cudaStream_t st = g->ctx->stream;
+    const int64_t n = g->n;
+    const int m = w.m;
+    const int ldh = m + 1;
+    const int nb = ceil_div(n, 256);
+    double* r = w.vec[0];
+    double* h1 = w.hbuf;
+    double* h2 = w.hbuf + (m + 2);
+    int total = 0;
+    double res = INFINITY;
+    bool have_x = !x_zero;
+    if (x_zero) YK_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    while (true) {
+        // r = b - A x
+        if (have_x) {
+            YK_TRY(matvec(g, x, r, prec));
+            ++*matvecs;
+            YK_LAUNCH(k_sub, nb, 256, 0, st, r, b, r, n);
+        } else {
+            YK_TRY_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        }
+        dots(g, r, 1, r, w.status + 2);
+        YK_LAUNCH(k_init_cycle, 1, 32, 0, st, m, w.status + 2, w.gvec, w.status);
+        double beta, dummy;
+        YK_TRY(read_status(g, &beta, &dummy));
+        res = beta;
+        if (beta <= tol_abs || beta == 0.0 || total >= max_iter) break;
+        YK_LAUNCH(k_scale, nb, 256, 0, st, w.V, r, n, w.status + 1, 0.0);
+        int j = 0;
+        bool done = false;
+        for (; j < m && total < max_iter; ++j) {
+            double* vj = w.V + (int64_t)j * n;
+            double* wv = w.V + (int64_t)(j + 1) * n;
+            YK_TRY(matvec(g, vj, wv, prec));
+            ++*matvecs;
+            // CGS2
+            dots(g, w.V, j + 1, wv, h1);
+            YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, j + 1, h1);
+            dots(g, w.V, j + 1, wv, h2);
+            YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, j + 1, h2);
+            dots(g, wv, 1, wv, w.status + 2);
+            YK_LAUNCH(k_arnoldi_col, 1, 32, 0, st, j, ldh, w.H, h1, h2, w.status + 2, w.cs, w.sn,
+                                            w.gvec, w.status);
+            double hn;
+            YK_TRY(read_status(g, &res, &hn));
+            ++total;
+            if (hn > 0.0) YK_LAUNCH(k_scale, nb, 256, 0, st, wv, wv, n, w.status + 1, 0.0);
+            if (res <= tol_abs || hn == 0.0 || !isfinite(res)) {
+                done = true;
+                ++j;
+                break;
+            }
+        }
+        // x += V y
+        YK_LAUNCH(k_tri_solve, 1, 32, 0, st, j, ldh, w.H, w.gvec, w.ybuf);
+        YK_LAUNCH(k_add_basis, nb, 256, 0, st, x, w.V, n, j, w.ybuf);
+        have_x = true;
+        YK_TRY_CUDA(cudaGetLastError());
+        if (done || total >= max_iter || !isfinite(res)) break;
+    }
+    *iters_out = total;
+    *res_out = res;
+    return YK_OK;
+}
+
+static double norm2(yk_geom* g, const double* v) {
+    dots(g, v, 1, v, g->ws.status + 2);
+    cudaStream_t st = g->ctx->stream;
+    cudaMemcpyAsync(g->ws.h_status + 2, g->ws.status + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                    st);
+    cudaStreamSynchronize(st);
+    return sqrt(g->ws.h_status[2]);
+}
+
+int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
+          yk_solve_info* info) {
+    const yk_params& P = g->prm;
+    cudaStream_t st = g->ctx->stream;
+    const int64_t n = g->n;
+    const int nb = ceil_div(n, 256);
+    yk_solve_info inf{};
+    const double fn = norm2(g, f);
+    if (fn == 0.0) {
+        YK_TRY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * n, st));
+        if (info) *info = inf;
+        return YK_OK;
+    }
+    if (sigma0 && sigma0 != sigma)
+        YK_TRY_CUDA(cudaMemcpyAsync(sigma, sigma0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    int rc = YK_OK;
+    if (P.precision == YK_FP64) {
+        int it = 0, nmv = 0;
+        double res = 0.0;
+        YK_TRY(gmres(g, Prec::F64, f, sigma, sigma0 == nullptr, P.gmres_tol * fn, P.max_iter, &it,
+                     &res, &nmv));
+        inf.iterations = it;
+        inf.rel_residual = res / fn;
+        inf.matvecs_fp64 = nmv;
+        if (!(inf.rel_residual <= P.gmres_tol)) rc = YK_ERR_NOT_CONVERGED;
+    } else {
+        double* r = g->ws.vec[1];
+        double* d = g->ws.vec[2];
+        double* ax = g->ws.vec[3];
+        if (sigma0) {
+            YK_TRY(matvec(g, sigma, ax, Prec::SPLIT));
+            YK_LAUNCH(k_sub, nb, 256, 0, st, r, f, ax, n);
+            inf.matvecs_fp64++;
+        } else {
+            YK_TRY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * n, st));
+            YK_TRY_CUDA(cudaMemcpyAsync(r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        }
+        double rel = norm2(g, r) / fn;
+        int total = 0;
+        int ref = 0;
+        while (rel > P.gmres_tol && ref < P.max_refine && total < P.max_iter) {
+            const double rn = rel * fn;
+            int it = 0, nmv = 0;
+            double res = 0.0;
+            YK_TRY(gmres(g, Prec::F32, r, d, true, P.inner_tol * rn, P.max_iter - total, &it, &res,
+                         &nmv));
+            total += it;
+            inf.matvecs_fp32 += nmv;
+            YK_LAUNCH(k_axpy1, nb, 256, 0, st, sigma, d, n);
+            YK_TRY(matvec(g, sigma, ax, Prec::SPLIT));
+            YK_LAUNCH(k_sub, nb, 256, 0, st, r, f, ax, n);
+            inf.matvecs_fp64++;
+            rel = norm2(g, r) / fn;
+            ++ref;
+        }
+        inf.iterations = total;
+        inf.refinements = ref;
+        inf.rel_residual = rel;
+        if (!(rel <= P.gmres_tol)) rc = YK_ERR_NOT_CONVERGED;
+    }
+    YK_TRY_CUDA(cudaGetLastError());
+    if (info) *info = inf;
+    return rc;
+}
+
+}  // namespace yk

@@ -1,0 +1,170 @@
+// Internal state of the yk library: contexts, geometries and workspaces.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/yk.h"
+
+#define YK_TRY_CUDA(expr)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) {                            \
+            yk::set_cuda_error(e_, #expr, __FILE__, __LINE__); \
+            return YK_ERR_CUDA;                             \
+        }                                                   \
+    } while (0)
+
+// Every kernel launch of the library goes through YK_LAUNCH so that the
+// number of launches can be reported (yk_kernel_launches).
+#define YK_LAUNCH(kernel, grid, block, smem, stream, ...)         \
+    do {                                                         \
+        ::yk::note_launch();                                     \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__); \
+    } while (0)
+
+#define YK_TRY(expr)                 \
+    do {                             \
+        int rc_ = (expr);            \
+        if (rc_ != YK_OK) return rc_; \
+    } while (0)
+
+namespace yk {
+
+// 32-byte aligned quadruple of doubles (one vectorised load)
+struct __align__(32) d4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline d4 make_d4(double x, double y, double z, double w) {
+    return d4{x, y, z, w};
+}
+
+constexpr double PI = 3.14159265358979323846;
+constexpr int MAX_NGL = 32;
+constexpr int MAX_ORDER = 24;
+constexpr int MAX_NEAR_PANELS = 9;      // (2 near_width + 1) <= 9
+constexpr int MAX_OVERSAMPLE = 16;
+
+void set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void note_launch();
+
+// Device-resident description of a discretised configuration. All arrays
+// are device pointers owned by the yk_geom that holds this view.
+struct GeomView {
+    int np;          // particles
+    int npan;        // panels per particle
+    int ngl;         // Gauss-Legendre nodes per panel
+    int npp;         // nodes per particle = npan * ngl
+    int64_t n;       // nodes
+    int near_w;      // near panels on each side (cyclic); all panels when 2w+1 >= npan
+    int n_near;      // near panels per target
+    double rho;
+    // per particle
+    const yk::d4* part;   // (cx, cy, bounding radius, perimeter)
+    const int* shape_of;   // index of the particle's shape block
+    // per node
+    const double* x;
+    const double* y;
+    const double* nx;
+    const double* ny;
+    const double* w;
+    const double* speed;
+    const float2* xi;      // FP32 offset from the particle centre
+    // QBX near rows per shape: [shape][local node][n_near * ngl]
+    const double* cval;
+    const double* cgrad;
+};
+
+struct Workspace {
+    double* partial = nullptr;   // [nchunk][n]
+    int nchunk = 0;
+    double* V = nullptr;         // Krylov basis [(m+1)][n]
+    double* H = nullptr;         // Hessenberg (m+1) x m, column-major
+    double* gvec = nullptr;      // rotated rhs, m+1
+    double* cs = nullptr;        // Givens cosines, m
+    double* sn = nullptr;        // Givens sines, m
+    double* hbuf = nullptr;      // 2 (m+2) dot products
+    double* ybuf = nullptr;      // m+1 least-squares coefficients
+    double* dotpart = nullptr;   // partial dots [(m+2)][nblk]
+    double* status = nullptr;    // [0] residual estimate, [1] norm, [2..] scratch
+    double* vec[6] = {};         // N-length scratch vectors
+    double* h_status = nullptr;  // pinned host mirror of status (8 doubles)
+    int m = 0;
+    int dot_blocks = 0;
+};
+
+}  // namespace yk
+
+struct yk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    void* server = nullptr;  // serving state (serve.cu)
+};
+
+struct yk_geom {
+    yk_ctx* ctx = nullptr;
+    yk_params prm{};
+    int np = 0, npan = 0, ngl = 0, npp = 0, n_near = 0, nshape = 0;
+    int64_t n = 0;
+    std::vector<yk_particle> parts;
+    std::vector<int> shape_of_h;           // host copy of shape indices
+    std::vector<double2> shape_ab;         // (A, B) of each shape
+    double max_perimeter = 0.0, max_radius = 0.0;
+    double split_gap = 0.0;                // gap above which FP32 is used (mixed)
+    // device allocations
+    yk::d4* d_part = nullptr;
+    int* d_shape_of = nullptr;
+    double2* d_shape_ab = nullptr;
+    double* d_x = nullptr;
+    double* d_y = nullptr;
+    double* d_nx = nullptr;
+    double* d_ny = nullptr;
+    double* d_w = nullptr;
+    double* d_speed = nullptr;
+    float2* d_xi = nullptr;
+    double* d_cval = nullptr;
+    double* d_cgrad = nullptr;
+    double* d_glx = nullptr;      // GL nodes [ngl]
+    double* d_glw = nullptr;      // GL weights [ngl]
+    double* d_interp = nullptr;   // Lagrange interpolation [os*ngl][ngl]
+    double* d_diff = nullptr;     // Lagrange differentiation [ngl][ngl]
+    double* d_fine_x = nullptr;   // fine reference nodes [os*ngl]
+    double* d_fine_w = nullptr;   // fine reference weights [os*ngl]
+    yk::Workspace ws;
+    yk::GeomView view() const;
+};
+
+namespace yk {
+
+// geometry.cu
+int build_geometry(yk_geom* g);
+int update_nodes(yk_geom* g);
+int launch_label(yk_geom* g, int kind, double param, double* f);
+
+// p2p.cu
+enum class Prec { F64 = 0, F32 = 1, SPLIT = 2 };
+int matvec(yk_geom* g, const double* sigma, double* y, Prec prec);
+int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec);
+int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u);
+
+// gmres.cu
+int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0, yk_solve_info* info);
+int alloc_workspace(yk_geom* g);
+void free_workspace(yk_geom* g);
+
+// forces.cu
+int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,
+                   double* F, double* tau, double* net);
+
+// serve.cu
+int destroy_server(yk_ctx* ctx);
+
+// capi.cu helpers
+bool is_device_ptr(const void* p);
+int dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace yk

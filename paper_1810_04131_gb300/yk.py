@@ -1,0 +1,332 @@
+"""Python binding of the yk C ABI (include/yk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments (numpy arrays, torch tensors, plain numbers)
+to pointers and sizes and turn error codes into exceptions. All arithmetic
+runs in the CUDA library ``lib/libyk.so``; importing this module on a
+machine without the built library raises, so nothing can fall back to a
+CPU path.
+
+Arrays may be numpy arrays (host) or CUDA torch tensors (device); the
+library detects which per pointer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libyk.so")
+
+YK_OK = 0
+YK_ERR_ARG = -1
+YK_ERR_BAD_GEOMETRY = -2
+YK_ERR_NO_MEMORY = -3
+YK_ERR_NOT_CONVERGED = -4
+YK_ERR_TIMEOUT = -5
+YK_ERR_CUDA = -6
+YK_ERR_NOT_FOUND = -7
+YK_ERR_BUSY = -8
+
+YK_SHAPE_DISK = 0
+YK_SHAPE_ELLIPSE = 1
+YK_FP64 = 0
+YK_MIXED = 1
+YK_FARFIELD_DENSE = 0
+YK_LABEL_TANH = 0
+YK_LABEL_SINP = 1
+YK_LABEL_COS = 2
+YK_LABEL_CUSTOM = 3
+YK_REQ_QUEUED, YK_REQ_RUNNING, YK_REQ_DONE, YK_REQ_FAILED = 0, 1, 2, 3
+
+# every entry point declared in include/yk.h
+EXPORTS = [
+    "yk_default_params", "yk_create", "yk_destroy", "yk_create_geometry",
+    "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
+    "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_eval_potential",
+    "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_strerror",
+]
+
+
+class yk_particle(C.Structure):
+    _fields_ = [("shape", C.c_int32), ("pad_", C.c_int32), ("cx", C.c_double),
+                ("cy", C.c_double), ("phi", C.c_double), ("A", C.c_double), ("B", C.c_double)]
+
+
+class yk_params(C.Structure):
+    _fields_ = [("rho", C.c_double), ("gamma", C.c_double), ("n_panels", C.c_int32),
+                ("n_gl", C.c_int32), ("qbx_order", C.c_int32), ("oversample", C.c_int32),
+                ("qbx_r_factor", C.c_double), ("near_width", C.c_int32),
+                ("gmres_restart", C.c_int32), ("max_iter", C.c_int32),
+                ("precision", C.c_int32), ("gmres_tol", C.c_double), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int32), ("farfield", C.c_int32), ("split_tol", C.c_double)]
+
+
+class yk_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32),
+                ("rel_residual", C.c_double), ("matvecs_fp64", C.c_int32),
+                ("matvecs_fp32", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class YKError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.yk_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s failed: %s (%d)" % (where, msg, code))
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("yk CUDA library not built: %s (run paper_1810_04131_gb300.build)" % path)
+    lib = C.CDLL(path)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "yk_default_params": [C.POINTER(yk_params)],
+        "yk_create": [C.POINTER(P), I, P],
+        "yk_destroy": [P],
+        "yk_create_geometry": [P, C.POINTER(yk_particle), I, C.POINTER(yk_params), C.POINTER(P)],
+        "yk_destroy_geometry": [P],
+        "yk_update_geometry": [P, C.POINTER(yk_particle), I],
+        "yk_kernel_launches": [C.POINTER(C.c_uint64)],
+        "yk_num_nodes": [P, C.POINTER(I64)],
+        "yk_nodes": [P, P, P, P],
+        "yk_label": [P, I, D, P, P],
+        "yk_matvec": [P, P, P, I],
+        "yk_normal_derivative": [P, P, P, I],
+        "yk_solve": [P, P, P, P, C.POINTER(yk_solve_info)],
+        "yk_forces_torques": [P, P, P, P, P, P],
+        "yk_eval_potential": [P, P, P, I64, P],
+        "yk_solve_forces": [P, P, P, P, P, C.POINTER(yk_solve_info)],
+        "yk_submit": [P, C.POINTER(yk_particle), I, C.POINTER(yk_params), I, D,
+                      C.POINTER(C.c_uint64)],
+        "yk_poll": [P, C.c_uint64, C.POINTER(I), P, P, P, C.POINTER(yk_solve_info),
+                    C.POINTER(D)],
+        "yk_drain": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = I
+    lib.yk_strerror.argtypes = [I]
+    lib.yk_strerror.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc, where, ok=(YK_OK,)):
+    if rc not in ok:
+        raise YKError(rc, where)
+    return rc
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected numpy array or torch tensor, got %r" % type(a))
+
+
+def _f64(a, n, name):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or a.size != n:
+            raise ValueError("%s: need float64 array of %d elements" % (name, n))
+    elif hasattr(a, "dtype"):
+        import torch
+        if a.dtype != torch.float64 or a.numel() != n:
+            raise ValueError("%s: need float64 tensor of %d elements" % (name, n))
+    return a
+
+
+def default_params(**kw):
+    p = yk_params()
+    load().yk_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def particles_array(rows):
+    """(n, 6) array of (shape, cx, cy, phi, A, B) -> ctypes yk_particle array."""
+    rows = np.asarray(rows, dtype=np.float64)
+    arr = (yk_particle * len(rows))()
+    for i, r in enumerate(rows):
+        arr[i].shape = int(r[0])
+        arr[i].cx, arr[i].cy, arr[i].phi, arr[i].A, arr[i].B = map(float, r[1:6])
+    return arr
+
+
+class Context:
+    """yk_create / yk_destroy."""
+
+    def __init__(self, device=0, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.yk_create(C.byref(h), int(device), stream), "yk_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().yk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # serving
+    def yk_submit(self, particles, params, label_kind=YK_LABEL_TANH, label_param=10.0):
+        arr = particles_array(particles)
+        rid = C.c_uint64()
+        _check(load().yk_submit(self.h, arr, len(arr), C.byref(params), int(label_kind),
+                                float(label_param), C.byref(rid)), "yk_submit")
+        return rid.value
+
+    def yk_poll(self, rid, n_nodes=None, n_particles=None):
+        st = C.c_int()
+        info = yk_solve_info()
+        lat = C.c_double()
+        sig = np.zeros(n_nodes) if n_nodes else None
+        F = np.zeros(2 * n_particles) if n_particles else None
+        tau = np.zeros(n_particles) if n_particles else None
+        _check(load().yk_poll(self.h, C.c_uint64(rid), C.byref(st), _ptr(sig), _ptr(F), _ptr(tau),
+                              C.byref(info), C.byref(lat)), "yk_poll")
+        return dict(status=st.value, sigma=sig, F=F, tau=tau, info=info.as_dict(),
+                    latency_ms=lat.value)
+
+    def yk_drain(self):
+        _check(load().yk_drain(self.h), "yk_drain")
+
+
+class Geometry:
+    """A discretised configuration (yk_create_geometry / yk_destroy_geometry)."""
+
+    def __init__(self, ctx, particles, params):
+        lib = load()
+        self.ctx = ctx
+        self.params = params
+        arr = particles_array(particles)
+        self.n_particles = len(arr)
+        h = C.c_void_p()
+        _check(lib.yk_create_geometry(ctx.h, arr, len(arr), C.byref(params), C.byref(h)),
+               "yk_create_geometry")
+        self.h = h
+        n = C.c_int64()
+        _check(lib.yk_num_nodes(h, C.byref(n)), "yk_num_nodes")
+        self.n = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().yk_destroy_geometry(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def yk_update_geometry(self, particles):
+        arr = particles_array(particles)
+        _check(load().yk_update_geometry(self.h, arr, len(arr)), "yk_update_geometry")
+
+    def yk_nodes(self):
+        xy = np.zeros((self.n, 2))
+        nrm = np.zeros((self.n, 2))
+        w = np.zeros(self.n)
+        _check(load().yk_nodes(self.h, _ptr(xy), _ptr(nrm), _ptr(w)), "yk_nodes")
+        return xy, nrm, w
+
+    def yk_label(self, kind=YK_LABEL_TANH, param=10.0, f_custom=None, out=None):
+        out = np.zeros(self.n) if out is None else _f64(out, self.n, "out")
+        _check(load().yk_label(self.h, int(kind), float(param), _ptr(f_custom), _ptr(out)),
+               "yk_label")
+        return out
+
+    def yk_matvec(self, sigma, precision=YK_FP64, out=None):
+        _f64(sigma, self.n, "sigma")
+        out = np.zeros(self.n) if out is None else _f64(out, self.n, "out")
+        _check(load().yk_matvec(self.h, _ptr(sigma), _ptr(out), int(precision)), "yk_matvec")
+        return out
+
+    def yk_normal_derivative(self, sigma, precision=YK_FP64, out=None):
+        _f64(sigma, self.n, "sigma")
+        out = np.zeros(self.n) if out is None else _f64(out, self.n, "out")
+        _check(load().yk_normal_derivative(self.h, _ptr(sigma), _ptr(out), int(precision)),
+               "yk_normal_derivative")
+        return out
+
+    def yk_solve(self, f, sigma0=None, out=None, allow_not_converged=False):
+        _f64(f, self.n, "f")
+        out = np.zeros(self.n) if out is None else _f64(out, self.n, "out")
+        info = yk_solve_info()
+        ok = (YK_OK, YK_ERR_NOT_CONVERGED) if allow_not_converged else (YK_OK,)
+        rc = _check(load().yk_solve(self.h, _ptr(f), _ptr(out), _ptr(sigma0), C.byref(info)),
+                    "yk_solve", ok)
+        d = info.as_dict()
+        d["converged"] = rc == YK_OK
+        return out, d
+
+    def yk_forces_torques(self, sigma, f, F=None, tau=None, want_net=True):
+        F = np.zeros((self.n_particles, 2)) if F is None else F
+        tau = np.zeros(self.n_particles) if tau is None else tau
+        net = np.zeros(3) if want_net else None
+        _check(load().yk_forces_torques(self.h, _ptr(sigma), _ptr(f), _ptr(F), _ptr(tau),
+                                        _ptr(net)), "yk_forces_torques")
+        return F, tau, net
+
+    def yk_eval_potential(self, sigma, targets, out=None):
+        t = np.ascontiguousarray(targets, dtype=np.float64) if isinstance(targets, (list, np.ndarray)) else targets
+        nt = t.shape[0]
+        out = np.zeros(nt) if out is None else out
+        _check(load().yk_eval_potential(self.h, _ptr(sigma), _ptr(t), C.c_int64(nt), _ptr(out)),
+               "yk_eval_potential")
+        return out
+
+    def yk_solve_forces(self, f, sigma=None, F=None, tau=None):
+        sigma = np.zeros(self.n) if sigma is None else sigma
+        F = np.zeros((self.n_particles, 2)) if F is None else F
+        tau = np.zeros(self.n_particles) if tau is None else tau
+        info = yk_solve_info()
+        _check(load().yk_solve_forces(self.h, _ptr(f), _ptr(sigma), _ptr(F), _ptr(tau),
+                                      C.byref(info)), "yk_solve_forces",
+               (YK_OK, YK_ERR_NOT_CONVERGED))
+        return sigma, F, tau, info.as_dict()
+
+
+def yk_kernel_launches():
+    c = C.c_uint64()
+    _check(load().yk_kernel_launches(C.byref(c)), "yk_kernel_launches")
+    return c.value
+
+
+def params_for(workload, **kw):
+    """yk_params for a named workload (paper_1810_04131_gb300.workloads)."""
+    p = default_params(rho=workload.rho, n_panels=workload.n_panels, n_gl=workload.n_gl,
+                       qbx_order=workload.qbx_order, gmres_tol=workload.gmres_tol)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p

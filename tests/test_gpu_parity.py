@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (relative 2-norm unless stated):
+  * FP64 matvec and normal derivative: 1e-12;
+  * mixed (FP32 far field) matvec: 1e-6;
+  * density after a solve to 1e-10 relative residual, and forces/torques
+    (max-norm relative to max |F|): 1e-9.
+Small systems span several 256-target tiles with a ragged tail; the
+512-disk system is checked on sampled rows and through properties that
+hold at any size (the oracle's residual of the GPU density).
+"""
+import numpy as np
+import pytest
+
+from oracle import yk_oracle as yo
+from paper_1810_04131_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def yk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_04131_gb300 import yk as Y
+    Y.load()
+    return Y
+
+
+@pytest.fixture(scope="module")
+def ctx(yk):
+    c = yk.Context(0)
+    yield c
+    c.close()
+
+
+def _params(yk, wl, **kw):
+    return yk.params_for(wl, **kw)
+
+
+SMALL = {
+    # name: (workload builder, extra oracle/gpu params)
+    "disks5_pan9": lambda: W.small_system(5, 21, n_panels=9, n_gl=16, rho=0.7, qbx_order=10),
+    "ellipses4_gl11": lambda: W.small_system(4, 22, shape=W.SHAPE_ELLIPSE, n_panels=12, n_gl=11,
+                                             rho=1.3, qbx_order=9, A=1.0, B=0.5, gap=0.3),
+    "disks2_allnear": lambda: W.small_system(2, 23, n_panels=3, n_gl=16, rho=0.5, qbx_order=8),
+    "single_disk": lambda: W.Workload("single", np.array([[0, 0.3, -0.2, 0.4, 1.0, 1.0]]),
+                                      rho=4.0, n_panels=16, n_gl=16, qbx_order=10),
+}
+
+
+@pytest.fixture(scope="module")
+def dense_cache():
+    return {}
+
+
+def _oracle(wl, dense_cache, want_grad=True):
+    key = wl.name
+    if key not in dense_cache:
+        o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+        A, Gn = o.dense(want_grad=True)
+        dense_cache[key] = (o, A, Gn)
+    return dense_cache[key]
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_geometry_and_label(yk, ctx, name):
+    wl = SMALL[name]()
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+    o = yo.make_geometry(wl.particles, wl.n_panels, wl.n_gl)
+    xy, nrm, w = g.yk_nodes()
+    assert np.abs(xy - o.x).max() < 1e-13
+    assert np.abs(nrm - o.nu).max() < 1e-14
+    assert np.abs(w - o.w).max() < 1e-15
+    for kind, par in ((0, 10.0), (1, 2.0), (1, 6.0), (2, 0.0)):
+        assert np.abs(g.yk_label(kind, par) - yo.label(o, kind, par)).max() < 1e-14
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_matvec_and_gradient_small(yk, ctx, dense_cache, name):
+    wl = SMALL[name]()
+    o, A, Gn = _oracle(wl, dense_cache)
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+    rng = np.random.default_rng(5)
+    for sig in (rng.standard_normal(g.n), yo.label(o.geom, 0, 10.0)):
+        y64 = g.yk_matvec(sig, yk.YK_FP64)
+        assert rel(y64, A @ sig) < 1e-12
+        y32 = g.yk_matvec(sig, yk.YK_MIXED)
+        assert rel(y32, A @ sig) < 1e-6
+        un64 = g.yk_normal_derivative(sig, yk.YK_FP64)
+        assert rel(un64, Gn @ sig) < 1e-12
+        unsp = g.yk_normal_derivative(sig, yk.YK_MIXED)
+        assert rel(unsp, Gn @ sig) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["disks5_pan9", "ellipses4_gl11"])
+def test_solve_forces_small(yk, ctx, dense_cache, name, precision):
+    wl = SMALL[name]()
+    o, A, Gn = _oracle(wl, dense_cache)
+    prec = yk.YK_FP64 if precision == "fp64" else yk.YK_MIXED
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec))
+    f = g.yk_label(0, 10.0)
+    sig, info = g.yk_solve(f)
+    s_ref = np.linalg.solve(A, f)
+    assert info["converged"] and info["rel_residual"] <= 1e-10
+    assert rel(sig, s_ref) < 1e-9
+    F, tau, net = g.yk_forces_torques(sig, f)
+    F_ref, tau_ref, tau0_ref = o.forces_torques(f, Gn @ s_ref)
+    scale = np.abs(F_ref).max()
+    assert np.abs(F - F_ref).max() < 1e-9 * scale
+    assert np.abs(tau - tau_ref).max() < 1e-9 * max(scale, np.abs(tau_ref).max())
+    assert np.abs(net[:2] - F_ref.sum(0)).max() < 1e-9 * scale
+
+
+def test_disks8_end_to_end(yk, ctx, dense_cache):
+    """8 disks, N = 2048, rho = 1, QBX order 8, tol 1e-10: density,
+    potential at 1000 off-surface targets, forces and torques, both modes."""
+    wl = W.disks8()
+    o, A, Gn = _oracle(wl, dense_cache)
+    f_ref = yo.label(o.geom, 0, 10.0)
+    s_ref = np.linalg.solve(A, f_ref)
+    F_ref, tau_ref, _ = o.forces_torques(f_ref, Gn @ s_ref)
+    u_ref = o.potential(s_ref, wl.targets)
+    for prec in (yk.YK_FP64, yk.YK_MIXED):
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec))
+        f = g.yk_label(0, 10.0)
+        assert np.abs(f - f_ref).max() < 1e-14
+        sig, info = g.yk_solve(f)
+        assert info["converged"]
+        assert rel(sig, s_ref) < 1e-9
+        F, tau, net = g.yk_forces_torques(sig, f)
+        sc = np.abs(F_ref).max()
+        assert np.abs(F - F_ref).max() < 1e-9 * sc
+        assert np.abs(tau - tau_ref).max() < 1e-9 * sc
+        u = g.yk_eval_potential(sig, wl.targets)
+        assert rel(u, u_ref) < 1e-9
+        g.close()
+
+
+def test_device_pointers_match_host(yk, ctx):
+    import torch
+    wl = SMALL["disks5_pan9"]()
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+    rng = np.random.default_rng(3)
+    sig = rng.standard_normal(g.n)
+    y_h = g.yk_matvec(sig, yk.YK_FP64)
+    sd = torch.from_numpy(sig).cuda()
+    yd = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    g.yk_matvec(sd, yk.YK_FP64, out=yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(yd.cpu().numpy(), y_h)
+
+
+def test_errors_and_edge_cases(yk, ctx):
+    wl = SMALL["disks5_pan9"]()
+    # overlapping particles
+    bad = np.array([[0, 0.0, 0.0, 0.0, 1.0, 1.0], [0, 0.5, 0.0, 0.0, 1.0, 1.0]])
+    with pytest.raises(yk.YKError) as e:
+        yk.Geometry(ctx, bad, _params(yk, wl))
+    assert e.value.code == yk.YK_ERR_BAD_GEOMETRY
+    # parameters out of range
+    for kw in (dict(n_gl=1), dict(n_gl=40), dict(qbx_order=30), dict(rho=-1.0),
+               dict(oversample=0), dict(near_width=5), dict(precision=7)):
+        with pytest.raises(yk.YKError) as e:
+            yk.Geometry(ctx, wl.particles, _params(yk, wl, **kw))
+        assert e.value.code == yk.YK_ERR_ARG
+    # not converged: outputs still written, residual reported
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=yk.YK_FP64, max_iter=2))
+    f = g.yk_label(0, 10.0)
+    sig, info = g.yk_solve(f, allow_not_converged=True)
+    assert not info["converged"] and info["iterations"] == 2
+    assert np.isfinite(sig).all() and 0 < info["rel_residual"] < 1
+    # zero data -> zero density
+    z, info = g.yk_solve(np.zeros(g.n))
+    assert np.all(z == 0)
+    # warm start from the exact solution converges at once
+    g2 = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=yk.YK_FP64))
+    s, _ = g2.yk_solve(f)
+    s2, info2 = g2.yk_solve(f, sigma0=s)
+    assert info2["iterations"] <= 1 and rel(s2, s) < 1e-10
+    # empty target list
+    assert g2.yk_eval_potential(s, np.zeros((0, 2))).size == 0
+
+
+def test_serving_alone_and_in_mix(yk):
+    """Requests of different sizes submitted together give the same density
+    and forces as each solved alone."""
+    ctx = yk.Context(0)
+    wls = [W.small_system(n, 40 + n, n_panels=np_, rho=r) for n, np_, r in
+           ((3, 8, 0.5), (6, 10, 1.0), (2, 16, 2.0), (9, 8, 1.0))]
+    alone = []
+    for wl in wls:
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+        f = g.yk_label(0, 10.0)
+        s, F, tau, _ = g.yk_solve_forces(f)
+        alone.append((s, F.reshape(-1), tau))
+        g.close()
+    ids = [ctx.yk_submit(wl.particles, _params(yk, wl)) for wl in wls]
+    ctx.yk_drain()
+    for wl, rid, (s, F, tau) in zip(wls, ids, alone):
+        r = ctx.yk_poll(rid, n_nodes=wl.n_nodes, n_particles=wl.n_particles)
+        assert r["status"] == yk.YK_REQ_DONE
+        assert rel(r["sigma"], s) < 1e-12
+        assert np.abs(r["F"] - F).max() < 1e-12 * np.abs(F).max()
+        assert r["latency_ms"] > 0
+    ctx.close()
+
+
+# --------------------------------------------------------------------------
+# full size (512 disks, N = 131072): sampled rows and properties
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big(yk, ctx):
+    wl = W.disks512()
+    o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+    return wl, o
+
+
+def test_full_size_matvec_sampled(yk, ctx, big):
+    wl, o = big
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+    rng = np.random.default_rng(11)
+    sig = rng.standard_normal(g.n)
+    rows = np.sort(rng.choice(g.n, 48, replace=False))
+    ref = o.apply_rows(sig, rows)
+    y64 = g.yk_matvec(sig, yk.YK_FP64)
+    assert rel(y64[rows], ref) < 1e-12
+    y32 = g.yk_matvec(sig, yk.YK_MIXED)
+    assert rel(y32[rows], ref) < 1e-6
+    # whole-vector agreement of the two precisions (any size)
+    assert rel(y32, y64) < 1e-6
+
+
+def test_full_size_mixed_solve_properties(yk, ctx, big):
+    """Mixed solve on the 512-disk system: the oracle's residual of the GPU
+    density at sampled rows, and forces of sampled particles recomputed by
+    the oracle from the GPU density."""
+    wl, o = big
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=yk.YK_MIXED))
+    f = g.yk_label(0, 10.0)
+    sig, info = g.yk_solve(f)
+    assert info["converged"] and info["rel_residual"] <= 1e-10
+    rng = np.random.default_rng(12)
+    rows = np.sort(rng.choice(g.n, 48, replace=False))
+    res = f[rows] - o.apply_rows(sig, rows)
+    assert np.abs(res).max() < 1e-9 * np.abs(f).max()
+    F, tau, net = g.yk_forces_torques(sig, f)
+    for p in rng.choice(wl.n_particles, 2, replace=False):
+        idx = np.arange(p * 256, (p + 1) * 256)
+        _, un = o.apply_rows(sig, idx, want_grad=True)
+        full = np.zeros(g.n)
+        full[idx] = un
+        F_o, tau_o, _ = o.forces_torques(f, full)
+        sc = max(np.abs(F_o[p]).max(), 1e-3)
+        assert np.abs(F[p] - F_o[p]).max() < 1e-9 * sc
+        assert abs(tau[p] - tau_o[p]) < 1e-9 * sc
