@@ -257,12 +257,27 @@ class Oracle:
         r = self.qbx.r_factor * g.h[g.part[i], g.panel[i]]
         return g.x[i] + r * g.nu[i], r
 
-    def fine_nodes(self, pidx, k):
-        """Positions, normals and weights of the oversampled nodes of panel k."""
+    def local_point(self, i):
+        """Target i and its expansion centre in its particle's frame (centre
+        at the origin, same axes): the expansion of Section 5 only involves
+        positions relative to the centre c, so working in the particle frame
+        avoids the rounding of world coordinates far from the origin."""
+        g = self.geom
+        p = g.particles[g.part[i]]
+        x, _ = curve(np.array([p[0], 0.0, 0.0, p[3], p[4], p[5]]), np.array([g.t[i]]))
+        r = self.qbx.r_factor * g.h[g.part[i], g.panel[i]]
+        return x[0], x[0] + r * g.nu[i], r
+
+    def fine_nodes(self, pidx, k, local=False):
+        """Positions, normals and weights of the oversampled nodes of panel k
+        (positions in the particle frame when local=True)."""
         g = self.geom
         dt = TWO_PI / g.n_panels
         t = k * dt + 0.5 * dt * (self.fine_ref + 1.0)
-        x, dx = curve(g.particles[pidx], t)
+        p = g.particles[pidx]
+        if local:
+            p = np.array([p[0], 0.0, 0.0, p[3], p[4], p[5]])
+        x, dx = curve(p, t)
         spd = np.hypot(dx[:, 0], dx[:, 1])
         nu = np.stack([dx[:, 1], -dx[:, 0]], axis=-1) / spd[:, None]
         w = 0.5 * dt * self.fine_wref * spd
@@ -281,7 +296,7 @@ class Oracle:
         g = self.geom
         rho = self.rho
         p = self.qbx.order
-        c, r = self.qbx_centre(i)
+        xl, c, r = self.local_point(i)
         pidx = int(g.part[i])
         panels = near_panels(g, i, self.qbx.near_width)
         ng = g.n_gl
@@ -289,7 +304,7 @@ class Oracle:
         n = np.arange(p + 2)
         alpha = np.zeros((p + 1, B), dtype=np.complex128)
         for q, k in enumerate(panels):
-            y, nu, w = self.fine_nodes(pidx, k)                  # (a) fine geometry
+            y, nu, w = self.fine_nodes(pidx, k, local=True)      # (a) fine geometry
             sf = self.interp @ sigma_near[q * ng:(q + 1) * ng]    # (a) fine density
             dy = y - c
             s = np.hypot(dy[:, 0], dy[:, 1])
@@ -305,7 +320,7 @@ class Oracle:
             dK = (nus[None, :] * Knp / rho - 1j * nn * nuphi[None, :] * Kn[:p + 1] / s[None, :]) \
                 * np.exp(-1j * nn * phi[None, :])
             alpha += (dK * w[None, :]) @ sf / TWO_PI               # (b)
-        dx = g.x[i] - c
+        dx = xl - c
         theta = math.atan2(dx[1], dx[0])
         z = r / rho
         nn = np.arange(p + 1)

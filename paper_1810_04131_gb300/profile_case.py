@@ -1,0 +1,55 @@
+"""Run one kernel case of the yk library on a named workload, for profilers.
+
+    python -m paper_1810_04131_gb300.profile_case --case p2p_f32 --workload disks512 --reps 2
+
+Cases: p2p_f32 (mixed matvec: FP32 far field + near rows), p2p_f64 (FP64
+matvec), grad (precision-split normal derivative), qbx (geometry + QBX rows), solve (one mixed solve +
+forces). The geometry is built first; then the case runs --reps times.
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="p2p_f32",
+                    choices=["p2p_f32", "p2p_f64", "grad", "qbx", "solve"])
+    ap.add_argument("--workload", default="disks512")
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    import torch
+    from paper_1810_04131_gb300 import workloads as W
+    from paper_1810_04131_gb300 import yk
+    wl = W.WORKLOADS[a.workload]()
+    ctx = yk.Context(0, torch.cuda.current_stream().cuda_stream)
+    prm = yk.params_for(wl)
+    g = yk.Geometry(ctx, wl.particles, prm)
+    dev = torch.device("cuda", 0)
+    f = torch.zeros(g.n, dtype=torch.float64, device=dev)
+    g.yk_label(yk.YK_LABEL_TANH, 10.0, out=f)
+    y = torch.zeros_like(f)
+    for _ in range(a.reps):
+        if a.case == "p2p_f32":
+            g.yk_matvec(f, yk.YK_MIXED, out=y)
+        elif a.case == "p2p_f64":
+            g.yk_matvec(f, yk.YK_FP64, out=y)
+        elif a.case == "grad":
+            g.yk_normal_derivative(f, yk.YK_MIXED, out=y)
+        elif a.case == "qbx":
+            g2 = yk.Geometry(ctx, wl.particles, prm)
+            g2.close()
+        elif a.case == "solve":
+            s, info = g.yk_solve(f, out=y)
+            g.yk_forces_torques(y, f, want_net=False)
+    torch.cuda.synchronize()
+    print("ok", a.case, a.workload, g.n)
+    g.close()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -356,7 +356,7 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert _circle_ok(yo)
     orig_kernel = yo.dl_kernel
     orig_qbx = yo.Oracle.qbx_eval
-    orig_centre = yo.Oracle.qbx_centre
+    orig_local = yo.Oracle.local_point
     orig_near = yo.near_panels
 
     mutations = {
@@ -365,8 +365,8 @@ def test_planted_mistakes_are_caught(monkeypatch):
         "kernel rho factor": lambda: monkeypatch.setattr(
             yo, "dl_kernel", lambda x, y, n, r: orig_kernel(x, y, n, r) * r),
         "interior centre": lambda: monkeypatch.setattr(
-            yo.Oracle, "qbx_centre",
-            lambda self, i: (2 * self.geom.x[i] - orig_centre(self, i)[0], orig_centre(self, i)[1])),
+            yo.Oracle, "local_point",
+            lambda self, i: (lambda xl, c, r: (xl, 2 * xl - c, r))(*orig_local(self, i))),
         "no neighbour panels": lambda: monkeypatch.setattr(
             yo, "near_panels", lambda g, i, w: orig_near(g, i, 0)),
         "qbx halved": lambda: monkeypatch.setattr(
