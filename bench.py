@@ -37,6 +37,26 @@ FLOPS_PER_PAIR = 34
 SMS, FP32_LANES = 152, 128
 
 
+def kernel_source_hash():
+    """Hash of the far-field kernel source, to match stored ncu counters."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1810_04131_gb300", "csrc", "p2p.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def stored_traffic():
+    """DRAM bytes per launch of k_p2p_f32 from the committed ncu summary, if
+    it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_p2p_f32_disks512.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("p2p_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,7 +282,7 @@ def main():
     achieved = pairs * FLOPS_PER_PAIR / t_p2p / 1e12
     peak = SMS * FP32_LANES * 2 * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": stored_traffic(),
                 "kernel": "k_p2p_f32 (+k_assemble)", "pairs_per_s": pairs / t_p2p,
                 "flops_per_pair": FLOPS_PER_PAIR,
                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max SM clock"}

@@ -106,9 +106,11 @@ typedef struct {
     double inner_tol;      /* YK_MIXED: inner (FP32) GMRES tolerance; 1e-6     */
     int32_t max_refine;    /* YK_MIXED: refinement steps; default 8            */
     int32_t farfield;      /* YK_FARFIELD_DENSE                                */
-    double split_tol;      /* YK_MIXED residual/gradient: a source particle is
+    double split_tol;      /* YK_MIXED refinement residual: a source particle is
                               evaluated in FP32 only where its FP32 error bound
-                              is below split_tol * max|sigma|; default 1e-16   */
+                              is below split_tol * max|sigma|; default 1e-15   */
+    double grad_split_tol; /* the same bound for the normal derivative that
+                              feeds the forces (YK_MIXED); default 1e-13       */
 } yk_params;
 
 /* Solve statistics (all host memory). */

@@ -107,7 +107,7 @@ static int check_params(const yk_params* p) {
     if (!(p->gmres_tol > 0.0) || !(p->inner_tol > 0.0) || p->inner_tol >= 1.0) return YK_ERR_ARG;
     if (p->max_refine < 1) return YK_ERR_ARG;
     if (p->farfield != YK_FARFIELD_DENSE) return YK_ERR_ARG;
-    if (!(p->split_tol > 0.0)) return YK_ERR_ARG;
+    if (!(p->split_tol > 0.0) || !(p->grad_split_tol > 0.0)) return YK_ERR_ARG;
     return YK_OK;
 }
 
@@ -181,7 +181,8 @@ int yk_default_params(yk_params* p) {
     p->inner_tol = 1e-6;
     p->max_refine = 8;
     p->farfield = YK_FARFIELD_DENSE;
-    p->split_tol = 1e-16;
+    p->split_tol = 1e-15;
+    p->grad_split_tol = 1e-13;
     return YK_OK;
 }
 
@@ -314,6 +315,7 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     }
     g->max_perimeter = perim;
     g->split_gap = split_gap(prm->rho, perim, rmax, prm->split_tol);
+    g->split_gap_grad = split_gap(prm->rho, perim, rmax, prm->grad_split_tol);
     const int os = prm->oversample;
     const size_t N = (size_t)n;
     const size_t rowlen = (size_t)g->n_near * g->ngl;

@@ -331,9 +331,12 @@ int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
         int ref = 0;
         while (rel > P.gmres_tol && ref < P.max_refine && total < P.max_iter) {
             const double rn = rel * fn;
+            // an inner solve need not go below what the remaining factor
+            // (rel -> gmres_tol, with a 10x margin) asks for
+            const double itol = std::max(P.inner_tol, std::min(0.1, 0.1 * P.gmres_tol / rel));
             int it = 0, nmv = 0;
             double res = 0.0;
-            YK_TRY(gmres(g, Prec::F32, r, d, true, P.inner_tol * rn, P.max_iter - total, &it, &res,
+            YK_TRY(gmres(g, Prec::F32, r, d, true, itol * rn, P.max_iter - total, &it, &res,
                          &nmv));
             total += it;
             inf.matvecs_fp32 += nmv;

@@ -103,24 +103,40 @@ __global__ void __launch_bounds__(TPB) k_p2p_f64(GeomView G, const double* __res
 // centre, pre-scaled by log2(e)/rho, so that exp(-r/rho) = exp2(-z') with
 // z' = |d'| and t = 2/z = 2 log2(e)/z'. A target-source particle pair
 // contributes through the FP64 centre difference rounded once to FP32.
-// For z > 2: K1(z) = exp(-z) z^{-1/2} P(2t - 1), t = 2/z.
+// For z > 2: K1(z) = exp(-z) z^{-1/2} P(2t - 1), t = 2/z. Each thread owns
+// two targets (tid and tid + 128) so that every staged source feeds two
+// pairs. The special functions are the single-instruction approximations
+// ex2.approx.ftz and rsqrt.approx.ftz (relative error ~2^-22).
 // ---------------------------------------------------------------------------
+constexpr int F32_TPB = 128;     // threads per block (2 targets each)
+
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct PairF32 {
     // z > 2: exp2(-z') P(s) z'^{-1/2} (D'.g)/z' = K1(z) (D'.g) / (z' sqrt(log2 e))
     __device__ __forceinline__ static float far(float dX, float dY, float gx, float gy) {
         const float z2 = fmaf(dX, dX, dY * dY);
-        const float rz = rsqrtf(z2);                  // 1/z'
+        const float rz = rsqrt_fast(z2);              // 1/z'
         const float zp = z2 * rz;                     // z' = z log2 e
         const float s = fmaf(4.0f * LOG2E_F, rz, -1.0f);   // 2t - 1
         const float P = hornerf(YK_P1_F32, s);
-        const float e = exp2f(-zp);
-        const float sq = rsqrtf(zp);                  // (z log2 e)^{-1/2}
-        return e * P * sq * (rz * fmaf(dX, gx, dY * gy));
+        const float e = ex2_fast(-zp);
+        const float sq = rsqrt_fast(zp);              // (z log2 e)^{-1/2}
+        return (e * P * sq) * (rz * fmaf(dX, gx, dY * gy));
     }
     // general pair (any z), same units as far(): K1(z) (D'.g) / (z' sqrt(log2 e))
     __device__ __forceinline__ static float any(float dX, float dY, float gx, float gy) {
         const float z2 = fmaf(dX, dX, dY * dY);
-        const float rz = rsqrtf(z2);
+        const float rz = rsqrt_fast(z2);
         const float zp = z2 * rz;
         const float z = zp * (1.0f / LOG2E_F);
         if (z > 2.0f) return far(dX, dY, gx, gy);
@@ -129,67 +145,96 @@ struct PairF32 {
     }
 };
 
-__global__ void __launch_bounds__(TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
-                                                 int ppc, float kscale,
-                                                 double* __restrict__ partial) {
+struct TargetF32 {
+    float TX, TY;       // scaled target position relative to the source particle
+    bool close, own;
+    int pan;
+};
+
+__device__ __forceinline__ void sweep_general(const float4* src, int jb, int cnt, const GeomView& G,
+                                              const TargetF32& T, float& acc) {
+    for (int q = 0; q < cnt; ++q) {
+        if (T.own && is_near_panel(T.pan, (jb + q) / G.ngl, G.npan, G.near_w)) continue;
+        const float4 S = src[q];
+        acc += PairF32::any(T.TX - S.x, T.TY - S.y, S.z, S.w);
+    }
+}
+
+__global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
+                                                     int ppc, float kscale,
+                                                     double* __restrict__ partial) {
     __shared__ float4 src[STILE];
-    const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const bool active = i < G.n;
-    const int64_t ii = active ? i : 0;
-    const float2 xit = G.xi[ii];
-    const int pt = (int)(ii / G.npp);
-    const int tpan = (int)(ii % G.npp) / G.ngl;
-    const yk::d4 at = G.part[pt];
+    const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
+    const int64_t i1 = i0 + F32_TPB;
+    const bool act0 = i0 < G.n, act1 = i1 < G.n;
+    const int64_t ii0 = act0 ? i0 : 0, ii1 = act1 ? i1 : 0;
+    const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
+    const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
+    const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
+    const yk::d4 at0 = G.part[pt0], at1 = G.part[pt1];
     const double kp = 1.4426950408889634 / G.rho;   // log2(e) / rho
-    const double near_gap = 2.0 * G.rho;   // below this a pair may have z <= 2
+    const float kpf = (float)kp;
+    const double near_gap = 2.0 * G.rho;            // below this a pair may have z <= 2
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
-    double acc = 0.0;
+    double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
         const int64_t base = (int64_t)s * G.npp;
         const yk::d4 as = G.part[s];
-        const bool own = (s == pt);
-        const double ddx = at.x - as.x, ddy = at.y - as.y;
-        const bool close = own || (sqrt(ddx * ddx + ddy * ddy) - at.z - as.z <= near_gap);
-        const float TX = (float)(kp * ddx) + (float)kp * xit.x;
-        const float TY = (float)(kp * ddy) + (float)kp * xit.y;
+        TargetF32 T0, T1;
+        {
+            const double dx = at0.x - as.x, dy = at0.y - as.y;
+            T0.own = (s == pt0);
+            T0.close = T0.own || (sqrt(dx * dx + dy * dy) - at0.z - as.z <= near_gap);
+            T0.TX = (float)(kp * dx) + kpf * xi0.x;
+            T0.TY = (float)(kp * dy) + kpf * xi0.y;
+            T0.pan = pan0;
+        }
+        {
+            const double dx = at1.x - as.x, dy = at1.y - as.y;
+            T1.own = (s == pt1);
+            T1.close = T1.own || (sqrt(dx * dx + dy * dy) - at1.z - as.z <= near_gap);
+            T1.TX = (float)(kp * dx) + kpf * xi1.x;
+            T1.TY = (float)(kp * dy) + kpf * xi1.y;
+            T1.pan = pan1;
+        }
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
             __syncthreads();
-            if (threadIdx.x < cnt) {
-                const int64_t j = base + jb + threadIdx.x;
+            for (int q = threadIdx.x; q < cnt; q += F32_TPB) {
+                const int64_t j = base + jb + q;
                 const float2 xs = G.xi[j];
                 const double ws = G.w[j] * sigma[j];
-                src[threadIdx.x] = make_float4((float)kp * xs.x, (float)kp * xs.y,
-                                               (float)(ws * G.nx[j]), (float)(ws * G.ny[j]));
+                src[q] = make_float4(kpf * xs.x, kpf * xs.y, (float)(ws * G.nx[j]),
+                                     (float)(ws * G.ny[j]));
             }
             __syncthreads();
-            if (!active) continue;
-            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-            if (!close) {
+            float a0 = 0.0f, b0 = 0.0f, a1 = 0.0f, b1 = 0.0f;
+            if (!T0.close && !T1.close) {
                 int q = 0;
-                for (; q + 4 <= cnt; q += 4) {
-                    const float4 S0 = src[q], S1 = src[q + 1], S2 = src[q + 2], S3 = src[q + 3];
-                    a0 += PairF32::far(TX - S0.x, TY - S0.y, S0.z, S0.w);
-                    a1 += PairF32::far(TX - S1.x, TY - S1.y, S1.z, S1.w);
-                    a2 += PairF32::far(TX - S2.x, TY - S2.y, S2.z, S2.w);
-                    a3 += PairF32::far(TX - S3.x, TY - S3.y, S3.z, S3.w);
+#pragma unroll 2
+                for (; q + 2 <= cnt; q += 2) {
+                    const float4 S = src[q], U = src[q + 1];
+                    a0 += PairF32::far(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
+                    a1 += PairF32::far(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
+                    b0 += PairF32::far(T0.TX - U.x, T0.TY - U.y, U.z, U.w);
+                    b1 += PairF32::far(T1.TX - U.x, T1.TY - U.y, U.z, U.w);
                 }
-                for (; q < cnt; ++q) {
+                if (q < cnt) {
                     const float4 S = src[q];
-                    a0 += PairF32::far(TX - S.x, TY - S.y, S.z, S.w);
+                    a0 += PairF32::far(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
+                    a1 += PairF32::far(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
                 }
             } else {
-                for (int q = 0; q < cnt; ++q) {
-                    if (own && is_near_panel(tpan, (jb + q) / G.ngl, G.npan, G.near_w)) continue;
-                    const float4 S = src[q];
-                    a0 += PairF32::any(TX - S.x, TY - S.y, S.z, S.w);
-                }
+                sweep_general(src, jb, cnt, G, T0, a0);
+                sweep_general(src, jb, cnt, G, T1, a1);
             }
-            acc += (double)((a0 + a1) + (a2 + a3));
+            acc0 += (double)(a0 + b0);
+            acc1 += (double)(a1 + b1);
         }
     }
-    if (active) partial[blockIdx.y * G.n + i] = acc * (double)kscale;
+    if (act0) partial[blockIdx.y * G.n + i0] = acc0 * (double)kscale;
+    if (act1) partial[blockIdx.y * G.n + i1] = acc1 * (double)kscale;
 }
 
 // ---------------------------------------------------------------------------
@@ -391,7 +436,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
     } else if (prec == Prec::F32) {
         // PairF32 returns K1(z) (d . g)/r / sqrt(log2 e) in scaled units
         const double ks = sqrt(1.4426950408889634) / (2.0 * PI * g->prm.rho);
-        YK_LAUNCH(k_p2p_f32, grid, TPB, 0, st, G, sigma, ppc, (float)ks, g->ws.partial);
+        YK_LAUNCH(k_p2p_f32, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks, g->ws.partial);
     } else {
         YK_LAUNCH(k_p2p_split<false>, grid, TPB, 0, st, G, sigma, ppc, g->split_gap, g->ws.partial);
     }
@@ -409,7 +454,8 @@ int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
     if (prec == Prec::F64) {
         YK_LAUNCH(k_p2p_f64<true>, grid, TPB, 0, st, G, sigma, ppc, g->ws.partial);
     } else {
-        YK_LAUNCH(k_p2p_split<true>, grid, TPB, 0, st, G, sigma, ppc, g->split_gap, g->ws.partial);
+        YK_LAUNCH(k_p2p_split<true>, grid, TPB, 0, st, G, sigma, ppc, g->split_gap_grad,
+                  g->ws.partial);
     }
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, nchunk, g->ws.partial, G.cgrad, sigma, un);
     YK_TRY_CUDA(cudaGetLastError());

@@ -111,7 +111,8 @@ struct yk_geom {
     std::vector<int> shape_of_h;           // host copy of shape indices
     std::vector<double2> shape_ab;         // (A, B) of each shape
     double max_perimeter = 0.0, max_radius = 0.0;
-    double split_gap = 0.0;                // gap above which FP32 is used (mixed)
+    double split_gap = 0.0;                // gap above which FP32 is used (mixed residual)
+    double split_gap_grad = 0.0;           // the same for the normal derivative
     // device allocations
     yk::d4* d_part = nullptr;
     int* d_shape_of = nullptr;

@@ -61,7 +61,8 @@ class yk_params(C.Structure):
                 ("qbx_r_factor", C.c_double), ("near_width", C.c_int32),
                 ("gmres_restart", C.c_int32), ("max_iter", C.c_int32),
                 ("precision", C.c_int32), ("gmres_tol", C.c_double), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int32), ("farfield", C.c_int32), ("split_tol", C.c_double)]
+                ("max_refine", C.c_int32), ("farfield", C.c_int32), ("split_tol", C.c_double),
+                ("grad_split_tol", C.c_double)]
 
 
 class yk_solve_info(C.Structure):
