@@ -148,6 +148,8 @@ yk::GeomView yk_geom::view() const {
     v.n_near = n_near;
     v.rho = prm.rho;
     v.part = d_part;
+    v.c32 = d_c32;
+    v.r32 = d_r32;
     v.shape_of = d_shape_of;
     v.x = d_x;
     v.y = d_y;
@@ -228,7 +230,8 @@ int yk_destroy_geometry(yk_geom* g) {
     cudaSetDevice(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
     free_workspace(g);
-    void* bufs[] = {g->d_part, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
+    for (auto& L : g->lists) dev_free(L.d);
+    void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
                     g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w};
     for (void* b : bufs) dev_free(b);
@@ -323,6 +326,9 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
 #define ALLOC(ptr, count) \
     if (rc == YK_OK) rc = dev_alloc((void**)&g->ptr, sizeof(*g->ptr) * (size_t)(count))
     ALLOC(d_part, n_particles);
+    ALLOC(d_c32, n_particles);
+    ALLOC(d_r32, n_particles);
+    ALLOC(d_counter, 1);
     ALLOC(d_shape_of, n_particles);
     ALLOC(d_shape_ab, g->nshape);
     ALLOC(d_x, N);

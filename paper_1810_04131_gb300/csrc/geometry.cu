@@ -135,7 +135,7 @@ __global__ void k_nodes(int64_t n, int npan, int ngl, const yk_particle* parts,
 
 // Per particle: centre, bounding radius and perimeter (sum of weights).
 __global__ void k_particle_info(int np, int npp, const yk_particle* parts, const double* W,
-                                yk::d4* out) {
+                                yk::d4* out, float4* c32, float* r32) {
     int p = blockIdx.x;
     double s = 0.0;
     for (int j = threadIdx.x; j < npp; j += blockDim.x) s += W[(int64_t)p * npp + j];
@@ -149,6 +149,9 @@ __global__ void k_particle_info(int np, int npp, const yk_particle* parts, const
     if (threadIdx.x == 0) {
         yk_particle P = parts[p];
         out[p] = make_d4(P.cx, P.cy, fmax(P.A, P.B), red[0]);
+        const float hx = (float)P.cx, hy = (float)P.cy;
+        c32[p] = make_float4(hx, hy, (float)(P.cx - (double)hx), (float)(P.cy - (double)hy));
+        r32[p] = (float)fmax(P.A, P.B);
     }
 }
 
@@ -315,7 +318,9 @@ int update_nodes(yk_geom* g) {
                                 cudaMemcpyHostToDevice, st));
     YK_LAUNCH(k_nodes, ceil_div(g->n, 256), 256, 0, st, g->n, g->npan, g->ngl, d_parts, g->d_glx,
               g->d_glw, g->d_x, g->d_y, g->d_nx, g->d_ny, g->d_w, g->d_speed, g->d_xi);
-    YK_LAUNCH(k_particle_info, g->np, 256, 0, st, g->np, g->npp, d_parts, g->d_w, g->d_part);
+    YK_LAUNCH(k_particle_info, g->np, 256, 0, st, g->np, g->npp, d_parts, g->d_w, g->d_part,
+              g->d_c32, g->d_r32);
+    for (auto& L : g->lists) L.valid = false;   // particle pairs change when particles move
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     dev_free(d_parts);

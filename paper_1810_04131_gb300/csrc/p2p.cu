@@ -7,14 +7,21 @@
 // Normal derivative at a boundary target with normal nu_x:
 //   nu_x . grad_x dG/dnu_y = [g (nu_y . nu_x) + g'(r) (d . nu_y)(d . nu_x)/r] / 2pi,
 //   g = K1(z)/(rho r), g' = -(K0(z)/rho + 2 K1(z)/r)/(rho r), z = r/rho, d = x - y.
-//
-// Work decomposition: blockIdx.x = 256 consecutive targets (one per thread),
-// blockIdx.y = a chunk of consecutive source particles. Each source
-// particle's nodes are staged in shared memory and swept by all targets;
-// the per-chunk sums go to partial[chunk][target] and k_assemble adds the
-// chunks in a fixed order (deterministic) plus the near rows.
 // Sources that are the target's own near panels are skipped: the QBX rows
 // replace them.
+//
+// Three evaluators share the work:
+//  * k_p2p_f32 / k_p2p_f32_grad: FP32 evaluation with FP64 accumulation per
+//    source particle; blockIdx.x = 256 consecutive targets (two per thread),
+//    blockIdx.y = a chunk of source particles, partial sums per chunk.
+//    With a skip distance they leave out the particle pairs that the FP64
+//    tiles handle (same FP64 predicate in both places).
+//  * k_tiles_f64<GRAD>: one block per listed particle pair (P, Q), P <= Q,
+//    all in FP64. The pair kernels are symmetric in (i, j) up to the sign of
+//    d (value) or exactly (gradient), so each kernel evaluation feeds both
+//    targets: P's nodes through registers, Q's through a warp reduction and
+//    shared-memory atomics. Results go to a FP64 buffer with atomics.
+//  * k_assemble: chunk partials (fixed order) + FP64 tile sums + near rows.
 #include <math.h>
 
 #include <algorithm>
@@ -24,9 +31,12 @@
 
 namespace yk {
 
-constexpr int TPB = 256;        // targets per block
-constexpr int STILE = 256;      // source nodes staged per pass
+constexpr int TPB = 256;         // targets per far-field block
+constexpr int STILE = 256;       // source nodes staged per pass
+constexpr int F32_TPB = 128;     // FP32 kernels: two targets per thread
+constexpr int TILE_TPB = 256;    // FP64 pair tiles
 constexpr float LOG2E_F = 1.4426950408889634f;
+constexpr double LOG2E = 1.4426950408889634;
 
 __device__ __forceinline__ bool is_near_panel(int pt_panel, int ps_panel, int npan, int w) {
     if (2 * w + 1 >= npan) return true;
@@ -35,80 +45,14 @@ __device__ __forceinline__ bool is_near_panel(int pt_panel, int ps_panel, int np
     return d <= w || npan - d <= w;
 }
 
-// ---------------------------------------------------------------------------
-// FP64 far field (value or normal derivative)
-// ---------------------------------------------------------------------------
-template <bool GRAD>
-__global__ void __launch_bounds__(TPB) k_p2p_f64(GeomView G, const double* __restrict__ sigma,
-                                                 int ppc, double* __restrict__ partial) {
-    __shared__ yk::d4 src[STILE];
-    const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const bool active = i < G.n;
-    const int64_t ii = active ? i : 0;
-    const double tx = G.x[ii], ty = G.y[ii];
-    const double tnx = GRAD ? G.nx[ii] : 0.0, tny = GRAD ? G.ny[ii] : 0.0;
-    const int pt = (int)(ii / G.npp);
-    const int tpan = (int)(ii % G.npp) / G.ngl;
-    const double rho = G.rho, kappa = 1.0 / rho, two_rho = 2.0 * rho;
-    const int s0 = blockIdx.y * ppc;
-    const int s1 = min(G.np, s0 + ppc);
-    double acc = 0.0;
-    for (int s = s0; s < s1; ++s) {
-        const int64_t base = (int64_t)s * G.npp;
-        const bool own = (s == pt);
-        for (int jb = 0; jb < G.npp; jb += STILE) {
-            const int cnt = min(STILE, G.npp - jb);
-            __syncthreads();
-            if (threadIdx.x < cnt) {
-                const int64_t j = base + jb + threadIdx.x;
-                const double ws = G.w[j] * sigma[j];
-                src[threadIdx.x] = make_d4(G.x[j], G.y[j], ws * G.nx[j], ws * G.ny[j]);
-            }
-            __syncthreads();
-            if (!active) continue;
-            for (int q = 0; q < cnt; ++q) {
-                if (own && is_near_panel(tpan, (jb + q) / G.ngl, G.npan, G.near_w)) continue;
-                const yk::d4 S = src[q];
-                const double dx = tx - S.x, dy = ty - S.y;
-                const double r2 = fma(dx, dx, dy * dy);
-                const double ri = rsqrt(r2);
-                const double z = r2 * ri * kappa;
-                if (!GRAD) {
-                    double k1v;
-                    if (z <= 2.0) k1v = k1_series(z);
-                    else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
-                    acc = fma(k1v * ri, fma(dx, S.z, dy * S.w), acc);
-                } else {
-                    double k0v, k1v;
-                    k01(z, k0v, k1v);
-                    const double g = k1v * ri * kappa;
-                    const double gp = -(k0v * kappa + 2.0 * k1v * ri) * kappa * ri;
-                    const double dn_s = fma(dx, S.z, dy * S.w);     // (d . nu_y) w sigma
-                    const double nn = fma(tnx, S.z, tny * S.w);     // (nu_x . nu_y) w sigma
-                    const double dn_t = fma(dx, tnx, dy * tny);     // d . nu_x
-                    acc += g * nn + gp * dn_s * dn_t * ri;
-                }
-            }
-        }
-    }
-    if (active) {
-        const double scale = GRAD ? 1.0 / (2.0 * PI) : 1.0 / (2.0 * PI * rho);
-        partial[blockIdx.y * G.n + i] = acc * scale;
-    }
+// The particle-pair predicate "handled by the FP64 tiles": the same particle,
+// or bounding circles closer than thr. Evaluated with explicitly rounded
+// operations so that the list builder and the FP32 kernels agree bitwise.
+__device__ __forceinline__ bool pair_in_tiles(const d4& a, const d4& b, double thr) {
+    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
+    const double s = __dadd_rn(__dadd_rn(a.z, b.z), thr);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < __dmul_rn(s, s);
 }
-
-// ---------------------------------------------------------------------------
-// FP32 far field with FP64 accumulation (value only; the inner operator of
-// the mixed solver). Coordinates are FP32 offsets from each particle's
-// centre, pre-scaled by log2(e)/rho, so that exp(-r/rho) = exp2(-z') with
-// z' = |d'| and t = 2/z = 2 log2(e)/z'. A target-source particle pair
-// contributes through the FP64 centre difference rounded once to FP32.
-// For z > 2: K1(z) = exp(-z) z^{-1/2} P(2t - 1), t = 2/z. Each thread owns
-// two targets (tid and tid + 128) so that every staged source feeds two
-// pairs. The special functions are the single-instruction approximations
-// ex2.approx.ftz and rsqrt.approx.ftz (relative error ~2^-22).
-// ---------------------------------------------------------------------------
-constexpr int F32_TPB = 128;     // threads per block (2 targets each)
 
 __device__ __forceinline__ float ex2_fast(float x) {
     float y;
@@ -121,19 +65,27 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 pair evaluation. Coordinates are FP32 offsets from each particle's
+// centre, pre-scaled by log2(e)/rho, so that exp(-r/rho) = exp2(-z') with
+// z' = |d'|, and t = 2/z = 2 log2(e)/z'. For z > 2:
+// K1(z) = exp(-z) z^{-1/2} P1(2t - 1). The special functions are the
+// single-instruction approximations ex2.approx.ftz and rsqrt.approx.ftz
+// (relative error ~2^-22).
+// ---------------------------------------------------------------------------
 struct PairF32 {
-    // z > 2: exp2(-z') P(s) z'^{-1/2} (D'.g)/z' = K1(z) (D'.g) / (z' sqrt(log2 e))
+    // z > 2: exp2(-z') P1(s) z'^{-1/2} (D'.g)/z' = K1(z) (D'.g) / (z' sqrt(log2 e))
     __device__ __forceinline__ static float far(float dX, float dY, float gx, float gy) {
         const float z2 = fmaf(dX, dX, dY * dY);
-        const float rz = rsqrt_fast(z2);              // 1/z'
-        const float zp = z2 * rz;                     // z' = z log2 e
-        const float s = fmaf(4.0f * LOG2E_F, rz, -1.0f);   // 2t - 1
+        const float rz = rsqrt_fast(z2);                     // 1/z'
+        const float zp = z2 * rz;                            // z' = z log2 e
+        const float s = fmaf(4.0f * LOG2E_F, rz, -1.0f);     // 2t - 1
         const float P = hornerf(YK_P1_F32, s);
         const float e = ex2_fast(-zp);
-        const float sq = rsqrt_fast(zp);              // (z log2 e)^{-1/2}
+        const float sq = rsqrt_fast(zp);                     // (z log2 e)^{-1/2}
         return (e * P * sq) * (rz * fmaf(dX, gx, dY * gy));
     }
-    // general pair (any z), same units as far(): K1(z) (D'.g) / (z' sqrt(log2 e))
+    // any z, same units as far()
     __device__ __forceinline__ static float any(float dX, float dY, float gx, float gy) {
         const float z2 = fmaf(dX, dX, dY * dY);
         const float rz = rsqrt_fast(z2);
@@ -143,25 +95,58 @@ struct PairF32 {
         const float k1v = k1f(z, 2.0f / z);
         return k1v * rsqrtf(LOG2E_F) * (rz * fmaf(dX, gx, dY * gy));
     }
+    // normal derivative, unscaled coordinates d = x - y, target normal (nx, ny):
+    // [g (nu_x . G) + g' (d . G)(d . nu_x)/r] with G = w sigma nu_y (2 pi left out)
+    __device__ __forceinline__ static float grad(float dx, float dy, float nx, float ny, float gx,
+                                                 float gy, float kappa, float rho) {
+        const float r2 = fmaf(dx, dx, dy * dy);
+        const float ri = rsqrt_fast(r2);
+        const float z = r2 * ri * kappa;
+        const float t = 2.0f * rho * ri;
+        float k0v, k1v;
+        if (z > 2.0f) {
+            const float e = ex2_fast(-z * LOG2E_F) * rsqrt_fast(z);
+            const float s = 2.0f * t - 1.0f;
+            k0v = e * hornerf(YK_P0_F32, s);
+            k1v = e * hornerf(YK_P1_F32, s);
+        } else {
+            k01f(z, t, k0v, k1v);
+        }
+        const float g = k1v * ri * kappa;
+        const float gp = -(k0v * kappa + 2.0f * k1v * ri) * kappa * ri;
+        const float dn_s = fmaf(dx, gx, dy * gy);
+        const float nn = fmaf(nx, gx, ny * gy);
+        const float dn_t = fmaf(dx, nx, dy * ny);
+        return fmaf(g, nn, gp * dn_s * dn_t * ri);
+    }
 };
 
 struct TargetF32 {
-    float TX, TY;       // scaled target position relative to the source particle
-    bool close, own;
+    float TX, TY;       // (scaled) target position relative to the source particle's centre
+    bool close, own, skip;
     int pan;
 };
 
-__device__ __forceinline__ void sweep_general(const float4* src, int jb, int cnt, const GeomView& G,
-                                              const TargetF32& T, float& acc) {
-    for (int q = 0; q < cnt; ++q) {
-        if (T.own && is_near_panel(T.pan, (jb + q) / G.ngl, G.npan, G.near_w)) continue;
-        const float4 S = src[q];
-        acc += PairF32::any(T.TX - S.x, T.TY - S.y, S.z, S.w);
-    }
+// Target-side set-up against source particle s (all in FP32 from the hi/lo
+// centres, plus the FP64 tile predicate when a skip distance is given).
+__device__ __forceinline__ void target_setup(TargetF32& T, const GeomView& G, int pt, int s,
+                                             float2 xit, float scale, float near_gap,
+                                             bool mask, double skip_gap, int pan) {
+    const float4 ct = G.c32[pt], cs = G.c32[s];
+    const float dX = (ct.x - cs.x) + (ct.z - cs.z);
+    const float dY = (ct.y - cs.y) + (ct.w - cs.w);
+    T.own = (s == pt);
+    const float gap = sqrtf(dX * dX + dY * dY) - G.r32[pt] - G.r32[s];
+    T.close = T.own || gap <= near_gap;
+    T.skip = mask && pair_in_tiles(G.part[pt], G.part[s], skip_gap);
+    T.TX = fmaf(scale, dX, scale * xit.x);
+    T.TY = fmaf(scale, dY, scale * xit.y);
+    T.pan = pan;
 }
 
+template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
-                                                     int ppc, float kscale,
+                                                     int ppc, float kscale, double skip_gap,
                                                      double* __restrict__ partial) {
     __shared__ float4 src[STILE];
     const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
@@ -171,33 +156,20 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
     const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
     const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
     const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
-    const yk::d4 at0 = G.part[pt0], at1 = G.part[pt1];
-    const double kp = 1.4426950408889634 / G.rho;   // log2(e) / rho
-    const float kpf = (float)kp;
-    const double near_gap = 2.0 * G.rho;            // below this a pair may have z <= 2
+    const float kpf = (float)(LOG2E / G.rho);          // log2(e) / rho
+    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;  // z <= 2 possible below
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
     double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
         const int64_t base = (int64_t)s * G.npp;
-        const yk::d4 as = G.part[s];
         TargetF32 T0, T1;
-        {
-            const double dx = at0.x - as.x, dy = at0.y - as.y;
-            T0.own = (s == pt0);
-            T0.close = T0.own || (sqrt(dx * dx + dy * dy) - at0.z - as.z <= near_gap);
-            T0.TX = (float)(kp * dx) + kpf * xi0.x;
-            T0.TY = (float)(kp * dy) + kpf * xi0.y;
-            T0.pan = pan0;
-        }
-        {
-            const double dx = at1.x - as.x, dy = at1.y - as.y;
-            T1.own = (s == pt1);
-            T1.close = T1.own || (sqrt(dx * dx + dy * dy) - at1.z - as.z <= near_gap);
-            T1.TX = (float)(kp * dx) + kpf * xi1.x;
-            T1.TY = (float)(kp * dy) + kpf * xi1.y;
-            T1.pan = pan1;
-        }
+        target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
+        target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
+        // skip the source particle only when every thread of the block agrees
+        // (a block-wide vote, reached by all threads), so barriers stay uniform
+        const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
+        if (block_skip) continue;
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
             __syncthreads();
@@ -210,7 +182,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
             }
             __syncthreads();
             float a0 = 0.0f, b0 = 0.0f, a1 = 0.0f, b1 = 0.0f;
-            if (!T0.close && !T1.close) {
+            if (!T0.close && !T1.close && !(MASK && (T0.skip || T1.skip))) {
                 int q = 0;
 #pragma unroll 2
                 for (; q + 2 <= cnt; q += 2) {
@@ -226,8 +198,16 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
                     a1 += PairF32::far(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
                 }
             } else {
-                sweep_general(src, jb, cnt, G, T0, a0);
-                sweep_general(src, jb, cnt, G, T1, a1);
+                for (int q = 0; q < cnt; ++q) {
+                    const float4 S = src[q];
+                    const int pq = (jb + q) / G.ngl;
+                    if (!(MASK && T0.skip) &&
+                        !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+                        a0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
+                    if (!(MASK && T1.skip) &&
+                        !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+                        a1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
+                }
             }
             acc0 += (double)(a0 + b0);
             acc1 += (double)(a1 + b1);
@@ -237,118 +217,180 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
     if (act1) partial[blockIdx.y * G.n + i1] = acc1 * (double)kscale;
 }
 
-// ---------------------------------------------------------------------------
-// Precision-split far field (value or normal derivative): a source particle
-// whose FP32 error bound is below the split tolerance (its gap to the
-// target's particle is at least split_gap) is swept in FP32; closer ones
-// in FP64. Used for the FP64-accurate residual and gradient of the mixed
-// solver.
-// ---------------------------------------------------------------------------
-template <bool GRAD>
-__global__ void __launch_bounds__(TPB) k_p2p_split(GeomView G, const double* __restrict__ sigma,
-                                                   int ppc, double split_gap,
-                                                   double* __restrict__ partial) {
-    __shared__ yk::d4 src[STILE];
-    __shared__ float4 srcf[STILE];
-    const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const bool active = i < G.n;
-    const int64_t ii = active ? i : 0;
-    const double tx = G.x[ii], ty = G.y[ii];
-    const double tnx = GRAD ? G.nx[ii] : 0.0, tny = GRAD ? G.ny[ii] : 0.0;
-    const float2 xit = G.xi[ii];
-    const int pt = (int)(ii / G.npp);
-    const int tpan = (int)(ii % G.npp) / G.ngl;
-    const yk::d4 at = G.part[pt];
-    const double rho = G.rho, kappa = 1.0 / rho, two_rho = 2.0 * rho;
-    const float rhof = (float)rho, kappaf = (float)kappa;
+// FP32 normal derivative of the far field (unscaled offsets), two targets
+// per thread, with the same masking as k_p2p_f32.
+template <bool MASK>
+__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
+                                                          const double* __restrict__ sigma,
+                                                          int ppc, double skip_gap,
+                                                          double* __restrict__ partial) {
+    __shared__ float4 src[STILE];
+    const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
+    const int64_t i1 = i0 + F32_TPB;
+    const bool act0 = i0 < G.n, act1 = i1 < G.n;
+    const int64_t ii0 = act0 ? i0 : 0, ii1 = act1 ? i1 : 0;
+    const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
+    const float nx0 = (float)G.nx[ii0], ny0 = (float)G.ny[ii0];
+    const float nx1 = (float)G.nx[ii1], ny1 = (float)G.ny[ii1];
+    const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
+    const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
+    const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
-    double acc = 0.0;
+    double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
         const int64_t base = (int64_t)s * G.npp;
-        const yk::d4 as = G.part[s];
-        const bool own = (s == pt);
-        const double ddx = at.x - as.x, ddy = at.y - as.y;
-        const bool use64 = own || (sqrt(ddx * ddx + ddy * ddy) - at.z - as.z < split_gap);
-        // block-uniform staging of both forms; each thread sweeps one
-        const float TX = (float)ddx + xit.x, TY = (float)ddy + xit.y;
+        TargetF32 T0, T1;
+        target_setup(T0, G, pt0, s, xi0, 1.0f, 0.0f, MASK, skip_gap, pan0);
+        target_setup(T1, G, pt1, s, xi1, 1.0f, 0.0f, MASK, skip_gap, pan1);
+        const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
+        if (block_skip) continue;
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
             __syncthreads();
-            if (threadIdx.x < cnt) {
-                const int64_t j = base + jb + threadIdx.x;
-                const double ws = G.w[j] * sigma[j];
-                const double gx = ws * G.nx[j], gy = ws * G.ny[j];
-                src[threadIdx.x] = make_d4(G.x[j], G.y[j], gx, gy);
+            for (int q = threadIdx.x; q < cnt; q += F32_TPB) {
+                const int64_t j = base + jb + q;
                 const float2 xs = G.xi[j];
-                srcf[threadIdx.x] = make_float4(xs.x, xs.y, (float)gx, (float)gy);
+                const double ws = G.w[j] * sigma[j];
+                src[q] = make_float4(xs.x, xs.y, (float)(ws * G.nx[j]), (float)(ws * G.ny[j]));
             }
             __syncthreads();
-            if (!active) continue;
-            if (use64) {
-                for (int q = 0; q < cnt; ++q) {
-                    if (own && is_near_panel(tpan, (jb + q) / G.ngl, G.npan, G.near_w)) continue;
-                    const yk::d4 S = src[q];
-                    const double dx = tx - S.x, dy = ty - S.y;
-                    const double r2 = fma(dx, dx, dy * dy);
-                    const double ri = rsqrt(r2);
-                    const double z = r2 * ri * kappa;
-                    if (!GRAD) {
-                        double k1v;
-                        if (z <= 2.0) k1v = k1_series(z);
-                        else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
-                        acc = fma(k1v * ri * kappa, fma(dx, S.z, dy * S.w), acc);
-                    } else {
-                        double k0v, k1v;
-                        k01(z, k0v, k1v);
-                        const double g = k1v * ri * kappa;
-                        const double gp = -(k0v * kappa + 2.0 * k1v * ri) * kappa * ri;
-                        const double dn_s = fma(dx, S.z, dy * S.w);
-                        const double nn = fma(tnx, S.z, tny * S.w);
-                        const double dn_t = fma(dx, tnx, dy * tny);
-                        acc += g * nn + gp * dn_s * dn_t * ri;
-                    }
-                }
-            } else {
-                float a0 = 0.0f, a1 = 0.0f;
-                const float tnxf = (float)tnx, tnyf = (float)tny;
-                for (int q = 0; q < cnt; ++q) {
-                    const float4 S = srcf[q];
-                    const float dx = TX - S.x, dy = TY - S.y;
-                    const float r2 = fmaf(dx, dx, dy * dy);
-                    const float ri = rsqrtf(r2);
-                    const float z = r2 * ri * kappaf;
-                    const float t = 2.0f * rhof * ri;
-                    if (!GRAD) {
-                        const float k1v = k1f(z, t);
-                        const float v = k1v * ri * kappaf * fmaf(dx, S.z, dy * S.w);
-                        if (q & 1) a1 += v; else a0 += v;
-                    } else {
-                        float k0v, k1v;
-                        k01f(z, t, k0v, k1v);
-                        const float g = k1v * ri * kappaf;
-                        const float gp = -(k0v * kappaf + 2.0f * k1v * ri) * kappaf * ri;
-                        const float dn_s = fmaf(dx, S.z, dy * S.w);
-                        const float nn = fmaf(tnxf, S.z, tnyf * S.w);
-                        const float dn_t = fmaf(dx, tnxf, dy * tnyf);
-                        const float v = g * nn + gp * dn_s * dn_t * ri;
-                        if (q & 1) a1 += v; else a0 += v;
-                    }
-                }
-                acc += (double)(a0 + a1);
+            float a0 = 0.0f, a1 = 0.0f;
+            const bool use0 = !(MASK && T0.skip), use1 = !(MASK && T1.skip);
+            for (int q = 0; q < cnt; ++q) {
+                const float4 S = src[q];
+                const int pq = (jb + q) / G.ngl;
+                if (use0 && !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+                    a0 += PairF32::grad(T0.TX - S.x, T0.TY - S.y, nx0, ny0, S.z, S.w, kappa, rho);
+                if (use1 && !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+                    a1 += PairF32::grad(T1.TX - S.x, T1.TY - S.y, nx1, ny1, S.z, S.w, kappa, rho);
             }
+            acc0 += (double)a0;
+            acc1 += (double)a1;
         }
     }
-    if (active) partial[blockIdx.y * G.n + i] = acc * (1.0 / (2.0 * PI));
+    const double sc = 1.0 / (2.0 * PI);
+    if (act0) partial[blockIdx.y * G.n + i0] = acc0 * sc;
+    if (act1) partial[blockIdx.y * G.n + i1] = acc1 * sc;
 }
 
-// y_i = sum_chunks partial[c][i] + sum_near C[shape][local i][c] sigma[near c]
+// ---------------------------------------------------------------------------
+// FP64 pair tiles. Value: k = K1(z)/r; the (i <- j) term is k (d . g_j) and
+// the (j <- i) term is -k (d . g_i), with g = w sigma nu and d = x_i - x_j.
+// Gradient: G_ij = g (nu_i . nu_j) + g' (d . nu_j)(d . nu_i)/r is symmetric;
+// the terms are G_ij (w sigma)_j and G_ij (w sigma)_i.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const double* __restrict__ sigma,
+                                                           const int2* __restrict__ tiles, int ntiles,
+                                                           double* __restrict__ out) {
+    __shared__ d4 srcQ[STILE];         // x, y, and (value) g = w sigma nu | (grad) nu
+    __shared__ double wsQ[STILE];      // (grad) w sigma
+    __shared__ double ys[STILE];       // Q-side sums for the staged chunk
+    const double rho = G.rho, kappa = 1.0 / rho, two_rho = 2.0 * rho;
+    const double scale = GRAD ? 1.0 / (2.0 * PI) : 1.0 / (2.0 * PI * rho);
+    const int lane = threadIdx.x & 31;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int P = tiles[t].x, Q = tiles[t].y;
+        const bool own = (P == Q);
+        for (int ib = 0; ib < G.npp; ib += TILE_TPB) {
+            const int li = ib + threadIdx.x;
+            const bool act = li < G.npp;
+            const int64_t i = (int64_t)P * G.npp + (act ? li : 0);
+            const double tx = G.x[i], ty = G.y[i];
+            const double tnx = G.nx[i], tny = G.ny[i];
+            const double tws = act ? G.w[i] * sigma[i] : 0.0;
+            const int tpan = (act ? li : 0) / G.ngl;
+            double acc = 0.0;
+            for (int jb = 0; jb < G.npp; jb += STILE) {
+                const int cnt = min(STILE, G.npp - jb);
+                __syncthreads();
+                if (threadIdx.x < cnt) {
+                    const int64_t j = (int64_t)Q * G.npp + jb + threadIdx.x;
+                    const double ws = G.w[j] * sigma[j];
+                    if (GRAD) {
+                        srcQ[threadIdx.x] = make_d4(G.x[j], G.y[j], G.nx[j], G.ny[j]);
+                        wsQ[threadIdx.x] = ws;
+                    } else {
+                        srcQ[threadIdx.x] = make_d4(G.x[j], G.y[j], ws * G.nx[j], ws * G.ny[j]);
+                    }
+                    ys[threadIdx.x] = 0.0;
+                }
+                __syncthreads();
+                for (int q = 0; q < cnt; ++q) {
+                    double ki = 0.0, kj = 0.0;
+                    const bool skip = own && is_near_panel(tpan, (jb + q) / G.ngl, G.npan, G.near_w);
+                    if (act && !skip) {
+                        const d4 S = srcQ[q];
+                        const double dx = tx - S.x, dy = ty - S.y;
+                        const double r2 = fma(dx, dx, dy * dy);
+                        const double ri = rsqrt(r2);
+                        const double z = r2 * ri * kappa;
+                        if (!GRAD) {
+                            double k1v;
+                            if (z <= 2.0) k1v = k1_series(z);
+                            else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
+                            const double k = k1v * ri;
+                            ki = k * fma(dx, S.z, dy * S.w);
+                            kj = -k * fma(dx, tnx * tws, dy * (tny * tws));
+                        } else {
+                            double k0v, k1v;
+                            k01(z, k0v, k1v);
+                            const double gg = k1v * ri * kappa;
+                            const double gp = -(k0v * kappa + 2.0 * k1v * ri) * kappa * ri;
+                            const double nn = fma(tnx, S.z, tny * S.w);
+                            const double dn_s = fma(dx, S.z, dy * S.w);
+                            const double dn_t = fma(dx, tnx, dy * tny);
+                            const double Gij = fma(gg, nn, gp * dn_s * dn_t * ri);
+                            ki = Gij * wsQ[q];
+                            kj = Gij * tws;
+                        }
+                    }
+                    acc += ki;
+                    if (!own) {   // tile-uniform: the whole block takes this branch
+                        const double v = warp_sum(kj);
+                        if (lane == 0 && v != 0.0) atomicAdd(&ys[q], v);
+                    }
+                }
+                if (!own) {
+                    __syncthreads();
+                    if (threadIdx.x < cnt)
+                        atomicAdd(&out[(int64_t)Q * G.npp + jb + threadIdx.x], ys[threadIdx.x] * scale);
+                }
+            }
+            if (act) atomicAdd(&out[i], acc * scale);
+        }
+    }
+}
+
+// List the particle pairs (P <= Q) with pair_in_tiles(P, Q, thr). Writes up
+// to cap entries; *count receives the total.
+__global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, int* count,
+                            int2* __restrict__ out, int cap) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= np) return;
+    const d4 a = part[P];
+    for (int Q = P; Q < np; ++Q) {
+        if (Q == P || pair_in_tiles(a, part[Q], thr)) {
+            const int k = atomicAdd(count, 1);
+            if (k < cap) out[k] = make_int2(P, Q);
+        }
+    }
+}
+
+// y_i = sum_chunks partial[c][i] + extra_i + sum_near C[shape][local i][c] sigma[near c]
 __global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ partial,
-                           const double* __restrict__ rows, const double* __restrict__ sigma,
-                           double* __restrict__ y) {
+                           const double* __restrict__ extra, const double* __restrict__ rows,
+                           const double* __restrict__ sigma, double* __restrict__ y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= G.n) return;
-    double acc = 0.0;
+    double acc = extra ? extra[i] : 0.0;
     for (int c = 0; c < nchunk; ++c) acc += partial[c * G.n + i];
     const int p = (int)(i / G.npp);
     const int li = (int)(i % G.npp);
@@ -371,7 +413,7 @@ __global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ pa
 __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __restrict__ sigma,
                                                    const double* __restrict__ tgt, int64_t nt,
                                                    int ppc, double* __restrict__ partial) {
-    __shared__ yk::d4 src[STILE];
+    __shared__ d4 src[STILE];
     const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
     const bool active = i < nt;
     const double tx = active ? tgt[2 * i] : 0.0, ty = active ? tgt[2 * i + 1] : 0.0;
@@ -392,7 +434,7 @@ __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __r
             __syncthreads();
             if (!active) continue;
             for (int q = 0; q < cnt; ++q) {
-                const yk::d4 S = src[q];
+                const d4 S = src[q];
                 const double dx = tx - S.x, dy = ty - S.y;
                 const double r2 = fma(dx, dx, dy * dy);
                 const double ri = rsqrt(r2);
@@ -417,30 +459,72 @@ __global__ void k_sum_chunks(int64_t n, int nchunk, const double* __restrict__ p
 }
 
 // ---------------------------------------------------------------------------
-static int chunking(const yk_geom* g, int* ppc) {
-    const int nct = ceil_div(g->n, TPB);
-    int nchunk = g->ws.nchunk;
-    *ppc = ceil_div(g->np, nchunk);
-    (void)nct;
-    return ceil_div(g->np, *ppc);
+
+// The FP64 tile list for a split distance (kind 0: residual, 1: gradient,
+// 2: all pairs), built on first use and after the particles move.
+static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
+    PairList& L = g->lists[kind];
+    if (!L.valid) {
+        cudaStream_t st = g->ctx->stream;
+        const double thr = kind == 0 ? g->split_gap : (kind == 1 ? g->split_gap_grad : INFINITY);
+        int* d_count = g->d_counter;
+        YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
+        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr, d_count,
+                  (int2*)nullptr, 0);
+        int n = 0;
+        YK_TRY_CUDA(cudaMemcpyAsync(&n, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        YK_TRY_CUDA(cudaStreamSynchronize(st));
+        if (n > L.cap) {
+            dev_free(L.d);
+            L.d = nullptr;
+            L.cap = 0;
+            YK_TRY(dev_alloc((void**)&L.d, sizeof(int2) * (size_t)n));
+            L.cap = n;
+        }
+        YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
+        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr, d_count,
+                  L.d, L.cap);
+        YK_TRY_CUDA(cudaGetLastError());
+        L.n = n;
+        L.valid = true;
+    }
+    *list = L.d;
+    *count = L.n;
+    return YK_OK;
 }
+
+static int tiles_grid(int ntiles) { return std::max(1, std::min(ntiles, 152 * 16)); }
 
 int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
-    int ppc;
-    const int nchunk = chunking(g, &ppc);
+    const int nchunk = g->ws.nchunk;
+    const int ppc = ceil_div(g->np, nchunk);
     dim3 grid(ceil_div(g->n, TPB), nchunk);
-    if (prec == Prec::F64) {
-        YK_LAUNCH(k_p2p_f64<false>, grid, TPB, 0, st, G, sigma, ppc, g->ws.partial);
-    } else if (prec == Prec::F32) {
-        // PairF32 returns K1(z) (d . g)/r / sqrt(log2 e) in scaled units
-        const double ks = sqrt(1.4426950408889634) / (2.0 * PI * g->prm.rho);
-        YK_LAUNCH(k_p2p_f32, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks, g->ws.partial);
+    const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);   // units of PairF32
+    double* extra = nullptr;
+    int used_chunks = nchunk;
+    if (prec == Prec::F32) {
+        YK_LAUNCH(k_p2p_f32<false>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks, 0.0,
+                  g->ws.partial);
     } else {
-        YK_LAUNCH(k_p2p_split<false>, grid, TPB, 0, st, G, sigma, ppc, g->split_gap, g->ws.partial);
+        const int kind = (prec == Prec::F64) ? 2 : 0;
+        const int2* list;
+        int ntiles;
+        YK_TRY(tile_list(g, kind, &list, &ntiles));
+        extra = g->ws.vec[5];
+        YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
+        if (prec == Prec::SPLIT) {
+            YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks,
+                      g->split_gap, g->ws.partial);
+        } else {
+            used_chunks = 0;
+        }
+        YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
+                  extra);
     }
-    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, nchunk, g->ws.partial, G.cval, sigma, y);
+    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used_chunks, g->ws.partial, extra,
+              G.cval, sigma, y);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }
@@ -448,16 +532,24 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
-    int ppc;
-    const int nchunk = chunking(g, &ppc);
+    const int nchunk = g->ws.nchunk;
+    const int ppc = ceil_div(g->np, nchunk);
     dim3 grid(ceil_div(g->n, TPB), nchunk);
-    if (prec == Prec::F64) {
-        YK_LAUNCH(k_p2p_f64<true>, grid, TPB, 0, st, G, sigma, ppc, g->ws.partial);
-    } else {
-        YK_LAUNCH(k_p2p_split<true>, grid, TPB, 0, st, G, sigma, ppc, g->split_gap_grad,
+    const int kind = (prec == Prec::F64) ? 2 : 1;
+    const int2* list;
+    int ntiles;
+    YK_TRY(tile_list(g, kind, &list, &ntiles));
+    double* extra = g->ws.vec[5];
+    YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
+    int used_chunks = 0;
+    if (prec != Prec::F64) {
+        YK_LAUNCH(k_p2p_f32_grad<true>, grid, F32_TPB, 0, st, G, sigma, ppc, g->split_gap_grad,
                   g->ws.partial);
+        used_chunks = nchunk;
     }
-    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, nchunk, g->ws.partial, G.cgrad, sigma, un);
+    YK_LAUNCH(k_tiles_f64<true>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles, extra);
+    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used_chunks, g->ws.partial, extra,
+              G.cgrad, sigma, un);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

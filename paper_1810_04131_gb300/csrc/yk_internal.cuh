@@ -62,6 +62,8 @@ struct GeomView {
     double rho;
     // per particle
     const yk::d4* part;   // (cx, cy, bounding radius, perimeter)
+    const float4* c32;    // centre as FP32 hi/lo pairs (hx, hy, lx, ly)
+    const float* r32;     // bounding radius, FP32
     const int* shape_of;   // index of the particle's shape block
     // per node
     const double* x;
@@ -94,6 +96,14 @@ struct Workspace {
     int dot_blocks = 0;
 };
 
+// Particle pairs (P <= Q) evaluated by the FP64 tiles.
+struct PairList {
+    int2* d = nullptr;
+    int n = 0;
+    int cap = 0;
+    bool valid = false;
+};
+
 }  // namespace yk
 
 struct yk_ctx {
@@ -115,6 +125,10 @@ struct yk_geom {
     double split_gap_grad = 0.0;           // the same for the normal derivative
     // device allocations
     yk::d4* d_part = nullptr;
+    float4* d_c32 = nullptr;
+    float* d_r32 = nullptr;
+    int* d_counter = nullptr;
+    yk::PairList lists[3];                 // residual split, gradient split, all pairs
     int* d_shape_of = nullptr;
     double2* d_shape_ab = nullptr;
     double* d_x = nullptr;

@@ -54,6 +54,8 @@ SMALL = {
     "ellipses4_gl11": lambda: W.small_system(4, 22, shape=W.SHAPE_ELLIPSE, n_panels=12, n_gl=11,
                                              rho=1.3, qbx_order=9, A=1.0, B=0.5, gap=0.3),
     "disks2_allnear": lambda: W.small_system(2, 23, n_panels=3, n_gl=16, rho=0.5, qbx_order=8),
+    # 320 nodes per particle: several 256-node chunks per particle pair
+    "disks3_npp320": lambda: W.small_system(3, 24, n_panels=20, n_gl=16, rho=0.6, qbx_order=10),
     "single_disk": lambda: W.Workload("single", np.array([[0, 0.3, -0.2, 0.4, 1.0, 1.0]]),
                                       rho=4.0, n_panels=16, n_gl=16, qbx_order=10),
 }
@@ -247,6 +249,10 @@ def test_full_size_matvec_sampled(yk, ctx, big):
     assert rel(y32[rows], ref) < 1e-6
     # whole-vector agreement of the two precisions (any size)
     assert rel(y32, y64) < 1e-6
+    # the precision-split normal derivative against the FP64 one (any size)
+    u64 = g.yk_normal_derivative(sig, yk.YK_FP64)
+    usp = g.yk_normal_derivative(sig, yk.YK_MIXED)
+    assert rel(usp, u64) < 1e-11
 
 
 def test_full_size_mixed_solve_properties(yk, ctx, big):
