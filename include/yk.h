@@ -108,7 +108,10 @@ typedef struct {
     int32_t farfield;      /* YK_FARFIELD_DENSE                                */
     double split_tol;      /* YK_MIXED refinement residual: a source particle is
                               evaluated in FP32 only where its FP32 error bound
-                              is below split_tol * max|sigma|; default 1e-15   */
+                              is below split_tol * max|sigma|; default 1e-14.
+                              The bounds decay like exp(-gap/rho), so their sum
+                              over all FP32 particles is a small multiple of
+                              one bound (about 2x at 4% area fraction)       */
     double grad_split_tol; /* the same bound for the normal derivative that
                               feeds the forces (YK_MIXED); default 1e-13       */
 } yk_params;
@@ -131,6 +134,8 @@ int yk_default_params(yk_params* p);
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream). The
  * stream is borrowed, not owned. Errors: YK_ERR_ARG, YK_ERR_CUDA.        */
 int yk_create(yk_ctx** ctx, int device, void* cuda_stream);
+/* Destroy a context, and with it every geometry made from it that is still
+ * alive and every pending serving request; their handles become invalid. */
 int yk_destroy(yk_ctx* ctx);
 
 /* ---- geometry (Section 2.1; Section 5: discretisation and QBX set-up) ----- */

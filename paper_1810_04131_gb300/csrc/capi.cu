@@ -183,7 +183,7 @@ int yk_default_params(yk_params* p) {
     p->inner_tol = 1e-6;
     p->max_refine = 8;
     p->farfield = YK_FARFIELD_DENSE;
-    p->split_tol = 1e-15;
+    p->split_tol = 1e-14;
     p->grad_split_tol = 1e-13;
     return YK_OK;
 }
@@ -221,12 +221,14 @@ int yk_create(yk_ctx** ctx, int device, void* cuda_stream) {
 int yk_destroy(yk_ctx* ctx) {
     if (!ctx) return YK_ERR_ARG;
     destroy_server(ctx);
+    while (!ctx->geoms.empty()) yk_destroy_geometry(*ctx->geoms.begin());
     delete ctx;
     return YK_OK;
 }
 
 int yk_destroy_geometry(yk_geom* g) {
     if (!g) return YK_ERR_ARG;
+    g->ctx->geoms.erase(g);
     cudaSetDevice(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
     free_workspace(g);
@@ -360,6 +362,7 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
         }
     }
     if (rc == YK_OK) rc = build_geometry(g);
+    ctx->geoms.insert(g);
     if (rc != YK_OK) {
         yk_destroy_geometry(g);
         return rc;

@@ -109,6 +109,33 @@ def main():
         err = check(nu, c, a, b, 2e-7, np.float32)
         out.append("// nu=%d, t in [%g, %g], degree %d, max rel. error %.2e (FP32 Horner)" % (nu, a, b, deg, err))
         out.append(arr(name, c, "float", "f"))
+    # FP32 far field in scaled coordinates: with z' = z log2(e) and rz = 1/z',
+    # t = 2/z = 2 log2(e) rz. P1 as a monomial in rz directly (no affine step):
+    # convert the Chebyshev fit to monomials in t on [0, 1], then scale.
+    for deg in (6, 7):
+        c = fit(1, deg, 0.0, 1.0)                      # monomial in s = 2t - 1
+        t_mono = [0.0] * (deg + 1)                     # expand in t: s = 2t - 1
+        from math import comb
+        for k, ck in enumerate(c):
+            for j in range(k + 1):
+                t_mono[j] += ck * comb(k, j) * (2.0 ** j) * ((-1.0) ** (k - j))
+        a = 2.0 * float(mp.log(2) ** -1)               # 2 log2(e)
+        rz_mono = [v * a ** j for j, v in enumerate(t_mono)]
+        worst = 0.0
+        for t in np.linspace(1e-6, 1.0, 800):
+            rz = np.float32(t / a)
+            acc = np.float32(rz_mono[-1])
+            for cf in reversed(rz_mono[:-1]):
+                acc = np.float32(acc * rz + np.float32(cf))
+            worst = max(worst, abs(float(acc) / float(p_nu(1, t)) - 1))
+        if deg == 6 and worst > 1.5e-7:
+            continue
+        if worst > 2e-7:
+            sys.exit("rz-monomial fit error %.3e" % worst)
+        out.append("// nu=1 in rz = 1/z' (z' = z log2 e), t = 2 log2(e) rz in [0, 1], degree %d, "
+                   "max rel. error %.2e (FP32 Horner)" % (deg, worst))
+        out.append(arr("YK_P1_F32_RZ", rz_mono, "float", "f"))
+        break
     kmax = 14
     i0, i1, k0, k1 = series_tables(kmax)
     out.append("// ascending series (DLMF 10.25.2, 10.31.1) in q = z^2/4, k = 0..%d" % kmax)

@@ -144,11 +144,46 @@ __device__ __forceinline__ void target_setup(TargetF32& T, const GeomView& G, in
     T.pan = pan;
 }
 
+// Packed FP32 evaluation of two far pairs at once (one target, two sources)
+// with the f32x2 FMA/ADD/MUL instructions of sm_100+: lanes .x/.y are the
+// two sources. Sources are staged as pairs: A = (-X0, -X1, -Y0, -Y1) in
+// scaled coordinates, B = (gx0, gx1, gy0, gy1). Returns the two terms in the
+// units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))), z > 2 only.
+struct PolyRZ {
+    float2 c[7];
+    __device__ __forceinline__ PolyRZ() {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) c[k] = make_float2(YK_P1_F32_RZ[k], YK_P1_F32_RZ[k]);
+    }
+};
+
+__device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, const float4& B,
+                                       const PolyRZ& P) {
+    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
+    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
+    const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
+    const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));   // 1/z'
+    const float2 zp = __fmul2_rn(z2, rz);                                 // z'
+    float2 p = P.c[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) p = __ffma2_rn(p, rz, P.c[k]);          // P1 in rz
+    const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
+    const float2 sq = make_float2(rsqrt_fast(zp.x), rsqrt_fast(zp.y));   // z'^{-1/2}
+    const float2 dot = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
+    return __fmul2_rn(__fmul2_rn(__fmul2_rn(e, p), sq), __fmul2_rn(rz, dot));
+}
+
+// Scalar view of source q in the pair-packed staging.
+__device__ __forceinline__ float4 src_scalar(const float4* A, const float4* B, int q) {
+    const float4 a = A[q >> 1], b = B[q >> 1];
+    return (q & 1) ? make_float4(-a.y, -a.w, b.y, b.w) : make_float4(-a.x, -a.z, b.x, b.z);
+}
+
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
                                                      int ppc, float kscale, double skip_gap,
                                                      double* __restrict__ partial) {
-    __shared__ float4 src[STILE];
+    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
     const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
     const int64_t i1 = i0 + F32_TPB;
     const bool act0 = i0 < G.n, act1 = i1 < G.n;
@@ -160,6 +195,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;  // z <= 2 possible below
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
+    const PolyRZ P;
     double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
         const int64_t base = (int64_t)s * G.npp;
@@ -172,45 +208,59 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
         if (block_skip) continue;
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
+            const int npair = (cnt + 1) >> 1;
             __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += F32_TPB) {
-                const int64_t j = base + jb + q;
-                const float2 xs = G.xi[j];
-                const double ws = G.w[j] * sigma[j];
-                src[q] = make_float4(kpf * xs.x, kpf * xs.y, (float)(ws * G.nx[j]),
-                                     (float)(ws * G.ny[j]));
+            for (int m = threadIdx.x; m < npair; m += F32_TPB) {
+                float xs[2], ys[2], gx[2], gy[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = 2 * m + h;
+                    if (q < cnt) {
+                        const int64_t j = base + jb + q;
+                        const float2 x = G.xi[j];
+                        const double ws = G.w[j] * sigma[j];
+                        xs[h] = -kpf * x.x;
+                        ys[h] = -kpf * x.y;
+                        gx[h] = (float)(ws * G.nx[j]);
+                        gy[h] = (float)(ws * G.ny[j]);
+                    } else {       // padding: a far, weightless source
+                        xs[h] = 1.0e6f;
+                        ys[h] = 0.0f;
+                        gx[h] = 0.0f;
+                        gy[h] = 0.0f;
+                    }
+                }
+                srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
+                srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
             }
             __syncthreads();
-            float a0 = 0.0f, b0 = 0.0f, a1 = 0.0f, b1 = 0.0f;
+            float r0 = 0.0f, r1 = 0.0f;
             if (!T0.close && !T1.close && !(MASK && (T0.skip || T1.skip))) {
-                int q = 0;
+                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
+                float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
 #pragma unroll 2
-                for (; q + 2 <= cnt; q += 2) {
-                    const float4 S = src[q], U = src[q + 1];
-                    a0 += PairF32::far(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
-                    a1 += PairF32::far(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
-                    b0 += PairF32::far(T0.TX - U.x, T0.TY - U.y, U.z, U.w);
-                    b1 += PairF32::far(T1.TX - U.x, T1.TY - U.y, U.z, U.w);
+                for (int m = 0; m < npair; ++m) {
+                    const float4 A = srcA[m], B = srcB[m];
+                    a0 = __fadd2_rn(a0, far2(TX0, TY0, A, B, P));
+                    a1 = __fadd2_rn(a1, far2(TX1, TY1, A, B, P));
                 }
-                if (q < cnt) {
-                    const float4 S = src[q];
-                    a0 += PairF32::far(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
-                    a1 += PairF32::far(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
-                }
+                r0 = a0.x + a0.y;
+                r1 = a1.x + a1.y;
             } else {
                 for (int q = 0; q < cnt; ++q) {
-                    const float4 S = src[q];
+                    const float4 S = src_scalar(srcA, srcB, q);
                     const int pq = (jb + q) / G.ngl;
                     if (!(MASK && T0.skip) &&
                         !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
-                        a0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
+                        r0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
                     if (!(MASK && T1.skip) &&
                         !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
-                        a1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
+                        r1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
                 }
             }
-            acc0 += (double)(a0 + b0);
-            acc1 += (double)(a1 + b1);
+            acc0 += (double)r0;
+            acc1 += (double)r1;
         }
     }
     if (act0) partial[blockIdx.y * G.n + i0] = acc0 * (double)kscale;

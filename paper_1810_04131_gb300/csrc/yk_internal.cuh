@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <set>
 #include <vector>
 
 #include "../../include/yk.h"
@@ -110,6 +111,7 @@ struct yk_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     void* server = nullptr;  // serving state (serve.cu)
+    std::set<yk_geom*> geoms;  // live geometries made from this context
 };
 
 struct yk_geom {

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -186,9 +187,12 @@ class Context:
         h = C.c_void_p()
         _check(lib.yk_create(C.byref(h), int(device), stream), "yk_create")
         self.h = h
+        self.geoms = weakref.WeakSet()
 
     def close(self):
         if self.h:
+            for g in list(self.geoms):   # the C call releases them; drop the handles first
+                g.h = None
             load().yk_destroy(self.h)
             self.h = None
 
@@ -235,6 +239,7 @@ class Geometry:
         _check(lib.yk_create_geometry(ctx.h, arr, len(arr), C.byref(params), C.byref(h)),
                "yk_create_geometry")
         self.h = h
+        ctx.geoms.add(self)
         n = C.c_int64()
         _check(lib.yk_num_nodes(h, C.byref(n)), "yk_num_nodes")
         self.n = n.value

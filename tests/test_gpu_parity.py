@@ -167,7 +167,8 @@ def test_device_pointers_match_host(yk, ctx):
     yd = torch.zeros(g.n, dtype=torch.float64, device="cuda")
     g.yk_matvec(sd, yk.YK_FP64, out=yd)
     torch.cuda.synchronize()
-    assert np.array_equal(yd.cpu().numpy(), y_h)
+    # the FP64 tiles accumulate with atomics, so the summation order varies
+    assert rel(yd.cpu().numpy(), y_h) < 1e-15
 
 
 def test_errors_and_edge_cases(yk, ctx):
