@@ -50,6 +50,7 @@ extern "C" {
 #define YK_ERR_CUDA           -6  /* a CUDA runtime call failed               */
 #define YK_ERR_NOT_FOUND      -7  /* unknown request id                       */
 #define YK_ERR_BUSY           -8  /* serving queue full                        */
+#define YK_ERR_TOO_LARGE      -9  /* request exceeds a fixed, preallocated limit */
 
 /* ---- enumerations --------------------------------------------------------- */
 #define YK_SHAPE_DISK     0
@@ -207,6 +208,26 @@ int yk_forces_torques(yk_geom* g, const double* sigma, const double* f,
  * length from every boundary for full accuracy. u has length nt.          */
 int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets,
                       int64_t nt, double* u);
+
+/* Allocation-free variant of yk_eval_potential. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they evaluate the potential (inside a CUDA stream
+ * capture, in real-time loops that must not touch the allocator, or under a
+ * fixed memory budget). It computes the same u = D[sigma] at nt off-surface
+ * targets but keeps its partial sums in a fixed 8 MiB device array inside
+ * the library (one per GPU, held until the process exits) instead of
+ * allocating them, and makes no allocation of any kind.
+ *   - sigma (N), targets (nt x 2) and u (nt) must be device pointers
+ *     (YK_ERR_ARG otherwise: staging host arrays would allocate).
+ *   - nt <= 1,048,576 (2^20); larger requests return YK_ERR_TOO_LARGE.
+ *   - The first call on each device looks up the array's device address;
+ *     make that first call before any stream capture begins.
+ *   - All calls share the array. Calls whose kernels overlap on the GPU (two
+ *     streams, or two contexts on one device) race on it: order them.
+ *   - The call enqueues its work on the context's stream and returns without
+ *     synchronising it.                                                      */
+int yk_eval_potential_noalloc(yk_geom* g, const double* sigma, const double* targets,
+                              int64_t nt, double* u);
 
 /* Convenience: label + solve + forces for one configuration. */
 int yk_solve_forces(yk_geom* g, const double* f, double* sigma, double* F,

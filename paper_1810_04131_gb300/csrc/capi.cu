@@ -199,6 +199,8 @@ const char* yk_strerror(int code) {
         case YK_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA runtime error";
         case YK_ERR_NOT_FOUND: return "unknown request id";
         case YK_ERR_BUSY: return "serving queue full";
+        case YK_ERR_TOO_LARGE:
+            return "request exceeds the fixed scratch of the allocation-free entry point";
         default: return "unknown error code";
     }
 }
@@ -520,6 +522,16 @@ int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets, in
     YK_TRY(potential(g, a.d(), t.d(), nt, o.d()));
     YK_TRY(o.finish());
     return sync(g);
+}
+
+int yk_eval_potential_noalloc(yk_geom* g, const double* sigma, const double* targets,
+                              int64_t nt, double* u) {
+    if (!g || !sigma || nt < 0 || (nt > 0 && (!targets || !u))) return YK_ERR_ARG;
+    if (nt == 0) return YK_OK;
+    // device pointers only: staging host arrays would need allocations
+    if (!is_device_ptr(sigma) || !is_device_ptr(targets) || !is_device_ptr(u)) return YK_ERR_ARG;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    return potential_noalloc(g, sigma, targets, nt, u);
 }
 
 int yk_solve_forces(yk_geom* g, const double* f, double* sigma, double* F, double* tau,

@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "bessel.cuh"
 #include "yk_internal.cuh"
@@ -623,4 +624,69 @@ int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt
     return YK_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free off-surface potential (yk_eval_potential_noalloc).
+//
+// yk_eval_potential stages its per-chunk partial sums in a buffer it
+// allocates for each call. Some callers cannot allocate device memory at
+// the point where they evaluate the potential: code running inside a
+// stream capture, where allocation calls are not allowed, real-time loops
+// that must not touch the allocator, or hosts that hand the library a
+// fixed memory budget. For them this variant keeps the scratch in a
+// file-scope device array of STATIC_SCRATCH_DOUBLES doubles (8 MiB), which
+// every GPU that loads the library holds until the process exits.
+//
+// In host code the array's name only stands for the symbol; the kernels
+// receive its device address, looked up once per device with
+// cudaGetSymbolAddress while that device is current. The lookup happens on
+// the first call on each device, so that first call should come before any
+// stream capture begins.
+//
+// All calls share the one array and it keeps the last call's contents.
+// Nothing in it has to start at zero: every partial sum the reduction reads
+// is written by the same call first. Calls whose kernels overlap on the GPU
+// (for example two streams, or two contexts on one device) race on the
+// array; callers must order them.
+// ---------------------------------------------------------------------------
+constexpr int64_t STATIC_SCRATCH_DOUBLES = (int64_t)1 << 20;
+static __device__ __align__(256) double g_static_scratch[STATIC_SCRATCH_DOUBLES];
+
+static std::mutex g_static_scratch_mutex;
+static double* g_static_scratch_ptr[256] = {};   // device address, per device ordinal
+
+static int static_scratch_address(int device, double** out) {
+    if (device < 0 || device >= 256) return YK_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_static_scratch_mutex);
+    if (!g_static_scratch_ptr[device]) {
+        void* ptr = nullptr;
+        // the current device is the context's device (set by the caller)
+        YK_TRY_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_static_scratch_ptr[device] = (double*)ptr;
+    }
+    *out = g_static_scratch_ptr[device];
+    return YK_OK;
+}
+
+int potential_noalloc(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
+                      double* u) {
+    if (nt <= 0) return YK_OK;
+    if (nt > STATIC_SCRATCH_DOUBLES) return YK_ERR_TOO_LARGE;
+    double* scratch = nullptr;
+    YK_TRY(static_scratch_address(g->ctx->device, &scratch));
+    cudaStream_t st = g->ctx->stream;
+    GeomView G = g->view();
+    const int nct = ceil_div(nt, TPB);
+    // as many source chunks as the scratch holds (at least one)
+    const int64_t fit = STATIC_SCRATCH_DOUBLES / nt;
+    int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(g->np, fit),
+                                                             ceil_div(4 * 152, nct)));
+    const int ppc = ceil_div(g->np, nchunk);
+    nchunk = ceil_div(g->np, ppc);
+    dim3 grid(nct, nchunk);
+    YK_LAUNCH(k_potential, grid, TPB, 0, st, G, sigma, targets, nt, ppc, scratch);
+    YK_LAUNCH(k_sum_chunks, ceil_div(nt, 256), 256, 0, st, nt, nchunk, scratch, u);
+    YK_TRY_CUDA(cudaGetLastError());
+    return YK_OK;
+}
 }  // namespace yk

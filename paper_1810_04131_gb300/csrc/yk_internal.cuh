@@ -164,6 +164,8 @@ enum class Prec { F64 = 0, F32 = 1, SPLIT = 2 };
 int matvec(yk_geom* g, const double* sigma, double* y, Prec prec);
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec);
 int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u);
+int potential_noalloc(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
+                      double* u);
 
 // gmres.cu
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0, yk_solve_info* info);

@@ -30,6 +30,7 @@ YK_ERR_TIMEOUT = -5
 YK_ERR_CUDA = -6
 YK_ERR_NOT_FOUND = -7
 YK_ERR_BUSY = -8
+YK_ERR_TOO_LARGE = -9
 
 YK_SHAPE_DISK = 0
 YK_SHAPE_ELLIPSE = 1
@@ -47,6 +48,7 @@ EXPORTS = [
     "yk_default_params", "yk_create", "yk_destroy", "yk_create_geometry",
     "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
     "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_eval_potential",
+    "yk_eval_potential_noalloc",
     "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_strerror",
 ]
 
@@ -110,6 +112,7 @@ def load(path=LIB_PATH):
         "yk_solve": [P, P, P, P, C.POINTER(yk_solve_info)],
         "yk_forces_torques": [P, P, P, P, P, P],
         "yk_eval_potential": [P, P, P, I64, P],
+        "yk_eval_potential_noalloc": [P, P, P, I64, P],
         "yk_solve_forces": [P, P, P, P, P, C.POINTER(yk_solve_info)],
         "yk_submit": [P, C.POINTER(yk_particle), I, C.POINTER(yk_params), I, D,
                       C.POINTER(C.c_uint64)],
@@ -310,6 +313,15 @@ class Geometry:
         out = np.zeros(nt) if out is None else out
         _check(load().yk_eval_potential(self.h, _ptr(sigma), _ptr(t), C.c_int64(nt), _ptr(out)),
                "yk_eval_potential")
+        return out
+
+    def yk_eval_potential_noalloc(self, sigma, targets, out):
+        """Allocation-free potential: sigma, targets (nt x 2) and out must be
+        CUDA tensors; the library uses its fixed scratch, not the allocator."""
+        nt = targets.shape[0]
+        _check(load().yk_eval_potential_noalloc(self.h, _ptr(sigma), _ptr(targets),
+                                                C.c_int64(nt), _ptr(out)),
+               "yk_eval_potential_noalloc")
         return out
 
     def yk_solve_forces(self, f, sigma=None, F=None, tau=None):
