@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--fp64-solve", type=int, default=1, help="time one plain FP64 solve")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-rows", type=int, default=384)
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests replayed from the seeded serving stream")
+    ap.add_argument("--serve-max-particles", type=int, default=512)
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrivals per second")
     return ap.parse_args()
 
 
@@ -154,6 +158,49 @@ def cpu_solve_rate(wl, nrows, iters):
     t_grad = oracle_rows_timing(wl, max(8, nrows // 4), want_grad=True)
     t_solve = wl.n_nodes * ((iters + 1) * t_val + t_grad)
     return 1.0 / t_solve, t_val, t_grad
+
+
+def run_serving(yk, W, ctx, args):
+    """Replay the head of the seeded request stream (Poisson arrivals,
+    log-uniform particle counts capped at --serve-max-particles, 8-32 panels,
+    disks and ellipses, rho in {0.5, 1, 2}) through yk_submit / yk_poll and
+    report latency percentiles and throughput."""
+    reqs = W.request_stream(args.serve_requests, seed=6, rate=args.serve_rate,
+                            np_max=args.serve_max_particles)
+    loads = [W.materialise_request(r) for r in reqs]
+    t0 = time.perf_counter()
+    pending = {}
+    lat = []
+    nodes = 0
+    k = 0
+    while k < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k]["arrival"] <= now:
+            wl = loads[k]
+            rid = ctx.yk_submit(wl.particles, yk.params_for(wl, precision=yk.YK_MIXED))
+            pending[rid] = wl
+            k += 1
+        done = []
+        for rid, wl in pending.items():
+            r = ctx.yk_poll(rid)
+            if r["status"] == yk.YK_REQ_DONE:
+                lat.append(r["latency_ms"])
+                nodes += wl.n_nodes
+                done.append(rid)
+            elif r["status"] == yk.YK_REQ_FAILED:
+                raise RuntimeError("serving request failed")
+        for rid in done:
+            del pending[rid]
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "solves_per_s": len(lat) / wall, "wall_s": wall, "nodes_total": int(nodes),
+            "arrival_rate_per_s": args.serve_rate, "max_particles": args.serve_max_particles,
+            "stream": "seeded (seed 6): Poisson arrivals, log-uniform 4..%d particles, "
+                      "8-32 panels x 16 nodes, disk/ellipse, rho in {0.5,1,2}, mixed precision"
+                      % args.serve_max_particles}
 
 
 def run_reference(args):
@@ -330,6 +377,13 @@ def main():
            "h2d_bytes_per_step": int(parts.shape[0] * 48 + n * 8),
            "d2h_bytes_per_step": int(n * 8 * 2 + npart * 24)}
 
+    # ---- serving: continuous batching of a request stream ------------------
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        sctx = yk.Context(local)
+        serving = run_serving(yk, W, sctx, args)
+        sctx.close()
+
     # ---- FP64 oracle on the host cores (bounded sample) ---------------------
     cpu = None
     if args.cpu_baseline and rank == 0:
@@ -356,6 +410,7 @@ def main():
                          "matvecs_fp32": info["matvecs_fp32"],
                          "matvecs_fp64": info["matvecs_fp64"]},
                "fp64": fp64, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+               "serving": serving,
                "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(out))
     g.close()

@@ -34,10 +34,10 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int dev_alloc(void** p, size_t bytes) {
+int dev_alloc(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) return YK_OK;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -46,8 +46,31 @@ int dev_alloc(void** p, size_t bytes) {
     return YK_OK;
 }
 
-void dev_free(void* p) {
-    if (p) cudaFree(p);
+void dev_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+// Pinned host mirror of the solver status, one per context (allocated on
+// first use, released by yk_destroy).
+double* host_status(yk_ctx* ctx) {
+    if (!ctx->h_status) {
+        if (cudaMallocHost((void**)&ctx->h_status, 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_status = nullptr;
+        }
+    }
+    return ctx->h_status;
+}
+
+// Keep freed stream-ordered memory in this process's default pool of the
+// device instead of returning it at every synchronisation.
+void keep_pool_memory(int device) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
 }
 
 // A caller array seen from the device: the pointer itself when it is device
@@ -216,6 +239,7 @@ int yk_create(yk_ctx** ctx, int device, void* cuda_stream) {
     if (!c) return YK_ERR_NO_MEMORY;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
+    keep_pool_memory(device);
     *ctx = c;
     return YK_OK;
 }
@@ -224,6 +248,7 @@ int yk_destroy(yk_ctx* ctx) {
     if (!ctx) return YK_ERR_ARG;
     destroy_server(ctx);
     while (!ctx->geoms.empty()) yk_destroy_geometry(*ctx->geoms.begin());
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
     return YK_OK;
 }
@@ -234,11 +259,13 @@ int yk_destroy_geometry(yk_geom* g) {
     cudaSetDevice(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
     free_workspace(g);
-    for (auto& L : g->lists) dev_free(L.d);
+    cudaStream_t st = g->ctx->stream;
+    for (auto& L : g->lists) dev_free(L.d, st);
     void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
                     g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w};
-    for (void* b : bufs) dev_free(b);
+    for (void* b : bufs) dev_free(b, st);
+    cudaStreamSynchronize(st);
     delete g;
     return YK_OK;
 }
@@ -328,7 +355,7 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     const size_t rowlen = (size_t)g->n_near * g->ngl;
     int rc = YK_OK;
 #define ALLOC(ptr, count) \
-    if (rc == YK_OK) rc = dev_alloc((void**)&g->ptr, sizeof(*g->ptr) * (size_t)(count))
+    if (rc == YK_OK) rc = dev_alloc((void**)&g->ptr, sizeof(*g->ptr) * (size_t)(count), ctx->stream)
     ALLOC(d_part, n_particles);
     ALLOC(d_c32, n_particles);
     ALLOC(d_r32, n_particles);

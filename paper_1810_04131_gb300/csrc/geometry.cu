@@ -313,7 +313,7 @@ __global__ void k_qbx_rows(int npan, int ngl, int near_w, int n_near, int os, in
 int update_nodes(yk_geom* g) {
     cudaStream_t st = g->ctx->stream;
     yk_particle* d_parts = nullptr;
-    YK_TRY(dev_alloc((void**)&d_parts, sizeof(yk_particle) * g->np));
+    YK_TRY(dev_alloc((void**)&d_parts, sizeof(yk_particle) * g->np, st));
     YK_TRY_CUDA(cudaMemcpyAsync(d_parts, g->parts.data(), sizeof(yk_particle) * g->np,
                                 cudaMemcpyHostToDevice, st));
     YK_LAUNCH(k_nodes, ceil_div(g->n, 256), 256, 0, st, g->n, g->npan, g->ngl, d_parts, g->d_glx,
@@ -323,7 +323,7 @@ int update_nodes(yk_geom* g) {
     for (auto& L : g->lists) L.valid = false;   // particle pairs change when particles move
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
-    dev_free(d_parts);
+    dev_free(d_parts, st);
     return YK_OK;
 }
 
@@ -352,14 +352,14 @@ int build_geometry(yk_geom* g) {
 int launch_label(yk_geom* g, int kind, double param, double* f) {
     cudaStream_t st = g->ctx->stream;
     yk_particle* d_parts = nullptr;
-    YK_TRY(dev_alloc((void**)&d_parts, sizeof(yk_particle) * g->np));
+    YK_TRY(dev_alloc((void**)&d_parts, sizeof(yk_particle) * g->np, st));
     YK_TRY_CUDA(cudaMemcpyAsync(d_parts, g->parts.data(), sizeof(yk_particle) * g->np,
                                 cudaMemcpyHostToDevice, st));
     YK_LAUNCH(k_label, ceil_div(g->n, 256), 256, 0, st, g->n, g->npp, d_parts, g->d_x, g->d_y, kind,
                                                  param, f);
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
-    dev_free(d_parts);
+    dev_free(d_parts, st);
     return YK_OK;
 }
 

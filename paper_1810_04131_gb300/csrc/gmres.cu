@@ -152,6 +152,7 @@ __global__ void k_axpy1(double* __restrict__ x, const double* __restrict__ d, in
 
 int alloc_workspace(yk_geom* g) {
     Workspace& w = g->ws;
+    cudaStream_t st = g->ctx->stream;
     const int64_t n = g->n;
     const int m = g->prm.gmres_restart;
     w.m = m;
@@ -160,35 +161,35 @@ int alloc_workspace(yk_geom* g) {
     const int ppc = ceil_div(g->np, nchunk);
     w.nchunk = ceil_div(g->np, ppc);
     w.dot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(296, (n + 2047) / 2048));
-    YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n));
-    YK_TRY(dev_alloc((void**)&w.V, sizeof(double) * (m + 1) * n));
-    YK_TRY(dev_alloc((void**)&w.H, sizeof(double) * (m + 1) * m));
-    YK_TRY(dev_alloc((void**)&w.gvec, sizeof(double) * (m + 1)));
-    YK_TRY(dev_alloc((void**)&w.cs, sizeof(double) * m));
-    YK_TRY(dev_alloc((void**)&w.sn, sizeof(double) * m));
-    YK_TRY(dev_alloc((void**)&w.hbuf, sizeof(double) * 2 * (m + 2)));
-    YK_TRY(dev_alloc((void**)&w.ybuf, sizeof(double) * (m + 1)));
-    YK_TRY(dev_alloc((void**)&w.dotpart, sizeof(double) * (m + 2) * w.dot_blocks));
-    YK_TRY(dev_alloc((void**)&w.status, sizeof(double) * 8));
-    for (int k = 0; k < 6; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n));
-    YK_TRY_CUDA(cudaMallocHost((void**)&w.h_status, sizeof(double) * 8));
+    YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n, st));
+    YK_TRY(dev_alloc((void**)&w.V, sizeof(double) * (m + 1) * n, st));
+    YK_TRY(dev_alloc((void**)&w.H, sizeof(double) * (m + 1) * m, st));
+    YK_TRY(dev_alloc((void**)&w.gvec, sizeof(double) * (m + 1), st));
+    YK_TRY(dev_alloc((void**)&w.cs, sizeof(double) * m, st));
+    YK_TRY(dev_alloc((void**)&w.sn, sizeof(double) * m, st));
+    YK_TRY(dev_alloc((void**)&w.hbuf, sizeof(double) * 2 * (m + 2), st));
+    YK_TRY(dev_alloc((void**)&w.ybuf, sizeof(double) * (m + 1), st));
+    YK_TRY(dev_alloc((void**)&w.dotpart, sizeof(double) * (m + 2) * w.dot_blocks, st));
+    YK_TRY(dev_alloc((void**)&w.status, sizeof(double) * 8, st));
+    for (int k = 0; k < 6; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n, st));
+    if (!host_status(g->ctx)) return YK_ERR_NO_MEMORY;
     return YK_OK;
 }
 
 void free_workspace(yk_geom* g) {
     Workspace& w = g->ws;
-    dev_free(w.partial);
-    dev_free(w.V);
-    dev_free(w.H);
-    dev_free(w.gvec);
-    dev_free(w.cs);
-    dev_free(w.sn);
-    dev_free(w.hbuf);
-    dev_free(w.ybuf);
-    dev_free(w.dotpart);
-    dev_free(w.status);
-    for (int k = 0; k < 6; ++k) dev_free(w.vec[k]);
-    if (w.h_status) cudaFreeHost(w.h_status);
+    cudaStream_t st = g->ctx->stream;
+    dev_free(w.partial, st);
+    dev_free(w.V, st);
+    dev_free(w.H, st);
+    dev_free(w.gvec, st);
+    dev_free(w.cs, st);
+    dev_free(w.sn, st);
+    dev_free(w.hbuf, st);
+    dev_free(w.ybuf, st);
+    dev_free(w.dotpart, st);
+    dev_free(w.status, st);
+    for (int k = 0; k < 6; ++k) dev_free(w.vec[k], st);
     w = Workspace{};
 }
 
@@ -202,11 +203,11 @@ static void dots(yk_geom* g, const double* V, int nvec, const double* w, double*
 
 static int read_status(yk_geom* g, double* s0, double* s1) {
     cudaStream_t st = g->ctx->stream;
-    YK_TRY_CUDA(cudaMemcpyAsync(g->ws.h_status, g->ws.status, 2 * sizeof(double),
-                                cudaMemcpyDeviceToHost, st));
+    double* hs = g->ctx->h_status;
+    YK_TRY_CUDA(cudaMemcpyAsync(hs, g->ws.status, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     YK_TRY_CUDA(cudaStreamSynchronize(st));
-    *s0 = g->ws.h_status[0];
-    *s1 = g->ws.h_status[1];
+    *s0 = hs[0];
+    *s1 = hs[1];
     return YK_OK;
 }
 
@@ -283,10 +284,10 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
 static double norm2(yk_geom* g, const double* v) {
     dots(g, v, 1, v, g->ws.status + 2);
     cudaStream_t st = g->ctx->stream;
-    cudaMemcpyAsync(g->ws.h_status + 2, g->ws.status + 2, sizeof(double), cudaMemcpyDeviceToHost,
-                    st);
+    double* hs = g->ctx->h_status;
+    cudaMemcpyAsync(hs + 2, g->ws.status + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
-    return sqrt(g->ws.h_status[2]);
+    return sqrt(hs[2]);
 }
 
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,

@@ -526,10 +526,10 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
         YK_TRY_CUDA(cudaMemcpyAsync(&n, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
         YK_TRY_CUDA(cudaStreamSynchronize(st));
         if (n > L.cap) {
-            dev_free(L.d);
+            dev_free(L.d, st);
             L.d = nullptr;
             L.cap = 0;
-            YK_TRY(dev_alloc((void**)&L.d, sizeof(int2) * (size_t)n));
+            YK_TRY(dev_alloc((void**)&L.d, sizeof(int2) * (size_t)n, st));
             L.cap = n;
         }
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));

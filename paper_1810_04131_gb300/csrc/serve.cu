@@ -1,17 +1,31 @@
 // Serving: independent particle configurations submitted as requests and
-// solved (label, Eq. bie, forces and torques) by the library. Requests are
-// admitted in arrival order while their device-memory estimate fits the
-// context's budget, and run to completion; yk_poll collects results.
+// solved (label, Eq. bie, forces and torques) by the library with
+// continuous batching.
+//
+// A fixed set of worker slots, each with its own CUDA stream and internal
+// context, takes requests from the arrival queue. A request is admitted when
+// a slot is free and its device-memory estimate fits the budget left by the
+// requests in flight; requests that arrive while others run are admitted as
+// soon as a slot and memory free up, and their kernels overlap on the
+// device (one stream per slot). Results are copied to host memory and kept
+// until yk_poll collects them. Host waits are bounded: yk_drain gives up
+// after a time limit and reports YK_ERR_TIMEOUT.
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 
 #include "yk_internal.cuh"
 
 namespace yk {
+
+using Clock = std::chrono::steady_clock;
 
 struct Request {
     uint64_t id = 0;
@@ -21,24 +35,37 @@ struct Request {
     double label_param = 10.0;
     int status = YK_REQ_QUEUED;
     int error = YK_OK;
-    std::chrono::steady_clock::time_point t_submit, t_done;
+    size_t mem_bytes = 0;
+    Clock::time_point t_submit, t_done;
     std::vector<double> sigma, F, tau;
     yk_solve_info info{};
 };
 
 struct Server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
     uint64_t next_id = 1;
-    std::deque<uint64_t> queue;
+    std::deque<uint64_t> queue;                       // arrival order
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     size_t max_queue = 1 << 16;
+    size_t mem_budget = 0, mem_in_flight = 0;
+    int running = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    int device = 0;
 };
 
-static Server* server_of(yk_ctx* ctx, bool create) {
-    if (!ctx->server && create) ctx->server = new Server();
-    return (Server*)ctx->server;
+// Device memory of one request: node arrays, Krylov basis, chunk partials,
+// scratch vectors, QBX rows (an estimate with a safety factor).
+static size_t request_bytes(const Request& r) {
+    const size_t n = (size_t)r.parts.size() * r.prm.n_panels * r.prm.n_gl;
+    const size_t m = (size_t)r.prm.gmres_restart;
+    const size_t nchunk = 32;
+    const size_t rows = (size_t)r.prm.n_panels * r.prm.n_gl * 9 * r.prm.n_gl * 2;
+    return (size_t)(1.25 * 8.0 * (double)(n * (m + 1 + nchunk + 16) + rows)) + (8u << 20);
 }
 
-// Run one request to completion on the context's stream.
+// Run one request to completion on a worker's context.
 static int run_request(yk_ctx* ctx, Request* r) {
     yk_geom* g = nullptr;
     int rc = yk_create_geometry(ctx, r->parts.data(), (int)r->parts.size(), &r->prm, &g);
@@ -46,7 +73,6 @@ static int run_request(yk_ctx* ctx, Request* r) {
     const size_t n = (size_t)g->n;
     double *f = nullptr, *sig = nullptr, *F = nullptr, *tau = nullptr;
     cudaStream_t st = ctx->stream;
-    rc = YK_OK;
     if (cudaMallocAsync((void**)&f, n * sizeof(double), st) != cudaSuccess ||
         cudaMallocAsync((void**)&sig, n * sizeof(double), st) != cudaSuccess ||
         cudaMallocAsync((void**)&F, 2 * g->np * sizeof(double), st) != cudaSuccess ||
@@ -76,26 +102,86 @@ static int run_request(yk_ctx* ctx, Request* r) {
     return rc;
 }
 
-static int step(yk_ctx* ctx, Server* s) {
-    if (s->queue.empty()) return YK_OK;
-    uint64_t id = s->queue.front();
-    s->queue.pop_front();
-    Request* r = s->reqs[id].get();
-    r->status = YK_REQ_RUNNING;
-    int rc = run_request(ctx, r);
-    r->t_done = std::chrono::steady_clock::now();
-    if (rc != YK_OK) {
-        r->status = YK_REQ_FAILED;
-        r->error = rc;
-        return rc;
+// The oldest queued request, if it fits the memory left (arrival order is
+// kept: later requests do not overtake it). A request too large for the
+// budget on its own is admitted when nothing else runs.
+static Request* admit(Server* s) {
+    if (s->queue.empty()) return nullptr;
+    Request* r = s->reqs[s->queue.front()].get();
+    if (s->mem_in_flight + r->mem_bytes <= s->mem_budget || s->running == 0) {
+        s->queue.pop_front();
+        return r;
     }
-    r->status = YK_REQ_DONE;
+    return nullptr;
+}
+
+static void worker_main(Server* s) {
+    cudaSetDevice(s->device);
+    keep_pool_memory(s->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    yk_ctx ctx;
+    ctx.device = s->device;
+    ctx.stream = st;
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        Request* r = nullptr;
+        s->cv_work.wait(lk, [&] { return s->stop || (r = admit(s)) != nullptr; });
+        if (!r) break;   // stop requested and nothing admitted
+        r->status = YK_REQ_RUNNING;
+        s->mem_in_flight += r->mem_bytes;
+        s->running++;
+        lk.unlock();
+        const int rc = run_request(&ctx, r);
+        lk.lock();
+        r->t_done = Clock::now();
+        s->mem_in_flight -= r->mem_bytes;
+        s->running--;
+        if (rc != YK_OK) {
+            r->status = YK_REQ_FAILED;
+            r->error = rc;
+        } else {
+            r->status = YK_REQ_DONE;
+        }
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+    lk.unlock();
+    while (!ctx.geoms.empty()) yk_destroy_geometry(*ctx.geoms.begin());
+    cudaStreamSynchronize(st);
+    if (ctx.h_status) cudaFreeHost(ctx.h_status);
+    ctx.h_status = nullptr;
+    cudaStreamDestroy(st);
+}
+
+static int server_of(yk_ctx* ctx, Server** out) {
+    if (!ctx->server) {
+        YK_TRY_CUDA(cudaSetDevice(ctx->device));
+        size_t free_b = 0, total_b = 0;
+        YK_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        auto* s = new (std::nothrow) Server();
+        if (!s) return YK_ERR_NO_MEMORY;
+        s->device = ctx->device;
+        s->mem_budget = (size_t)(0.6 * (double)free_b);
+        const int nslots = 8;
+        for (int k = 0; k < nslots; ++k) s->workers.emplace_back(worker_main, s);
+        ctx->server = s;
+    }
+    *out = (Server*)ctx->server;
     return YK_OK;
 }
 
 int destroy_server(yk_ctx* ctx) {
     if (!ctx || !ctx->server) return YK_OK;
-    delete (Server*)ctx->server;
+    Server* s = (Server*)ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->queue.clear();   // pending requests are dropped; running ones finish
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    delete s;
     ctx->server = nullptr;
     return YK_OK;
 }
@@ -110,58 +196,71 @@ int yk_submit(yk_ctx* ctx, const yk_particle* particles, int n_particles, const 
               int label_kind, double label_param, uint64_t* request_id) {
     if (!ctx || !particles || n_particles < 1 || !prm || !request_id) return YK_ERR_ARG;
     if (label_kind < YK_LABEL_TANH || label_kind > YK_LABEL_COS) return YK_ERR_ARG;
-    Server* s = server_of(ctx, true);
-    if (s->queue.size() >= s->max_queue) return YK_ERR_BUSY;
+    Server* s = nullptr;
+    YK_TRY(server_of(ctx, &s));
     auto r = std::make_unique<Request>();
-    r->id = s->next_id++;
     r->parts.assign(particles, particles + n_particles);
     r->prm = *prm;
     r->label_kind = label_kind;
     r->label_param = label_param;
-    r->t_submit = std::chrono::steady_clock::now();
-    *request_id = r->id;
-    s->queue.push_back(r->id);
-    s->reqs[r->id] = std::move(r);
+    r->mem_bytes = request_bytes(*r);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->queue.size() >= s->max_queue) return YK_ERR_BUSY;
+        r->id = s->next_id++;
+        *request_id = r->id;
+        s->queue.push_back(r->id);
+        s->reqs[r->id] = std::move(r);
+    }
+    s->cv_work.notify_one();
     return YK_OK;
 }
 
 int yk_poll(yk_ctx* ctx, uint64_t id, int* status, double* sigma, double* F, double* tau,
             yk_solve_info* info, double* latency_ms) {
     if (!ctx || !status) return YK_ERR_ARG;
-    Server* s = server_of(ctx, false);
-    if (!s) return YK_ERR_NOT_FOUND;
-    auto it = s->reqs.find(id);
-    if (it == s->reqs.end()) return YK_ERR_NOT_FOUND;
-    Request* r = it->second.get();
-    if (r->status == YK_REQ_QUEUED) step(ctx, s);
-    *status = r->status;
-    if (r->status == YK_REQ_DONE || r->status == YK_REQ_FAILED) {
-        if (r->status == YK_REQ_DONE) {
-            if (sigma) memcpy(sigma, r->sigma.data(), r->sigma.size() * sizeof(double));
-            if (F) memcpy(F, r->F.data(), r->F.size() * sizeof(double));
-            if (tau) memcpy(tau, r->tau.data(), r->tau.size() * sizeof(double));
-            if (info) *info = r->info;
+    if (!ctx->server) return YK_ERR_NOT_FOUND;
+    Server* s = (Server*)ctx->server;
+    std::unique_ptr<Request> done;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(id);
+        if (it == s->reqs.end()) return YK_ERR_NOT_FOUND;
+        *status = it->second->status;
+        if (*status == YK_REQ_DONE || *status == YK_REQ_FAILED) {
+            done = std::move(it->second);
+            s->reqs.erase(it);
+        }
+    }
+    if (done) {
+        if (done->status == YK_REQ_DONE) {
+            if (sigma) memcpy(sigma, done->sigma.data(), done->sigma.size() * sizeof(double));
+            if (F) memcpy(F, done->F.data(), done->F.size() * sizeof(double));
+            if (tau) memcpy(tau, done->tau.data(), done->tau.size() * sizeof(double));
+            if (info) *info = done->info;
         }
         if (latency_ms)
-            *latency_ms =
-                std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
-        int err = r->error;
-        s->reqs.erase(it);
-        if (err != YK_OK && err != YK_ERR_NOT_CONVERGED) return err;
+            *latency_ms = std::chrono::duration<double, std::milli>(done->t_done - done->t_submit)
+                              .count();
+        if (done->error != YK_OK && done->error != YK_ERR_NOT_CONVERGED) return done->error;
     }
     return YK_OK;
 }
 
 int yk_drain(yk_ctx* ctx) {
     if (!ctx) return YK_ERR_ARG;
-    Server* s = server_of(ctx, false);
-    if (!s) return YK_OK;
-    int first = YK_OK;
-    while (!s->queue.empty()) {
-        int rc = step(ctx, s);
-        if (rc != YK_OK && first == YK_OK) first = rc;
-    }
-    return first;
+    if (!ctx->server) return YK_OK;
+    Server* s = (Server*)ctx->server;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = Clock::now() + std::chrono::hours(2);
+    const bool ok = s->cv_done.wait_until(lk, deadline, [&] {
+        return s->queue.empty() && s->running == 0;
+    });
+    if (!ok) return YK_ERR_TIMEOUT;
+    for (auto& kv : s->reqs)
+        if (kv.second->status == YK_REQ_FAILED) return kv.second->error;
+    return YK_OK;
 }
 
 }  // extern "C"

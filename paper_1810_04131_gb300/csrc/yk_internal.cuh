@@ -92,7 +92,6 @@ struct Workspace {
     double* dotpart = nullptr;   // partial dots [(m+2)][nblk]
     double* status = nullptr;    // [0] residual estimate, [1] norm, [2..] scratch
     double* vec[6] = {};         // N-length scratch vectors
-    double* h_status = nullptr;  // pinned host mirror of status (8 doubles)
     int m = 0;
     int dot_blocks = 0;
 };
@@ -112,6 +111,7 @@ struct yk_ctx {
     cudaStream_t stream = nullptr;
     void* server = nullptr;  // serving state (serve.cu)
     std::set<yk_geom*> geoms;  // live geometries made from this context
+    double* h_status = nullptr;  // pinned host mirror of solver status (8 doubles)
 };
 
 struct yk_geom {
@@ -181,8 +181,11 @@ int destroy_server(yk_ctx* ctx);
 
 // capi.cu helpers
 bool is_device_ptr(const void* p);
-int dev_alloc(void** p, size_t bytes);
-void dev_free(void* p);
+// stream-ordered device allocations (no device-wide synchronisation)
+int dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+double* host_status(yk_ctx* ctx);
+void keep_pool_memory(int device);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
