@@ -160,6 +160,20 @@ def cpu_solve_rate(wl, nrows, iters):
     return 1.0 / t_solve, t_val, t_grad
 
 
+def combine_ranks(t_local, steps, world, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank solved
+    `steps` systems; the job took as long as the slowest rank (max over
+    ranks). Returns (t_max, solves per second over all ranks)."""
+    t_max = t_local
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    return t_max, world * steps / t_max
+
+
 def run_serving(yk, W, ctx, args):
     """Replay the head of the seeded request stream (Poisson arrivals,
     log-uniform particle counts capped at --serve-max-particles, 8-32 panels,
@@ -298,15 +312,7 @@ def main():
     torch.cuda.synchronize()
     launches = yk.yk_kernel_launches() - launches0
     clk = clocks.stop()
-    t_local = total_ms / 1e3
-    if dist:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        dist.barrier()
-    else:
-        t_max = t_local
-    value = world * args.steps / t_max
+    t_max, value = combine_ranks(total_ms / 1e3, args.steps, world, dist, dev)
     info = infos[-1]
     sig_mixed = sig.clone()
 
