@@ -60,7 +60,16 @@ extern "C" {
 #define YK_MIXED  1   /* FP32 far-field evaluation with FP64 accumulation inside
                          an FP64 iterative-refinement outer solve              */
 
+#define YK_PRECOND_NONE   0  /* plain GMRES                                   */
+#define YK_PRECOND_BLOCK  1  /* right preconditioning by the inverse of each
+                                particle's self-interaction block (the same
+                                block for all particles of one shape)        */
+
 #define YK_FARFIELD_DENSE  0  /* every far source pair evaluated              */
+#define YK_FARFIELD_CUTOFF 1  /* source particles whose whole contribution is
+                                 bounded below cutoff_tol * max|sigma| are
+                                 left out (cut-off localisation, Section 3.3);
+                                 the K1 kernel decays like exp(-r/rho)        */
 
 /* Dirichlet data generators; theta is the polar angle of x - a_i measured
  * from the director d_i = (cos phi_i, sin phi_i) (Section 2.1).           */
@@ -106,7 +115,7 @@ typedef struct {
     double gmres_tol;      /* relative residual ||f - A sigma|| / ||f||; 1e-10 */
     double inner_tol;      /* YK_MIXED: inner (FP32) GMRES tolerance; 1e-6     */
     int32_t max_refine;    /* YK_MIXED: refinement steps; default 8            */
-    int32_t farfield;      /* YK_FARFIELD_DENSE                                */
+    int32_t farfield;      /* YK_FARFIELD_DENSE or YK_FARFIELD_CUTOFF          */
     double split_tol;      /* YK_MIXED refinement residual: a source particle is
                               evaluated in FP32 only where its FP32 error bound
                               is below split_tol * max|sigma|; default 1e-14.
@@ -115,6 +124,13 @@ typedef struct {
                               one bound (about 2x at 4% area fraction)       */
     double grad_split_tol; /* the same bound for the normal derivative that
                               feeds the forces (YK_MIXED); default 1e-13       */
+    int32_t precond;       /* YK_PRECOND_NONE or YK_PRECOND_BLOCK (needs
+                              n_panels * n_gl <= 1024); default BLOCK        */
+    int32_t pad_;
+    double cutoff_tol;     /* YK_FARFIELD_CUTOFF: a source particle is dropped
+                              for a target particle when its contribution
+                              (value or normal derivative) is bounded below
+                              cutoff_tol * max|sigma|; default 1e-15         */
 } yk_params;
 
 /* Solve statistics (all host memory). */

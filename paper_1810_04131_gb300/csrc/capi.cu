@@ -129,7 +129,10 @@ static int check_params(const yk_params* p) {
     if (p->precision != YK_FP64 && p->precision != YK_MIXED) return YK_ERR_ARG;
     if (!(p->gmres_tol > 0.0) || !(p->inner_tol > 0.0) || p->inner_tol >= 1.0) return YK_ERR_ARG;
     if (p->max_refine < 1) return YK_ERR_ARG;
-    if (p->farfield != YK_FARFIELD_DENSE) return YK_ERR_ARG;
+    if (p->farfield != YK_FARFIELD_DENSE && p->farfield != YK_FARFIELD_CUTOFF) return YK_ERR_ARG;
+    if (!(p->cutoff_tol > 0.0)) return YK_ERR_ARG;
+    if (p->precond != YK_PRECOND_NONE && p->precond != YK_PRECOND_BLOCK) return YK_ERR_ARG;
+    if (p->precond == YK_PRECOND_BLOCK && (int64_t)p->n_panels * p->n_gl > 1024) return YK_ERR_ARG;
     if (!(p->split_tol > 0.0) || !(p->grad_split_tol > 0.0)) return YK_ERR_ARG;
     return YK_OK;
 }
@@ -140,6 +143,24 @@ static int check_params(const yk_params* p) {
 // K1(z) <= sqrt(pi/(2z)) e^{-z} (1 + 1/z), and the FP32 per-pair relative
 // error model eps(z) = 4e-7 (4 + 2 z + 2 R/rho) (fitted K1, exp2 argument
 // rounding, FP32 coordinate rounding at distance ~ g + 2R).
+// Smallest surface gap beyond which a whole source particle's contribution
+// (value or normal derivative) is below tol * max|sigma|:
+// L/(2 pi rho) K1(z) (1 + 2/z) * 2 with the same K1 bound, z = gap/rho.
+static double cutoff_gap(double rho, double perim, double tol) {
+    auto bound = [&](double z) {
+        const double k1ub = sqrt(PI / (2.0 * z)) * exp(-z) * (1.0 + 1.0 / z);
+        return perim / (2.0 * PI * rho) * k1ub * (1.0 + 2.0 / z) * 2.0;
+    };
+    double lo = 0.5, hi = 4000.0;
+    if (bound(hi) > tol) return INFINITY;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (bound(mid) > tol) lo = mid;
+        else hi = mid;
+    }
+    return hi * rho;
+}
+
 static double split_gap(double rho, double perim, double rmax, double tol) {
     auto bound = [&](double z) {
         const double k1ub = sqrt(PI / (2.0 * z)) * exp(-z) * (1.0 + 1.0 / z);
@@ -208,6 +229,8 @@ int yk_default_params(yk_params* p) {
     p->farfield = YK_FARFIELD_DENSE;
     p->split_tol = 1e-14;
     p->grad_split_tol = 1e-13;
+    p->cutoff_tol = 1e-15;
+    p->precond = YK_PRECOND_BLOCK;
     return YK_OK;
 }
 
@@ -261,9 +284,11 @@ int yk_destroy_geometry(yk_geom* g) {
     free_workspace(g);
     cudaStream_t st = g->ctx->stream;
     for (auto& L : g->lists) dev_free(L.d, st);
+    dev_free(g->nbr_off, st);
+    dev_free(g->nbr, st);
     void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
-                    g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w};
+                    g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w, g->d_minv, g->d_minv32};
     for (void* b : bufs) dev_free(b, st);
     cudaStreamSynchronize(st);
     delete g;
@@ -350,6 +375,11 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     g->max_perimeter = perim;
     g->split_gap = split_gap(prm->rho, perim, rmax, prm->split_tol);
     g->split_gap_grad = split_gap(prm->rho, perim, rmax, prm->grad_split_tol);
+    g->cutoff_gap = (prm->farfield == YK_FARFIELD_CUTOFF)
+                        ? cutoff_gap(prm->rho, perim, prm->cutoff_tol) : INFINITY;
+    // the FP64 tiles of the split operators stay inside the cut-off
+    g->split_gap = std::min(g->split_gap, g->cutoff_gap);
+    g->split_gap_grad = std::min(g->split_gap_grad, g->cutoff_gap);
     const int os = prm->oversample;
     const size_t N = (size_t)n;
     const size_t rowlen = (size_t)g->n_near * g->ngl;
@@ -377,6 +407,10 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     ALLOC(d_diff, (size_t)g->ngl * g->ngl);
     ALLOC(d_fine_x, (size_t)os * g->ngl);
     ALLOC(d_fine_w, (size_t)os * g->ngl);
+    if (prm->precond == YK_PRECOND_BLOCK) {
+        ALLOC(d_minv, (size_t)g->nshape * npp * npp);
+        ALLOC(d_minv32, (size_t)g->nshape * npp * npp);
+    }
 #undef ALLOC
     if (rc == YK_OK) rc = alloc_workspace(g);
     if (rc == YK_OK) {

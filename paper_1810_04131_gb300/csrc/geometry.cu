@@ -309,6 +309,171 @@ __global__ void k_qbx_rows(int npan, int ngl, int near_w, int n_near, int os, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Block preconditioner. The self-interaction block of a particle (targets
+// and sources on the same particle: QBX rows for near columns, the plain
+// double-layer kernel otherwise) depends only on its shape, so one block and
+// its inverse serve every particle of that shape. GMRES is right
+// preconditioned by blockdiag(inverse blocks).
+// ---------------------------------------------------------------------------
+__global__ void k_self_block(int npan, int ngl, int near_w, int n_near, double rho,
+                             const double2* shape_ab, const double* glx, const double* glw,
+                             const double* cval, double* A) {
+    const int npp = npan * ngl;
+    const int s = blockIdx.y, i = blockIdx.x;
+    const double a = shape_ab[s].x, b = shape_ab[s].y;
+    const double dt = 2.0 * PI / npan;
+    const int k = i / ngl;
+    double xi, yi, dxi, dyi;
+    curve_point(0.0, 0.0, 1.0, 0.0, a, b, k * dt + 0.5 * dt * (glx[i % ngl] + 1.0), xi, yi, dxi,
+                dyi);
+    const int rowlen = n_near * ngl;
+    const double* row = cval + ((int64_t)s * npp + i) * rowlen;
+    double* out = A + ((int64_t)s * npp + i) * npp;
+    const bool all_near = 2 * near_w + 1 >= npan;
+    for (int j = threadIdx.x; j < npp; j += blockDim.x) {
+        const int kj = j / ngl;
+        int d = ((kj - k) % npan + npan) % npan;
+        const bool near = all_near || d <= near_w || npan - d <= near_w;
+        double v;
+        if (near) {
+            const int q = all_near ? kj : ((kj - k + near_w) % npan + npan) % npan;
+            v = row[q * ngl + (j % ngl)];
+        } else {
+            double x, y, dx, dy;
+            curve_point(0.0, 0.0, 1.0, 0.0, a, b, kj * dt + 0.5 * dt * (glx[j % ngl] + 1.0), x, y,
+                        dx, dy);
+            const double spd = sqrt(dx * dx + dy * dy);
+            const double nx = dy / spd, ny = -dx / spd;
+            const double w = glw[j % ngl] * 0.5 * dt * spd;
+            const double ex = xi - x, ey = yi - y;
+            const double r = sqrt(ex * ex + ey * ey);
+            double k0v, k1v;
+            k01(r / rho, k0v, k1v);
+            v = k1v * (ex * nx + ey * ny) / (2.0 * PI * rho * r) * w;
+        }
+        out[j] = v;
+    }
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting of the n x n block
+// of shape blockIdx.x, on the augmented n x 2n matrix W (one CTA per shape).
+// Writes the inverse transposed (minv[j][i] = inv[i][j]) in FP64 and FP32.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, const double* A, double* W,
+                                                       double* minv, float* minv32) {
+    const int s = blockIdx.x;
+    const double* As = A + (int64_t)s * n * n;
+    double* Ws = W + (int64_t)s * n * 2 * n;
+    const int n2 = 2 * n;
+    extern __shared__ double fac[];            // n factors
+    __shared__ double red_v[32];
+    __shared__ int red_i[32];
+    __shared__ int piv_row;
+    for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
+        const int r = e / n2, c = e % n2;
+        Ws[e] = (c < n) ? As[(int64_t)r * n + c] : (c - n == r ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int c = 0; c < n; ++c) {
+        // pivot: row r >= c with the largest |W[r][c]|
+        double best = -1.0;
+        int bi = c;
+        for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+            const double v = fabs(Ws[(int64_t)r * n2 + c]);
+            if (v > best) best = v, bi = r;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+        }
+        if ((threadIdx.x & 31) == 0) red_v[threadIdx.x >> 5] = best, red_i[threadIdx.x >> 5] = bi;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = -1.0;
+            int b = c;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (red_v[w] > bv) bv = red_v[w], b = red_i[w];
+            piv_row = b;
+        }
+        __syncthreads();
+        const int pr = piv_row;
+        if (pr != c)
+            for (int col = threadIdx.x; col < n2; col += blockDim.x) {
+                const double t = Ws[(int64_t)c * n2 + col];
+                Ws[(int64_t)c * n2 + col] = Ws[(int64_t)pr * n2 + col];
+                Ws[(int64_t)pr * n2 + col] = t;
+            }
+        __syncthreads();
+        const double inv_p = 1.0 / Ws[(int64_t)c * n2 + c];
+        __syncthreads();
+        for (int col = threadIdx.x; col < n2; col += blockDim.x) Ws[(int64_t)c * n2 + col] *= inv_p;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == c) ? 0.0 : Ws[(int64_t)r * n2 + c];
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
+            const int r = e / n2, col = e % n2;
+            if (fac[r] != 0.0) Ws[e] = fma(-fac[r], Ws[(int64_t)c * n2 + col], Ws[e]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double v = Ws[(int64_t)i * n2 + n + j];
+        minv[(int64_t)s * n * n + (int64_t)j * n + i] = v;
+        minv32[(int64_t)s * n * n + (int64_t)j * n + i] = (float)v;
+    }
+}
+
+// y_P = inv(block of P's shape) x_P, one CTA per particle.
+template <typename T>
+__global__ void k_block_apply(int np, int npp, const int* __restrict__ shape_of,
+                              const T* __restrict__ minv, const double* __restrict__ x,
+                              double* __restrict__ y) {
+    extern __shared__ unsigned char smraw[];
+    T* xs = reinterpret_cast<T*>(smraw);
+    const int p = blockIdx.x;
+    const int64_t base = (int64_t)p * npp;
+    for (int j = threadIdx.x; j < npp; j += blockDim.x) xs[j] = (T)x[base + j];
+    __syncthreads();
+    const T* M = minv + (int64_t)shape_of[p] * npp * npp;
+    for (int i = threadIdx.x; i < npp; i += blockDim.x) {
+        T acc = 0;
+        for (int j = 0; j < npp; ++j) acc += M[(int64_t)j * npp + i] * xs[j];
+        y[base + i] = (double)acc;
+    }
+}
+
+int build_preconditioner(yk_geom* g) {
+    if (g->prm.precond != YK_PRECOND_BLOCK) return YK_OK;
+    cudaStream_t st = g->ctx->stream;
+    const int npp = g->npp;
+    const size_t nn = (size_t)npp * npp;
+    double *A = nullptr, *W = nullptr;
+    YK_TRY(dev_alloc((void**)&A, sizeof(double) * nn * g->nshape, st));
+    YK_TRY(dev_alloc((void**)&W, sizeof(double) * 2 * nn * g->nshape, st));
+    dim3 grid(npp, g->nshape);
+    YK_LAUNCH(k_self_block, grid, 128, 0, st, g->npan, g->ngl, g->prm.near_width, g->n_near,
+              g->prm.rho, g->d_shape_ab, g->d_glx, g->d_glw, g->d_cval, A);
+    YK_LAUNCH(k_gauss_jordan, g->nshape, 1024, sizeof(double) * npp, st, npp, A, W, g->d_minv,
+              g->d_minv32);
+    YK_TRY_CUDA(cudaGetLastError());
+    dev_free(A, st);
+    dev_free(W, st);
+    return YK_OK;
+}
+
+int apply_preconditioner(yk_geom* g, const double* x, double* y, bool fp32) {
+    cudaStream_t st = g->ctx->stream;
+    if (fp32)
+        YK_LAUNCH(k_block_apply<float>, g->np, 256, sizeof(float) * g->npp, st, g->np, g->npp,
+                  g->d_shape_of, g->d_minv32, x, y);
+    else
+        YK_LAUNCH(k_block_apply<double>, g->np, 256, sizeof(double) * g->npp, st, g->np, g->npp,
+                  g->d_shape_of, g->d_minv, x, y);
+    YK_TRY_CUDA(cudaGetLastError());
+    return YK_OK;
+}
+
 // Node arrays and per-particle data from the current particle list.
 int update_nodes(yk_geom* g) {
     cudaStream_t st = g->ctx->stream;
@@ -321,6 +486,7 @@ int update_nodes(yk_geom* g) {
     YK_LAUNCH(k_particle_info, g->np, 256, 0, st, g->np, g->npp, d_parts, g->d_w, g->d_part,
               g->d_c32, g->d_r32);
     for (auto& L : g->lists) L.valid = false;   // particle pairs change when particles move
+    g->nbr_valid = false;
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     dev_free(d_parts, st);
@@ -345,6 +511,7 @@ int build_geometry(yk_geom* g) {
               P.qbx_order, P.qbx_r_factor, P.rho, g->d_shape_ab, g->d_glx, g->d_glw,
               g->d_fine_x, g->d_fine_w, g->d_interp, g->d_cval, g->d_cgrad);
     YK_TRY_CUDA(cudaGetLastError());
+    YK_TRY(build_preconditioner(g));
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     return YK_OK;
 }

@@ -171,7 +171,7 @@ int alloc_workspace(yk_geom* g) {
     YK_TRY(dev_alloc((void**)&w.ybuf, sizeof(double) * (m + 1), st));
     YK_TRY(dev_alloc((void**)&w.dotpart, sizeof(double) * (m + 2) * w.dot_blocks, st));
     YK_TRY(dev_alloc((void**)&w.status, sizeof(double) * 8, st));
-    for (int k = 0; k < 6; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n, st));
+    for (int k = 0; k < 8; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n, st));
     if (!host_status(g->ctx)) return YK_ERR_NO_MEMORY;
     return YK_OK;
 }
@@ -189,7 +189,7 @@ void free_workspace(yk_geom* g) {
     dev_free(w.ybuf, st);
     dev_free(w.dotpart, st);
     dev_free(w.status, st);
-    for (int k = 0; k < 6; ++k) dev_free(w.vec[k], st);
+    for (int k = 0; k < 8; ++k) dev_free(w.vec[k], st);
     w = Workspace{};
 }
 
@@ -221,6 +221,7 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
     const int m = w.m;
     const int ldh = m + 1;
     const int nb = ceil_div(n, 256);
+    const bool pc = g->prm.precond == YK_PRECOND_BLOCK;
     double* r = w.vec[0];
     double* h1 = w.hbuf;
     double* h2 = w.hbuf + (m + 2);
@@ -249,6 +250,10 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
         for (; j < m && total < max_iter; ++j) {
             double* vj = w.V + (int64_t)j * n;
             double* wv = w.V + (int64_t)(j + 1) * n;
+            if (pc) {   // right preconditioning: w = A M^{-1} v_j
+                YK_TRY(apply_preconditioner(g, vj, w.vec[6], prec == Prec::F32));
+                vj = w.vec[6];
+            }
             YK_TRY(matvec(g, vj, wv, prec));
             ++*matvecs;
             // CGS2
@@ -271,7 +276,15 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
         }
         // x += V y
         YK_LAUNCH(k_tri_solve, 1, 32, 0, st, j, ldh, w.H, w.gvec, w.ybuf);
-        YK_LAUNCH(k_add_basis, nb, 256, 0, st, x, w.V, n, j, w.ybuf);
+        if (pc) {   // x += M^{-1} (V y)
+            double* t = w.vec[7];
+            YK_TRY_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, st));
+            YK_LAUNCH(k_add_basis, nb, 256, 0, st, t, w.V, n, j, w.ybuf);
+            YK_TRY(apply_preconditioner(g, t, w.vec[6], prec == Prec::F32));
+            YK_LAUNCH(k_axpy1, nb, 256, 0, st, x, w.vec[6], n);
+        } else {
+            YK_LAUNCH(k_add_basis, nb, 256, 0, st, x, w.V, n, j, w.ybuf);
+        }
         have_x = true;
         YK_TRY_CUDA(cudaGetLastError());
         if (done || total >= max_iter || !isfinite(res)) break;

@@ -326,6 +326,199 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
 }
 
 // ---------------------------------------------------------------------------
+// Cut-off far field: one block per target particle, sweeping only the source
+// particles in its neighbour list (bounding-circle gap below the cut-off);
+// the block owns all its targets, so it writes complete sums. Same pair
+// evaluation and masking as the chunked kernels.
+// ---------------------------------------------------------------------------
+template <bool MASK>
+__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const double* __restrict__ sigma,
+                                                         float kscale, double skip_gap,
+                                                         const int* __restrict__ nbr_off,
+                                                         const int* __restrict__ nbr,
+                                                         double* __restrict__ out) {
+    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
+    const int pt = blockIdx.x;
+    const float kpf = (float)(LOG2E / G.rho);
+    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
+    const PolyRZ P;
+    const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
+    for (int ib = 0; ib < G.npp; ib += TPB) {
+        const int l0 = ib + threadIdx.x, l1 = l0 + F32_TPB;
+        const bool act0 = l0 < G.npp, act1 = l1 < G.npp;
+        const int64_t ii0 = (int64_t)pt * G.npp + (act0 ? l0 : 0);
+        const int64_t ii1 = (int64_t)pt * G.npp + (act1 ? l1 : 0);
+        const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
+        const int pan0 = (act0 ? l0 : 0) / G.ngl, pan1 = (act1 ? l1 : 0) / G.ngl;
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int k = n0; k < n1; ++k) {
+            const int s = nbr[k];
+            TargetF32 T0, T1;
+            target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
+            target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
+            if (MASK && T0.skip) continue;   // uniform: one target particle per block
+            const int64_t base = (int64_t)s * G.npp;
+            for (int jb = 0; jb < G.npp; jb += STILE) {
+                const int cnt = min(STILE, G.npp - jb);
+                const int npair = (cnt + 1) >> 1;
+                __syncthreads();
+                for (int m = threadIdx.x; m < npair; m += F32_TPB) {
+                    float xs[2], ys[2], gx[2], gy[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = 2 * m + h;
+                        if (q < cnt) {
+                            const int64_t j = base + jb + q;
+                            const float2 x = G.xi[j];
+                            const double ws = G.w[j] * sigma[j];
+                            xs[h] = -kpf * x.x;
+                            ys[h] = -kpf * x.y;
+                            gx[h] = (float)(ws * G.nx[j]);
+                            gy[h] = (float)(ws * G.ny[j]);
+                        } else {
+                            xs[h] = 1.0e6f;
+                            ys[h] = 0.0f;
+                            gx[h] = 0.0f;
+                            gy[h] = 0.0f;
+                        }
+                    }
+                    srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
+                    srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
+                }
+                __syncthreads();
+                float r0 = 0.0f, r1 = 0.0f;
+                if (!T0.close) {
+                    const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+                    const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
+                    float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+#pragma unroll 2
+                    for (int m = 0; m < npair; ++m) {
+                        const float4 A = srcA[m], B = srcB[m];
+                        a0 = __fadd2_rn(a0, far2(TX0, TY0, A, B, P));
+                        a1 = __fadd2_rn(a1, far2(TX1, TY1, A, B, P));
+                    }
+                    r0 = a0.x + a0.y;
+                    r1 = a1.x + a1.y;
+                } else {
+                    for (int q = 0; q < cnt; ++q) {
+                        const float4 S = src_scalar(srcA, srcB, q);
+                        const int pq = (jb + q) / G.ngl;
+                        if (!(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+                            r0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
+                        if (!(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+                            r1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
+                    }
+                }
+                acc0 += (double)r0;
+                acc1 += (double)r1;
+            }
+        }
+        if (act0) out[ii0] = acc0 * (double)kscale;
+        if (act1) out[ii1] = acc1 * (double)kscale;
+    }
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
+                                                              const double* __restrict__ sigma,
+                                                              double skip_gap,
+                                                              const int* __restrict__ nbr_off,
+                                                              const int* __restrict__ nbr,
+                                                              double* __restrict__ out) {
+    __shared__ float4 src[STILE];
+    const int pt = blockIdx.x;
+    const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
+    const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
+    for (int ib = 0; ib < G.npp; ib += TPB) {
+        const int l0 = ib + threadIdx.x, l1 = l0 + F32_TPB;
+        const bool act0 = l0 < G.npp, act1 = l1 < G.npp;
+        const int64_t ii0 = (int64_t)pt * G.npp + (act0 ? l0 : 0);
+        const int64_t ii1 = (int64_t)pt * G.npp + (act1 ? l1 : 0);
+        const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
+        const float nx0 = (float)G.nx[ii0], ny0 = (float)G.ny[ii0];
+        const float nx1 = (float)G.nx[ii1], ny1 = (float)G.ny[ii1];
+        const int pan0 = (act0 ? l0 : 0) / G.ngl, pan1 = (act1 ? l1 : 0) / G.ngl;
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int k = n0; k < n1; ++k) {
+            const int s = nbr[k];
+            TargetF32 T0, T1;
+            target_setup(T0, G, pt, s, xi0, 1.0f, 0.0f, MASK, skip_gap, pan0);
+            target_setup(T1, G, pt, s, xi1, 1.0f, 0.0f, MASK, skip_gap, pan1);
+            if (MASK && T0.skip) continue;
+            const int64_t base = (int64_t)s * G.npp;
+            for (int jb = 0; jb < G.npp; jb += STILE) {
+                const int cnt = min(STILE, G.npp - jb);
+                __syncthreads();
+                for (int q = threadIdx.x; q < cnt; q += F32_TPB) {
+                    const int64_t j = base + jb + q;
+                    const float2 xs = G.xi[j];
+                    const double ws = G.w[j] * sigma[j];
+                    src[q] = make_float4(xs.x, xs.y, (float)(ws * G.nx[j]), (float)(ws * G.ny[j]));
+                }
+                __syncthreads();
+                float a0 = 0.0f, a1 = 0.0f;
+                for (int q = 0; q < cnt; ++q) {
+                    const float4 S = src[q];
+                    const int pq = (jb + q) / G.ngl;
+                    if (!(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+                        a0 += PairF32::grad(T0.TX - S.x, T0.TY - S.y, nx0, ny0, S.z, S.w, kappa, rho);
+                    if (!(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+                        a1 += PairF32::grad(T1.TX - S.x, T1.TY - S.y, nx1, ny1, S.z, S.w, kappa, rho);
+                }
+                acc0 += (double)a0;
+                acc1 += (double)a1;
+            }
+        }
+        const double sc = 1.0 / (2.0 * PI);
+        if (act0) out[ii0] = acc0 * sc;
+        if (act1) out[ii1] = acc1 * sc;
+    }
+}
+
+// Cut-off neighbour lists: counts, a single-block exclusive scan, fill.
+__global__ void k_nbr_count(int np, const d4* __restrict__ part, double thr, int* counts) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= np) return;
+    const d4 a = part[P];
+    int c = 0;
+    for (int Q = 0; Q < np; ++Q) c += (Q == P || pair_in_tiles(a, part[Q], thr)) ? 1 : 0;
+    counts[P] = c;
+}
+
+__global__ void k_scan_offsets(int np, const int* __restrict__ counts, int* __restrict__ off) {
+    __shared__ int buf[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < np; b += 1024) {
+        const int i = b + threadIdx.x;
+        buf[threadIdx.x] = (i < np) ? counts[i] : 0;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
+            const int v = (threadIdx.x >= o) ? buf[threadIdx.x - o] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (i < np) off[i + 1] = carry + buf[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[0] = 0;
+}
+
+__global__ void k_nbr_fill(int np, const d4* __restrict__ part, double thr,
+                           const int* __restrict__ off, int* __restrict__ nbr) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= np) return;
+    const d4 a = part[P];
+    int k = off[P];
+    for (int Q = 0; Q < np; ++Q)
+        if (Q == P || pair_in_tiles(a, part[Q], thr)) nbr[k++] = Q;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 pair tiles. Value: k = K1(z)/r; the (i <- j) term is k (d . g_j) and
 // the (j <- i) term is -k (d . g_i), with g = w sigma nu and d = x_i - x_j.
 // Gradient: G_ij = g (nu_i . nu_j) + g' (d . nu_j)(d . nu_i)/r is symmetric;
@@ -517,7 +710,9 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
     PairList& L = g->lists[kind];
     if (!L.valid) {
         cudaStream_t st = g->ctx->stream;
-        const double thr = kind == 0 ? g->split_gap : (kind == 1 ? g->split_gap_grad : INFINITY);
+        const double thr = kind == 0 ? g->split_gap
+                           : kind == 1 ? g->split_gap_grad
+                           : kind == 2 ? INFINITY : g->cutoff_gap;
         int* d_count = g->d_counter;
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
         YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr, d_count,
@@ -546,7 +741,82 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
 
 static int tiles_grid(int ntiles) { return std::max(1, std::min(ntiles, 152 * 16)); }
 
+// Cut-off neighbour lists (CSR), built on first use and after the particles move.
+static int neighbours(yk_geom* g) {
+    if (g->nbr_valid) return YK_OK;
+    cudaStream_t st = g->ctx->stream;
+    if (!g->nbr_off) YK_TRY(dev_alloc((void**)&g->nbr_off, sizeof(int) * (g->np + 1), st));
+    int* counts = (int*)g->ws.partial;   // np ints of scratch (partial holds >= n doubles)
+    YK_LAUNCH(k_nbr_count, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, g->cutoff_gap,
+              counts);
+    YK_LAUNCH(k_scan_offsets, 1, 1024, 0, st, g->np, counts, g->nbr_off);
+    int total = 0;
+    YK_TRY_CUDA(cudaMemcpyAsync(&total, g->nbr_off + g->np, sizeof(int), cudaMemcpyDeviceToHost, st));
+    YK_TRY_CUDA(cudaStreamSynchronize(st));
+    if (total > g->nbr_cap) {
+        dev_free(g->nbr, st);
+        g->nbr = nullptr;
+        g->nbr_cap = 0;
+        YK_TRY(dev_alloc((void**)&g->nbr, sizeof(int) * (size_t)total, st));
+        g->nbr_cap = total;
+    }
+    YK_LAUNCH(k_nbr_fill, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, g->cutoff_gap,
+              g->nbr_off, g->nbr);
+    YK_TRY_CUDA(cudaGetLastError());
+    g->nbr_valid = true;
+    return YK_OK;
+}
+
+// Cut-off far field: FP32 per target particle over its neighbours (masked
+// against the FP64 tiles for the split operators), FP64 tiles over the
+// in-cut-off pairs for the FP64 path.
+static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, bool grad) {
+    cudaStream_t st = g->ctx->stream;
+    GeomView G = g->view();
+    YK_TRY(neighbours(g));
+    const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
+    double* extra = nullptr;
+    int used = 1;
+    if (prec == Prec::F32) {
+        if (grad)
+            YK_LAUNCH(k_p2p_f32_grad_cut<false>, g->np, F32_TPB, 0, st, G, sigma, 0.0, g->nbr_off,
+                      g->nbr, g->ws.partial);
+        else
+            YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, 0.0,
+                      g->nbr_off, g->nbr, g->ws.partial);
+    } else {
+        const int kind = (prec == Prec::F64) ? 3 : (grad ? 1 : 0);
+        const int2* list;
+        int ntiles;
+        YK_TRY(tile_list(g, kind, &list, &ntiles));
+        extra = g->ws.vec[5];
+        YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
+        if (prec == Prec::SPLIT) {
+            const double gap = grad ? g->split_gap_grad : g->split_gap;
+            if (grad)
+                YK_LAUNCH(k_p2p_f32_grad_cut<true>, g->np, F32_TPB, 0, st, G, sigma, gap,
+                          g->nbr_off, g->nbr, g->ws.partial);
+            else
+                YK_LAUNCH(k_p2p_f32_cut<true>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, gap,
+                          g->nbr_off, g->nbr, g->ws.partial);
+        } else {
+            used = 0;
+        }
+        if (grad)
+            YK_LAUNCH(k_tiles_f64<true>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list,
+                      ntiles, extra);
+        else
+            YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list,
+                      ntiles, extra);
+    }
+    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used, g->ws.partial, extra,
+              grad ? G.cgrad : G.cval, sigma, y);
+    YK_TRY_CUDA(cudaGetLastError());
+    return YK_OK;
+}
+
 int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
+    if (g->prm.farfield == YK_FARFIELD_CUTOFF) return matvec_cutoff(g, sigma, y, prec, false);
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
     const int nchunk = g->ws.nchunk;
@@ -581,6 +851,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
 }
 
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
+    if (g->prm.farfield == YK_FARFIELD_CUTOFF) return matvec_cutoff(g, sigma, un, prec, true);
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
     const int nchunk = g->ws.nchunk;

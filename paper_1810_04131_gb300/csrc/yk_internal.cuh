@@ -1,6 +1,7 @@
 // Internal state of the yk library: contexts, geometries and workspaces.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <set>
@@ -91,7 +92,7 @@ struct Workspace {
     double* ybuf = nullptr;      // m+1 least-squares coefficients
     double* dotpart = nullptr;   // partial dots [(m+2)][nblk]
     double* status = nullptr;    // [0] residual estimate, [1] norm, [2..] scratch
-    double* vec[6] = {};         // N-length scratch vectors
+    double* vec[8] = {};         // N-length scratch vectors
     int m = 0;
     int dot_blocks = 0;
 };
@@ -125,12 +126,17 @@ struct yk_geom {
     double max_perimeter = 0.0, max_radius = 0.0;
     double split_gap = 0.0;                // gap above which FP32 is used (mixed residual)
     double split_gap_grad = 0.0;           // the same for the normal derivative
+    double cutoff_gap = INFINITY;          // far field: source particles beyond are left out
+    int* nbr_off = nullptr;                // cut-off neighbour lists (CSR offsets, np + 1)
+    int* nbr = nullptr;                    // neighbour particle indices
+    int nbr_cap = 0;
+    bool nbr_valid = false;
     // device allocations
     yk::d4* d_part = nullptr;
     float4* d_c32 = nullptr;
     float* d_r32 = nullptr;
     int* d_counter = nullptr;
-    yk::PairList lists[3];                 // residual split, gradient split, all pairs
+    yk::PairList lists[4];                 // residual split, gradient split, all, cut-off
     int* d_shape_of = nullptr;
     double2* d_shape_ab = nullptr;
     double* d_x = nullptr;
@@ -148,6 +154,9 @@ struct yk_geom {
     double* d_diff = nullptr;     // Lagrange differentiation [ngl][ngl]
     double* d_fine_x = nullptr;   // fine reference nodes [os*ngl]
     double* d_fine_w = nullptr;   // fine reference weights [os*ngl]
+    double* d_minv = nullptr;     // block preconditioner: inverse self block per shape,
+                                  // transposed, [shape][col j][row i]
+    float* d_minv32 = nullptr;    // the same in FP32
     yk::Workspace ws;
     yk::GeomView view() const;
 };
@@ -158,6 +167,8 @@ namespace yk {
 int build_geometry(yk_geom* g);
 int update_nodes(yk_geom* g);
 int launch_label(yk_geom* g, int kind, double param, double* f);
+int build_preconditioner(yk_geom* g);
+int apply_preconditioner(yk_geom* g, const double* x, double* y, bool fp32);
 
 // p2p.cu
 enum class Prec { F64 = 0, F32 = 1, SPLIT = 2 };

@@ -131,6 +131,27 @@ def test_solve_forces_small(yk, ctx, dense_cache, name, precision):
     assert np.abs(net[:2] - F_ref.sum(0)).max() < 1e-9 * scale
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_block_preconditioner(yk, ctx, dense_cache, precision):
+    """Right preconditioning by the inverse self-interaction block of each
+    particle changes the iteration count, not the solution."""
+    wl = SMALL["ellipses4_gl11"]()
+    o, A, Gn = _oracle(wl, dense_cache)
+    prec = yk.YK_FP64 if precision == "fp64" else yk.YK_MIXED
+    s_ref = None
+    its = {}
+    for pc in (yk.YK_PRECOND_NONE, yk.YK_PRECOND_BLOCK):
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec, precond=pc,
+                                                   gmres_tol=1e-12))
+        f = g.yk_label(0, 10.0)
+        s, info = g.yk_solve(f)
+        s_ref = np.linalg.solve(A, f) if s_ref is None else s_ref
+        assert info["converged"] and rel(s, s_ref) < 1e-9
+        its[pc] = info["iterations"]
+        g.close()
+    assert its[yk.YK_PRECOND_BLOCK] < its[yk.YK_PRECOND_NONE]
+
+
 def test_disks8_end_to_end(yk, ctx, dense_cache):
     """8 disks, N = 2048, rho = 1, QBX order 8, tol 1e-10: density,
     potential at 1000 off-surface targets, forces and torques, both modes."""
@@ -154,6 +175,37 @@ def test_disks8_end_to_end(yk, ctx, dense_cache):
         u = g.yk_eval_potential(sig, wl.targets)
         assert rel(u, u_ref) < 1e-9
         g.close()
+
+
+def test_cutoff_far_field(yk, ctx, dense_cache):
+    """Cut-off far field: a source particle is dropped when its whole
+    contribution is bounded below cutoff_tol * max|sigma|. On a sparse
+    system (many pairs beyond the cut-off) the FP64 cut-off operator stays
+    within a few cutoff_tol of the dense one, and a mixed cut-off solve
+    matches the oracle's dense solution."""
+    wl = W.small_system(24, 31, n_panels=8, n_gl=16, rho=0.5, qbx_order=10, gap=0.4)
+    wl.particles[:, 1:3] *= 2.5   # spread out: box ~ 2.5x larger
+    o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+    A = o.dense()
+    rng = np.random.default_rng(9)
+    sig = rng.standard_normal(A.shape[0])
+    for tol in (1e-8, 1e-15):
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF,
+                                                   cutoff_tol=tol))
+        y = g.yk_matvec(sig, yk.YK_FP64)
+        assert np.abs(y - A @ sig).max() <= 20 * tol * np.abs(sig).max() + 1e-13
+        y32 = g.yk_matvec(sig, yk.YK_MIXED)
+        assert rel(y32, A @ sig) < 1e-6
+        g.close()
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF,
+                                               precision=yk.YK_MIXED, gmres_tol=1e-12))
+    f = g.yk_label(0, 10.0)
+    s, info = g.yk_solve(f)
+    assert info["converged"] and rel(s, np.linalg.solve(A, f)) < 1e-9
+    # the cut-off drops something here (otherwise the test would be vacuous)
+    gd = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF,
+                                                cutoff_tol=1e-3))
+    assert rel(gd.yk_matvec(sig, yk.YK_FP64), A @ sig) > 1e-8
 
 
 def test_device_pointers_match_host(yk, ctx):
