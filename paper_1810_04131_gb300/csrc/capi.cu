@@ -286,6 +286,12 @@ int yk_destroy_geometry(yk_geom* g) {
     for (auto& L : g->lists) dev_free(L.d, st);
     dev_free(g->nbr_off, st);
     dev_free(g->nbr, st);
+    for (auto& B : g->bands) {
+        dev_free(B.off, st);
+        dev_free(B.idx, st);
+    }
+    dev_free(g->d_counts, st);
+    dev_free(g->d_mpole, st);
     void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
                     g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w, g->d_minv, g->d_minv32};
@@ -380,6 +386,8 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     // the FP64 tiles of the split operators stay inside the cut-off
     g->split_gap = std::min(g->split_gap, g->cutoff_gap);
     g->split_gap_grad = std::min(g->split_gap_grad, g->cutoff_gap);
+    g->tile_gap = std::min(g->split_gap, EXPANSION_GAP_RADII * rmax);
+    g->tile_gap_grad = std::min(g->split_gap_grad, EXPANSION_GAP_RADII * rmax);
     const int os = prm->oversample;
     const size_t N = (size_t)n;
     const size_t rowlen = (size_t)g->n_near * g->ngl;
@@ -390,6 +398,8 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     ALLOC(d_c32, n_particles);
     ALLOC(d_r32, n_particles);
     ALLOC(d_counter, 1);
+    ALLOC(d_counts, n_particles);
+    ALLOC(d_mpole, (size_t)n_particles * EXPANSION_TERMS);
     ALLOC(d_shape_of, n_particles);
     ALLOC(d_shape_ab, g->nshape);
     ALLOC(d_x, N);

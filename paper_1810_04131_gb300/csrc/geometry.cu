@@ -487,6 +487,7 @@ int update_nodes(yk_geom* g) {
               g->d_c32, g->d_r32);
     for (auto& L : g->lists) L.valid = false;   // particle pairs change when particles move
     g->nbr_valid = false;
+    for (auto& B : g->bands) B.valid = false;
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     dev_free(d_parts, st);

@@ -710,8 +710,8 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
     PairList& L = g->lists[kind];
     if (!L.valid) {
         cudaStream_t st = g->ctx->stream;
-        const double thr = kind == 0 ? g->split_gap
-                           : kind == 1 ? g->split_gap_grad
+        const double thr = kind == 0 ? g->tile_gap
+                           : kind == 1 ? g->tile_gap_grad
                            : kind == 2 ? INFINITY : g->cutoff_gap;
         int* d_count = g->d_counter;
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
@@ -808,6 +808,7 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
         else
             YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list,
                       ntiles, extra);
+        if (prec == Prec::SPLIT) YK_TRY(band_expansions(g, sigma, extra, grad));
     }
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used, g->ws.partial, extra,
               grad ? G.cgrad : G.cval, sigma, y);
@@ -843,6 +844,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
         }
         YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
                   extra);
+        if (prec == Prec::SPLIT) YK_TRY(band_expansions(g, sigma, extra, false));
     }
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used_chunks, g->ws.partial, extra,
               G.cval, sigma, y);
@@ -870,6 +872,7 @@ int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
         used_chunks = nchunk;
     }
     YK_LAUNCH(k_tiles_f64<true>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles, extra);
+    if (prec != Prec::F64) YK_TRY(band_expansions(g, sigma, extra, true));
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used_chunks, g->ws.partial, extra,
               G.cgrad, sigma, un);
     YK_TRY_CUDA(cudaGetLastError());

@@ -97,6 +97,15 @@ struct Workspace {
     int dot_blocks = 0;
 };
 
+// Per-target-particle source lists (CSR) for the expansion band.
+struct BandList {
+    int* off = nullptr;
+    int* idx = nullptr;
+    int n = 0;
+    int cap = 0;
+    bool valid = false;
+};
+
 // Particle pairs (P <= Q) evaluated by the FP64 tiles.
 struct PairList {
     int2* d = nullptr;
@@ -127,6 +136,11 @@ struct yk_geom {
     double split_gap = 0.0;                // gap above which FP32 is used (mixed residual)
     double split_gap_grad = 0.0;           // the same for the normal derivative
     double cutoff_gap = INFINITY;          // far field: source particles beyond are left out
+    double tile_gap = 0.0;                 // split operators: FP64 tiles below this gap,
+    double tile_gap_grad = 0.0;            //   FP64 expansions up to the split gap
+    yk::BandList bands[2];                 // expansion bands (value, normal derivative)
+    int* d_counts = nullptr;               // np ints of scratch for list building
+    double2* d_mpole = nullptr;            // multipole moments [np][order + 1]
     int* nbr_off = nullptr;                // cut-off neighbour lists (CSR offsets, np + 1)
     int* nbr = nullptr;                    // neighbour particle indices
     int nbr_cap = 0;
@@ -177,6 +191,11 @@ int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec);
 int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u);
 int potential_noalloc(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
                       double* u);
+
+// expansions.cu
+constexpr int EXPANSION_TERMS = 41;        // orders 0..40 of the particle expansions
+constexpr double EXPANSION_GAP_RADII = 4.0;  // band starts at a gap of 4 bounding radii
+int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad);
 
 // gmres.cu
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0, yk_solve_info* info);

@@ -39,7 +39,9 @@ def main():
     out = {}
     modes = [("mixed", yk.YK_MIXED)] + ([("fp64", yk.YK_FP64)] if a.fp64 else [])
     for name, prec in modes:
-        g = yk.Geometry(ctx, wl.particles, yk.params_for(wl, precision=prec,
+        # the FP64 solve is the reference: run it to a 1e-12 residual
+        tol = 1e-12 if prec == yk.YK_FP64 else wl.gmres_tol
+        g = yk.Geometry(ctx, wl.particles, yk.params_for(wl, precision=prec, gmres_tol=tol,
                                                          farfield=yk.YK_FARFIELD_CUTOFF))
         dev = torch.device("cuda", 0)
         f = torch.zeros(g.n, dtype=torch.float64, device=dev)
