@@ -110,10 +110,17 @@ def main():
         out.append("// nu=%d, t in [%g, %g], degree %d, max rel. error %.2e (FP32 Horner)" % (nu, a, b, deg, err))
         out.append(arr(name, c, "float", "f"))
     # FP32 far field in scaled coordinates: with z' = z log2(e) and rz = 1/z',
-    # t = 2/z = 2 log2(e) rz. P1 as a monomial in rz directly (no affine step):
-    # convert the Chebyshev fit to monomials in t on [0, 1], then scale.
+    # t = 2/z = 2 log2(e) rz. P0, P1 as monomials in rz directly (no affine
+    # step): convert the Chebyshev fit to monomials in t on [0, 1], then scale.
+    for nu, name in ((1, "YK_P1_F32_RZ"), (0, "YK_P0_F32_RZ")):
+        emit_rz(out, nu, name)
+    kmax = 14
+    return finish(out, kmax)
+
+
+def emit_rz(out, nu, name):
     for deg in (6, 7):
-        c = fit(1, deg, 0.0, 1.0)                      # monomial in s = 2t - 1
+        c = fit(nu, deg, 0.0, 1.0)                     # monomial in s = 2t - 1
         t_mono = [0.0] * (deg + 1)                     # expand in t: s = 2t - 1
         from math import comb
         for k, ck in enumerate(c):
@@ -127,16 +134,19 @@ def main():
             acc = np.float32(rz_mono[-1])
             for cf in reversed(rz_mono[:-1]):
                 acc = np.float32(acc * rz + np.float32(cf))
-            worst = max(worst, abs(float(acc) / float(p_nu(1, t)) - 1))
+            worst = max(worst, abs(float(acc) / float(p_nu(nu, t)) - 1))
         if deg == 6 and worst > 1.5e-7:
             continue
         if worst > 2e-7:
             sys.exit("rz-monomial fit error %.3e" % worst)
-        out.append("// nu=1 in rz = 1/z' (z' = z log2 e), t = 2 log2(e) rz in [0, 1], degree %d, "
-                   "max rel. error %.2e (FP32 Horner)" % (deg, worst))
-        out.append(arr("YK_P1_F32_RZ", rz_mono, "float", "f"))
-        break
-    kmax = 14
+        out.append("// nu=%d in rz = 1/z' (z' = z log2 e), t = 2 log2(e) rz in [0, 1], degree %d, "
+                   "max rel. error %.2e (FP32 Horner)" % (nu, deg, worst))
+        out.append(arr(name, rz_mono, "float", "f"))
+        return
+    sys.exit("no rz-monomial fit for nu=%d" % nu)
+
+
+def finish(out, kmax):
     i0, i1, k0, k1 = series_tables(kmax)
     out.append("// ascending series (DLMF 10.25.2, 10.31.1) in q = z^2/4, k = 0..%d" % kmax)
     out.append("#define YK_SERIES_TERMS %d" % (kmax + 1))
@@ -154,6 +164,7 @@ def main():
     with open(path, "w") as fh:
         fh.write("\n".join(out) + "\n")
     print("wrote", path)
+    return path
 
 
 if __name__ == "__main__":

@@ -149,7 +149,7 @@ __device__ __forceinline__ void target_setup(TargetF32& T, const GeomView& G, in
 // with the f32x2 FMA/ADD/MUL instructions of sm_100+: lanes .x/.y are the
 // two sources. Sources are staged as pairs: A = (-X0, -X1, -Y0, -Y1) in
 // scaled coordinates, B = (gx0, gx1, gy0, gy1). Returns the two terms in the
-// units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))), z > 2 only.
+// units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))) added to acc, z > 2 only.
 struct PolyRZ {
     float2 c[7];
     __device__ __forceinline__ PolyRZ() {
@@ -159,7 +159,7 @@ struct PolyRZ {
 };
 
 __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, const float4& B,
-                                       const PolyRZ& P) {
+                                       const PolyRZ& P, float2 acc) {
     const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
     const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
     const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
@@ -171,13 +171,123 @@ __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, co
     const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
     const float2 sq = make_float2(rsqrt_fast(zp.x), rsqrt_fast(zp.y));   // z'^{-1/2}
     const float2 dot = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
-    return __fmul2_rn(__fmul2_rn(__fmul2_rn(e, p), sq), __fmul2_rn(rz, dot));
+    return __ffma2_rn(__fmul2_rn(__fmul2_rn(e, p), sq), __fmul2_rn(rz, dot), acc);
 }
 
 // Scalar view of source q in the pair-packed staging.
 __device__ __forceinline__ float4 src_scalar(const float4* A, const float4* B, int q) {
     const float4 a = A[q >> 1], b = B[q >> 1];
     return (q & 1) ? make_float4(-a.y, -a.w, b.y, b.w) : make_float4(-a.x, -a.z, b.x, b.z);
+}
+
+// Packed FP32 normal derivative of two far pairs (one target with normal
+// (nx, ny), two sources), same scaled coordinates and staging as far2. With
+// E = exp2(-z') z'^{-1/2}, rz = 1/z', G = w sigma nu_y, D' the scaled d:
+//   [g (nu.G) + g' (d.G)(d.nu)/r] = sqrt(log2 e) kappa kappa' E rz
+//       [P1 (nu.G) - (ln2 P0 + 2 rz P1) (D'.G)(D'.nu) rz]
+// (kappa = 1/rho, kappa' = log2(e)/rho, kappa/kappa' = ln 2); the constant
+// sqrt(log2 e) kappa kappa' is applied by the caller.
+struct PolyRZ2 {
+    float2 c0[7], c1[7];
+    __device__ __forceinline__ PolyRZ2() {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            c0[k] = make_float2(YK_P0_F32_RZ[k], YK_P0_F32_RZ[k]);
+            c1[k] = make_float2(YK_P1_F32_RZ[k], YK_P1_F32_RZ[k]);
+        }
+    }
+};
+
+__device__ __forceinline__ float2 grad2(float2 TX, float2 TY, float2 NX, float2 NY, const float4& A,
+                                        const float4& B, const PolyRZ2& P, float2 acc) {
+    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
+    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
+    const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
+    const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));
+    const float2 zp = __fmul2_rn(z2, rz);
+    float2 p0 = P.c0[6], p1 = P.c1[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        p0 = __ffma2_rn(p0, rz, P.c0[k]);
+        p1 = __ffma2_rn(p1, rz, P.c1[k]);
+    }
+    const float2 E = make_float2(ex2_fast(-zp.x) * rsqrt_fast(zp.x), ex2_fast(-zp.y) * rsqrt_fast(zp.y));
+    const float2 Gx = make_float2(B.x, B.y), Gy = make_float2(B.z, B.w);
+    const float2 nn = __ffma2_rn(NX, Gx, __fmul2_rn(NY, Gy));
+    const float2 dnG = __ffma2_rn(dX, Gx, __fmul2_rn(dY, Gy));
+    const float2 dnT = __ffma2_rn(dX, NX, __fmul2_rn(dY, NY));
+    const float2 aneg = __ffma2_rn(make_float2(-0.69314718f, -0.69314718f), p0,
+                                   __fmul2_rn(__fmul2_rn(make_float2(-2.0f, -2.0f), rz), p1));
+    const float2 bneg = __fmul2_rn(__fmul2_rn(aneg, dnG), __fmul2_rn(dnT, rz));
+    const float2 br = __ffma2_rn(p1, nn, bneg);
+    return __ffma2_rn(__fmul2_rn(E, rz), br, acc);
+}
+
+// Stage sources [jb, jb + cnt) of the particle at `base` in pair-packed form
+// (scaled coordinates negated, g = w sigma nu); pads with a far weightless source.
+__device__ __forceinline__ void stage_pairs(const GeomView& G, const double* __restrict__ sigma,
+                                            int64_t base, int jb, int cnt, float kpf,
+                                            float4* srcA, float4* srcB) {
+    const int npair = (cnt + 1) >> 1;
+    for (int m = threadIdx.x; m < npair; m += blockDim.x) {
+        float xs[2], ys[2], gx[2], gy[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = 2 * m + h;
+            if (q < cnt) {
+                const int64_t j = base + jb + q;
+                const float2 x = G.xi[j];
+                const double ws = G.w[j] * sigma[j];
+                xs[h] = -kpf * x.x;
+                ys[h] = -kpf * x.y;
+                gx[h] = (float)(ws * G.nx[j]);
+                gy[h] = (float)(ws * G.ny[j]);
+            } else {
+                xs[h] = 1.0e6f;
+                ys[h] = 0.0f;
+                gx[h] = 0.0f;
+                gy[h] = 0.0f;
+            }
+        }
+        srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
+        srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
+    }
+}
+
+// One staged tile of the normal derivative for two targets: packed far
+// pairs into f0/f1 (scaled units), near/own pairs (scalar) into s0/s1.
+__device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB, int jb, int cnt,
+                                          const GeomView& G, const TargetF32& T0,
+                                          const TargetF32& T1, bool use0, bool use1, float nx0,
+                                          float ny0, float nx1, float ny1, float inv_kp,
+                                          float kappa, float rho, const PolyRZ2& P, float& f0,
+                                          float& f1, float& s0, float& s1) {
+    const int npair = (cnt + 1) >> 1;
+    if (use0 && use1 && !T0.close && !T1.close) {
+        const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+        const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
+        const float2 NX0 = make_float2(nx0, nx0), NY0 = make_float2(ny0, ny0);
+        const float2 NX1 = make_float2(nx1, nx1), NY1 = make_float2(ny1, ny1);
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+        for (int m = 0; m < npair; ++m) {
+            const float4 A = srcA[m], B = srcB[m];
+            a0 = grad2(TX0, TY0, NX0, NY0, A, B, P, a0);
+            a1 = grad2(TX1, TY1, NX1, NY1, A, B, P, a1);
+        }
+        f0 += a0.x + a0.y;
+        f1 += a1.x + a1.y;
+        return;
+    }
+    for (int q = 0; q < cnt; ++q) {
+        const float4 S = src_scalar(srcA, srcB, q);
+        const int pq = (jb + q) / G.ngl;
+        if (use0 && !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+            s0 += PairF32::grad((T0.TX - S.x) * inv_kp, (T0.TY - S.y) * inv_kp, nx0, ny0, S.z, S.w,
+                                kappa, rho);
+        if (use1 && !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+            s1 += PairF32::grad((T1.TX - S.x) * inv_kp, (T1.TY - S.y) * inv_kp, nx1, ny1, S.z, S.w,
+                                kappa, rho);
+    }
 }
 
 template <bool MASK>
@@ -243,8 +353,8 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
 #pragma unroll 2
                 for (int m = 0; m < npair; ++m) {
                     const float4 A = srcA[m], B = srcB[m];
-                    a0 = __fadd2_rn(a0, far2(TX0, TY0, A, B, P));
-                    a1 = __fadd2_rn(a1, far2(TX1, TY1, A, B, P));
+                    a0 = far2(TX0, TY0, A, B, P, a0);
+                    a1 = far2(TX1, TY1, A, B, P, a1);
                 }
                 r0 = a0.x + a0.y;
                 r1 = a1.x + a1.y;
@@ -268,14 +378,14 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
     if (act1) partial[blockIdx.y * G.n + i1] = acc1 * (double)kscale;
 }
 
-// FP32 normal derivative of the far field (unscaled offsets), two targets
-// per thread, with the same masking as k_p2p_f32.
+// FP32 normal derivative of the far field, two targets per thread, packed
+// pairs (same staging and masking as k_p2p_f32).
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
                                                           const double* __restrict__ sigma,
                                                           int ppc, double skip_gap,
                                                           double* __restrict__ partial) {
-    __shared__ float4 src[STILE];
+    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
     const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
     const int64_t i1 = i0 + F32_TPB;
     const bool act0 = i0 < G.n, act1 = i1 < G.n;
@@ -286,43 +396,38 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
     const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
     const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
     const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
+    const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
+    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
+    const PolyRZ2 P;
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
-    double acc0 = 0.0, acc1 = 0.0;
+    double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
     for (int s = s0; s < s1; ++s) {
         const int64_t base = (int64_t)s * G.npp;
         TargetF32 T0, T1;
-        target_setup(T0, G, pt0, s, xi0, 1.0f, 0.0f, MASK, skip_gap, pan0);
-        target_setup(T1, G, pt1, s, xi1, 1.0f, 0.0f, MASK, skip_gap, pan1);
+        target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
+        target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
         const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
         if (block_skip) continue;
+        const bool use0 = !(MASK && T0.skip), use1 = !(MASK && T1.skip);
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
             __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += F32_TPB) {
-                const int64_t j = base + jb + q;
-                const float2 xs = G.xi[j];
-                const double ws = G.w[j] * sigma[j];
-                src[q] = make_float4(xs.x, xs.y, (float)(ws * G.nx[j]), (float)(ws * G.ny[j]));
-            }
+            stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
             __syncthreads();
-            float a0 = 0.0f, a1 = 0.0f;
-            const bool use0 = !(MASK && T0.skip), use1 = !(MASK && T1.skip);
-            for (int q = 0; q < cnt; ++q) {
-                const float4 S = src[q];
-                const int pq = (jb + q) / G.ngl;
-                if (use0 && !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
-                    a0 += PairF32::grad(T0.TX - S.x, T0.TY - S.y, nx0, ny0, S.z, S.w, kappa, rho);
-                if (use1 && !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
-                    a1 += PairF32::grad(T1.TX - S.x, T1.TY - S.y, nx1, ny1, S.z, S.w, kappa, rho);
-            }
-            acc0 += (double)a0;
-            acc1 += (double)a1;
+            float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+            grad_tile(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1, inv_kp,
+                      kappa, rho, P, a0, a1, b0, b1);
+            fast0 += (double)a0;
+            fast1 += (double)a1;
+            slow0 += (double)b0;
+            slow1 += (double)b1;
         }
     }
+    const double cf = sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho);
     const double sc = 1.0 / (2.0 * PI);
-    if (act0) partial[blockIdx.y * G.n + i0] = acc0 * sc;
-    if (act1) partial[blockIdx.y * G.n + i1] = acc1 * sc;
+    if (act0) partial[blockIdx.y * G.n + i0] = (fast0 * cf + slow0) * sc;
+    if (act1) partial[blockIdx.y * G.n + i1] = (fast1 * cf + slow1) * sc;
 }
 
 // ---------------------------------------------------------------------------
@@ -394,8 +499,8 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
 #pragma unroll 2
                     for (int m = 0; m < npair; ++m) {
                         const float4 A = srcA[m], B = srcB[m];
-                        a0 = __fadd2_rn(a0, far2(TX0, TY0, A, B, P));
-                        a1 = __fadd2_rn(a1, far2(TX1, TY1, A, B, P));
+                        a0 = far2(TX0, TY0, A, B, P, a0);
+                        a1 = far2(TX1, TY1, A, B, P, a1);
                     }
                     r0 = a0.x + a0.y;
                     r1 = a1.x + a1.y;
@@ -425,9 +530,13 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
                                                               const int* __restrict__ nbr_off,
                                                               const int* __restrict__ nbr,
                                                               double* __restrict__ out) {
-    __shared__ float4 src[STILE];
+    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
     const int pt = blockIdx.x;
     const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
+    const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
+    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
+    const PolyRZ2 P;
+    const double cf = sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho);
     const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
     for (int ib = 0; ib < G.npp; ib += TPB) {
         const int l0 = ib + threadIdx.x, l1 = l0 + F32_TPB;
@@ -438,40 +547,31 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
         const float nx0 = (float)G.nx[ii0], ny0 = (float)G.ny[ii0];
         const float nx1 = (float)G.nx[ii1], ny1 = (float)G.ny[ii1];
         const int pan0 = (act0 ? l0 : 0) / G.ngl, pan1 = (act1 ? l1 : 0) / G.ngl;
-        double acc0 = 0.0, acc1 = 0.0;
+        double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
         for (int k = n0; k < n1; ++k) {
             const int s = nbr[k];
             TargetF32 T0, T1;
-            target_setup(T0, G, pt, s, xi0, 1.0f, 0.0f, MASK, skip_gap, pan0);
-            target_setup(T1, G, pt, s, xi1, 1.0f, 0.0f, MASK, skip_gap, pan1);
-            if (MASK && T0.skip) continue;
+            target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
+            target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
+            if (MASK && T0.skip) continue;   // uniform: one target particle per block
             const int64_t base = (int64_t)s * G.npp;
             for (int jb = 0; jb < G.npp; jb += STILE) {
                 const int cnt = min(STILE, G.npp - jb);
                 __syncthreads();
-                for (int q = threadIdx.x; q < cnt; q += F32_TPB) {
-                    const int64_t j = base + jb + q;
-                    const float2 xs = G.xi[j];
-                    const double ws = G.w[j] * sigma[j];
-                    src[q] = make_float4(xs.x, xs.y, (float)(ws * G.nx[j]), (float)(ws * G.ny[j]));
-                }
+                stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
                 __syncthreads();
-                float a0 = 0.0f, a1 = 0.0f;
-                for (int q = 0; q < cnt; ++q) {
-                    const float4 S = src[q];
-                    const int pq = (jb + q) / G.ngl;
-                    if (!(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
-                        a0 += PairF32::grad(T0.TX - S.x, T0.TY - S.y, nx0, ny0, S.z, S.w, kappa, rho);
-                    if (!(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
-                        a1 += PairF32::grad(T1.TX - S.x, T1.TY - S.y, nx1, ny1, S.z, S.w, kappa, rho);
-                }
-                acc0 += (double)a0;
-                acc1 += (double)a1;
+                float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+                grad_tile(srcA, srcB, jb, cnt, G, T0, T1, true, true, nx0, ny0, nx1, ny1, inv_kp,
+                          kappa, rho, P, a0, a1, b0, b1);
+                fast0 += (double)a0;
+                fast1 += (double)a1;
+                slow0 += (double)b0;
+                slow1 += (double)b1;
             }
         }
         const double sc = 1.0 / (2.0 * PI);
-        if (act0) out[ii0] = acc0 * sc;
-        if (act1) out[ii1] = acc1 * sc;
+        if (act0) out[ii0] = (fast0 * cf + slow0) * sc;
+        if (act1) out[ii1] = (fast1 * cf + slow1) * sc;
     }
 }
 

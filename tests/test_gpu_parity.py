@@ -186,7 +186,7 @@ def test_cutoff_far_field(yk, ctx, dense_cache):
     wl = W.small_system(24, 31, n_panels=8, n_gl=16, rho=0.5, qbx_order=10, gap=0.4)
     wl.particles[:, 1:3] *= 2.5   # spread out: box ~ 2.5x larger
     o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
-    A = o.dense()
+    A, Gn = o.dense(want_grad=True)
     rng = np.random.default_rng(9)
     sig = rng.standard_normal(A.shape[0])
     for tol in (1e-8, 1e-15):
@@ -196,6 +196,10 @@ def test_cutoff_far_field(yk, ctx, dense_cache):
         assert np.abs(y - A @ sig).max() <= 20 * tol * np.abs(sig).max() + 1e-13
         y32 = g.yk_matvec(sig, yk.YK_MIXED)
         assert rel(y32, A @ sig) < 1e-6
+        # normal derivative: FP64 tiles, expansions and FP32 far pairs all in play
+        for prec in (yk.YK_FP64, yk.YK_MIXED):
+            un = g.yk_normal_derivative(sig, prec)
+            assert np.abs(un - Gn @ sig).max() <= 40 * tol * np.abs(sig).max() / wl.rho + 1e-12
         g.close()
     g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF,
                                                precision=yk.YK_MIXED, gmres_tol=1e-12))
