@@ -357,40 +357,43 @@ __global__ void k_self_block(int npan, int ngl, int near_w, int n_near, double r
 }
 
 // In-place Gauss-Jordan inversion with partial pivoting of the n x n block
-// of shape blockIdx.x, on the augmented n x 2n matrix W (one CTA per shape).
+// of shape blockIdx.x, on the augmented n x 2n matrix W (one CTA per shape),
+// in FP32: the inverse only preconditions GMRES (it is applied as a fixed
+// linear operator, so its own rounding changes the convergence rate, not the
+// solution), and the block (1/2 I plus a compact part) is well conditioned.
 // Writes the inverse transposed (minv[j][i] = inv[i][j]) in FP64 and FP32.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, const double* A, double* W,
+__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, const double* A, float* W,
                                                        double* minv, float* minv32) {
     const int s = blockIdx.x;
     const double* As = A + (int64_t)s * n * n;
-    double* Ws = W + (int64_t)s * n * 2 * n;
+    float* Ws = W + (int64_t)s * n * 2 * n;
     const int n2 = 2 * n;
-    extern __shared__ double fac[];            // n factors
-    __shared__ double red_v[32];
+    extern __shared__ float fac[];             // n factors
+    __shared__ float red_v[32];
     __shared__ int red_i[32];
     __shared__ int piv_row;
     for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
         const int r = e / n2, c = e % n2;
-        Ws[e] = (c < n) ? As[(int64_t)r * n + c] : (c - n == r ? 1.0 : 0.0);
+        Ws[e] = (c < n) ? (float)As[(int64_t)r * n + c] : (c - n == r ? 1.0f : 0.0f);
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
         // pivot: row r >= c with the largest |W[r][c]|
-        double best = -1.0;
+        float best = -1.0f;
         int bi = c;
         for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-            const double v = fabs(Ws[(int64_t)r * n2 + c]);
+            const float v = fabsf(Ws[(int64_t)r * n2 + c]);
             if (v > best) best = v, bi = r;
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
         }
         if ((threadIdx.x & 31) == 0) red_v[threadIdx.x >> 5] = best, red_i[threadIdx.x >> 5] = bi;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double bv = -1.0;
+            float bv = -1.0f;
             int b = c;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
                 if (red_v[w] > bv) bv = red_v[w], b = red_i[w];
@@ -400,27 +403,28 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(int n, const double* A, d
         const int pr = piv_row;
         if (pr != c)
             for (int col = threadIdx.x; col < n2; col += blockDim.x) {
-                const double t = Ws[(int64_t)c * n2 + col];
+                const float t = Ws[(int64_t)c * n2 + col];
                 Ws[(int64_t)c * n2 + col] = Ws[(int64_t)pr * n2 + col];
                 Ws[(int64_t)pr * n2 + col] = t;
             }
         __syncthreads();
-        const double inv_p = 1.0 / Ws[(int64_t)c * n2 + c];
+        const float inv_p = 1.0f / Ws[(int64_t)c * n2 + c];
         __syncthreads();
         for (int col = threadIdx.x; col < n2; col += blockDim.x) Ws[(int64_t)c * n2 + col] *= inv_p;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == c) ? 0.0 : Ws[(int64_t)r * n2 + c];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == c) ? 0.0f : Ws[(int64_t)r * n2 + c];
         __syncthreads();
         for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
             const int r = e / n2, col = e % n2;
-            if (fac[r] != 0.0) Ws[e] = fma(-fac[r], Ws[(int64_t)c * n2 + col], Ws[e]);
+            const float f = fac[r];
+            if (f != 0.0f) Ws[e] = fmaf(-f, Ws[(int64_t)c * n2 + col], Ws[e]);
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        const double v = Ws[(int64_t)i * n2 + n + j];
-        minv[(int64_t)s * n * n + (int64_t)j * n + i] = v;
-        minv32[(int64_t)s * n * n + (int64_t)j * n + i] = (float)v;
+        const float v = Ws[(int64_t)i * n2 + n + j];
+        minv[(int64_t)s * n * n + (int64_t)j * n + i] = (double)v;
+        minv32[(int64_t)s * n * n + (int64_t)j * n + i] = v;
     }
 }
 
@@ -448,13 +452,14 @@ int build_preconditioner(yk_geom* g) {
     cudaStream_t st = g->ctx->stream;
     const int npp = g->npp;
     const size_t nn = (size_t)npp * npp;
-    double *A = nullptr, *W = nullptr;
+    double* A = nullptr;
+    float* W = nullptr;
     YK_TRY(dev_alloc((void**)&A, sizeof(double) * nn * g->nshape, st));
-    YK_TRY(dev_alloc((void**)&W, sizeof(double) * 2 * nn * g->nshape, st));
+    YK_TRY(dev_alloc((void**)&W, sizeof(float) * 2 * nn * g->nshape, st));
     dim3 grid(npp, g->nshape);
     YK_LAUNCH(k_self_block, grid, 128, 0, st, g->npan, g->ngl, g->prm.near_width, g->n_near,
               g->prm.rho, g->d_shape_ab, g->d_glx, g->d_glw, g->d_cval, A);
-    YK_LAUNCH(k_gauss_jordan, g->nshape, 1024, sizeof(double) * npp, st, npp, A, W, g->d_minv,
+    YK_LAUNCH(k_gauss_jordan, g->nshape, 1024, sizeof(float) * npp, st, npp, A, W, g->d_minv,
               g->d_minv32);
     YK_TRY_CUDA(cudaGetLastError());
     dev_free(A, st);

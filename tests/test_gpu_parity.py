@@ -259,6 +259,48 @@ def test_errors_and_edge_cases(yk, ctx):
     assert g2.yk_eval_potential(s, np.zeros((0, 2))).size == 0
 
 
+def test_allocation_failure_is_an_error_not_a_fault(yk, ctx):
+    """Fault injection on the host side: a geometry whose Krylov basis cannot
+    fit in device memory (1001 x 2^28 doubles, ~2 TB) fails with
+    YK_ERR_NO_MEMORY, frees what it took, and the context keeps working."""
+    n_particles = (1 << 28) // 256
+    parts = np.zeros((n_particles, 6))
+    parts[:, 0] = 0
+    parts[:, 1] = (np.arange(n_particles) % 4096) * 3.0
+    parts[:, 2] = (np.arange(n_particles) // 4096) * 3.0
+    parts[:, 4] = parts[:, 5] = 1.0
+    wl = SMALL["disks5_pan9"]()
+    with pytest.raises(yk.YKError) as e:
+        yk.Geometry(ctx, parts, _params(yk, wl, n_panels=16, n_gl=16, gmres_restart=1000,
+                                        precond=yk.YK_PRECOND_NONE))
+    assert e.value.code == yk.YK_ERR_NO_MEMORY
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+    assert np.isfinite(g.yk_matvec(np.ones(g.n), yk.YK_FP64)).all()
+    g.close()
+
+
+def test_serving_failed_request_does_not_stop_others(yk):
+    """A corrupted request (overlapping particles) fails with
+    YK_ERR_BAD_GEOMETRY; requests around it complete."""
+    ctx = yk.Context(0)
+    good = W.small_system(3, 50, n_panels=8)
+    bad = np.array([[0, 0.0, 0.0, 0.0, 1.0, 1.0], [0, 0.5, 0.0, 0.0, 1.0, 1.0]])
+    ids = [ctx.yk_submit(good.particles, _params(yk, good)),
+           ctx.yk_submit(bad, _params(yk, good)),
+           ctx.yk_submit(good.particles, _params(yk, good))]
+    with pytest.raises(yk.YKError):
+        ctx.yk_drain()
+    r0 = ctx.yk_poll(ids[0], n_nodes=good.n_nodes, n_particles=3)
+    assert r0["status"] == yk.YK_REQ_DONE
+    with pytest.raises(yk.YKError) as e:
+        ctx.yk_poll(ids[1])
+    assert e.value.code == yk.YK_ERR_BAD_GEOMETRY
+    r2 = ctx.yk_poll(ids[2], n_nodes=good.n_nodes, n_particles=3)
+    assert r2["status"] == yk.YK_REQ_DONE
+    assert rel(r2["sigma"], r0["sigma"]) < 1e-12
+    ctx.close()
+
+
 def test_serving_alone_and_in_mix(yk):
     """Continuous batching: requests of different sizes, shapes and rho,
     submitted together (several in flight at once on different streams),
