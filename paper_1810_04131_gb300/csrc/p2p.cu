@@ -290,94 +290,92 @@ __device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB
     }
 }
 
-constexpr int F32V_NT = 4;                    // value kernel: targets per thread
-constexpr int F32V_TPB = TPB / F32V_NT;       // 64 threads, 256 targets per block
-
-// FP32 value kernel: four targets per thread (more independent FMA2 chains
-// to hide the special-function latency), packed source pairs.
 template <bool MASK>
-__global__ void __launch_bounds__(F32V_TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
-                                                      int ppc, float kscale, double skip_gap,
-                                                      double* __restrict__ partial) {
+__global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
+                                                     int ppc, float kscale, double skip_gap,
+                                                     double* __restrict__ partial) {
     __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
-    constexpr int NT = F32V_NT;
-    int64_t ti[NT];
-    bool act[NT];
-    float2 xi[NT];
-    int pt[NT], pan[NT];
-#pragma unroll
-    for (int k = 0; k < NT; ++k) {
-        ti[k] = blockIdx.x * (int64_t)TPB + threadIdx.x + k * F32V_TPB;
-        act[k] = ti[k] < G.n;
-        const int64_t ii = act[k] ? ti[k] : 0;
-        xi[k] = G.xi[ii];
-        pt[k] = (int)(ii / G.npp);
-        pan[k] = (int)(ii % G.npp) / G.ngl;
-    }
+    const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
+    const int64_t i1 = i0 + F32_TPB;
+    const bool act0 = i0 < G.n, act1 = i1 < G.n;
+    const int64_t ii0 = act0 ? i0 : 0, ii1 = act1 ? i1 : 0;
+    const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
+    const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
+    const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
     const float kpf = (float)(LOG2E / G.rho);          // log2(e) / rho
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;  // z <= 2 possible below
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
     const PolyRZ P;
-    double acc[NT];
-#pragma unroll
-    for (int k = 0; k < NT; ++k) acc[k] = 0.0;
+    double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
         const int64_t base = (int64_t)s * G.npp;
-        TargetF32 T[NT];
-        bool all_skip = true, any_slow = false;
-#pragma unroll
-        for (int k = 0; k < NT; ++k) {
-            target_setup(T[k], G, pt[k], s, xi[k], kpf, near_gap, MASK, skip_gap, pan[k]);
-            all_skip = all_skip && T[k].skip;
-            any_slow = any_slow || T[k].close || (MASK && T[k].skip);
-        }
+        TargetF32 T0, T1;
+        target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
+        target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
         // skip the source particle only when every thread of the block agrees
         // (a block-wide vote, reached by all threads), so barriers stay uniform
-        const bool block_skip = MASK ? __syncthreads_and(all_skip) : false;
+        const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
         if (block_skip) continue;
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
             const int npair = (cnt + 1) >> 1;
             __syncthreads();
-            stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
-            __syncthreads();
-            float r[NT];
+            for (int m = threadIdx.x; m < npair; m += F32_TPB) {
+                float xs[2], ys[2], gx[2], gy[2];
 #pragma unroll
-            for (int k = 0; k < NT; ++k) r[k] = 0.0f;
-            if (!any_slow) {
-                float2 TX[NT], TY[NT], a[NT];
-#pragma unroll
-                for (int k = 0; k < NT; ++k) {
-                    TX[k] = make_float2(T[k].TX, T[k].TX);
-                    TY[k] = make_float2(T[k].TY, T[k].TY);
-                    a[k] = make_float2(0.0f, 0.0f);
+                for (int h = 0; h < 2; ++h) {
+                    const int q = 2 * m + h;
+                    if (q < cnt) {
+                        const int64_t j = base + jb + q;
+                        const float2 x = G.xi[j];
+                        const double ws = G.w[j] * sigma[j];
+                        xs[h] = -kpf * x.x;
+                        ys[h] = -kpf * x.y;
+                        gx[h] = (float)(ws * G.nx[j]);
+                        gy[h] = (float)(ws * G.ny[j]);
+                    } else {       // padding: a far, weightless source
+                        xs[h] = 1.0e6f;
+                        ys[h] = 0.0f;
+                        gx[h] = 0.0f;
+                        gy[h] = 0.0f;
+                    }
                 }
+                srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
+                srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
+            }
+            __syncthreads();
+            float r0 = 0.0f, r1 = 0.0f;
+            if (!T0.close && !T1.close && !(MASK && (T0.skip || T1.skip))) {
+                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
+                float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+#pragma unroll 2
                 for (int m = 0; m < npair; ++m) {
                     const float4 A = srcA[m], B = srcB[m];
-#pragma unroll
-                    for (int k = 0; k < NT; ++k) a[k] = far2(TX[k], TY[k], A, B, P, a[k]);
+                    a0 = far2(TX0, TY0, A, B, P, a0);
+                    a1 = far2(TX1, TY1, A, B, P, a1);
                 }
-#pragma unroll
-                for (int k = 0; k < NT; ++k) r[k] = a[k].x + a[k].y;
+                r0 = a0.x + a0.y;
+                r1 = a1.x + a1.y;
             } else {
                 for (int q = 0; q < cnt; ++q) {
                     const float4 S = src_scalar(srcA, srcB, q);
                     const int pq = (jb + q) / G.ngl;
-#pragma unroll
-                    for (int k = 0; k < NT; ++k)
-                        if (!(MASK && T[k].skip) &&
-                            !(T[k].own && is_near_panel(T[k].pan, pq, G.npan, G.near_w)))
-                            r[k] += PairF32::any(T[k].TX - S.x, T[k].TY - S.y, S.z, S.w);
+                    if (!(MASK && T0.skip) &&
+                        !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+                        r0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
+                    if (!(MASK && T1.skip) &&
+                        !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+                        r1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
                 }
             }
-#pragma unroll
-            for (int k = 0; k < NT; ++k) acc[k] += (double)r[k];
+            acc0 += (double)r0;
+            acc1 += (double)r1;
         }
     }
-#pragma unroll
-    for (int k = 0; k < NT; ++k)
-        if (act[k]) partial[blockIdx.y * G.n + ti[k]] = acc[k] * (double)kscale;
+    if (act0) partial[blockIdx.y * G.n + i0] = acc0 * (double)kscale;
+    if (act1) partial[blockIdx.y * G.n + i1] = acc1 * (double)kscale;
 }
 
 // FP32 normal derivative of the far field, two targets per thread, packed
@@ -929,7 +927,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
     double* extra = nullptr;
     int used_chunks = nchunk;
     if (prec == Prec::F32) {
-        YK_LAUNCH(k_p2p_f32<false>, grid, F32V_TPB, 0, st, G, sigma, ppc, (float)ks, 0.0,
+        YK_LAUNCH(k_p2p_f32<false>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks, 0.0,
                   g->ws.partial);
     } else {
         const int kind = (prec == Prec::F64) ? 2 : 0;
@@ -939,7 +937,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
         extra = g->ws.vec[5];
         YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
         if (prec == Prec::SPLIT) {
-            YK_LAUNCH(k_p2p_f32<true>, grid, F32V_TPB, 0, st, G, sigma, ppc, (float)ks,
+            YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks,
                       g->split_gap, g->ws.partial);
         } else {
             used_chunks = 0;
