@@ -2,8 +2,9 @@
 // solved (label, Eq. bie, forces and torques) by the library with
 // continuous batching.
 //
-// A fixed set of worker slots, each with its own CUDA stream and internal
-// context, takes requests from the arrival queue. A request is admitted when
+// A fixed set of worker slots, each with its own CUDA streams (a
+// high-priority one for small requests, a low-priority one for large ones)
+// and internal context, takes requests from the arrival queue. A request is admitted when
 // a slot is free and its device-memory estimate fits the budget left by the
 // requests in flight; requests that arrive while others run are admitted as
 // soon as a slot and memory free up, and their kernels overlap on the
@@ -115,14 +116,21 @@ static Request* admit(Server* s) {
     return nullptr;
 }
 
+// Requests up to this many nodes run on a high-priority stream, so that
+// their blocks are scheduled ahead of those of large requests sharing the GPU.
+constexpr int64_t SMALL_REQUEST_NODES = 65536;
+
 static void worker_main(Server* s) {
     cudaSetDevice(s->device);
     keep_pool_memory(s->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    cudaStream_t st_hi = nullptr, st_lo = nullptr;
+    cudaStreamCreateWithPriority(&st_hi, cudaStreamNonBlocking, prio_high);
+    cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, prio_low);
     yk_ctx ctx;
     ctx.device = s->device;
-    ctx.stream = st;
+    ctx.stream = st_lo;
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         Request* r = nullptr;
@@ -132,6 +140,8 @@ static void worker_main(Server* s) {
         s->mem_in_flight += r->mem_bytes;
         s->running++;
         lk.unlock();
+        const int64_t nodes = (int64_t)r->parts.size() * r->prm.n_panels * r->prm.n_gl;
+        ctx.stream = nodes <= SMALL_REQUEST_NODES ? st_hi : st_lo;
         const int rc = run_request(&ctx, r);
         lk.lock();
         r->t_done = Clock::now();
@@ -148,10 +158,12 @@ static void worker_main(Server* s) {
     }
     lk.unlock();
     while (!ctx.geoms.empty()) yk_destroy_geometry(*ctx.geoms.begin());
-    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(st_hi);
+    cudaStreamSynchronize(st_lo);
     if (ctx.h_status) cudaFreeHost(ctx.h_status);
     ctx.h_status = nullptr;
-    cudaStreamDestroy(st);
+    cudaStreamDestroy(st_hi);
+    cudaStreamDestroy(st_lo);
 }
 
 static int server_of(yk_ctx* ctx, Server** out) {
