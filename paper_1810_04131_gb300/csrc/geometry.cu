@@ -5,6 +5,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
+#include <utility>
 
 #include "bessel.cuh"
 #include "yk_internal.cuh"
@@ -356,76 +358,139 @@ __global__ void k_self_block(int npan, int ngl, int near_w, int n_near, double r
     }
 }
 
-// In-place Gauss-Jordan inversion with partial pivoting of the n x n block
-// of shape blockIdx.x, on the augmented n x 2n matrix W (one CTA per shape),
-// in FP32: the inverse only preconditions GMRES (it is applied as a fixed
-// linear operator, so its own rounding changes the convergence rate, not the
-// solution), and the block (1/2 I plus a compact part) is well conditioned.
-// Writes the inverse transposed (minv[j][i] = inv[i][j]) in FP64 and FP32.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, const double* A, float* W,
-                                                       double* minv, float* minv32) {
+// Inverse of the self block by the Newton-Schulz (hyperpower, order 2)
+// iteration X <- X (2I - A X) (G. Schulz, ZAMM 13, 1933), in FP32. The
+// inverse only preconditions GMRES: it is applied as a fixed linear operator,
+// so its rounding changes the convergence rate, not the solution. Starting
+// from X0 = A^T / (|A|_1 |A|_inf), every singular value of A X0 lies in
+// (0, 1], and each step maps s -> s (2 - s): small singular values double
+// until they near 1, then the residual I - A X squares. The block (1/2 I plus
+// a compact part) is well conditioned, so this takes about ten steps, each two
+// batched n x n GEMMs spread over many SMs.
+
+// Column and row sums of |A| (FP64 block -> FP32 copy), one CTA per shape:
+// scale[s] = 1 / (max column sum * max row sum).
+__global__ void k_ns_setup(int n, const double* __restrict__ A, float* __restrict__ A32,
+                           float* __restrict__ scale) {
     const int s = blockIdx.x;
     const double* As = A + (int64_t)s * n * n;
-    float* Ws = W + (int64_t)s * n * 2 * n;
-    const int n2 = 2 * n;
-    extern __shared__ float fac[];             // n factors
-    __shared__ float red_v[32];
-    __shared__ int red_i[32];
-    __shared__ int piv_row;
-    for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
-        const int r = e / n2, c = e % n2;
-        Ws[e] = (c < n) ? (float)As[(int64_t)r * n + c] : (c - n == r ? 1.0f : 0.0f);
+    float* Bs = A32 + (int64_t)s * n * n;
+    double cmax = 0.0, rmax = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double c = 0.0, r = 0.0;
+        for (int i = 0; i < n; ++i) {
+            c += fabs(As[(int64_t)i * n + j]);
+            r += fabs(As[(int64_t)j * n + i]);
+        }
+        cmax = fmax(cmax, c);
+        rmax = fmax(rmax, r);
     }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Bs[e] = (float)As[e];
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = cmax, red[1][threadIdx.x >> 5] = rmax;
     __syncthreads();
-    for (int c = 0; c < n; ++c) {
-        // pivot: row r >= c with the largest |W[r][c]|
-        float best = -1.0f;
-        int bi = c;
-        for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-            const float v = fabsf(Ws[(int64_t)r * n2 + c]);
-            if (v > best) best = v, bi = r;
+    if (threadIdx.x == 0) {
+        double c = 0.0, r = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) c = fmax(c, red[0][w]), r = fmax(r, red[1][w]);
+        scale[s] = (float)(1.0 / (c * r));
+    }
+}
+
+// X0 = scale * A^T (FP32).
+__global__ void k_ns_init(int n, const float* __restrict__ A32, const float* __restrict__ scale,
+                          float* __restrict__ X) {
+    const int s = blockIdx.y;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * n) return;
+    const int i = (int)(e / n), j = (int)(e % n);
+    X[(int64_t)s * n * n + e] = scale[s] * A32[(int64_t)s * n * n + (int64_t)j * n + i];
+}
+
+// Batched C_s = L_s R_s for n x n row-major FP32 matrices (blockIdx.z = s),
+// 64 x 64 output tile per CTA, 16-deep k slices staged in shared memory, each
+// of 256 threads accumulating a 4 x 4 block (rows ty + 16a, columns tx + 16b).
+// RESID: the product is T = A X; the epilogue stores 2I - T and raises
+// *err_bits to the largest |(I - T)_ij| (non-negative floats order like their
+// bit patterns).
+constexpr int NS_TILE = 64, NS_K = 16;
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_ns_gemm(int n, const float* __restrict__ L,
+                                                 const float* __restrict__ R,
+                                                 float* __restrict__ C,
+                                                 unsigned* __restrict__ err_bits) {
+    __shared__ float Ls[NS_K][NS_TILE + 4];
+    __shared__ float Rs[NS_K][NS_TILE + 4];
+    const int64_t off = (int64_t)blockIdx.z * n * n;
+    L += off;
+    R += off;
+    C += off;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.y * NS_TILE, col0 = blockIdx.x * NS_TILE;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    for (int k0 = 0; k0 < n; k0 += NS_K) {
+        for (int e = threadIdx.x; e < NS_TILE * NS_K; e += 256) {
+            const int r = e / NS_K, k = e % NS_K;
+            const int gr = row0 + r, gk = k0 + k;
+            Ls[k][r] = (gr < n && gk < n) ? L[(int64_t)gr * n + gk] : 0.0f;
+            const int kk = e / NS_TILE, c = e % NS_TILE;
+            const int gk2 = k0 + kk, gc = col0 + c;
+            Rs[kk][c] = (gk2 < n && gc < n) ? R[(int64_t)gk2 * n + gc] : 0.0f;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
-        }
-        if ((threadIdx.x & 31) == 0) red_v[threadIdx.x >> 5] = best, red_i[threadIdx.x >> 5] = bi;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float bv = -1.0f;
-            int b = c;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-                if (red_v[w] > bv) bv = red_v[w], b = red_i[w];
-            piv_row = b;
+#pragma unroll
+        for (int k = 0; k < NS_K; ++k) {
+            float l[4], r[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) l[a] = Ls[k][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) r[b] = Rs[k][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(l[a], r[b], acc[a][b]);
         }
         __syncthreads();
-        const int pr = piv_row;
-        if (pr != c)
-            for (int col = threadIdx.x; col < n2; col += blockDim.x) {
-                const float t = Ws[(int64_t)c * n2 + col];
-                Ws[(int64_t)c * n2 + col] = Ws[(int64_t)pr * n2 + col];
-                Ws[(int64_t)pr * n2 + col] = t;
+    }
+    float emax = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = row0 + ty + 16 * a, j = col0 + tx + 16 * b;
+            if (i < n && j < n) {
+                float v = acc[a][b];
+                if (RESID) {
+                    const float res = (i == j ? 1.0f : 0.0f) - v;
+                    emax = fmaxf(emax, fabsf(res));
+                    v = (i == j ? 1.0f : 0.0f) + res;
+                }
+                C[(int64_t)i * n + j] = v;
             }
-        __syncthreads();
-        const float inv_p = 1.0f / Ws[(int64_t)c * n2 + c];
-        __syncthreads();
-        for (int col = threadIdx.x; col < n2; col += blockDim.x) Ws[(int64_t)c * n2 + col] *= inv_p;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) fac[r] = (r == c) ? 0.0f : Ws[(int64_t)r * n2 + c];
-        __syncthreads();
-        for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
-            const int r = e / n2, col = e % n2;
-            const float f = fac[r];
-            if (f != 0.0f) Ws[e] = fmaf(-f, Ws[(int64_t)c * n2 + col], Ws[e]);
         }
-        __syncthreads();
+    if (RESID) {
+        for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(err_bits, __float_as_uint(emax));
     }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        const float v = Ws[(int64_t)i * n2 + n + j];
-        minv[(int64_t)s * n * n + (int64_t)j * n + i] = (double)v;
-        minv32[(int64_t)s * n * n + (int64_t)j * n + i] = v;
-    }
+}
+
+// minv[s][j][i] = X[s][i][j] in FP64 and FP32.
+__global__ void k_ns_store(int n, const float* __restrict__ X, double* __restrict__ minv,
+                           float* __restrict__ minv32) {
+    const int s = blockIdx.y;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * n) return;
+    const int j = (int)(e / n), i = (int)(e % n);
+    const float v = X[(int64_t)s * n * n + (int64_t)i * n + j];
+    minv[(int64_t)s * n * n + e] = (double)v;
+    minv32[(int64_t)s * n * n + e] = v;
 }
 
 // y_P = inv(block of P's shape) x_P, one CTA per particle.
@@ -447,24 +512,71 @@ __global__ void k_block_apply(int np, int npp, const int* __restrict__ shape_of,
     }
 }
 
+// Newton-Schulz steps: stop once the largest entry of I - A X is below
+// NS_TOL, or once it is below 1e-3 and has stopped shrinking (the FP32
+// floor). A block whose residual does not fall below 1/2 is singular to
+// working precision.
+constexpr int NS_MAX_STEPS = 100;
+constexpr float NS_TOL = 1e-6f;
+
 int build_preconditioner(yk_geom* g) {
     if (g->prm.precond != YK_PRECOND_BLOCK) return YK_OK;
     cudaStream_t st = g->ctx->stream;
-    const int npp = g->npp;
-    const size_t nn = (size_t)npp * npp;
+    double* hs = host_status(g->ctx);
+    if (!hs) return YK_ERR_NO_MEMORY;
+    const int n = g->npp, ns = g->nshape;
+    const size_t nn = (size_t)n * n;
     double* A = nullptr;
     float* W = nullptr;
-    YK_TRY(dev_alloc((void**)&A, sizeof(double) * nn * g->nshape, st));
-    YK_TRY(dev_alloc((void**)&W, sizeof(float) * 2 * nn * g->nshape, st));
-    dim3 grid(npp, g->nshape);
-    YK_LAUNCH(k_self_block, grid, 128, 0, st, g->npan, g->ngl, g->prm.near_width, g->n_near,
-              g->prm.rho, g->d_shape_ab, g->d_glx, g->d_glw, g->d_cval, A);
-    YK_LAUNCH(k_gauss_jordan, g->nshape, 1024, sizeof(float) * npp, st, npp, A, W, g->d_minv,
-              g->d_minv32);
-    YK_TRY_CUDA(cudaGetLastError());
+    YK_TRY(dev_alloc((void**)&A, sizeof(double) * nn * ns, st));
+    int rc = dev_alloc((void**)&W, sizeof(float) * (4 * nn * ns + ns + 32), st);
+    if (rc != YK_OK) {
+        dev_free(A, st);
+        return rc;
+    }
+    float* A32 = W;
+    float* X = W + nn * ns;
+    float* T = W + 2 * nn * ns;
+    float* Xn = W + 3 * nn * ns;
+    float* scale = W + 4 * nn * ns;
+    unsigned* err_bits = reinterpret_cast<unsigned*>(scale + ns);
+    YK_LAUNCH(k_self_block, dim3(n, ns), 128, 0, st, g->npan, g->ngl, g->prm.near_width,
+              g->n_near, g->prm.rho, g->d_shape_ab, g->d_glx, g->d_glw, g->d_cval, A);
+    YK_LAUNCH(k_ns_setup, ns, 256, 0, st, n, A, A32, scale);
+    const dim3 eg((unsigned)((nn + 255) / 256), ns);
+    YK_LAUNCH(k_ns_init, eg, 256, 0, st, n, A32, scale, X);
+    const dim3 gg((n + NS_TILE - 1) / NS_TILE, (n + NS_TILE - 1) / NS_TILE, ns);
+    float prev = INFINITY, err = INFINITY;
+    for (int it = 0; it < NS_MAX_STEPS; ++it) {
+        // T = 2I - A X, recording max |I - A X|; then X <- X T
+        if (cudaMemsetAsync(err_bits, 0, sizeof(unsigned), st) != cudaSuccess) {
+            rc = YK_ERR_CUDA;
+            break;
+        }
+        YK_LAUNCH(k_ns_gemm<true>, gg, 256, 0, st, n, A32, X, T, err_bits);
+        unsigned bits = 0;
+        if (cudaMemcpyAsync(hs, err_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = YK_ERR_CUDA;
+            break;
+        }
+        std::memcpy(&bits, hs, sizeof(unsigned));
+        std::memcpy(&err, &bits, sizeof(float));
+        if (!(err == err)) break;                                   // NaN: singular
+        if (err < NS_TOL || (err < 1e-3f && err > 0.25f * prev)) break;
+        YK_LAUNCH(k_ns_gemm<false>, gg, 256, 0, st, n, X, T, Xn, nullptr);
+        std::swap(X, Xn);
+        prev = err;
+    }
+    if (rc == YK_OK && !(err < 0.5f)) rc = YK_ERR_BAD_GEOMETRY;
+    if (rc == YK_OK) {
+        YK_LAUNCH(k_ns_store, eg, 256, 0, st, n, X, g->d_minv, g->d_minv32);
+        if (cudaGetLastError() != cudaSuccess) rc = YK_ERR_CUDA;
+    }
     dev_free(A, st);
     dev_free(W, st);
-    return YK_OK;
+    return rc;
 }
 
 int apply_preconditioner(yk_geom* g, const double* x, double* y, bool fp32) {
