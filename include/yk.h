@@ -70,6 +70,16 @@ extern "C" {
                                  bounded below cutoff_tol * max|sigma| are
                                  left out (cut-off localisation, Section 3.3);
                                  the K1 kernel decays like exp(-r/rho)        */
+#define YK_FARFIELD_FMM    2  /* YK_MIXED: the inner (FP32) operator's far
+                                 field by a uniform-quadtree fast multipole
+                                 method (multipole/local expansions of order
+                                 fmm_order by Graf's addition theorem, the
+                                 Yukawa form of Eq. graf-addition); particles
+                                 in leaves at most two boxes apart interact
+                                 directly. The refinement residuals, the
+                                 normal derivative and YK_FP64 use the
+                                 YK_FARFIELD_CUTOFF operator, so results keep
+                                 the accuracy of that operator               */
 
 /* Dirichlet data generators; theta is the polar angle of x - a_i measured
  * from the director d_i = (cos phi_i, sin phi_i) (Section 2.1).           */
@@ -115,7 +125,7 @@ typedef struct {
     double gmres_tol;      /* relative residual ||f - A sigma|| / ||f||; 1e-10 */
     double inner_tol;      /* YK_MIXED: inner (FP32) GMRES tolerance; 1e-6     */
     int32_t max_refine;    /* YK_MIXED: refinement steps; default 8            */
-    int32_t farfield;      /* YK_FARFIELD_DENSE or YK_FARFIELD_CUTOFF          */
+    int32_t farfield;      /* YK_FARFIELD_DENSE, _CUTOFF or _FMM; default DENSE */
     double split_tol;      /* YK_MIXED refinement residual: a source particle is
                               evaluated in FP32 only where its FP32 error bound
                               is below split_tol * max|sigma|; default 1e-14.
@@ -130,7 +140,14 @@ typedef struct {
     double cutoff_tol;     /* YK_FARFIELD_CUTOFF: a source particle is dropped
                               for a target particle when its contribution
                               (value or normal derivative) is bounded below
-                              cutoff_tol * max|sigma|; default 1e-15         */
+                              cutoff_tol * max|sigma|; default 1e-15 (also
+                              bounds the reach of YK_FARFIELD_FMM)           */
+    int32_t fmm_order;     /* YK_FARFIELD_FMM: expansion order p, terms
+                              |n| <= p, 2..30; default 12                    */
+    int32_t pad2_;
+    double fmm_leaf;       /* YK_FARFIELD_FMM: leaf box side; 0 (default)
+                              chooses it by timing the admissible leaf sizes
+                              on the first FMM operator application          */
 } yk_params;
 
 /* Solve statistics (all host memory). */

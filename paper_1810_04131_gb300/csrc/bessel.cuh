@@ -90,6 +90,57 @@ __device__ __forceinline__ void k01(double z, double& k0, double& k1) {
     k1 = e * p1_large(t);
 }
 
+// 1/d for an integer-valued d in [1, 2^24): the FP32 rcp.approx estimate
+// refined by two Newton-Raphson steps r <- r + r (1 - d r) (each step
+// doubles the number of correct bits: 2^-23 -> 2^-46 -> FP64 rounding).
+__device__ __forceinline__ double recip_int(double d) {
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)d));
+    double r = (double)rf;
+    r = fma(r, fma(-d, r, 1.0), r);
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
+// 1/n! for n = 0..63 (constant-initialised at compile time)
+constexpr double inv_fact_c(int n) {
+    double r = 1.0;
+    for (int k = 2; k <= n; ++k) r /= k;
+    return r;
+}
+#define YK_IF4(n) inv_fact_c(n), inv_fact_c(n + 1), inv_fact_c(n + 2), inv_fact_c(n + 3)
+static __constant__ double c_inv_fact[64] = {
+    YK_IF4(0),  YK_IF4(4),  YK_IF4(8),  YK_IF4(12), YK_IF4(16), YK_IF4(20), YK_IF4(24), YK_IF4(28),
+    YK_IF4(32), YK_IF4(36), YK_IF4(40), YK_IF4(44), YK_IF4(48), YK_IF4(52), YK_IF4(56), YK_IF4(60)};
+#undef YK_IF4
+
+// I_n(x) and I_{n-1}(x), 1 <= n <= 63, from one ascending series (DLMF 10.25.2):
+// with t_k = (x/2)^{n+2k} / (k! (n+k)!), I_n = sum t_k and
+// I_{n-1} = (2/x) sum (n+k) t_k.
+__device__ inline void bessel_i_pair(int n, double x, double& In, double& In1) {
+    const double h = 0.5 * x, q = h * h;
+    double hn = 1.0;
+    for (int k = 0; k < n; ++k) hn *= h;
+    double t = hn * c_inv_fact[n];
+    double s1 = t, s2 = n * t;
+    for (int k = 1; k < 200; ++k) {
+        t *= q * recip_int((double)k * (double)(n + k));
+        s1 += t;
+        s2 = fma((double)(n + k), t, s2);
+        if (t < 1e-17 * s1) break;
+    }
+    In = s1;
+    In1 = s2 / h;
+}
+
+// I_0..I_top(x), 1 <= top <= 63, x > 0: the top two orders from the series,
+// then the backward recurrence I_{k-1} = I_{k+1} + (2k/x) I_k (stable
+// downwards).
+__device__ inline void bessel_i_down(int top, double x, double* I) {
+    bessel_i_pair(top, x, I[top], I[top - 1]);
+    const double xi2 = 2.0 / x;
+    for (int k = top - 1; k >= 1; --k) I[k - 1] = fma(k * xi2, I[k], I[k + 1]);
+}
+
 // I_n(z) for n = 0..nmax (ascending series, DLMF 10.25.2); small to moderate z.
 __device__ inline double bessel_i_series(int n, double z) {
     const double q = 0.25 * z * z;

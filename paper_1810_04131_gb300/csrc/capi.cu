@@ -129,7 +129,11 @@ static int check_params(const yk_params* p) {
     if (p->precision != YK_FP64 && p->precision != YK_MIXED) return YK_ERR_ARG;
     if (!(p->gmres_tol > 0.0) || !(p->inner_tol > 0.0) || p->inner_tol >= 1.0) return YK_ERR_ARG;
     if (p->max_refine < 1) return YK_ERR_ARG;
-    if (p->farfield != YK_FARFIELD_DENSE && p->farfield != YK_FARFIELD_CUTOFF) return YK_ERR_ARG;
+    if (p->farfield != YK_FARFIELD_DENSE && p->farfield != YK_FARFIELD_CUTOFF &&
+        p->farfield != YK_FARFIELD_FMM)
+        return YK_ERR_ARG;
+    if (p->fmm_order < 2 || p->fmm_order > FMM_PMAX) return YK_ERR_ARG;
+    if (!(p->fmm_leaf >= 0.0) || !isfinite(p->fmm_leaf)) return YK_ERR_ARG;
     if (!(p->cutoff_tol > 0.0)) return YK_ERR_ARG;
     if (p->precond != YK_PRECOND_NONE && p->precond != YK_PRECOND_BLOCK) return YK_ERR_ARG;
     if (p->precond == YK_PRECOND_BLOCK && (int64_t)p->n_panels * p->n_gl > 1024) return YK_ERR_ARG;
@@ -231,6 +235,8 @@ int yk_default_params(yk_params* p) {
     p->grad_split_tol = 1e-13;
     p->cutoff_tol = 1e-15;
     p->precond = YK_PRECOND_BLOCK;
+    p->fmm_order = 12;
+    p->fmm_leaf = 0.0;
     return YK_OK;
 }
 
@@ -286,15 +292,18 @@ int yk_destroy_geometry(yk_geom* g) {
     for (auto& L : g->lists) dev_free(L.d, st);
     dev_free(g->nbr_off, st);
     dev_free(g->nbr, st);
+    fmm_free(g);
     for (auto& B : g->bands) {
         dev_free(B.off, st);
         dev_free(B.idx, st);
     }
     dev_free(g->d_counts, st);
     dev_free(g->d_mpole, st);
+    dev_free(g->d_local, st);
     void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
-                    g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w, g->d_minv, g->d_minv32};
+                    g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w, g->d_minv, g->d_minv32,
+                    g->d_self, g->d_self_grad};
     for (void* b : bufs) dev_free(b, st);
     cudaStreamSynchronize(st);
     delete g;
@@ -381,8 +390,11 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     g->max_perimeter = perim;
     g->split_gap = split_gap(prm->rho, perim, rmax, prm->split_tol);
     g->split_gap_grad = split_gap(prm->rho, perim, rmax, prm->grad_split_tol);
-    g->cutoff_gap = (prm->farfield == YK_FARFIELD_CUTOFF)
+    g->cutoff_gap = (prm->farfield != YK_FARFIELD_DENSE)
                         ? cutoff_gap(prm->rho, perim, prm->cutoff_tol) : INFINITY;
+    // the FMM far field serves the FP32 inner operator (pairs carry ~1e-7
+    // relative error), so it reaches only as far as 1e-10 of max|sigma|
+    g->fmm_gap = cutoff_gap(prm->rho, perim, std::max(prm->cutoff_tol, FMM_REACH_TOL));
     // the FP64 tiles of the split operators stay inside the cut-off
     g->split_gap = std::min(g->split_gap, g->cutoff_gap);
     g->split_gap_grad = std::min(g->split_gap_grad, g->cutoff_gap);
@@ -400,6 +412,7 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     ALLOC(d_counter, 1);
     ALLOC(d_counts, n_particles);
     ALLOC(d_mpole, (size_t)n_particles * EXPANSION_TERMS);
+    ALLOC(d_local, (size_t)n_particles * EXPANSION_TERMS);
     ALLOC(d_shape_of, n_particles);
     ALLOC(d_shape_ab, g->nshape);
     ALLOC(d_x, N);
@@ -411,6 +424,11 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     ALLOC(d_xi, N);
     ALLOC(d_cval, (size_t)g->nshape * npp * rowlen);
     ALLOC(d_cgrad, (size_t)g->nshape * npp * rowlen);
+    g->use_self = npp <= SELF_BLOCK_MAX_NODES;
+    if (g->use_self) {
+        ALLOC(d_self, (size_t)g->nshape * npp * npp);
+        ALLOC(d_self_grad, (size_t)g->nshape * npp * npp);
+    }
     ALLOC(d_glx, g->ngl);
     ALLOC(d_glw, g->ngl);
     ALLOC(d_interp, (size_t)os * g->ngl * g->ngl);

@@ -29,15 +29,6 @@ namespace yk {
 constexpr int EXP_ORDER = EXPANSION_TERMS - 1;   // terms |n|, |m| <= EXP_ORDER
 constexpr int EXP_N = EXPANSION_TERMS;
 
-// I_0..I_{EXP_ORDER+1}(x) for 0 < x (series for the top two orders, then the
-// backward recurrence I_{k-1} = I_{k+1} + (2k/x) I_k, stable downwards).
-__device__ inline void bessel_i_all(double x, double* I) {
-    const int top = EXP_ORDER + 1;
-    I[top] = bessel_i_series(top, x);
-    I[top - 1] = bessel_i_series(top - 1, x);
-    for (int k = top - 1; k >= 1; --k) I[k - 1] = I[k + 1] + (2.0 * k / x) * I[k];
-}
-
 // P2M: one warp per particle.
 __global__ void k_p2m(GeomView G, const double* __restrict__ sigma, double2* __restrict__ M) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -45,29 +36,29 @@ __global__ void k_p2m(GeomView G, const double* __restrict__ sigma, double2* __r
     if (warp >= G.np) return;
     const int p = warp;
     const d4 c = G.part[p];
-    const double rho = G.rho;
+    const double rinv = 1.0 / G.rho;
     double mre[EXP_N], mim[EXP_N], I[EXP_N + 1];
     for (int n = 0; n < EXP_N; ++n) mre[n] = mim[n] = 0.0;
     for (int l = lane; l < G.npp; l += 32) {
         const int64_t j = (int64_t)p * G.npp + l;
         const double ex = G.x[j] - c.x, ey = G.y[j] - c.y;
         const double s = sqrt(ex * ex + ey * ey);
-        const double esx = ex / s, esy = ey / s;
+        const double sinv = 1.0 / s;
+        const double esx = ex * sinv, esy = ey * sinv;
         const double a_s = G.nx[j] * esx + G.ny[j] * esy;       // nu . e_s
         const double a_p = -G.nx[j] * esy + G.ny[j] * esx;      // nu . e_phi
         const double ws = G.w[j] * sigma[j];
-        bessel_i_all(s / rho, I);
-        double cph = esx, sph = esy;                             // e^{i phi}
+        bessel_i_down(EXP_ORDER + 1, s * rinv, I);
         double cn = 1.0, sn = 0.0;                               // e^{i n phi}
         for (int n = 0; n <= EXP_ORDER; ++n) {
             const double ip = (n == 0) ? I[1] : 0.5 * (I[n - 1] + I[n + 1]);
-            const double ar = a_s * ip / rho;                    // real part of the bracket
-            const double ai = -n * a_p * I[n] / s;               // imaginary part
+            const double ar = a_s * ip * rinv;                   // real part of the bracket
+            const double ai = -n * a_p * I[n] * sinv;            // imaginary part
             // e^{-i n phi} (ar + i ai) = (cn - i sn)(ar + i ai)
             mre[n] += ws * (cn * ar + sn * ai);
             mim[n] += ws * (cn * ai - sn * ar);
-            const double c2 = cn * cph - sn * sph;
-            sn = sn * cph + cn * sph;
+            const double c2 = cn * esx - sn * esy;
+            sn = sn * esx + cn * esy;
             cn = c2;
         }
     }
@@ -81,99 +72,114 @@ __global__ void k_p2m(GeomView G, const double* __restrict__ sigma, double2* __r
     }
 }
 
-// M2L from the band neighbours of target particle Q, then L2P (value or
-// normal derivative), added to out[]. One CTA per target particle.
-template <bool GRAD>
-__global__ void __launch_bounds__(256) k_m2l_l2p(GeomView G, const double2* __restrict__ M,
-                                                 const int* __restrict__ off,
-                                                 const int* __restrict__ nbr,
-                                                 double* __restrict__ out) {
-    const int q = blockIdx.x;
+// M2L from the band neighbours of each target particle Q into its local
+// coefficients L[Q][m], m = 0..EXP_ORDER (written; zero without neighbours).
+// One warp per target particle; lane t handles m = t and m = t + 32.
+__global__ void __launch_bounds__(128) k_band_m2l(GeomView G, const double2* __restrict__ M,
+                                                  const int* __restrict__ off,
+                                                  const int* __restrict__ nbr,
+                                                  double2* __restrict__ Lout) {
+    __shared__ double Ksh[4][2 * EXP_ORDER + 1];       // K_k(|D|/rho), k = 0..2p
+    __shared__ double2 Esh[4][3 * EXP_ORDER + 1];      // e^{i k psi}, k = -p..2p
+    __shared__ double2 Msh[4][EXP_N];
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (q >= G.np) return;                                // warp-uniform
+    double* Kr = Ksh[wib];
+    double2* eps = Esh[wib];
+    double2* Ms = Msh[wib];
     const int k0 = off[q], k1 = off[q + 1];
-    if (k0 == k1) return;                       // uniform: no band neighbours
-    __shared__ double Kr[2 * EXP_ORDER + 1];    // K_k(|D|/rho), k = 0..2p
-    __shared__ double2 eps[3 * EXP_ORDER + 1];  // e^{i k psi}, k = -p..2p
-    __shared__ double2 Ms[EXP_N];
-    __shared__ double2 L[EXP_N];
     const double rho = G.rho;
     const d4 cq = G.part[q];
-    if (threadIdx.x < EXP_N) L[threadIdx.x] = make_double2(0.0, 0.0);
+    double lr0 = 0.0, li0 = 0.0, lr1 = 0.0, li1 = 0.0;   // m = lane, lane + 32
     for (int k = k0; k < k1; ++k) {
         const int p = nbr[k];
         const d4 cp = G.part[p];
         const double Dx = cq.x - cp.x, Dy = cq.y - cp.y;
-        const double Dn = sqrt(Dx * Dx + Dy * Dy);
+        const double z = sqrt(Dx * Dx + Dy * Dy) / rho;
         const double psi = atan2(Dy, Dx);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double z = Dn / rho;
+        __syncwarp();
+        if (lane == 0) {
             double a, b;
             k01(z, a, b);
             Kr[0] = a;
             Kr[1] = b;
-            for (int n = 1; n < 2 * EXP_ORDER; ++n) Kr[n + 1] = Kr[n - 1] + (2.0 * n / z) * Kr[n];
+            const double zi2 = 2.0 / z;
+            for (int n = 1; n < 2 * EXP_ORDER; ++n) Kr[n + 1] = fma(n * zi2, Kr[n], Kr[n - 1]);
         }
-        for (int t = threadIdx.x; t < 3 * EXP_ORDER + 1; t += blockDim.x) {
+        for (int t = lane; t < 3 * EXP_ORDER + 1; t += 32) {
             double s_, c_;
             sincos((t - EXP_ORDER) * psi, &s_, &c_);
             eps[t] = make_double2(c_, s_);
         }
-        if (threadIdx.x < EXP_N) Ms[threadIdx.x] = M[(int64_t)p * EXP_N + threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x < EXP_N) {
-            const int m = threadIdx.x;
+        for (int t = lane; t < EXP_N; t += 32) Ms[t] = M[(int64_t)p * EXP_N + t];
+        __syncwarp();
+        for (int h = 0; h < 2; ++h) {
+            const int m = lane + 32 * h;
+            if (m > EXP_ORDER) break;
             double lr = 0.0, li = 0.0;
             for (int n = -EXP_ORDER; n <= EXP_ORDER; ++n) {
                 const double2 Mn = n >= 0 ? Ms[n] : make_double2(Ms[-n].x, -Ms[-n].y);
                 const int kk = n + m;                            // in [-p, 2p]
                 const double Kv = Kr[kk < 0 ? -kk : kk];
                 const double2 e = eps[kk + EXP_ORDER];
-                // M_n * K * e^{i (n+m) psi}
-                lr += Kv * (Mn.x * e.x - Mn.y * e.y);
+                lr += Kv * (Mn.x * e.x - Mn.y * e.y);            // M_n K e^{i (n+m) psi}
                 li += Kv * (Mn.x * e.y + Mn.y * e.x);
             }
             const double sg = (m & 1) ? -1.0 : 1.0;
-            L[m].x += sg * lr;
-            L[m].y += sg * li;
+            if (h == 0) lr0 += sg * lr, li0 += sg * li;
+            else lr1 += sg * lr, li1 += sg * li;
         }
     }
-    __syncthreads();
-    // L2P
+    Lout[(int64_t)q * EXP_N + lane] = make_double2(lr0, li0);
+    if (lane + 32 <= EXP_ORDER) Lout[(int64_t)q * EXP_N + lane + 32] = make_double2(lr1, li1);
+}
+
+// L2P: value or normal derivative of each node's particle local expansion,
+// added to out[] (particles without band neighbours are skipped).
+template <bool GRAD>
+__global__ void __launch_bounds__(128) k_band_l2p(GeomView G, const double2* __restrict__ Lin,
+                                                  const int* __restrict__ off,
+                                                  double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= G.n) return;
+    const int q = (int)(i / G.npp);
+    if (off[q] == off[q + 1]) return;
+    const double2* L = Lin + (int64_t)q * EXP_N;
+    const d4 cq = G.part[q];
+    const double rinv = 1.0 / G.rho;
+    const double vx = G.x[i] - cq.x, vy = G.y[i] - cq.y;
+    const double r = sqrt(vx * vx + vy * vy);
+    const double r_inv = 1.0 / r;
+    const double erx = vx * r_inv, ery = vy * r_inv;
     double I[EXP_N + 1];
-    for (int l = threadIdx.x; l < G.npp; l += blockDim.x) {
-        const int64_t i = (int64_t)q * G.npp + l;
-        const double vx = G.x[i] - cq.x, vy = G.y[i] - cq.y;
-        const double r = sqrt(vx * vx + vy * vy);
-        const double erx = vx / r, ery = vy / r;
-        bessel_i_all(r / rho, I);
-        double nr = 0.0, nt = 0.0;
-        if (GRAD) {
-            nr = G.nx[i] * erx + G.ny[i] * ery;        // nu . e_r
-            nt = -G.nx[i] * ery + G.ny[i] * erx;       // nu . e_theta
-        }
-        double acc = 0.0;
-        double cm = 1.0, sm = 0.0;                     // e^{-i m theta} = cm - i sm... (cos, sin of m theta)
-        for (int m = 0; m <= EXP_ORDER; ++m) {
-            const double2 Lm = L[m];
-            // Re[L_m e^{-i m theta} X] with X real (value) or complex (gradient)
-            const double er = cm, ei = -sm;            // e^{-i m theta}
-            const double zr = Lm.x * er - Lm.y * ei, zi = Lm.x * ei + Lm.y * er;
-            double term;
-            if (!GRAD) {
-                term = zr * I[m];
-            } else {
-                const double ip = (m == 0) ? I[1] : 0.5 * (I[m - 1] + I[m + 1]);
-                const double xr = nr * ip / rho;       // X = nu.e_r I_m'/rho - i m nu.e_theta I_m/r
-                const double xi = -m * nt * I[m] / r;
-                term = zr * xr - zi * xi;
-            }
-            acc += (m == 0 ? 1.0 : 2.0) * term;
-            const double c2 = cm * erx - sm * ery;     // advance (cos, sin)(m theta)
-            sm = sm * erx + cm * ery;
-            cm = c2;
-        }
-        out[i] += acc / (2.0 * PI);
+    bessel_i_down(EXP_ORDER + 1, r * rinv, I);
+    double nr = 0.0, nt = 0.0;
+    if (GRAD) {
+        nr = G.nx[i] * erx + G.ny[i] * ery;        // nu . e_r
+        nt = -G.nx[i] * ery + G.ny[i] * erx;       // nu . e_theta
     }
+    double acc = 0.0;
+    double cm = 1.0, sm = 0.0;                     // (cos, sin)(m theta)
+    for (int m = 0; m <= EXP_ORDER; ++m) {
+        const double2 Lm = L[m];
+        // z = L_m e^{-i m theta}; Re[z X] with X real (value) or complex (gradient)
+        const double zr = Lm.x * cm + Lm.y * sm, zi = Lm.y * cm - Lm.x * sm;
+        double term;
+        if (!GRAD) {
+            term = zr * I[m];
+        } else {
+            const double ip = (m == 0) ? I[1] : 0.5 * (I[m - 1] + I[m + 1]);
+            const double xr = nr * ip * rinv;      // X = nu.e_r I_m'/rho - i m nu.e_theta I_m/r
+            const double xi = -m * nt * I[m] * r_inv;
+            term = zr * xr - zi * xi;
+        }
+        acc += (m == 0 ? 1.0 : 2.0) * term;
+        const double c2 = cm * erx - sm * ery;
+        sm = sm * erx + cm * ery;
+        cm = c2;
+    }
+    out[i] += acc / (2.0 * PI);
 }
 
 // Band lists per target particle: source particles P != Q with
@@ -265,12 +271,14 @@ int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad) {
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
     YK_LAUNCH(k_p2m, ceil_div((int64_t)g->np * 32, 128), 128, 0, st, G, sigma, g->d_mpole);
+    YK_LAUNCH(k_band_m2l, ceil_div((int64_t)g->np * 32, 128), 128, 0, st, G, g->d_mpole,
+              g->bands[kind].off, g->bands[kind].idx, g->d_local);
     if (grad)
-        YK_LAUNCH(k_m2l_l2p<true>, g->np, 256, 0, st, G, g->d_mpole, g->bands[kind].off,
-                  g->bands[kind].idx, out);
+        YK_LAUNCH(k_band_l2p<true>, ceil_div(g->n, 128), 128, 0, st, G, g->d_local,
+                  g->bands[kind].off, out);
     else
-        YK_LAUNCH(k_m2l_l2p<false>, g->np, 256, 0, st, G, g->d_mpole, g->bands[kind].off,
-                  g->bands[kind].idx, out);
+        YK_LAUNCH(k_band_l2p<false>, ceil_div(g->n, 128), 128, 0, st, G, g->d_local,
+                  g->bands[kind].off, out);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

@@ -512,6 +512,58 @@ __global__ void k_block_apply(int np, int npp, const int* __restrict__ shape_of,
     }
 }
 
+// Far part of the self-interaction block of each shape: own-particle sources
+// outside the target's near panels (zero on the near columns, which the QBX
+// rows cover), for the value (GRAD = false: dG/dnu_y, Eq. double-layer-def)
+// or the normal derivative (GRAD = true: nu_x . grad_x dG/dnu_y), quadrature
+// weights included, stored transposed (S[s][j][i]). Both depend only on the
+// shape: the kernels involve only distances and dot products of normals,
+// which rigid motions keep, so the blocks are built once in the particle frame.
+template <bool GRAD>
+__global__ void k_self_far(int npan, int ngl, int near_w, double rho, const double2* shape_ab,
+                           const double* glx, const double* glw, double* S) {
+    const int npp = npan * ngl;
+    const int s = blockIdx.y, i = blockIdx.x;
+    const double a = shape_ab[s].x, b = shape_ab[s].y;
+    const double dt = 2.0 * PI / npan;
+    const int k = i / ngl;
+    double xi, yi, dxi, dyi;
+    curve_point(0.0, 0.0, 1.0, 0.0, a, b, k * dt + 0.5 * dt * (glx[i % ngl] + 1.0), xi, yi, dxi,
+                dyi);
+    const double spi = sqrt(dxi * dxi + dyi * dyi);
+    const double nxi = dyi / spi, nyi = -dxi / spi;
+    double* out = S + (int64_t)s * npp * npp;
+    const bool all_near = 2 * near_w + 1 >= npan;
+    for (int j = threadIdx.x; j < npp; j += blockDim.x) {
+        const int kj = j / ngl;
+        const int d = ((kj - k) % npan + npan) % npan;
+        double v = 0.0;
+        if (!(all_near || d <= near_w || npan - d <= near_w)) {
+            double x, y, dx, dy;
+            curve_point(0.0, 0.0, 1.0, 0.0, a, b, kj * dt + 0.5 * dt * (glx[j % ngl] + 1.0), x, y,
+                        dx, dy);
+            const double spd = sqrt(dx * dx + dy * dy);
+            const double nx = dy / spd, ny = -dx / spd;
+            const double w = glw[j % ngl] * 0.5 * dt * spd;
+            const double ex = xi - x, ey = yi - y;
+            const double r = sqrt(ex * ex + ey * ey);
+            double k0v, k1v;
+            k01(r / rho, k0v, k1v);
+            const double dn_s = ex * nx + ey * ny;
+            if (!GRAD) {
+                v = k1v * dn_s / (2.0 * PI * rho * r) * w;
+            } else {
+                const double gg = k1v / (r * rho);
+                const double gp = -(k0v / rho + 2.0 * k1v / r) / (rho * r);
+                const double nn = nxi * nx + nyi * ny;
+                const double dn_t = ex * nxi + ey * nyi;
+                v = (gg * nn + gp * dn_s * dn_t / r) * w / (2.0 * PI);
+            }
+        }
+        out[(int64_t)j * npp + i] = v;
+    }
+}
+
 // Newton-Schulz steps: stop once the largest entry of I - A X is below
 // NS_TOL, or once it is below 1e-3 and has stopped shrinking (the FP32
 // floor). A block whose residual does not fall below 1/2 is singular to
@@ -604,6 +656,7 @@ int update_nodes(yk_geom* g) {
               g->d_c32, g->d_r32);
     for (auto& L : g->lists) L.valid = false;   // particle pairs change when particles move
     g->nbr_valid = false;
+    g->fmm.valid = false;                       // the quadtree follows the particles
     for (auto& B : g->bands) B.valid = false;
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
@@ -628,6 +681,12 @@ int build_geometry(yk_geom* g) {
     YK_LAUNCH(k_qbx_rows, grid, 128, smem, st, g->npan, g->ngl, P.near_width, g->n_near, os,
               P.qbx_order, P.qbx_r_factor, P.rho, g->d_shape_ab, g->d_glx, g->d_glw,
               g->d_fine_x, g->d_fine_w, g->d_interp, g->d_cval, g->d_cgrad);
+    if (g->use_self) {
+        YK_LAUNCH(k_self_far<false>, grid, 128, 0, st, g->npan, g->ngl, P.near_width, P.rho,
+                  g->d_shape_ab, g->d_glx, g->d_glw, g->d_self);
+        YK_LAUNCH(k_self_far<true>, grid, 128, 0, st, g->npan, g->ngl, P.near_width, P.rho,
+                  g->d_shape_ab, g->d_glx, g->d_glw, g->d_self_grad);
+    }
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY(build_preconditioner(g));
     YK_TRY_CUDA(cudaStreamSynchronize(st));

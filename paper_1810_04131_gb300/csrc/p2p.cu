@@ -713,18 +713,36 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
     }
 }
 
-// List the particle pairs (P <= Q) with pair_in_tiles(P, Q, thr). Writes up
-// to cap entries; *count receives the total.
-__global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, int* count,
-                            int2* __restrict__ out, int cap) {
+// List the particle pairs (P <= Q) with pair_in_tiles(P, Q, thr), leaving out
+// P == Q when self_pairs is false (the self blocks cover them). Writes up to
+// cap entries; *count receives the total.
+__global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, bool self_pairs,
+                            int* count, int2* __restrict__ out, int cap) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= np) return;
     const d4 a = part[P];
-    for (int Q = P; Q < np; ++Q) {
+    for (int Q = self_pairs ? P : P + 1; Q < np; ++Q) {
         if (Q == P || pair_in_tiles(a, part[Q], thr)) {
             const int k = atomicAdd(count, 1);
             if (k < cap) out[k] = make_int2(P, Q);
         }
+    }
+}
+
+// out_P += S[shape(P)] sigma_P for the far part of the self block (value or
+// normal derivative, stored transposed), one CTA per particle.
+__global__ void k_self_apply(GeomView G, const double* __restrict__ S,
+                             const double* __restrict__ sigma, double* __restrict__ out) {
+    extern __shared__ double xs[];
+    const int P = blockIdx.x;
+    const int64_t base = (int64_t)P * G.npp;
+    for (int j = threadIdx.x; j < G.npp; j += blockDim.x) xs[j] = sigma[base + j];
+    __syncthreads();
+    const double* M = S + (int64_t)G.shape_of[P] * G.npp * G.npp;
+    for (int i = threadIdx.x; i < G.npp; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < G.npp; ++j) acc = fma(M[(int64_t)j * G.npp + i], xs[j], acc);
+        out[base + i] += acc;
     }
 }
 
@@ -815,8 +833,8 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
                            : kind == 2 ? INFINITY : g->cutoff_gap;
         int* d_count = g->d_counter;
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
-        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr, d_count,
-                  (int2*)nullptr, 0);
+        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr,
+                  !g->use_self, d_count, (int2*)nullptr, 0);
         int n = 0;
         YK_TRY_CUDA(cudaMemcpyAsync(&n, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
         YK_TRY_CUDA(cudaStreamSynchronize(st));
@@ -828,8 +846,8 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
             L.cap = n;
         }
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
-        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr, d_count,
-                  L.d, L.cap);
+        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr,
+                  !g->use_self, d_count, L.d, L.cap);
         YK_TRY_CUDA(cudaGetLastError());
         L.n = n;
         L.valid = true;
@@ -840,6 +858,15 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
 }
 
 static int tiles_grid(int ntiles) { return std::max(1, std::min(ntiles, 152 * 16)); }
+
+// Own-particle far pairs of the FP64 operators: the precomputed self blocks
+// (the pair lists then hold no P == Q tiles).
+static int self_blocks(yk_geom* g, const double* sigma, double* extra, bool grad) {
+    if (!g->use_self) return YK_OK;
+    YK_LAUNCH(k_self_apply, g->np, 256, sizeof(double) * g->npp, g->ctx->stream, g->view(),
+              grad ? g->d_self_grad : g->d_self, sigma, extra);
+    return YK_OK;
+}
 
 // Cut-off neighbour lists (CSR), built on first use and after the particles move.
 static int neighbours(yk_geom* g) {
@@ -891,6 +918,7 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
         YK_TRY(tile_list(g, kind, &list, &ntiles));
         extra = g->ws.vec[5];
         YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
+        YK_TRY(self_blocks(g, sigma, extra, grad));
         if (prec == Prec::SPLIT) {
             const double gap = grad ? g->split_gap_grad : g->split_gap;
             if (grad)
@@ -916,8 +944,92 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
     return YK_OK;
 }
 
+// FP32 inner operator with the FMM far field: near lists by FP32 P2P, the
+// rest by expansions (fmm.cu), plus the QBX rows.
+static int fmm_apply(yk_geom* g, const double* sigma, double* y) {
+    cudaStream_t st = g->ctx->stream;
+    GeomView G = g->view();
+    double* extra = g->ws.vec[5];
+    YK_TRY(fmm_far(g, sigma, extra));
+    const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
+    YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, 0.0,
+              g->fmm.near_off, g->fmm.near, g->ws.partial);
+    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, 1, g->ws.partial, extra, G.cval,
+              sigma, y);
+    YK_TRY_CUDA(cudaGetLastError());
+    return YK_OK;
+}
+
+// Leaf level of the FMM: the one given (fmm_leaf) or the fastest of the
+// admissible ones, timed with CUDA events on the first application (each
+// candidate applied once to warm up, then twice timed). Without an
+// admissible level the far field falls back to the cut-off P2P.
+static int fmm_tune(yk_geom* g, const double* sigma, double* y) {
+    FmmTree& F = g->fmm;
+    const double leaf = g->prm.fmm_leaf;
+    int lo = 0, hi = -1;
+    if (leaf > 0.0) {
+        double x0, y0, side;
+        fmm_root_box(g, &x0, &y0, &side);
+        int L = 0;
+        while (L < FMM_LMAX && side / (double)(1 << L) > leaf) ++L;
+        const double b = side / (double)(1 << L), R = g->max_radius;
+        // the discs of an interacting pair must be disjoint: 2 (b/sqrt2 + R) < 3 b
+        F.far_off = !(2.0 * (b * M_SQRT1_2 + R) < 3.0 * b);
+        F.Lsel = L;
+        F.tuned = true;
+        return YK_OK;
+    }
+    YK_TRY(fmm_candidates(g, &lo, &hi));
+    if (lo > hi) {
+        F.far_off = true;
+        F.tuned = true;
+        return YK_OK;
+    }
+    F.far_off = false;
+    F.Lsel = hi;
+    if (lo < hi) {
+        cudaStream_t st = g->ctx->stream;
+        cudaEvent_t e0, e1;
+        YK_TRY_CUDA(cudaEventCreate(&e0));
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return YK_ERR_CUDA;
+        }
+        float best = INFINITY;
+        int rc = YK_OK;
+        for (int L = lo; L <= hi && rc == YK_OK; ++L) {
+            rc = fmm_build(g, L);
+            if (rc == YK_OK) rc = fmm_apply(g, sigma, y);
+            if (rc == YK_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = YK_ERR_CUDA;
+            for (int r = 0; r < 2 && rc == YK_OK; ++r) rc = fmm_apply(g, sigma, y);
+            float ms = 0.0f;
+            if (rc == YK_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = YK_ERR_CUDA;
+            if (rc == YK_OK && ms < best) best = ms, F.Lsel = L;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        YK_TRY(rc);
+        F.valid = false;
+    }
+    F.tuned = true;
+    return YK_OK;
+}
+
+static int matvec_fmm(yk_geom* g, const double* sigma, double* y) {
+    FmmTree& F = g->fmm;
+    if (!F.tuned) YK_TRY(fmm_tune(g, sigma, y));
+    if (F.far_off) return matvec_cutoff(g, sigma, y, Prec::F32, false);
+    if (!F.valid || F.L != F.Lsel) YK_TRY(fmm_build(g, F.Lsel));
+    return fmm_apply(g, sigma, y);
+}
+
 int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
-    if (g->prm.farfield == YK_FARFIELD_CUTOFF) return matvec_cutoff(g, sigma, y, prec, false);
+    if (g->prm.farfield == YK_FARFIELD_FMM && prec == Prec::F32) return matvec_fmm(g, sigma, y);
+    if (g->prm.farfield != YK_FARFIELD_DENSE) return matvec_cutoff(g, sigma, y, prec, false);
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
     const int nchunk = g->ws.nchunk;
@@ -936,6 +1048,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
         YK_TRY(tile_list(g, kind, &list, &ntiles));
         extra = g->ws.vec[5];
         YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
+        YK_TRY(self_blocks(g, sigma, extra, false));
         if (prec == Prec::SPLIT) {
             YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks,
                       g->split_gap, g->ws.partial);
@@ -953,7 +1066,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
 }
 
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
-    if (g->prm.farfield == YK_FARFIELD_CUTOFF) return matvec_cutoff(g, sigma, un, prec, true);
+    if (g->prm.farfield != YK_FARFIELD_DENSE) return matvec_cutoff(g, sigma, un, prec, true);
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
     const int nchunk = g->ws.nchunk;
@@ -965,6 +1078,7 @@ int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
     YK_TRY(tile_list(g, kind, &list, &ntiles));
     double* extra = g->ws.vec[5];
     YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
+    YK_TRY(self_blocks(g, sigma, extra, true));
     int used_chunks = 0;
     if (prec != Prec::F64) {
         YK_LAUNCH(k_p2p_f32_grad<true>, grid, F32_TPB, 0, st, G, sigma, ppc, g->split_gap_grad,

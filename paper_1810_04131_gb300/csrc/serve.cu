@@ -57,13 +57,17 @@ struct Server {
 };
 
 // Device memory of one request: node arrays, Krylov basis, chunk partials,
-// scratch vectors, QBX rows (an estimate with a safety factor).
+// scratch vectors, QBX rows, and per shape (at most two) the two self blocks
+// and the FP64 + FP32 preconditioner inverse (an estimate with a safety factor).
 static size_t request_bytes(const Request& r) {
-    const size_t n = (size_t)r.parts.size() * r.prm.n_panels * r.prm.n_gl;
+    const size_t npp = (size_t)r.prm.n_panels * r.prm.n_gl;
+    const size_t n = (size_t)r.parts.size() * npp;
     const size_t m = (size_t)r.prm.gmres_restart;
     const size_t nchunk = 32;
-    const size_t rows = (size_t)r.prm.n_panels * r.prm.n_gl * 9 * r.prm.n_gl * 2;
-    return (size_t)(1.25 * 8.0 * (double)(n * (m + 1 + nchunk + 16) + rows)) + (8u << 20);
+    const size_t rows = npp * 9 * r.prm.n_gl * 2;
+    const size_t blocks = 2 * npp * npp * (8 * 2 + 8 + 4);
+    return (size_t)(1.25 * (8.0 * (double)(n * (m + 1 + nchunk + 16) + rows) + (double)blocks)) +
+           (8u << 20);
 }
 
 // Run one request to completion on a worker's context.

@@ -47,6 +47,7 @@ constexpr int MAX_NGL = 32;
 constexpr int MAX_ORDER = 24;
 constexpr int MAX_NEAR_PANELS = 9;      // (2 near_width + 1) <= 9
 constexpr int MAX_OVERSAMPLE = 16;
+constexpr int SELF_BLOCK_MAX_NODES = 2048;   // nodes per particle with precomputed self blocks
 
 void set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void note_launch();
@@ -124,6 +125,44 @@ struct yk_ctx {
     double* h_status = nullptr;  // pinned host mirror of solver status (8 doubles)
 };
 
+namespace yk {
+// Uniform quadtree of the FMM far field (fmm.cu). Boxes of level l are
+// numbered j * 2^l + i after those of the coarser levels
+// (offset (4^l - 1) / 3); particles belong to the leaf holding their centre.
+struct FmmTree {
+    bool valid = false;        // built for the current particle positions
+    bool tuned = false;        // leaf size chosen (autotuned or given)
+    bool far_off = false;      // no admissible leaf size: far field by cut-off P2P
+    int L = -1;                // leaf level
+    int Lsel = -1;             // leaf level chosen for these particles
+    int lmin = 2;              // coarsest level with interactions
+    int p = 12;                // expansion order (terms |n| <= p)
+    double x0 = 0.0, y0 = 0.0, side = 0.0;   // root box
+    double leaf = 0.0;         // chosen leaf side
+    double gcut = 0.0;         // interactions across larger gaps are left out
+    int64_t nbox = 0;
+    int* leaf_of = nullptr;    // [np] leaf of each particle
+    int* leaf_part = nullptr;  // [np] particles by leaf (CSR with leaf_off)
+    int* near_off = nullptr;   // [np + 1] near lists (CSR)
+    int* near = nullptr;       // particles in leaves within FMM_SEP boxes
+    int64_t near_cap = 0;
+    int* leaf_off = nullptr;   // [nleaf + 1]
+    int* cursor = nullptr;     // [nleaf] scratch
+    int64_t leaf_cap = 0;
+    int* box_count = nullptr;  // [nbox] particles per box
+    double2* M = nullptr;      // [nbox][p + 1] multipole moments
+    double2* Lc = nullptr;     // [nbox][p + 1] local coefficients
+    int64_t box_cap = 0;       // capacity of box_count (boxes)
+    int64_t coef_cap = 0;      // capacity of M and Lc (coefficients)
+    double2* T = nullptr;      // M2L tables [level][offset][3p + 1]
+    int64_t t_cap = 0;
+    float2* T32 = nullptr;     // the same rounded to FP32
+    int64_t t32_cap = 0;
+    bool use32[11] = {};       // level translates in FP32 (table within FP32 range)
+    bool all32 = false;        // every active level does (L2P in FP32)
+};
+}  // namespace yk
+
 struct yk_geom {
     yk_ctx* ctx = nullptr;
     yk_params prm{};
@@ -136,15 +175,18 @@ struct yk_geom {
     double split_gap = 0.0;                // gap above which FP32 is used (mixed residual)
     double split_gap_grad = 0.0;           // the same for the normal derivative
     double cutoff_gap = INFINITY;          // far field: source particles beyond are left out
+    double fmm_gap = INFINITY;             // reach of the FMM far field (inner operator)
     double tile_gap = 0.0;                 // split operators: FP64 tiles below this gap,
     double tile_gap_grad = 0.0;            //   FP64 expansions up to the split gap
     yk::BandList bands[2];                 // expansion bands (value, normal derivative)
     int* d_counts = nullptr;               // np ints of scratch for list building
     double2* d_mpole = nullptr;            // multipole moments [np][order + 1]
+    double2* d_local = nullptr;            // local coefficients [np][order + 1]
     int* nbr_off = nullptr;                // cut-off neighbour lists (CSR offsets, np + 1)
     int* nbr = nullptr;                    // neighbour particle indices
     int nbr_cap = 0;
     bool nbr_valid = false;
+    yk::FmmTree fmm;                       // FMM far field (YK_FARFIELD_FMM)
     // device allocations
     yk::d4* d_part = nullptr;
     float4* d_c32 = nullptr;
@@ -171,6 +213,10 @@ struct yk_geom {
     double* d_minv = nullptr;     // block preconditioner: inverse self block per shape,
                                   // transposed, [shape][col j][row i]
     float* d_minv32 = nullptr;    // the same in FP32
+    bool use_self = false;        // own-particle far pairs by the blocks below
+    double* d_self = nullptr;     // far part of the self block per shape (value),
+                                  // transposed, [shape][col j][row i]
+    double* d_self_grad = nullptr;  // the same for the normal derivative
     yk::Workspace ws;
     yk::GeomView view() const;
 };
@@ -196,6 +242,17 @@ int potential_noalloc(yk_geom* g, const double* sigma, const double* targets, in
 constexpr int EXPANSION_TERMS = 41;        // orders 0..40 of the particle expansions
 constexpr double EXPANSION_GAP_RADII = 4.0;  // band starts at a gap of 4 bounding radii
 int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad);
+
+// fmm.cu
+constexpr int FMM_PMAX = 30;      // largest expansion order (one warp lane per order)
+constexpr int FMM_SEP = 2;        // near field: leaves at most FMM_SEP boxes apart
+constexpr int FMM_LMAX = 10;      // deepest leaf level
+constexpr double FMM_REACH_TOL = 1e-10;   // FMM interactions bounded below this x max|sigma| are left out
+void fmm_root_box(yk_geom* g, double* x0, double* y0, double* side);
+int fmm_candidates(yk_geom* g, int* lo, int* hi);
+int fmm_build(yk_geom* g, int L);
+int fmm_far(yk_geom* g, const double* sigma, double* out);
+void fmm_free(yk_geom* g);
 
 // gmres.cu
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0, yk_solve_info* info);

@@ -40,6 +40,7 @@ YK_PRECOND_NONE = 0
 YK_PRECOND_BLOCK = 1
 YK_FARFIELD_DENSE = 0
 YK_FARFIELD_CUTOFF = 1
+YK_FARFIELD_FMM = 2
 YK_LABEL_TANH = 0
 YK_LABEL_SINP = 1
 YK_LABEL_COS = 2
@@ -69,7 +70,8 @@ class yk_params(C.Structure):
                 ("precision", C.c_int32), ("gmres_tol", C.c_double), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("farfield", C.c_int32), ("split_tol", C.c_double),
                 ("grad_split_tol", C.c_double), ("precond", C.c_int32), ("pad_", C.c_int32),
-                ("cutoff_tol", C.c_double)]
+                ("cutoff_tol", C.c_double), ("fmm_order", C.c_int32), ("pad2_", C.c_int32),
+                ("fmm_leaf", C.c_double)]
 
 
 class yk_solve_info(C.Structure):

@@ -213,6 +213,97 @@ def test_cutoff_far_field(yk, ctx, dense_cache):
     assert rel(gd.yk_matvec(sig, yk.YK_FP64), A @ sig) > 1e-8
 
 
+def test_fmm_far_field_against_direct_sums(yk, ctx):
+    """FMM far field (expansions in FP64): with the density nonzero on one
+    particle only, a target more than three leaf sides away from it (in x or
+    y) has no source in its near list, so it receives the expansions' value
+    alone. That value is checked against the direct double-layer sum with the
+    oracle's kernel at orders 12 and 20 (sources and targets spread over
+    every level of the tree: rho = 2 reaches across the whole box)."""
+    wl = W.small_system(60, 41, n_panels=8, n_gl=16, rho=2.0, qbx_order=10, gap=0.4)
+    geo = yo.make_geometry(wl.particles, wl.n_panels, wl.n_gl)
+    npp = wl.n_panels * wl.n_gl
+    rng = np.random.default_rng(17)
+    leaf = 8.0
+    c = wl.particles[:, 1:3]
+    for P in (7, 33):
+        sl = slice(P * npp, (P + 1) * npp)
+        sig = np.zeros(geo.w.size)
+        sig[sl] = 1.0 + 0.3 * np.cos(3 * geo.t[sl]) + 0.2 * rng.standard_normal(npp)
+        ws = geo.w[sl] * sig[sl]
+        far = np.maximum(np.abs(c[:, 0] - c[P, 0]), np.abs(c[:, 1] - c[P, 1])) > 3 * leaf
+        rows = np.flatnonzero(np.repeat(far, npp))
+        assert rows.size > 1000
+        ref = np.array([(yo.dl_kernel(geo.x[r][None], geo.x[sl], geo.nu[sl], wl.rho) * ws).sum()
+                        for r in rows])
+        assert np.abs(ref).max() > 1e-8 * np.abs(ws).sum()   # not negligible
+        errs = {}
+        for order, tol in ((12, 1e-8), (20, 1e-11)):
+            g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_FMM,
+                                                       fmm_order=order, fmm_leaf=leaf))
+            y = g.yk_matvec(sig, yk.YK_MIXED)
+            errs[order] = np.abs(y[rows] - ref).max()
+            assert errs[order] <= tol * np.abs(ws).sum(), (P, order, errs[order])
+            g.close()
+        assert errs[20] < errs[12]
+
+
+def test_fmm_operator_and_solve(yk, ctx):
+    """YK_FARFIELD_FMM as the inner operator of the mixed solver: the FP32
+    operator (FP32 near lists + FMM far field) within the FP32 bar of the
+    dense operator, for a given and an autotuned leaf size; the FP64 path and
+    the refinement residual use the cut-off operator, so a mixed FMM solve
+    matches the oracle's dense solution and forces to 1e-9."""
+    wl = W.small_system(24, 31, n_panels=8, n_gl=16, rho=1.5, qbx_order=10, gap=0.4)
+    wl.particles[:, 1:3] *= 2.5
+    o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+    A, Gn = o.dense(want_grad=True)
+    rng = np.random.default_rng(19)
+    sig = rng.standard_normal(A.shape[0])
+    for leaf in (6.0, 0.0):
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_FMM,
+                                                   fmm_leaf=leaf))
+        y32 = g.yk_matvec(sig, yk.YK_MIXED)
+        assert rel(y32, A @ sig) < 1e-6
+        assert rel(g.yk_matvec(sig, yk.YK_MIXED), y32) == 0.0      # deterministic
+        y64 = g.yk_matvec(sig, yk.YK_FP64)
+        assert np.abs(y64 - A @ sig).max() <= 20 * 1e-15 * np.abs(sig).max() + 1e-13
+        g.close()
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_FMM, fmm_leaf=6.0,
+                                               precision=yk.YK_MIXED, gmres_tol=1e-12))
+    f = g.yk_label(0, 10.0)
+    s, info = g.yk_solve(f)
+    s_ref = np.linalg.solve(A, f)
+    assert info["converged"] and rel(s, s_ref) < 1e-9
+    F, tau, net = g.yk_forces_torques(s, f)
+    F_ref, tau_ref, _ = o.forces_torques(f, Gn @ s_ref)
+    scale = np.abs(F_ref).max()
+    assert np.abs(F - F_ref).max() < 1e-9 * scale
+    assert np.abs(tau - tau_ref).max() < 1e-9 * max(scale, np.abs(tau_ref).max())
+    # moving the particles rebuilds the tree: the moved system still matches
+    moved = wl.particles.copy()
+    moved[:, 1] += 0.37
+    moved[:, 3] += 0.2
+    g.yk_update_geometry(moved)
+    o2 = yo.Oracle(moved, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+    rows = np.sort(rng.choice(A.shape[0], 40, replace=False))
+    y32 = g.yk_matvec(sig, yk.YK_MIXED)
+    ref = o2.apply_rows(sig, rows)
+    assert np.abs(y32[rows] - ref).max() < 1e-6 * np.abs(A @ sig).max()
+
+
+def test_fmm_without_admissible_leaf_falls_back_to_cutoff(yk, ctx):
+    """When no leaf size satisfies the FMM's accuracy conditions (here order 4
+    at rho = 0.5: a leaf would have to be both wider than 2.9 radii and
+    narrower than 0.7), the inner operator's far field is the cut-off P2P."""
+    wl = W.small_system(24, 31, n_panels=8, n_gl=16, rho=0.5, qbx_order=10, gap=0.4)
+    rng = np.random.default_rng(20)
+    sig = rng.standard_normal(24 * 128)
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_FMM, fmm_order=4))
+    gc = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF))
+    assert np.array_equal(g.yk_matvec(sig, yk.YK_MIXED), gc.yk_matvec(sig, yk.YK_MIXED))
+
+
 def test_device_pointers_match_host(yk, ctx):
     import torch
     wl = SMALL["disks5_pan9"]()
@@ -237,7 +328,8 @@ def test_errors_and_edge_cases(yk, ctx):
     assert e.value.code == yk.YK_ERR_BAD_GEOMETRY
     # parameters out of range
     for kw in (dict(n_gl=1), dict(n_gl=40), dict(qbx_order=30), dict(rho=-1.0),
-               dict(oversample=0), dict(near_width=-1), dict(precision=7)):
+               dict(oversample=0), dict(near_width=-1), dict(precision=7), dict(farfield=3),
+               dict(fmm_order=1), dict(fmm_order=31), dict(fmm_leaf=-1.0)):
         with pytest.raises(yk.YKError) as e:
             yk.Geometry(ctx, wl.particles, _params(yk, wl, **kw))
         assert e.value.code == yk.YK_ERR_ARG
