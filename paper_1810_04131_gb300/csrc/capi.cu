@@ -303,7 +303,7 @@ int yk_destroy_geometry(yk_geom* g) {
     void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
                     g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w, g->d_minv, g->d_minv32,
-                    g->d_self, g->d_self_grad};
+                    g->d_self, g->d_self_grad, g->d_self32};
     for (void* b : bufs) dev_free(b, st);
     cudaStreamSynchronize(st);
     delete g;
@@ -428,6 +428,7 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
     if (g->use_self) {
         ALLOC(d_self, (size_t)g->nshape * npp * npp);
         ALLOC(d_self_grad, (size_t)g->nshape * npp * npp);
+        ALLOC(d_self32, (size_t)g->nshape * npp * npp);
     }
     ALLOC(d_glx, g->ngl);
     ALLOC(d_glw, g->ngl);

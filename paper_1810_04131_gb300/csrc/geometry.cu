@@ -512,6 +512,11 @@ __global__ void k_block_apply(int np, int npp, const int* __restrict__ shape_of,
     }
 }
 
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 // Far part of the self-interaction block of each shape: own-particle sources
 // outside the target's near panels (zero on the near columns, which the QBX
 // rows cover), for the value (GRAD = false: dG/dnu_y, Eq. double-layer-def)
@@ -686,6 +691,8 @@ int build_geometry(yk_geom* g) {
                   g->d_shape_ab, g->d_glx, g->d_glw, g->d_self);
         YK_LAUNCH(k_self_far<true>, grid, 128, 0, st, g->npan, g->ngl, P.near_width, P.rho,
                   g->d_shape_ab, g->d_glx, g->d_glw, g->d_self_grad);
+        const int64_t cnt = (int64_t)g->nshape * g->npp * g->npp;
+        YK_LAUNCH(k_to_f32, ceil_div(cnt, 256), 256, 0, st, cnt, g->d_self, g->d_self32);
     }
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY(build_preconditioner(g));

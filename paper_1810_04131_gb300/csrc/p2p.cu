@@ -180,6 +180,21 @@ __device__ __forceinline__ float4 src_scalar(const float4* A, const float4* B, i
     return (q & 1) ? make_float4(-a.y, -a.w, b.y, b.w) : make_float4(-a.x, -a.z, b.x, b.z);
 }
 
+// Two pairs of a close (non-own) source particle: the packed far form,
+// except that a lane with z <= 2 (z'^2 <= (2 log2 e)^2, outside the fitted
+// polynomial's range) takes the series of PairF32::any instead.
+constexpr float ZCUT2 = 4.0f * LOG2E_F * LOG2E_F;
+__device__ __forceinline__ float2 close2(float2 TX, float2 TY, const float4& A, const float4& B,
+                                         const PolyRZ& P, float2 acc) {
+    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
+    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
+    const float z2x = fmaf(dX.x, dX.x, dY.x * dY.x), z2y = fmaf(dX.y, dX.y, dY.y * dY.y);
+    if (z2x > ZCUT2 && z2y > ZCUT2) return far2(TX, TY, A, B, P, acc);
+    acc.x += PairF32::any(dX.x, dY.x, B.x, B.z);
+    acc.y += PairF32::any(dX.y, dY.y, B.y, B.w);
+    return acc;
+}
+
 // Packed FP32 normal derivative of two far pairs (one target with normal
 // (nx, ny), two sources), same scaled coordinates and staging as far2. With
 // E = exp2(-z') z'^{-1/2}, rz = 1/z', G = w sigma nu_y, D' the scaled d:
@@ -291,8 +306,9 @@ __device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB
 }
 
 template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
+__global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
                                                      int ppc, float kscale, double skip_gap,
+                                                     bool own_by_block,
                                                      double* __restrict__ partial) {
     __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
     const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
@@ -313,9 +329,14 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
         TargetF32 T0, T1;
         target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
         target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-        // skip the source particle only when every thread of the block agrees
-        // (a block-wide vote, reached by all threads), so barriers stay uniform
-        const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
+        // a target skips the source particle when the FP64 tiles hold the pair
+        // (MASK) or when it is the target's own particle and the self block
+        // adds it (own_by_block); the particle is skipped only when every
+        // thread of the block agrees (a block-wide vote reached by all
+        // threads), so barriers stay uniform
+        const bool skip0 = (MASK && T0.skip) || (own_by_block && T0.own);
+        const bool skip1 = (MASK && T1.skip) || (own_by_block && T1.own);
+        const bool block_skip = (MASK || own_by_block) ? __syncthreads_and(skip0 && skip1) : false;
         if (block_skip) continue;
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
@@ -346,7 +367,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
             }
             __syncthreads();
             float r0 = 0.0f, r1 = 0.0f;
-            if (!T0.close && !T1.close && !(MASK && (T0.skip || T1.skip))) {
+            if (!T0.close && !T1.close && !skip0 && !skip1) {
                 const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
                 const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
                 float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
@@ -362,11 +383,9 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32(GeomView G, const double* _
                 for (int q = 0; q < cnt; ++q) {
                     const float4 S = src_scalar(srcA, srcB, q);
                     const int pq = (jb + q) / G.ngl;
-                    if (!(MASK && T0.skip) &&
-                        !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
+                    if (!skip0 && !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
                         r0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
-                    if (!(MASK && T1.skip) &&
-                        !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
+                    if (!skip1 && !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
                         r1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
                 }
             }
@@ -439,6 +458,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const double* __restrict__ sigma,
                                                          float kscale, double skip_gap,
+                                                         bool own_by_block,
                                                          const int* __restrict__ nbr_off,
                                                          const int* __restrict__ nbr,
                                                          double* __restrict__ out) {
@@ -461,7 +481,8 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
             TargetF32 T0, T1;
             target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
             target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-            if (MASK && T0.skip) continue;   // uniform: one target particle per block
+            // uniform: one target particle per block
+            if ((MASK && T0.skip) || (own_by_block && T0.own)) continue;
             const int64_t base = (int64_t)s * G.npp;
             for (int jb = 0; jb < G.npp; jb += STILE) {
                 const int cnt = min(STILE, G.npp - jb);
@@ -492,15 +513,24 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
                 }
                 __syncthreads();
                 float r0 = 0.0f, r1 = 0.0f;
+                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
                 if (!T0.close) {
-                    const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
-                    const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
                     float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
 #pragma unroll 2
                     for (int m = 0; m < npair; ++m) {
                         const float4 A = srcA[m], B = srcB[m];
                         a0 = far2(TX0, TY0, A, B, P, a0);
                         a1 = far2(TX1, TY1, A, B, P, a1);
+                    }
+                    r0 = a0.x + a0.y;
+                    r1 = a1.x + a1.y;
+                } else if (!T0.own) {
+                    float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+                    for (int m = 0; m < npair; ++m) {
+                        const float4 A = srcA[m], B = srcB[m];
+                        a0 = close2(TX0, TY0, A, B, P, a0);
+                        a1 = close2(TX1, TY1, A, B, P, a1);
                     }
                     r0 = a0.x + a0.y;
                     r1 = a1.x + a1.y;
@@ -746,6 +776,24 @@ __global__ void k_self_apply(GeomView G, const double* __restrict__ S,
     }
 }
 
+// The same in FP32 for the inner operator: out_P (+)= S32[shape(P)] sigma_P.
+template <bool ACC>
+__global__ void k_self_apply_f32(GeomView G, const float* __restrict__ S,
+                                 const double* __restrict__ sigma, double* __restrict__ out) {
+    extern __shared__ float xf[];
+    const int P = blockIdx.x;
+    const int64_t base = (int64_t)P * G.npp;
+    for (int j = threadIdx.x; j < G.npp; j += blockDim.x) xf[j] = (float)sigma[base + j];
+    __syncthreads();
+    const float* M = S + (int64_t)G.shape_of[P] * G.npp * G.npp;
+    for (int i = threadIdx.x; i < G.npp; i += blockDim.x) {
+        float acc = 0.0f;
+        for (int j = 0; j < G.npp; ++j) acc = fmaf(M[(int64_t)j * G.npp + i], xf[j], acc);
+        if (ACC) out[base + i] += (double)acc;
+        else out[base + i] = (double)acc;
+    }
+}
+
 // y_i = sum_chunks partial[c][i] + extra_i + sum_near C[shape][local i][c] sigma[near c]
 __global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ partial,
                            const double* __restrict__ extra, const double* __restrict__ rows,
@@ -861,6 +909,17 @@ static int tiles_grid(int ntiles) { return std::max(1, std::min(ntiles, 152 * 16
 
 // Own-particle far pairs of the FP64 operators: the precomputed self blocks
 // (the pair lists then hold no P == Q tiles).
+static int self_blocks_f32(yk_geom* g, const double* sigma, double* extra, bool accumulate) {
+    if (!g->use_self) return YK_OK;
+    if (accumulate)
+        YK_LAUNCH(k_self_apply_f32<true>, g->np, 256, sizeof(float) * g->npp, g->ctx->stream,
+                  g->view(), g->d_self32, sigma, extra);
+    else
+        YK_LAUNCH(k_self_apply_f32<false>, g->np, 256, sizeof(float) * g->npp, g->ctx->stream,
+                  g->view(), g->d_self32, sigma, extra);
+    return YK_OK;
+}
+
 static int self_blocks(yk_geom* g, const double* sigma, double* extra, bool grad) {
     if (!g->use_self) return YK_OK;
     YK_LAUNCH(k_self_apply, g->np, 256, sizeof(double) * g->npp, g->ctx->stream, g->view(),
@@ -910,7 +969,11 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
                       g->nbr, g->ws.partial);
         else
             YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, 0.0,
-                      g->nbr_off, g->nbr, g->ws.partial);
+                      g->use_self, g->nbr_off, g->nbr, g->ws.partial);
+        if (!grad && g->use_self) {
+            extra = g->ws.vec[5];
+            YK_TRY(self_blocks_f32(g, sigma, extra, false));
+        }
     } else {
         const int kind = (prec == Prec::F64) ? 3 : (grad ? 1 : 0);
         const int2* list;
@@ -926,7 +989,7 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
                           g->nbr_off, g->nbr, g->ws.partial);
             else
                 YK_LAUNCH(k_p2p_f32_cut<true>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, gap,
-                          g->nbr_off, g->nbr, g->ws.partial);
+                          false, g->nbr_off, g->nbr, g->ws.partial);
         } else {
             used = 0;
         }
@@ -951,9 +1014,10 @@ static int fmm_apply(yk_geom* g, const double* sigma, double* y) {
     GeomView G = g->view();
     double* extra = g->ws.vec[5];
     YK_TRY(fmm_far(g, sigma, extra));
+    YK_TRY(self_blocks_f32(g, sigma, extra, true));
     const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
     YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, 0.0,
-              g->fmm.near_off, g->fmm.near, g->ws.partial);
+              g->use_self, g->fmm.near_off, g->fmm.near, g->ws.partial);
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, 1, g->ws.partial, extra, G.cval,
               sigma, y);
     YK_TRY_CUDA(cudaGetLastError());
@@ -1040,7 +1104,11 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
     int used_chunks = nchunk;
     if (prec == Prec::F32) {
         YK_LAUNCH(k_p2p_f32<false>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks, 0.0,
-                  g->ws.partial);
+                  g->use_self, g->ws.partial);
+        if (g->use_self) {
+            extra = g->ws.vec[5];
+            YK_TRY(self_blocks_f32(g, sigma, extra, false));
+        }
     } else {
         const int kind = (prec == Prec::F64) ? 2 : 0;
         const int2* list;
@@ -1051,7 +1119,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
         YK_TRY(self_blocks(g, sigma, extra, false));
         if (prec == Prec::SPLIT) {
             YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks,
-                      g->split_gap, g->ws.partial);
+                      g->split_gap, false, g->ws.partial);
         } else {
             used_chunks = 0;
         }

@@ -217,6 +217,7 @@ struct yk_geom {
     double* d_self = nullptr;     // far part of the self block per shape (value),
                                   // transposed, [shape][col j][row i]
     double* d_self_grad = nullptr;  // the same for the normal derivative
+    float* d_self32 = nullptr;    // d_self rounded to FP32 (inner operator)
     yk::Workspace ws;
     yk::GeomView view() const;
 };
