@@ -37,11 +37,17 @@ FLOPS_PER_PAIR = 34
 SMS, FP32_LANES = 152, 128
 
 
+KERNEL_SOURCES = ("p2p_kernels.cuh", "bessel.cuh", "bessel_tables.h", "yk_internal.cuh")
+
+
 def kernel_source_hash():
-    """Hash of the far-field kernel source, to match stored ncu counters."""
+    """Hash of the sources the far-field kernels compile from (device code,
+    Bessel tables, shared structures), to match stored ncu counters."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1810_04131_gb300", "csrc", "p2p.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1810_04131_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def stored_traffic():
@@ -52,7 +58,7 @@ def stored_traffic():
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if d.get("p2p_source_sha256_16") != kernel_source_hash():
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -68,7 +74,9 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=384)
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests replayed from the seeded serving stream")
-    ap.add_argument("--serve-max-particles", type=int, default=512)
+    ap.add_argument("--serve-max-particles", type=int, default=2048)
+    ap.add_argument("--serve-fmm-above", type=int, default=256,
+                    help="requests with more particles use the FMM far field")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrivals per second")
     return ap.parse_args()
 
@@ -191,7 +199,11 @@ def run_serving(yk, W, ctx, args):
         now = time.perf_counter() - t0
         while k < len(reqs) and reqs[k]["arrival"] <= now:
             wl = loads[k]
-            rid = ctx.yk_submit(wl.particles, yk.params_for(wl, precision=yk.YK_MIXED))
+            # large systems take the FMM far field for the inner operator
+            ff = yk.YK_FARFIELD_FMM if len(wl.particles) > args.serve_fmm_above \
+                else yk.YK_FARFIELD_DENSE
+            rid = ctx.yk_submit(wl.particles, yk.params_for(wl, precision=yk.YK_MIXED,
+                                                            farfield=ff))
             pending[rid] = wl
             k += 1
         done = []
@@ -213,8 +225,9 @@ def run_serving(yk, W, ctx, args):
             "solves_per_s": len(lat) / wall, "wall_s": wall, "nodes_total": int(nodes),
             "arrival_rate_per_s": args.serve_rate, "max_particles": args.serve_max_particles,
             "stream": "seeded (seed 6): Poisson arrivals, log-uniform 4..%d particles, "
-                      "8-32 panels x 16 nodes, disk/ellipse, rho in {0.5,1,2}, mixed precision"
-                      % args.serve_max_particles}
+                      "8-32 panels x 16 nodes, disk/ellipse, rho in {0.5,1,2}, mixed precision; "
+                      "dense far field up to %d particles, FMM above"
+                      % (args.serve_max_particles, args.serve_fmm_above)}
 
 
 def run_reference(args):

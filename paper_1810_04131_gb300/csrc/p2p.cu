@@ -1,874 +1,15 @@
-// Far-field (point-to-point) part of the double-layer operator and of its
-// normal derivative, and the assembly y = far + near (Eq. bie with the QBX
-// near rows of Section 5).
-//
-// Far kernel (Eq. double-layer-def with G = K0(r/rho)/2pi, Eq. Gfunc):
-//   dG/dnu_y = K1(r/rho) ((x - y) . nu_y) / (2 pi rho r).
-// Normal derivative at a boundary target with normal nu_x:
-//   nu_x . grad_x dG/dnu_y = [g (nu_y . nu_x) + g'(r) (d . nu_y)(d . nu_x)/r] / 2pi,
-//   g = K1(z)/(rho r), g' = -(K0(z)/rho + 2 K1(z)/r)/(rho r), z = r/rho, d = x - y.
-// Sources that are the target's own near panels are skipped: the QBX rows
-// replace them.
-//
-// Three evaluators share the work:
-//  * k_p2p_f32 / k_p2p_f32_grad: FP32 evaluation with FP64 accumulation per
-//    source particle; blockIdx.x = 256 consecutive targets (two per thread),
-//    blockIdx.y = a chunk of source particles, partial sums per chunk.
-//    With a skip distance they leave out the particle pairs that the FP64
-//    tiles handle (same FP64 predicate in both places).
-//  * k_tiles_f64<GRAD>: one block per listed particle pair (P, Q), P <= Q,
-//    all in FP64. The pair kernels are symmetric in (i, j) up to the sign of
-//    d (value) or exactly (gradient), so each kernel evaluation feeds both
-//    targets: P's nodes through registers, Q's through a warp reduction and
-//    shared-memory atomics. Results go to a FP64 buffer with atomics.
-//  * k_assemble: chunk partials (fixed order) + FP64 tile sums + near rows.
-#include <math.h>
-
+// Host side of the far-field evaluators (kernels in p2p_kernels.cuh): the FP64
+// tile and neighbour lists, the matvec and normal-derivative drivers for the
+// dense, cut-off and FMM far fields, the FMM leaf-size autotuner, and the
+// off-surface potential.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 
-#include "bessel.cuh"
-#include "yk_internal.cuh"
+#include "p2p_kernels.cuh"
 
 namespace yk {
-
-constexpr int TPB = 256;         // targets per far-field block
-constexpr int STILE = 256;       // source nodes staged per pass
-constexpr int F32_TPB = 128;     // FP32 kernels: two targets per thread
-constexpr int TILE_TPB = 256;    // FP64 pair tiles
-constexpr float LOG2E_F = 1.4426950408889634f;
-constexpr double LOG2E = 1.4426950408889634;
-
-__device__ __forceinline__ bool is_near_panel(int pt_panel, int ps_panel, int npan, int w) {
-    if (2 * w + 1 >= npan) return true;
-    int d = ps_panel - pt_panel;
-    d = ((d % npan) + npan) % npan;
-    return d <= w || npan - d <= w;
-}
-
-// The particle-pair predicate "handled by the FP64 tiles": the same particle,
-// or bounding circles closer than thr. Evaluated with explicitly rounded
-// operations so that the list builder and the FP32 kernels agree bitwise.
-__device__ __forceinline__ bool pair_in_tiles(const d4& a, const d4& b, double thr) {
-    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
-    const double s = __dadd_rn(__dadd_rn(a.z, b.z), thr);
-    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < __dmul_rn(s, s);
-}
-
-__device__ __forceinline__ float ex2_fast(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rsqrt_fast(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// ---------------------------------------------------------------------------
-// FP32 pair evaluation. Coordinates are FP32 offsets from each particle's
-// centre, pre-scaled by log2(e)/rho, so that exp(-r/rho) = exp2(-z') with
-// z' = |d'|, and t = 2/z = 2 log2(e)/z'. For z > 2:
-// K1(z) = exp(-z) z^{-1/2} P1(2t - 1). The special functions are the
-// single-instruction approximations ex2.approx.ftz and rsqrt.approx.ftz
-// (relative error ~2^-22).
-// ---------------------------------------------------------------------------
-struct PairF32 {
-    // z > 2: exp2(-z') P1(s) z'^{-1/2} (D'.g)/z' = K1(z) (D'.g) / (z' sqrt(log2 e))
-    __device__ __forceinline__ static float far(float dX, float dY, float gx, float gy) {
-        const float z2 = fmaf(dX, dX, dY * dY);
-        const float rz = rsqrt_fast(z2);                     // 1/z'
-        const float zp = z2 * rz;                            // z' = z log2 e
-        const float s = fmaf(4.0f * LOG2E_F, rz, -1.0f);     // 2t - 1
-        const float P = hornerf(YK_P1_F32, s);
-        const float e = ex2_fast(-zp);
-        const float sq = rsqrt_fast(zp);                     // (z log2 e)^{-1/2}
-        return (e * P * sq) * (rz * fmaf(dX, gx, dY * gy));
-    }
-    // any z, same units as far()
-    __device__ __forceinline__ static float any(float dX, float dY, float gx, float gy) {
-        const float z2 = fmaf(dX, dX, dY * dY);
-        const float rz = rsqrt_fast(z2);
-        const float zp = z2 * rz;
-        const float z = zp * (1.0f / LOG2E_F);
-        if (z > 2.0f) return far(dX, dY, gx, gy);
-        const float k1v = k1f(z, 2.0f / z);
-        return k1v * rsqrtf(LOG2E_F) * (rz * fmaf(dX, gx, dY * gy));
-    }
-    // normal derivative, unscaled coordinates d = x - y, target normal (nx, ny):
-    // [g (nu_x . G) + g' (d . G)(d . nu_x)/r] with G = w sigma nu_y (2 pi left out)
-    __device__ __forceinline__ static float grad(float dx, float dy, float nx, float ny, float gx,
-                                                 float gy, float kappa, float rho) {
-        const float r2 = fmaf(dx, dx, dy * dy);
-        const float ri = rsqrt_fast(r2);
-        const float z = r2 * ri * kappa;
-        const float t = 2.0f * rho * ri;
-        float k0v, k1v;
-        if (z > 2.0f) {
-            const float e = ex2_fast(-z * LOG2E_F) * rsqrt_fast(z);
-            const float s = 2.0f * t - 1.0f;
-            k0v = e * hornerf(YK_P0_F32, s);
-            k1v = e * hornerf(YK_P1_F32, s);
-        } else {
-            k01f(z, t, k0v, k1v);
-        }
-        const float g = k1v * ri * kappa;
-        const float gp = -(k0v * kappa + 2.0f * k1v * ri) * kappa * ri;
-        const float dn_s = fmaf(dx, gx, dy * gy);
-        const float nn = fmaf(nx, gx, ny * gy);
-        const float dn_t = fmaf(dx, nx, dy * ny);
-        return fmaf(g, nn, gp * dn_s * dn_t * ri);
-    }
-};
-
-struct TargetF32 {
-    float TX, TY;       // (scaled) target position relative to the source particle's centre
-    bool close, own, skip;
-    int pan;
-};
-
-// Target-side set-up against source particle s (all in FP32 from the hi/lo
-// centres, plus the FP64 tile predicate when a skip distance is given).
-__device__ __forceinline__ void target_setup(TargetF32& T, const GeomView& G, int pt, int s,
-                                             float2 xit, float scale, float near_gap,
-                                             bool mask, double skip_gap, int pan) {
-    const float4 ct = G.c32[pt], cs = G.c32[s];
-    const float dX = (ct.x - cs.x) + (ct.z - cs.z);
-    const float dY = (ct.y - cs.y) + (ct.w - cs.w);
-    T.own = (s == pt);
-    const float gap = sqrtf(dX * dX + dY * dY) - G.r32[pt] - G.r32[s];
-    T.close = T.own || gap <= near_gap;
-    T.skip = mask && pair_in_tiles(G.part[pt], G.part[s], skip_gap);
-    T.TX = fmaf(scale, dX, scale * xit.x);
-    T.TY = fmaf(scale, dY, scale * xit.y);
-    T.pan = pan;
-}
-
-// Packed FP32 evaluation of two far pairs at once (one target, two sources)
-// with the f32x2 FMA/ADD/MUL instructions of sm_100+: lanes .x/.y are the
-// two sources. Sources are staged as pairs: A = (-X0, -X1, -Y0, -Y1) in
-// scaled coordinates, B = (gx0, gx1, gy0, gy1). Returns the two terms in the
-// units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))) added to acc, z > 2 only.
-struct PolyRZ {
-    float2 c[7];
-    __device__ __forceinline__ PolyRZ() {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) c[k] = make_float2(YK_P1_F32_RZ[k], YK_P1_F32_RZ[k]);
-    }
-};
-
-__device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, const float4& B,
-                                       const PolyRZ& P, float2 acc) {
-    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
-    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
-    const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
-    const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));   // 1/z'
-    const float2 zp = __fmul2_rn(z2, rz);                                 // z'
-    float2 p = P.c[6];
-#pragma unroll
-    for (int k = 5; k >= 0; --k) p = __ffma2_rn(p, rz, P.c[k]);          // P1 in rz
-    const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
-    const float2 sq = make_float2(rsqrt_fast(zp.x), rsqrt_fast(zp.y));   // z'^{-1/2}
-    const float2 dot = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
-    return __ffma2_rn(__fmul2_rn(__fmul2_rn(e, p), sq), __fmul2_rn(rz, dot), acc);
-}
-
-// Scalar view of source q in the pair-packed staging.
-__device__ __forceinline__ float4 src_scalar(const float4* A, const float4* B, int q) {
-    const float4 a = A[q >> 1], b = B[q >> 1];
-    return (q & 1) ? make_float4(-a.y, -a.w, b.y, b.w) : make_float4(-a.x, -a.z, b.x, b.z);
-}
-
-// Two pairs of a close (non-own) source particle: the packed far form,
-// except that a lane with z <= 2 (z'^2 <= (2 log2 e)^2, outside the fitted
-// polynomial's range) takes the series of PairF32::any instead.
-constexpr float ZCUT2 = 4.0f * LOG2E_F * LOG2E_F;
-__device__ __forceinline__ float2 close2(float2 TX, float2 TY, const float4& A, const float4& B,
-                                         const PolyRZ& P, float2 acc) {
-    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
-    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
-    const float z2x = fmaf(dX.x, dX.x, dY.x * dY.x), z2y = fmaf(dX.y, dX.y, dY.y * dY.y);
-    if (z2x > ZCUT2 && z2y > ZCUT2) return far2(TX, TY, A, B, P, acc);
-    acc.x += PairF32::any(dX.x, dY.x, B.x, B.z);
-    acc.y += PairF32::any(dX.y, dY.y, B.y, B.w);
-    return acc;
-}
-
-// Packed FP32 normal derivative of two far pairs (one target with normal
-// (nx, ny), two sources), same scaled coordinates and staging as far2. With
-// E = exp2(-z') z'^{-1/2}, rz = 1/z', G = w sigma nu_y, D' the scaled d:
-//   [g (nu.G) + g' (d.G)(d.nu)/r] = sqrt(log2 e) kappa kappa' E rz
-//       [P1 (nu.G) - (ln2 P0 + 2 rz P1) (D'.G)(D'.nu) rz]
-// (kappa = 1/rho, kappa' = log2(e)/rho, kappa/kappa' = ln 2); the constant
-// sqrt(log2 e) kappa kappa' is applied by the caller.
-struct PolyRZ2 {
-    float2 c0[7], c1[7];
-    __device__ __forceinline__ PolyRZ2() {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            c0[k] = make_float2(YK_P0_F32_RZ[k], YK_P0_F32_RZ[k]);
-            c1[k] = make_float2(YK_P1_F32_RZ[k], YK_P1_F32_RZ[k]);
-        }
-    }
-};
-
-__device__ __forceinline__ float2 grad2(float2 TX, float2 TY, float2 NX, float2 NY, const float4& A,
-                                        const float4& B, const PolyRZ2& P, float2 acc) {
-    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
-    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
-    const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
-    const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));
-    const float2 zp = __fmul2_rn(z2, rz);
-    float2 p0 = P.c0[6], p1 = P.c1[6];
-#pragma unroll
-    for (int k = 5; k >= 0; --k) {
-        p0 = __ffma2_rn(p0, rz, P.c0[k]);
-        p1 = __ffma2_rn(p1, rz, P.c1[k]);
-    }
-    const float2 E = make_float2(ex2_fast(-zp.x) * rsqrt_fast(zp.x), ex2_fast(-zp.y) * rsqrt_fast(zp.y));
-    const float2 Gx = make_float2(B.x, B.y), Gy = make_float2(B.z, B.w);
-    const float2 nn = __ffma2_rn(NX, Gx, __fmul2_rn(NY, Gy));
-    const float2 dnG = __ffma2_rn(dX, Gx, __fmul2_rn(dY, Gy));
-    const float2 dnT = __ffma2_rn(dX, NX, __fmul2_rn(dY, NY));
-    const float2 aneg = __ffma2_rn(make_float2(-0.69314718f, -0.69314718f), p0,
-                                   __fmul2_rn(__fmul2_rn(make_float2(-2.0f, -2.0f), rz), p1));
-    const float2 bneg = __fmul2_rn(__fmul2_rn(aneg, dnG), __fmul2_rn(dnT, rz));
-    const float2 br = __ffma2_rn(p1, nn, bneg);
-    return __ffma2_rn(__fmul2_rn(E, rz), br, acc);
-}
-
-// Stage sources [jb, jb + cnt) of the particle at `base` in pair-packed form
-// (scaled coordinates negated, g = w sigma nu); pads with a far weightless source.
-__device__ __forceinline__ void stage_pairs(const GeomView& G, const double* __restrict__ sigma,
-                                            int64_t base, int jb, int cnt, float kpf,
-                                            float4* srcA, float4* srcB) {
-    const int npair = (cnt + 1) >> 1;
-    for (int m = threadIdx.x; m < npair; m += blockDim.x) {
-        float xs[2], ys[2], gx[2], gy[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = 2 * m + h;
-            if (q < cnt) {
-                const int64_t j = base + jb + q;
-                const float2 x = G.xi[j];
-                const double ws = G.w[j] * sigma[j];
-                xs[h] = -kpf * x.x;
-                ys[h] = -kpf * x.y;
-                gx[h] = (float)(ws * G.nx[j]);
-                gy[h] = (float)(ws * G.ny[j]);
-            } else {
-                xs[h] = 1.0e6f;
-                ys[h] = 0.0f;
-                gx[h] = 0.0f;
-                gy[h] = 0.0f;
-            }
-        }
-        srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
-        srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
-    }
-}
-
-// One staged tile of the normal derivative for two targets: packed far
-// pairs into f0/f1 (scaled units), near/own pairs (scalar) into s0/s1.
-__device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB, int jb, int cnt,
-                                          const GeomView& G, const TargetF32& T0,
-                                          const TargetF32& T1, bool use0, bool use1, float nx0,
-                                          float ny0, float nx1, float ny1, float inv_kp,
-                                          float kappa, float rho, const PolyRZ2& P, float& f0,
-                                          float& f1, float& s0, float& s1) {
-    const int npair = (cnt + 1) >> 1;
-    if (use0 && use1 && !T0.close && !T1.close) {
-        const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
-        const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
-        const float2 NX0 = make_float2(nx0, nx0), NY0 = make_float2(ny0, ny0);
-        const float2 NX1 = make_float2(nx1, nx1), NY1 = make_float2(ny1, ny1);
-        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-        for (int m = 0; m < npair; ++m) {
-            const float4 A = srcA[m], B = srcB[m];
-            a0 = grad2(TX0, TY0, NX0, NY0, A, B, P, a0);
-            a1 = grad2(TX1, TY1, NX1, NY1, A, B, P, a1);
-        }
-        f0 += a0.x + a0.y;
-        f1 += a1.x + a1.y;
-        return;
-    }
-    for (int q = 0; q < cnt; ++q) {
-        const float4 S = src_scalar(srcA, srcB, q);
-        const int pq = (jb + q) / G.ngl;
-        if (use0 && !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
-            s0 += PairF32::grad((T0.TX - S.x) * inv_kp, (T0.TY - S.y) * inv_kp, nx0, ny0, S.z, S.w,
-                                kappa, rho);
-        if (use1 && !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
-            s1 += PairF32::grad((T1.TX - S.x) * inv_kp, (T1.TY - S.y) * inv_kp, nx1, ny1, S.z, S.w,
-                                kappa, rho);
-    }
-}
-
-template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
-                                                     int ppc, float kscale, double skip_gap,
-                                                     bool own_by_block,
-                                                     double* __restrict__ partial) {
-    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
-    const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const int64_t i1 = i0 + F32_TPB;
-    const bool act0 = i0 < G.n, act1 = i1 < G.n;
-    const int64_t ii0 = act0 ? i0 : 0, ii1 = act1 ? i1 : 0;
-    const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
-    const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
-    const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
-    const float kpf = (float)(LOG2E / G.rho);          // log2(e) / rho
-    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;  // z <= 2 possible below
-    const int s0 = blockIdx.y * ppc;
-    const int s1 = min(G.np, s0 + ppc);
-    const PolyRZ P;
-    double acc0 = 0.0, acc1 = 0.0;
-    for (int s = s0; s < s1; ++s) {
-        const int64_t base = (int64_t)s * G.npp;
-        TargetF32 T0, T1;
-        target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
-        target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-        // a target skips the source particle when the FP64 tiles hold the pair
-        // (MASK) or when it is the target's own particle and the self block
-        // adds it (own_by_block); the particle is skipped only when every
-        // thread of the block agrees (a block-wide vote reached by all
-        // threads), so barriers stay uniform
-        const bool skip0 = (MASK && T0.skip) || (own_by_block && T0.own);
-        const bool skip1 = (MASK && T1.skip) || (own_by_block && T1.own);
-        const bool block_skip = (MASK || own_by_block) ? __syncthreads_and(skip0 && skip1) : false;
-        if (block_skip) continue;
-        for (int jb = 0; jb < G.npp; jb += STILE) {
-            const int cnt = min(STILE, G.npp - jb);
-            const int npair = (cnt + 1) >> 1;
-            __syncthreads();
-            for (int m = threadIdx.x; m < npair; m += F32_TPB) {
-                float xs[2], ys[2], gx[2], gy[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = 2 * m + h;
-                    if (q < cnt) {
-                        const int64_t j = base + jb + q;
-                        const float2 x = G.xi[j];
-                        const double ws = G.w[j] * sigma[j];
-                        xs[h] = -kpf * x.x;
-                        ys[h] = -kpf * x.y;
-                        gx[h] = (float)(ws * G.nx[j]);
-                        gy[h] = (float)(ws * G.ny[j]);
-                    } else {       // padding: a far, weightless source
-                        xs[h] = 1.0e6f;
-                        ys[h] = 0.0f;
-                        gx[h] = 0.0f;
-                        gy[h] = 0.0f;
-                    }
-                }
-                srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
-                srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
-            }
-            __syncthreads();
-            float r0 = 0.0f, r1 = 0.0f;
-            if (!T0.close && !T1.close && !skip0 && !skip1) {
-                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
-                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
-                float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-#pragma unroll 2
-                for (int m = 0; m < npair; ++m) {
-                    const float4 A = srcA[m], B = srcB[m];
-                    a0 = far2(TX0, TY0, A, B, P, a0);
-                    a1 = far2(TX1, TY1, A, B, P, a1);
-                }
-                r0 = a0.x + a0.y;
-                r1 = a1.x + a1.y;
-            } else {
-                for (int q = 0; q < cnt; ++q) {
-                    const float4 S = src_scalar(srcA, srcB, q);
-                    const int pq = (jb + q) / G.ngl;
-                    if (!skip0 && !(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
-                        r0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
-                    if (!skip1 && !(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
-                        r1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
-                }
-            }
-            acc0 += (double)r0;
-            acc1 += (double)r1;
-        }
-    }
-    if (act0) partial[blockIdx.y * G.n + i0] = acc0 * (double)kscale;
-    if (act1) partial[blockIdx.y * G.n + i1] = acc1 * (double)kscale;
-}
-
-// FP32 normal derivative of the far field, two targets per thread, packed
-// pairs (same staging and masking as k_p2p_f32).
-template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
-                                                          const double* __restrict__ sigma,
-                                                          int ppc, double skip_gap,
-                                                          double* __restrict__ partial) {
-    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
-    const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const int64_t i1 = i0 + F32_TPB;
-    const bool act0 = i0 < G.n, act1 = i1 < G.n;
-    const int64_t ii0 = act0 ? i0 : 0, ii1 = act1 ? i1 : 0;
-    const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
-    const float nx0 = (float)G.nx[ii0], ny0 = (float)G.ny[ii0];
-    const float nx1 = (float)G.nx[ii1], ny1 = (float)G.ny[ii1];
-    const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
-    const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
-    const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
-    const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
-    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const PolyRZ2 P;
-    const int s0 = blockIdx.y * ppc;
-    const int s1 = min(G.np, s0 + ppc);
-    double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
-    for (int s = s0; s < s1; ++s) {
-        const int64_t base = (int64_t)s * G.npp;
-        TargetF32 T0, T1;
-        target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
-        target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-        const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
-        if (block_skip) continue;
-        const bool use0 = !(MASK && T0.skip), use1 = !(MASK && T1.skip);
-        for (int jb = 0; jb < G.npp; jb += STILE) {
-            const int cnt = min(STILE, G.npp - jb);
-            __syncthreads();
-            stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
-            __syncthreads();
-            float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-            grad_tile(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1, inv_kp,
-                      kappa, rho, P, a0, a1, b0, b1);
-            fast0 += (double)a0;
-            fast1 += (double)a1;
-            slow0 += (double)b0;
-            slow1 += (double)b1;
-        }
-    }
-    const double cf = sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho);
-    const double sc = 1.0 / (2.0 * PI);
-    if (act0) partial[blockIdx.y * G.n + i0] = (fast0 * cf + slow0) * sc;
-    if (act1) partial[blockIdx.y * G.n + i1] = (fast1 * cf + slow1) * sc;
-}
-
-// ---------------------------------------------------------------------------
-// Cut-off far field: one block per target particle, sweeping only the source
-// particles in its neighbour list (bounding-circle gap below the cut-off);
-// the block owns all its targets, so it writes complete sums. Same pair
-// evaluation and masking as the chunked kernels.
-// ---------------------------------------------------------------------------
-template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const double* __restrict__ sigma,
-                                                         float kscale, double skip_gap,
-                                                         bool own_by_block,
-                                                         const int* __restrict__ nbr_off,
-                                                         const int* __restrict__ nbr,
-                                                         double* __restrict__ out) {
-    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
-    const int pt = blockIdx.x;
-    const float kpf = (float)(LOG2E / G.rho);
-    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const PolyRZ P;
-    const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
-    for (int ib = 0; ib < G.npp; ib += TPB) {
-        const int l0 = ib + threadIdx.x, l1 = l0 + F32_TPB;
-        const bool act0 = l0 < G.npp, act1 = l1 < G.npp;
-        const int64_t ii0 = (int64_t)pt * G.npp + (act0 ? l0 : 0);
-        const int64_t ii1 = (int64_t)pt * G.npp + (act1 ? l1 : 0);
-        const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
-        const int pan0 = (act0 ? l0 : 0) / G.ngl, pan1 = (act1 ? l1 : 0) / G.ngl;
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int k = n0; k < n1; ++k) {
-            const int s = nbr[k];
-            TargetF32 T0, T1;
-            target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
-            target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-            // uniform: one target particle per block
-            if ((MASK && T0.skip) || (own_by_block && T0.own)) continue;
-            const int64_t base = (int64_t)s * G.npp;
-            for (int jb = 0; jb < G.npp; jb += STILE) {
-                const int cnt = min(STILE, G.npp - jb);
-                const int npair = (cnt + 1) >> 1;
-                __syncthreads();
-                for (int m = threadIdx.x; m < npair; m += F32_TPB) {
-                    float xs[2], ys[2], gx[2], gy[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int q = 2 * m + h;
-                        if (q < cnt) {
-                            const int64_t j = base + jb + q;
-                            const float2 x = G.xi[j];
-                            const double ws = G.w[j] * sigma[j];
-                            xs[h] = -kpf * x.x;
-                            ys[h] = -kpf * x.y;
-                            gx[h] = (float)(ws * G.nx[j]);
-                            gy[h] = (float)(ws * G.ny[j]);
-                        } else {
-                            xs[h] = 1.0e6f;
-                            ys[h] = 0.0f;
-                            gx[h] = 0.0f;
-                            gy[h] = 0.0f;
-                        }
-                    }
-                    srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
-                    srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
-                }
-                __syncthreads();
-                float r0 = 0.0f, r1 = 0.0f;
-                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
-                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
-                if (!T0.close) {
-                    float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-#pragma unroll 2
-                    for (int m = 0; m < npair; ++m) {
-                        const float4 A = srcA[m], B = srcB[m];
-                        a0 = far2(TX0, TY0, A, B, P, a0);
-                        a1 = far2(TX1, TY1, A, B, P, a1);
-                    }
-                    r0 = a0.x + a0.y;
-                    r1 = a1.x + a1.y;
-                } else if (!T0.own) {
-                    float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-                    for (int m = 0; m < npair; ++m) {
-                        const float4 A = srcA[m], B = srcB[m];
-                        a0 = close2(TX0, TY0, A, B, P, a0);
-                        a1 = close2(TX1, TY1, A, B, P, a1);
-                    }
-                    r0 = a0.x + a0.y;
-                    r1 = a1.x + a1.y;
-                } else {
-                    for (int q = 0; q < cnt; ++q) {
-                        const float4 S = src_scalar(srcA, srcB, q);
-                        const int pq = (jb + q) / G.ngl;
-                        if (!(T0.own && is_near_panel(T0.pan, pq, G.npan, G.near_w)))
-                            r0 += PairF32::any(T0.TX - S.x, T0.TY - S.y, S.z, S.w);
-                        if (!(T1.own && is_near_panel(T1.pan, pq, G.npan, G.near_w)))
-                            r1 += PairF32::any(T1.TX - S.x, T1.TY - S.y, S.z, S.w);
-                    }
-                }
-                acc0 += (double)r0;
-                acc1 += (double)r1;
-            }
-        }
-        if (act0) out[ii0] = acc0 * (double)kscale;
-        if (act1) out[ii1] = acc1 * (double)kscale;
-    }
-}
-
-template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
-                                                              const double* __restrict__ sigma,
-                                                              double skip_gap,
-                                                              const int* __restrict__ nbr_off,
-                                                              const int* __restrict__ nbr,
-                                                              double* __restrict__ out) {
-    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
-    const int pt = blockIdx.x;
-    const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
-    const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
-    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const PolyRZ2 P;
-    const double cf = sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho);
-    const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
-    for (int ib = 0; ib < G.npp; ib += TPB) {
-        const int l0 = ib + threadIdx.x, l1 = l0 + F32_TPB;
-        const bool act0 = l0 < G.npp, act1 = l1 < G.npp;
-        const int64_t ii0 = (int64_t)pt * G.npp + (act0 ? l0 : 0);
-        const int64_t ii1 = (int64_t)pt * G.npp + (act1 ? l1 : 0);
-        const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
-        const float nx0 = (float)G.nx[ii0], ny0 = (float)G.ny[ii0];
-        const float nx1 = (float)G.nx[ii1], ny1 = (float)G.ny[ii1];
-        const int pan0 = (act0 ? l0 : 0) / G.ngl, pan1 = (act1 ? l1 : 0) / G.ngl;
-        double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
-        for (int k = n0; k < n1; ++k) {
-            const int s = nbr[k];
-            TargetF32 T0, T1;
-            target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
-            target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-            if (MASK && T0.skip) continue;   // uniform: one target particle per block
-            const int64_t base = (int64_t)s * G.npp;
-            for (int jb = 0; jb < G.npp; jb += STILE) {
-                const int cnt = min(STILE, G.npp - jb);
-                __syncthreads();
-                stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
-                __syncthreads();
-                float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-                grad_tile(srcA, srcB, jb, cnt, G, T0, T1, true, true, nx0, ny0, nx1, ny1, inv_kp,
-                          kappa, rho, P, a0, a1, b0, b1);
-                fast0 += (double)a0;
-                fast1 += (double)a1;
-                slow0 += (double)b0;
-                slow1 += (double)b1;
-            }
-        }
-        const double sc = 1.0 / (2.0 * PI);
-        if (act0) out[ii0] = (fast0 * cf + slow0) * sc;
-        if (act1) out[ii1] = (fast1 * cf + slow1) * sc;
-    }
-}
-
-// Cut-off neighbour lists: counts, a single-block exclusive scan, fill.
-__global__ void k_nbr_count(int np, const d4* __restrict__ part, double thr, int* counts) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= np) return;
-    const d4 a = part[P];
-    int c = 0;
-    for (int Q = 0; Q < np; ++Q) c += (Q == P || pair_in_tiles(a, part[Q], thr)) ? 1 : 0;
-    counts[P] = c;
-}
-
-__global__ void k_scan_offsets(int np, const int* __restrict__ counts, int* __restrict__ off) {
-    __shared__ int buf[1024];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b = 0; b < np; b += 1024) {
-        const int i = b + threadIdx.x;
-        buf[threadIdx.x] = (i < np) ? counts[i] : 0;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {   // inclusive Hillis-Steele scan
-            const int v = (threadIdx.x >= o) ? buf[threadIdx.x - o] : 0;
-            __syncthreads();
-            buf[threadIdx.x] += v;
-            __syncthreads();
-        }
-        if (i < np) off[i + 1] = carry + buf[threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += buf[1023];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) off[0] = 0;
-}
-
-__global__ void k_nbr_fill(int np, const d4* __restrict__ part, double thr,
-                           const int* __restrict__ off, int* __restrict__ nbr) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= np) return;
-    const d4 a = part[P];
-    int k = off[P];
-    for (int Q = 0; Q < np; ++Q)
-        if (Q == P || pair_in_tiles(a, part[Q], thr)) nbr[k++] = Q;
-}
-
-// ---------------------------------------------------------------------------
-// FP64 pair tiles. Value: k = K1(z)/r; the (i <- j) term is k (d . g_j) and
-// the (j <- i) term is -k (d . g_i), with g = w sigma nu and d = x_i - x_j.
-// Gradient: G_ij = g (nu_i . nu_j) + g' (d . nu_j)(d . nu_i)/r is symmetric;
-// the terms are G_ij (w sigma)_j and G_ij (w sigma)_i.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <bool GRAD>
-__global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const double* __restrict__ sigma,
-                                                           const int2* __restrict__ tiles, int ntiles,
-                                                           double* __restrict__ out) {
-    __shared__ d4 srcQ[STILE];         // x, y, and (value) g = w sigma nu | (grad) nu
-    __shared__ double wsQ[STILE];      // (grad) w sigma
-    __shared__ double ys[STILE];       // Q-side sums for the staged chunk
-    const double rho = G.rho, kappa = 1.0 / rho, two_rho = 2.0 * rho;
-    const double scale = GRAD ? 1.0 / (2.0 * PI) : 1.0 / (2.0 * PI * rho);
-    const int lane = threadIdx.x & 31;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int P = tiles[t].x, Q = tiles[t].y;
-        const bool own = (P == Q);
-        for (int ib = 0; ib < G.npp; ib += TILE_TPB) {
-            const int li = ib + threadIdx.x;
-            const bool act = li < G.npp;
-            const int64_t i = (int64_t)P * G.npp + (act ? li : 0);
-            const double tx = G.x[i], ty = G.y[i];
-            const double tnx = G.nx[i], tny = G.ny[i];
-            const double tws = act ? G.w[i] * sigma[i] : 0.0;
-            const int tpan = (act ? li : 0) / G.ngl;
-            double acc = 0.0;
-            for (int jb = 0; jb < G.npp; jb += STILE) {
-                const int cnt = min(STILE, G.npp - jb);
-                __syncthreads();
-                if (threadIdx.x < cnt) {
-                    const int64_t j = (int64_t)Q * G.npp + jb + threadIdx.x;
-                    const double ws = G.w[j] * sigma[j];
-                    if (GRAD) {
-                        srcQ[threadIdx.x] = make_d4(G.x[j], G.y[j], G.nx[j], G.ny[j]);
-                        wsQ[threadIdx.x] = ws;
-                    } else {
-                        srcQ[threadIdx.x] = make_d4(G.x[j], G.y[j], ws * G.nx[j], ws * G.ny[j]);
-                    }
-                    ys[threadIdx.x] = 0.0;
-                }
-                __syncthreads();
-                for (int q = 0; q < cnt; ++q) {
-                    double ki = 0.0, kj = 0.0;
-                    const bool skip = own && is_near_panel(tpan, (jb + q) / G.ngl, G.npan, G.near_w);
-                    if (act && !skip) {
-                        const d4 S = srcQ[q];
-                        const double dx = tx - S.x, dy = ty - S.y;
-                        const double r2 = fma(dx, dx, dy * dy);
-                        const double ri = rsqrt(r2);
-                        const double z = r2 * ri * kappa;
-                        if (!GRAD) {
-                            double k1v;
-                            if (z <= 2.0) k1v = k1_series(z);
-                            else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
-                            const double k = k1v * ri;
-                            ki = k * fma(dx, S.z, dy * S.w);
-                            kj = -k * fma(dx, tnx * tws, dy * (tny * tws));
-                        } else {
-                            double k0v, k1v;
-                            k01(z, k0v, k1v);
-                            const double gg = k1v * ri * kappa;
-                            const double gp = -(k0v * kappa + 2.0 * k1v * ri) * kappa * ri;
-                            const double nn = fma(tnx, S.z, tny * S.w);
-                            const double dn_s = fma(dx, S.z, dy * S.w);
-                            const double dn_t = fma(dx, tnx, dy * tny);
-                            const double Gij = fma(gg, nn, gp * dn_s * dn_t * ri);
-                            ki = Gij * wsQ[q];
-                            kj = Gij * tws;
-                        }
-                    }
-                    acc += ki;
-                    if (!own) {   // tile-uniform: the whole block takes this branch
-                        const double v = warp_sum(kj);
-                        if (lane == 0 && v != 0.0) atomicAdd(&ys[q], v);
-                    }
-                }
-                if (!own) {
-                    __syncthreads();
-                    if (threadIdx.x < cnt)
-                        atomicAdd(&out[(int64_t)Q * G.npp + jb + threadIdx.x], ys[threadIdx.x] * scale);
-                }
-            }
-            if (act) atomicAdd(&out[i], acc * scale);
-        }
-    }
-}
-
-// List the particle pairs (P <= Q) with pair_in_tiles(P, Q, thr), leaving out
-// P == Q when self_pairs is false (the self blocks cover them). Writes up to
-// cap entries; *count receives the total.
-__global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, bool self_pairs,
-                            int* count, int2* __restrict__ out, int cap) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= np) return;
-    const d4 a = part[P];
-    for (int Q = self_pairs ? P : P + 1; Q < np; ++Q) {
-        if (Q == P || pair_in_tiles(a, part[Q], thr)) {
-            const int k = atomicAdd(count, 1);
-            if (k < cap) out[k] = make_int2(P, Q);
-        }
-    }
-}
-
-// out_P += S[shape(P)] sigma_P for the far part of the self block (value or
-// normal derivative, stored transposed), one CTA per particle.
-__global__ void k_self_apply(GeomView G, const double* __restrict__ S,
-                             const double* __restrict__ sigma, double* __restrict__ out) {
-    extern __shared__ double xs[];
-    const int P = blockIdx.x;
-    const int64_t base = (int64_t)P * G.npp;
-    for (int j = threadIdx.x; j < G.npp; j += blockDim.x) xs[j] = sigma[base + j];
-    __syncthreads();
-    const double* M = S + (int64_t)G.shape_of[P] * G.npp * G.npp;
-    for (int i = threadIdx.x; i < G.npp; i += blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < G.npp; ++j) acc = fma(M[(int64_t)j * G.npp + i], xs[j], acc);
-        out[base + i] += acc;
-    }
-}
-
-// The same in FP32 for the inner operator: out_P (+)= S32[shape(P)] sigma_P.
-template <bool ACC>
-__global__ void k_self_apply_f32(GeomView G, const float* __restrict__ S,
-                                 const double* __restrict__ sigma, double* __restrict__ out) {
-    extern __shared__ float xf[];
-    const int P = blockIdx.x;
-    const int64_t base = (int64_t)P * G.npp;
-    for (int j = threadIdx.x; j < G.npp; j += blockDim.x) xf[j] = (float)sigma[base + j];
-    __syncthreads();
-    const float* M = S + (int64_t)G.shape_of[P] * G.npp * G.npp;
-    for (int i = threadIdx.x; i < G.npp; i += blockDim.x) {
-        float acc = 0.0f;
-        for (int j = 0; j < G.npp; ++j) acc = fmaf(M[(int64_t)j * G.npp + i], xf[j], acc);
-        if (ACC) out[base + i] += (double)acc;
-        else out[base + i] = (double)acc;
-    }
-}
-
-// y_i = sum_chunks partial[c][i] + extra_i + sum_near C[shape][local i][c] sigma[near c]
-__global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ partial,
-                           const double* __restrict__ extra, const double* __restrict__ rows,
-                           const double* __restrict__ sigma, double* __restrict__ y) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= G.n) return;
-    double acc = extra ? extra[i] : 0.0;
-    for (int c = 0; c < nchunk; ++c) acc += partial[c * G.n + i];
-    const int p = (int)(i / G.npp);
-    const int li = (int)(i % G.npp);
-    const int k = li / G.ngl;
-    const int rowlen = G.n_near * G.ngl;
-    const double* row = rows + ((int64_t)G.shape_of[p] * G.npp + li) * rowlen;
-    const int64_t base = (int64_t)p * G.npp;
-    double nr = 0.0;
-    for (int q = 0; q < G.n_near; ++q) {
-        const int pk = (2 * G.near_w + 1 >= G.npan) ? q
-                       : ((k - G.near_w + q) % G.npan + G.npan) % G.npan;
-        const double* sq = sigma + base + (int64_t)pk * G.ngl;
-        const double* rq = row + q * G.ngl;
-        for (int j = 0; j < G.ngl; ++j) nr = fma(rq[j], sq[j], nr);
-    }
-    y[i] = acc + nr;
-}
-
-// u(t) = D[sigma](t) at off-surface targets, FP64, all sources.
-__global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __restrict__ sigma,
-                                                   const double* __restrict__ tgt, int64_t nt,
-                                                   int ppc, double* __restrict__ partial) {
-    __shared__ d4 src[STILE];
-    const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const bool active = i < nt;
-    const double tx = active ? tgt[2 * i] : 0.0, ty = active ? tgt[2 * i + 1] : 0.0;
-    const double rho = G.rho, kappa = 1.0 / rho, two_rho = 2.0 * rho;
-    const int s0 = blockIdx.y * ppc;
-    const int s1 = min(G.np, s0 + ppc);
-    double acc = 0.0;
-    for (int s = s0; s < s1; ++s) {
-        const int64_t base = (int64_t)s * G.npp;
-        for (int jb = 0; jb < G.npp; jb += STILE) {
-            const int cnt = min(STILE, G.npp - jb);
-            __syncthreads();
-            if (threadIdx.x < cnt) {
-                const int64_t j = base + jb + threadIdx.x;
-                const double ws = G.w[j] * sigma[j];
-                src[threadIdx.x] = make_d4(G.x[j], G.y[j], ws * G.nx[j], ws * G.ny[j]);
-            }
-            __syncthreads();
-            if (!active) continue;
-            for (int q = 0; q < cnt; ++q) {
-                const d4 S = src[q];
-                const double dx = tx - S.x, dy = ty - S.y;
-                const double r2 = fma(dx, dx, dy * dy);
-                const double ri = rsqrt(r2);
-                const double z = r2 * ri * kappa;
-                double k1v;
-                if (z <= 2.0) k1v = k1_series(z);
-                else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
-                acc = fma(k1v * ri, fma(dx, S.z, dy * S.w), acc);
-            }
-        }
-    }
-    if (active) partial[blockIdx.y * nt + i] = acc / (2.0 * PI * rho);
-}
-
-__global__ void k_sum_chunks(int64_t n, int nchunk, const double* __restrict__ partial,
-                             double* __restrict__ out) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double acc = 0.0;
-    for (int c = 0; c < nchunk; ++c) acc += partial[c * n + i];
-    out[i] = acc;
-}
-
-// ---------------------------------------------------------------------------
 
 // The FP64 tile list for a split distance (kind 0: residual, 1: gradient,
 // 2: all pairs), built on first use and after the particles move.
@@ -1024,10 +165,28 @@ static int fmm_apply(yk_geom* g, const double* sigma, double* y) {
     return YK_OK;
 }
 
-// Leaf level of the FMM: the one given (fmm_leaf) or the fastest of the
-// admissible ones, timed with CUDA events on the first application (each
-// candidate applied once to warm up, then twice timed). Without an
-// admissible level the far field falls back to the cut-off P2P.
+// Autotuned leaf sides (in units of the bounding radius R), shared by every
+// geometry of the process: systems with the same order, nodes per particle,
+// rho/R and particle density (both on a quarter-octave grid) reuse the
+// choice instead of timing the candidates again.
+using FmmTuneKey = std::tuple<int, int, int, int>;
+static std::mutex g_fmm_tune_mutex;
+static std::map<FmmTuneKey, double> g_fmm_tune;
+
+static FmmTuneKey fmm_tune_key(yk_geom* g) {
+    double x0, y0, side;
+    fmm_root_box(g, &x0, &y0, &side);
+    const double R = g->max_radius;
+    const double dens = (double)g->np * R * R / std::max(side * side, R * R);
+    return FmmTuneKey(g->prm.fmm_order, g->npp, (int)lround(4.0 * log2(g->prm.rho / R)),
+                      (int)lround(4.0 * log2(dens)));
+}
+
+// Leaf level of the FMM: the one given (fmm_leaf), the cached choice for
+// similar systems, or the fastest of the admissible ones, timed with CUDA
+// events on the first application (each candidate applied once to warm up,
+// then twice timed). Without an admissible level the far field falls back
+// to the cut-off P2P.
 static int fmm_tune(yk_geom* g, const double* sigma, double* y) {
     FmmTree& F = g->fmm;
     const double leaf = g->prm.fmm_leaf;
@@ -1052,7 +211,23 @@ static int fmm_tune(yk_geom* g, const double* sigma, double* y) {
     }
     F.far_off = false;
     F.Lsel = hi;
-    if (lo < hi) {
+    const FmmTuneKey key = fmm_tune_key(g);
+    double cached = 0.0;
+    {
+        std::lock_guard<std::mutex> lk(g_fmm_tune_mutex);
+        auto it = g_fmm_tune.find(key);
+        if (it != g_fmm_tune.end()) cached = it->second;
+    }
+    if (lo < hi && cached > 0.0) {
+        // the admissible level whose leaf side is closest to the cached one
+        double x0, y0, side;
+        fmm_root_box(g, &x0, &y0, &side);
+        double best = INFINITY;
+        for (int L = lo; L <= hi; ++L) {
+            const double d = fabs(log(side / (double)(1 << L) / (cached * g->max_radius)));
+            if (d < best) best = d, F.Lsel = L;
+        }
+    } else if (lo < hi) {
         cudaStream_t st = g->ctx->stream;
         cudaEvent_t e0, e1;
         YK_TRY_CUDA(cudaEventCreate(&e0));
@@ -1078,6 +253,10 @@ static int fmm_tune(yk_geom* g, const double* sigma, double* y) {
         cudaEventDestroy(e1);
         YK_TRY(rc);
         F.valid = false;
+        double x0, y0, side;
+        fmm_root_box(g, &x0, &y0, &side);
+        std::lock_guard<std::mutex> lk(g_fmm_tune_mutex);
+        g_fmm_tune[key] = side / (double)(1 << F.Lsel) / g->max_radius;
     }
     F.tuned = true;
     return YK_OK;

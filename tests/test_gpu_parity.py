@@ -398,21 +398,27 @@ def test_serving_alone_and_in_mix(yk):
     submitted together (several in flight at once on different streams),
     give the same density, forces and torques as each solved alone."""
     ctx = yk.Context(0)
-    specs = [(3, 8, 0.5, 0), (6, 10, 1.0, 1), (2, 16, 2.0, 0), (9, 8, 1.0, 1), (14, 12, 0.5, 0),
-             (5, 20, 2.0, 1), (1, 16, 1.0, 0), (11, 9, 1.0, 0), (7, 14, 0.5, 1), (4, 24, 2.0, 0),
-             (16, 8, 1.0, 1), (8, 11, 2.0, 0)]
-    wls = []
-    for k, (n, npan, rho, shape) in enumerate(specs):
+    # (particles, panels, rho, shape, far field); the FMM requests tune their
+    # leaf size when solved alone and reuse the cached choice in the mix
+    dense, fmm = yk.YK_FARFIELD_DENSE, yk.YK_FARFIELD_FMM
+    specs = [(3, 8, 0.5, 0, dense), (6, 10, 1.0, 1, dense), (2, 16, 2.0, 0, dense),
+             (9, 8, 1.0, 1, dense), (14, 12, 0.5, 0, dense), (5, 20, 2.0, 1, dense),
+             (1, 16, 1.0, 0, dense), (11, 9, 1.0, 0, dense), (7, 14, 0.5, 1, dense),
+             (4, 24, 2.0, 0, dense), (16, 8, 1.0, 1, dense), (8, 11, 2.0, 0, dense),
+             (40, 8, 1.0, 0, fmm), (30, 10, 2.0, 1, fmm)]
+    wls, prms = [], []
+    for k, (n, npan, rho, shape, ff) in enumerate(specs):
         wls.append(W.small_system(n, 40 + k, shape=shape, n_panels=npan, rho=rho,
                                   A=1.0, B=0.5 if shape else 1.0, gap=0.3))
+        prms.append(_params(yk, wls[-1], farfield=ff))
     alone = []
-    for wl in wls:
-        g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+    for wl, prm in zip(wls, prms):
+        g = yk.Geometry(ctx, wl.particles, prm)
         f = g.yk_label(0, 10.0)
         s, F, tau, info = g.yk_solve_forces(f)
         alone.append((s, F.reshape(-1), tau))
         g.close()
-    ids = [ctx.yk_submit(wl.particles, _params(yk, wl)) for wl in wls]
+    ids = [ctx.yk_submit(wl.particles, prm) for wl, prm in zip(wls, prms)]
     # poll while requests are in flight, then drain the rest
     seen = {}
     for _ in range(3):
