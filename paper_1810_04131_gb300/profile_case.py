@@ -1,6 +1,7 @@
 """Run one kernel case of the yk library on a named workload, for profilers.
 
     python -m paper_1810_04131_gb300.profile_case --case p2p_f32 --workload disks512 --reps 2
+        [--farfield dense|cutoff|fmm]
 
 Cases: p2p_f32 (mixed matvec: FP32 far field + near rows), p2p_f64 (FP64
 matvec), grad (precision-split normal derivative), qbx (geometry + QBX rows), solve (one mixed solve +
@@ -20,13 +21,16 @@ def main():
                     choices=["p2p_f32", "p2p_f64", "grad", "qbx", "solve"])
     ap.add_argument("--workload", default="disks512")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--farfield", default="dense", choices=["dense", "cutoff", "fmm"])
     a = ap.parse_args()
     import torch
     from paper_1810_04131_gb300 import workloads as W
     from paper_1810_04131_gb300 import yk
     wl = W.WORKLOADS[a.workload]()
     ctx = yk.Context(0, torch.cuda.current_stream().cuda_stream)
-    prm = yk.params_for(wl)
+    prm = yk.params_for(wl, farfield={"dense": yk.YK_FARFIELD_DENSE,
+                                      "cutoff": yk.YK_FARFIELD_CUTOFF,
+                                      "fmm": yk.YK_FARFIELD_FMM}[a.farfield])
     g = yk.Geometry(ctx, wl.particles, prm)
     dev = torch.device("cuda", 0)
     f = torch.zeros(g.n, dtype=torch.float64, device=dev)
