@@ -462,6 +462,19 @@ class Oracle:
         tau = tau0 - (a[:, 0] * F[:, 1] - a[:, 1] * F[:, 0])
         return F, tau, tau0
 
+    def energy(self, f, un):
+        """Eq. main, Phi = gamma min I[u] with I[u] = int_Omega rho |grad u|^2 +
+        u^2 / rho dx, in boundary form. Green's first identity on the water
+        domain Omega (outward normal n = -nu on each particle boundary) with
+        Delta u = u / rho^2 (Eq. SL) gives int rho |grad u|^2 = -rho int_Sigma u
+        du/dnu - int u^2 / rho, so I[u] = -rho int_Sigma f du/dnu ds (u -> 0 at
+        infinity). Returns the per-particle parts -gamma rho int_{Sigma_i} f u_nu ds
+        (Np,); Phi is their sum."""
+        g = self.geom
+        e = np.zeros(g.n_particles)
+        np.add.at(e, g.part, -self.gamma * self.rho * g.w * f * un)
+        return e
+
     # ---- 6. off-surface potential (Eq. intrep) ------------------------------
     def potential(self, sigma, targets):
         g = self.geom

@@ -379,3 +379,69 @@ def test_planted_mistakes_are_caught(monkeypatch):
         assert not _circle_ok(yo), name
         monkeypatch.undo()
     assert _circle_ok(yo)
+
+
+# --------------------------------------------------------------------------
+# energy (Eq. main) and its variation (Section 7.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho", [0.25, 1.0, 4.0])
+def test_energy_single_disk_closed_form(rho):
+    """Eq. main for the unit disk with f = (1 + cos theta)/2: the oracle's
+    boundary form -gamma rho int f u_nu ds against the closed form
+    -(pi/4) [2 K0'(z)/K0(z) + K1'(z)/K1(z)], z = 1/rho (from Eq. true_soln),
+    and the closed form against the domain integral of Eq. main2,
+    int rho |grad u|^2 + u^2/rho dx, by radial quadrature of the exact
+    field's two Fourier modes (which pins the Green-identity reduction)."""
+    o = yo.Oracle(_disk(phi=0.3), 16, 16, rho, yo.QBXParams(order=10))
+    f = yo.label(o.geom, 2)
+    res = yo.solve_dense(o, f)
+    E = o.energy(f, res["un"]).sum()
+    z = 1.0 / rho
+    Ec = -(np.pi / 4) * (2 * sp.kvp(0, z) / sp.k0(z) + sp.kvp(1, z) / sp.k1(z))
+
+    def mode(n):
+        Kn = sp.kv(n, z)
+
+        def g(r):
+            return (rho * ((sp.kvp(n, r / rho) / rho / Kn) ** 2 + (n * sp.kv(n, r / rho) / Kn / r) ** 2)
+                    + (sp.kv(n, r / rho) / Kn) ** 2 / rho) * r
+        return si.quad(g, 1.0, np.inf, limit=200, epsabs=1e-14, epsrel=1e-13)[0]
+
+    I = 2 * np.pi * 0.25 * mode(0) + np.pi * 0.25 * mode(1)
+    assert abs(I - Ec) < 1e-12 * Ec
+    assert abs(E - Ec) < 1e-8 * Ec
+
+
+def test_forces_are_minus_energy_gradient():
+    """Section 7.1: F_i . v = -dPhi/d(a_i + eps v) and tau_i = -dPhi/d(theta_i)
+    by centered differences of the energy, eps = 1e-3, on three close ellipses
+    with smooth data (the label turns with its particle). Agreement to a few
+    1e-6 of max |F| (the difference is the centered-difference truncation); a
+    wrong sign or factor in Eqs. stress, force_torque or scalar-torque fails
+    by O(1)."""
+    parts = W.make_particles(3, 7.0, 0.3, seed=11, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
+
+    def solve(P):
+        o = yo.Oracle(P, 10, 12, 1.0, yo.QBXParams(order=10))
+        f = yo.label(o.geom, 1, 2.0)
+        r = yo.solve_dense(o, f)
+        return o.energy(f, r["un"]).sum(), r
+
+    _, r0 = solve(parts)
+    eps = 1e-3
+    Ffd, tfd = np.zeros((3, 2)), np.zeros(3)
+    for i in range(3):
+        for k, col in enumerate((1, 2, 3)):
+            Pp, Pm = parts.copy(), parts.copy()
+            Pp[i, col] += eps
+            Pm[i, col] -= eps
+            d = -(solve(Pp)[0] - solve(Pm)[0]) / (2 * eps)
+            if k < 2:
+                Ffd[i, k] = d
+            else:
+                tfd[i] = d
+    sc = np.abs(r0["F"]).max()
+    assert sc > 0.1
+    assert np.abs(Ffd - r0["F"]).max() < 2e-5 * sc
+    assert np.abs(tfd - r0["tau"]).max() < 2e-5 * sc
