@@ -236,6 +236,18 @@ int yk_solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
 int yk_forces_torques(yk_geom* g, const double* sigma, const double* f,
                       double* F, double* tau, double* net);
 
+/* Energy of Eq. main, Phi = gamma min I[u] with I[u] = int rho |grad u|^2 +
+ * u^2/rho over the water, in its boundary form (Green's first identity with
+ * Delta u = u / rho^2): Phi = -gamma rho sum_i int_{Sigma_i} f du/dnu ds, with
+ * u_nu from sigma as in yk_forces_torques (the solved density of f).
+ *   - phi (n_particles, nullable): the per-particle parts
+ *     -gamma rho int_{Sigma_i} f u_nu ds;
+ *   - phi_total (1, nullable): Phi; at least one of the two must be given.
+ * Its centered differences in a particle's position and angle are minus the
+ * force and torque of yk_forces_torques (Section 7.1).                     */
+int yk_energy(yk_geom* g, const double* sigma, const double* f, double* phi,
+              double* phi_total);
+
 /* u = D[sigma] (Eq. intrep) at nt off-surface targets (nt x 2) by plain
  * quadrature, FP64. Targets must lie in the water at least about one panel
  * length from every boundary for full accuracy. u has length nt.          */

@@ -600,6 +600,27 @@ int yk_forces_torques(yk_geom* g, const double* sigma, const double* f, double* 
     return sync(g);
 }
 
+int yk_energy(yk_geom* g, const double* sigma, const double* f, double* phi, double* phi_total) {
+    if (!g || !sigma || !f || (!phi && !phi_total)) return YK_ERR_ARG;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    const size_t bytes = (size_t)g->n * sizeof(double);
+    Arg a, b, op, ot;
+    YK_TRY(a.init(g, sigma, bytes, false));
+    YK_TRY(b.init(g, f, bytes, false));
+    YK_TRY(ot.init(g, phi_total, sizeof(double), true));
+    double* un = g->ws.vec[4];
+    double* ph = g->ws.vec[3];          // per-particle parts when the caller wants none
+    if (phi) {
+        YK_TRY(op.init(g, phi, g->np * sizeof(double), true));
+        ph = op.d();
+    }
+    YK_TRY(normal_derivative(g, a.d(), un, g->prm.precision == YK_FP64 ? Prec::F64 : Prec::SPLIT));
+    YK_TRY(energy(g, b.d(), un, ph, phi_total ? ot.d() : nullptr));
+    if (phi) YK_TRY(op.finish());
+    YK_TRY(ot.finish());
+    return sync(g);
+}
+
 int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
                       double* u) {
     if (!g || !sigma || nt < 0 || (nt > 0 && (!targets || !u))) return YK_ERR_ARG;

@@ -7,6 +7,12 @@
 //   T.nu = gamma [f^2/rho + rho u_tau^2 - rho u_nu^2] nu - 2 gamma rho u_nu u_tau tau,
 //   F_i = sum_nodes w T.nu,  tau0_i = sum_nodes w (x cross T.nu),
 //   tau_i = tau0_i - a_i cross F_i   (2-D cross a x b = a_x b_y - a_y b_x).
+//
+// Energy (Eq. main): Phi = gamma min I[u], I[u] = int_Omega rho |grad u|^2 +
+// u^2/rho dx. Green's first identity on the water domain (outward normal
+// -nu) with Delta u = u/rho^2 (Eq. SL) and u -> 0 at infinity leaves the
+// boundary form Phi = -gamma rho sum_i int_{Sigma_i} f u_nu ds, summed per
+// particle here from the same u_nu as the forces.
 #include "yk_internal.cuh"
 
 namespace yk {
@@ -86,6 +92,36 @@ __global__ void k_net(int np, const double* __restrict__ F, const double* __rest
         net[1] = b;
         net[2] = c;
     }
+}
+
+// phi[p] = -gamma rho sum over particle p's nodes of w f u_nu; total[0] = sum_p phi[p]
+__global__ void __launch_bounds__(FT_TPB) k_energy(GeomView G, const double* __restrict__ f,
+                                                   const double* __restrict__ un, double gamma,
+                                                   double* __restrict__ phi) {
+    const int p = blockIdx.x;
+    const int64_t base = (int64_t)p * G.npp;
+    double e = 0.0, z1 = 0.0, z2 = 0.0;
+    for (int li = threadIdx.x; li < G.npp; li += FT_TPB) {
+        const int64_t i = base + li;
+        e = fma(G.w[i] * f[i], un[i], e);
+    }
+    block_sum3(e, z1, z2);
+    if (threadIdx.x == 0) phi[p] = -gamma * G.rho * e;
+}
+
+__global__ void k_energy_total(int np, const double* __restrict__ phi, double* __restrict__ total) {
+    double a = 0.0, z1 = 0.0, z2 = 0.0;
+    for (int p = threadIdx.x; p < np; p += FT_TPB) a += phi[p];
+    block_sum3(a, z1, z2);
+    if (threadIdx.x == 0) total[0] = a;
+}
+
+int energy(yk_geom* g, const double* f, const double* un, double* phi, double* total) {
+    cudaStream_t st = g->ctx->stream;
+    YK_LAUNCH(k_energy, g->np, FT_TPB, 0, st, g->view(), f, un, g->prm.gamma, phi);
+    if (total) YK_LAUNCH(k_energy_total, 1, FT_TPB, 0, st, g->np, phi, total);
+    YK_TRY_CUDA(cudaGetLastError());
+    return YK_OK;
 }
 
 int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,

@@ -263,6 +263,7 @@ void free_workspace(yk_geom* g);
 // forces.cu
 int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,
                    double* F, double* tau, double* net);
+int energy(yk_geom* g, const double* f, const double* un, double* phi, double* total);
 
 // serve.cu
 int destroy_server(yk_ctx* ctx);

@@ -51,7 +51,7 @@ YK_REQ_QUEUED, YK_REQ_RUNNING, YK_REQ_DONE, YK_REQ_FAILED = 0, 1, 2, 3
 EXPORTS = [
     "yk_default_params", "yk_create", "yk_destroy", "yk_create_geometry",
     "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
-    "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_eval_potential",
+    "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_energy", "yk_eval_potential",
     "yk_eval_potential_noalloc",
     "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_strerror",
 ]
@@ -117,6 +117,7 @@ def load(path=LIB_PATH):
         "yk_normal_derivative": [P, P, P, I],
         "yk_solve": [P, P, P, P, C.POINTER(yk_solve_info)],
         "yk_forces_torques": [P, P, P, P, P, P],
+        "yk_energy": [P, P, P, P, P],
         "yk_eval_potential": [P, P, P, I64, P],
         "yk_eval_potential_noalloc": [P, P, P, I64, P],
         "yk_solve_forces": [P, P, P, P, P, C.POINTER(yk_solve_info)],
@@ -312,6 +313,14 @@ class Geometry:
         _check(load().yk_forces_torques(self.h, _ptr(sigma), _ptr(f), _ptr(F), _ptr(tau),
                                         _ptr(net)), "yk_forces_torques")
         return F, tau, net
+
+    def yk_energy(self, sigma, f, phi=None):
+        """Energy of Eq. main (boundary form): returns (per-particle parts, total)."""
+        phi = np.zeros(self.n_particles) if phi is None else phi
+        total = np.zeros(1)
+        _check(load().yk_energy(self.h, _ptr(sigma), _ptr(f), _ptr(phi), _ptr(total)),
+               "yk_energy")
+        return phi, float(total[0])
 
     def yk_eval_potential(self, sigma, targets, out=None):
         t = np.ascontiguousarray(targets, dtype=np.float64) if isinstance(targets, (list, np.ndarray)) else targets

@@ -132,6 +132,63 @@ def test_solve_forces_small(yk, ctx, dense_cache, name, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["disks5_pan9", "ellipses4_gl11"])
+def test_energy_small(yk, ctx, dense_cache, name, precision):
+    """Energy of Eq. main (boundary form) from the same density: per-particle
+    parts and total against the oracle's, to the normal derivative's bar."""
+    wl = SMALL[name]()
+    o, A, Gn = _oracle(wl, dense_cache)
+    prec = yk.YK_FP64 if precision == "fp64" else yk.YK_MIXED
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec))
+    f = g.yk_label(1, 2.0)
+    s = np.linalg.solve(A, f)
+    phi, total = g.yk_energy(s, f)
+    ref = o.energy(f, Gn @ s)
+    scale = np.abs(o.geom.w * f).sum() * (np.abs(Gn) @ np.abs(s)).max() * wl.rho
+    assert np.abs(phi - ref).max() < 1e-12 * scale
+    assert abs(total - ref.sum()) < 1e-12 * scale
+
+
+def test_forces_are_minus_energy_gradient_gpu(yk, ctx):
+    """Section 7.1 on the GPU path: centered differences (eps = 1e-3) of the
+    energy after moving or turning one particle (yk_update_geometry, mixed
+    solves to 1e-12) against yk_forces_torques, as in the oracle's pin."""
+    parts = W.make_particles(3, 7.0, 0.3, seed=11, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
+    wl = W.Workload("fd3", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
+    g = yk.Geometry(ctx, parts, _params(yk, wl, gmres_tol=1e-12))
+
+    def solve(P):
+        g.yk_update_geometry(P)
+        f = g.yk_label(1, 2.0)
+        s, info = g.yk_solve(f)
+        assert info["converged"]
+        return f, s
+
+    f0, s0 = solve(parts)
+    F0, tau0, _ = g.yk_forces_torques(s0, f0)
+    F0 = F0.reshape(-1, 2)
+    eps = 1e-3
+    Ffd, tfd = np.zeros((3, 2)), np.zeros(3)
+    for i in range(3):
+        for k, col in enumerate((1, 2, 3)):
+            E = []
+            for sgn in (1.0, -1.0):
+                P = parts.copy()
+                P[i, col] += sgn * eps
+                f, s = solve(P)
+                E.append(g.yk_energy(s, f)[1])
+            d = -(E[0] - E[1]) / (2 * eps)
+            if k < 2:
+                Ffd[i, k] = d
+            else:
+                tfd[i] = d
+    sc = np.abs(F0).max()
+    assert sc > 0.1
+    assert np.abs(Ffd - F0).max() < 2e-5 * sc
+    assert np.abs(tfd - tau0).max() < 2e-5 * sc
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_block_preconditioner(yk, ctx, dense_cache, precision):
     """Right preconditioning by the inverse self-interaction block of each
     particle changes the iteration count, not the solution."""
