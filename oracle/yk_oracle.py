@@ -499,3 +499,68 @@ def solve_dense(orc, f, want_grad=True):
         F, tau, tau0 = orc.forces_torques(f, un)
         out.update(Gn=Gn, un=un, F=F, tau=tau, tau0=tau0)
     return out
+
+
+# ----------------------------------------------------------------------------
+# 7. Excluded-volume repulsion (Eq. repul, Section S1) and constant-drag
+#    dynamics (Eq. euler; Algorithm 1 with constant drag coefficients)
+# ----------------------------------------------------------------------------
+
+def repulsion_circles(p):
+    """Circle decomposition of Section S1: an ellipse (A > B) is three circles
+    of radius B at a_i + k h d_i, h = A - B, k in {-1, 0, +1}; a disk is one
+    circle of its radius. Returns a list per particle of (centres (n, 2),
+    lever arms (n, 2), radius)."""
+    out = []
+    for row in np.asarray(p, float):
+        shape, cx, cy, phi, A, B = row
+        if int(shape) == 0 or A == B:
+            out.append((np.array([[cx, cy]]), np.zeros((1, 2)), A))
+        else:
+            d = np.array([math.cos(phi), math.sin(phi)])
+            arms = np.array([k * (A - B) * d for k in (-1, 0, 1)])
+            out.append((np.array([cx, cy]) + arms, arms, B))
+    return out
+
+
+def repulsion(p, c0, q=3):
+    """Eq. repul between every pair of circles of different particles, with
+    c0 / (n_i n_j) per circle pair (n = 3 circles for an ellipse, 1 for a
+    disk), so that circles recover Eq. repul exactly (the reading taken of
+    Section S1's normalisation):
+        f = c q / (|c_i - c_j| - (b_i + b_j))^{q+1} (c_i - c_j)/|c_i - c_j|,
+    the force on particle i, its torque about a_i (lever arm x f) and the
+    potential c / (|c_i - c_j| - (b_i + b_j))^q, half to each particle.
+    Returns F (Np, 2), tau (Np,), phi (Np,)."""
+    circ = repulsion_circles(p)
+    n = len(circ)
+    F = np.zeros((n, 2))
+    tau = np.zeros(n)
+    phi = np.zeros(n)
+    for i in range(n):
+        ci, ai, bi = circ[i]
+        for j in range(n):
+            if j == i:
+                continue
+            cj, _, bj = circ[j]
+            c = c0 / (len(ci) * len(cj))
+            for k in range(len(ci)):
+                for l in range(len(cj)):
+                    dvec = ci[k] - cj[l]
+                    dist = math.hypot(*dvec)
+                    s = dist - (bi + bj)
+                    f = c * q / s ** (q + 1) * dvec / dist
+                    F[i] += f
+                    tau[i] += ai[k][0] * f[1] - ai[k][1] * f[0]
+                    phi[i] += 0.5 * c / s ** q
+    return F, tau, phi
+
+
+def euler_step(p, F, tau, dt, xi_x, xi_theta):
+    """Eq. euler (forward Euler with constant drag): a += dt F / xi_x,
+    theta += dt tau / xi_theta, with F and tau the total (hydrophobic plus
+    repulsive) force and torque."""
+    q = np.array(p, float, copy=True)
+    q[:, 1:3] += dt * np.asarray(F) / xi_x
+    q[:, 3] += dt * np.asarray(tau) / xi_theta
+    return q

@@ -445,3 +445,41 @@ def test_forces_are_minus_energy_gradient():
     assert sc > 0.1
     assert np.abs(Ffd - r0["F"]).max() < 2e-5 * sc
     assert np.abs(tfd - r0["tau"]).max() < 2e-5 * sc
+
+
+# --------------------------------------------------------------------------
+# excluded-volume repulsion (Eq. repul, Section S1) and the drag update
+# --------------------------------------------------------------------------
+
+def test_repulsion_two_disks_is_eq_repul():
+    """Two unit disks 2.5 apart, c0 = 0.01, q = 3: the surface gap is 0.5, so
+    Eq. repul gives |F| = c0 q / 0.5^4 = 0.48 along a_1 - a_2, and the
+    potential c0 / 0.5^3 = 0.08 (half to each)."""
+    p = np.array([[0, 0.0, 0.0, 0.7, 1.0, 1.0], [0, 2.5, 0.0, 2.0, 1.0, 1.0]])
+    F, tau, phi = yo.repulsion(p, 0.01, 3)
+    assert np.allclose(F, [[-0.48, 0.0], [0.48, 0.0]], rtol=1e-14, atol=1e-16)
+    assert np.allclose(tau, 0.0, atol=1e-16)
+    assert np.allclose(phi, [0.04, 0.04], rtol=1e-14)
+
+
+def test_repulsion_is_minus_gradient_of_its_potential():
+    """Ellipses (three circles each) and a disk: F_i = -dPhi/da_i and
+    tau_i = -dPhi/dtheta_i by centered differences of the total repulsion
+    potential; Newton's third law (sum F = 0) and zero total angular momentum
+    (sum a_i x F_i + tau_i = 0)."""
+    p = np.array([[1, 0.0, 0.0, 0.3, 1.0, 0.5], [0, 2.5, 0.4, 0.0, 1.0, 1.0],
+                  [1, 0.5, 2.2, 1.2, 1.0, 0.5]])
+    F, tau, phi = yo.repulsion(p, 0.01, 3)
+    eps = 1e-6
+    for i in range(3):
+        for col in (1, 2, 3):
+            pp, pm = p.copy(), p.copy()
+            pp[i, col] += eps
+            pm[i, col] -= eps
+            d = -(yo.repulsion(pp, 0.01, 3)[2].sum() - yo.repulsion(pm, 0.01, 3)[2].sum()) / (2 * eps)
+            ref = F[i, col - 1] if col < 3 else tau[i]
+            assert abs(d - ref) < 1e-7 * np.abs(F).max()
+    assert np.abs(F.sum(0)).max() < 1e-15
+    L = (p[:, 1] * F[:, 1] - p[:, 2] * F[:, 0] + tau).sum()
+    assert abs(L) < 1e-15
+    assert abs(tau[1]) < 1e-18               # a disk feels no repulsive torque
