@@ -150,6 +150,24 @@ typedef struct {
                               on the first FMM operator application          */
 } yk_params;
 
+/* Constant-drag dynamics (Eq. euler) with the excluded-volume repulsion of
+ * Eq. repul. yk_default_dynamics() fills the defaults given here.           */
+typedef struct {
+    double dt;             /* time step Delta t; default 0.1                   */
+    double xi_x;           /* translational drag xi_x; default 4 pi (Section
+                              S2: 4 pi mu a with mu = a = 1)                  */
+    double xi_theta;       /* rotational drag xi_theta; default 4 pi          */
+    double c0;             /* repulsion strength c0 of Eq. repul; default 0.01 */
+    int32_t q;             /* repulsion order q; default 3 (two dimensions)    */
+    int32_t label_kind;    /* Dirichlet data each step: YK_LABEL_TANH, _SINP or
+                              _COS (the label turns with its particle);
+                              default YK_LABEL_TANH                          */
+    double label_param;    /* its parameter; default 10                      */
+    int32_t warm_start;    /* 1 (default): the previous step's density is the
+                              initial guess of the next solve                 */
+    int32_t pad_;
+} yk_dynamics;
+
 /* Solve statistics (all host memory). */
 typedef struct {
     int32_t iterations;      /* GMRES iterations (inner ones for YK_MIXED)    */
@@ -247,6 +265,34 @@ int yk_forces_torques(yk_geom* g, const double* sigma, const double* f,
  * force and torque of yk_forces_torques (Section 7.1).                     */
 int yk_energy(yk_geom* g, const double* sigma, const double* f, double* phi,
               double* phi_total);
+
+/* Excluded-volume repulsion at the geometry's current positions: an ellipse
+ * is three circles of radius B at a_i + k (A - B) d_i, k in {-1, 0, 1}, a disk
+ * one circle (Section S1); every pair of circles of different particles
+ * repels by Eq. repul with c0 / (n_i n_j) (n circles per particle), so that
+ * circles recover Eq. repul exactly. F (2 n_particles), tau (n_particles,
+ * torque about a_i from the circles' lever arms) and phi (n_particles, half
+ * of each pair's potential c / gap^q) may each be NULL. YK_ERR_BAD_GEOMETRY
+ * if two circles overlap.                                                   */
+int yk_repulsion(yk_geom* g, double c0, int q, double* F, double* tau, double* phi);
+
+int yk_default_dynamics(yk_dynamics* d);
+
+/* Algorithm 1 with constant drag: n_steps forward-Euler steps (Eq. euler),
+ * each one Dirichlet label, GMRES (yk_solve, warm-started from the previous
+ * step's density when d->warm_start), the hydrophobic force and torque
+ * (yk_forces_torques), the repulsion (yk_repulsion), then
+ *   a_i += dt (F_i + F_rep_i) / xi_x,  theta_i += dt (tau_i + tau_rep_i) / xi_theta,
+ * and the re-discretisation at the new positions (yk_update_geometry).
+ *   - particles (n_particles, nullable): the positions after the last step;
+ *   - energy (n_steps, nullable): Phi of Eq. main plus the repulsion
+ *     potential at the configuration each step starts from;
+ *   - info (n_steps, nullable): the solve statistics of each step.
+ * Stops at the first failing step (YK_ERR_NOT_CONVERGED, or
+ * YK_ERR_BAD_GEOMETRY when particles overlap) with the particles where that
+ * step found them.                                                         */
+int yk_step(yk_geom* g, const yk_dynamics* d, int n_steps, yk_particle* particles,
+            double* energy, yk_solve_info* info);
 
 /* u = D[sigma] (Eq. intrep) at nt off-surface targets (nt x 2) by plain
  * quadrature, FP64. Targets must lie in the water at least about one panel

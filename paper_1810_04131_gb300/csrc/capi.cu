@@ -293,6 +293,7 @@ int yk_destroy_geometry(yk_geom* g) {
     dev_free(g->nbr_off, st);
     dev_free(g->nbr, st);
     fmm_free(g);
+    dyn_free(g);
     for (auto& B : g->bands) {
         dev_free(B.off, st);
         dev_free(B.idx, st);
@@ -597,6 +598,61 @@ int yk_forces_torques(yk_geom* g, const double* sigma, const double* f, double* 
     YK_TRY(oF.finish());
     YK_TRY(ot.finish());
     YK_TRY(on.finish());
+    return sync(g);
+}
+
+int yk_repulsion(yk_geom* g, double c0, int q, double* F, double* tau, double* phi) {
+    if (!g || !(c0 >= 0.0) || !isfinite(c0) || q < 1 || q > 16) return YK_ERR_ARG;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    Arg oF, ot, op;
+    YK_TRY(oF.init(g, F, 2 * g->np * sizeof(double), true));
+    YK_TRY(ot.init(g, tau, g->np * sizeof(double), true));
+    YK_TRY(op.init(g, phi, g->np * sizeof(double), true));
+    double* scratch = nullptr;
+    YK_TRY_CUDA(cudaMallocAsync((void**)&scratch, sizeof(double) * 4 * g->np, g->ctx->stream));
+    int rc = repulsion_host(g, c0, q, F ? oF.d() : scratch, tau ? ot.d() : scratch + 2 * g->np,
+                            phi ? op.d() : scratch + 3 * g->np);
+    if (rc == YK_OK) rc = oF.finish();
+    if (rc == YK_OK) rc = ot.finish();
+    if (rc == YK_OK) rc = op.finish();
+    cudaFreeAsync(scratch, g->ctx->stream);
+    YK_TRY(rc);
+    return sync(g);
+}
+
+int yk_default_dynamics(yk_dynamics* d) {
+    if (!d) return YK_ERR_ARG;
+    memset(d, 0, sizeof(*d));
+    d->dt = 0.1;
+    d->xi_x = 4.0 * PI;
+    d->xi_theta = 4.0 * PI;
+    d->c0 = 0.01;
+    d->q = 3;
+    d->label_kind = YK_LABEL_TANH;
+    d->label_param = 10.0;
+    d->warm_start = 1;
+    return YK_OK;
+}
+
+int yk_step(yk_geom* g, const yk_dynamics* d, int n_steps, yk_particle* particles,
+            double* energy, yk_solve_info* info) {
+    if (!g || !d || n_steps < 0) return YK_ERR_ARG;
+    if (!(d->dt >= 0.0) || !(d->xi_x > 0.0) || !(d->xi_theta > 0.0) || !(d->c0 >= 0.0) ||
+        !isfinite(d->dt) || !isfinite(d->c0) || d->q < 1 || d->q > 16)
+        return YK_ERR_ARG;
+    if (d->label_kind != YK_LABEL_TANH && d->label_kind != YK_LABEL_SINP &&
+        d->label_kind != YK_LABEL_COS)
+        return YK_ERR_ARG;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    for (int s = 0; s < n_steps; ++s)
+        YK_TRY(step(g, *d, info ? info + s : nullptr, energy ? energy + s : nullptr));
+    if (particles) {
+        if (is_device_ptr(particles))
+            YK_TRY_CUDA(cudaMemcpyAsync(particles, g->parts.data(), sizeof(yk_particle) * g->np,
+                                        cudaMemcpyHostToDevice, g->ctx->stream));
+        else
+            memcpy(particles, g->parts.data(), sizeof(yk_particle) * g->np);
+    }
     return sync(g);
 }
 

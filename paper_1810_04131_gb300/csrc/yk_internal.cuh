@@ -163,6 +163,19 @@ struct FmmTree {
 };
 }  // namespace yk
 
+namespace yk {
+// Device state of the particle dynamics (dynamics.cu).
+struct Dynamics {
+    yk_particle* parts = nullptr;  // [np] device copy of the particles
+    double* sigma = nullptr;       // [n] density of the last step (warm start)
+    double* f = nullptr;           // [n] Dirichlet data
+    double* un = nullptr;          // [n] normal derivative
+    double* work = nullptr;        // forces, torques, repulsion, energies
+    int* bad = nullptr;            // overlap flag of the repulsion
+    bool have_sigma = false;
+};
+}  // namespace yk
+
 struct yk_geom {
     yk_ctx* ctx = nullptr;
     yk_params prm{};
@@ -187,6 +200,7 @@ struct yk_geom {
     int nbr_cap = 0;
     bool nbr_valid = false;
     yk::FmmTree fmm;                       // FMM far field (YK_FARFIELD_FMM)
+    yk::Dynamics dyn;                      // particle dynamics (yk_step)
     // device allocations
     yk::d4* d_part = nullptr;
     float4* d_c32 = nullptr;
@@ -264,6 +278,13 @@ void free_workspace(yk_geom* g);
 int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,
                    double* F, double* tau, double* net);
 int energy(yk_geom* g, const double* f, const double* un, double* phi, double* total);
+
+// dynamics.cu
+int repulsion(yk_geom* g, const yk_particle* d_parts, double c0, int q, double* F, double* tau,
+              double* phi);
+int repulsion_host(yk_geom* g, double c0, int q, double* F, double* tau, double* phi);
+int step(yk_geom* g, const yk_dynamics& d, yk_solve_info* info, double* energy_out);
+void dyn_free(yk_geom* g);
 
 // serve.cu
 int destroy_server(yk_ctx* ctx);

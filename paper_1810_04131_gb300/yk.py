@@ -52,7 +52,7 @@ EXPORTS = [
     "yk_default_params", "yk_create", "yk_destroy", "yk_create_geometry",
     "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
     "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_energy", "yk_eval_potential",
-    "yk_eval_potential_noalloc",
+    "yk_eval_potential_noalloc", "yk_repulsion", "yk_default_dynamics", "yk_step",
     "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_strerror",
 ]
 
@@ -72,6 +72,12 @@ class yk_params(C.Structure):
                 ("grad_split_tol", C.c_double), ("precond", C.c_int32), ("pad_", C.c_int32),
                 ("cutoff_tol", C.c_double), ("fmm_order", C.c_int32), ("pad2_", C.c_int32),
                 ("fmm_leaf", C.c_double)]
+
+
+class yk_dynamics(C.Structure):
+    _fields_ = [("dt", C.c_double), ("xi_x", C.c_double), ("xi_theta", C.c_double),
+                ("c0", C.c_double), ("q", C.c_int32), ("label_kind", C.c_int32),
+                ("label_param", C.c_double), ("warm_start", C.c_int32), ("pad_", C.c_int32)]
 
 
 class yk_solve_info(C.Structure):
@@ -118,6 +124,9 @@ def load(path=LIB_PATH):
         "yk_solve": [P, P, P, P, C.POINTER(yk_solve_info)],
         "yk_forces_torques": [P, P, P, P, P, P],
         "yk_energy": [P, P, P, P, P],
+        "yk_repulsion": [P, D, I, P, P, P],
+        "yk_default_dynamics": [C.POINTER(yk_dynamics)],
+        "yk_step": [P, C.POINTER(yk_dynamics), I, P, P, P],
         "yk_eval_potential": [P, P, P, I64, P],
         "yk_eval_potential_noalloc": [P, P, P, I64, P],
         "yk_solve_forces": [P, P, P, P, P, C.POINTER(yk_solve_info)],
@@ -322,6 +331,28 @@ class Geometry:
                "yk_energy")
         return phi, float(total[0])
 
+    def yk_repulsion(self, c0=0.01, q=3):
+        """Excluded-volume repulsion (Eq. repul): returns F (Np, 2), tau, phi."""
+        F = np.zeros((self.n_particles, 2))
+        tau = np.zeros(self.n_particles)
+        phi = np.zeros(self.n_particles)
+        _check(load().yk_repulsion(self.h, float(c0), int(q), _ptr(F), _ptr(tau), _ptr(phi)),
+               "yk_repulsion")
+        return F, tau, phi
+
+    def yk_step(self, n_steps=1, **kw):
+        """Constant-drag dynamics (Algorithm 1, Eq. euler): returns the particles
+        after n_steps (Np x 6 like the input), the energy and the solve
+        statistics of every step."""
+        d = default_dynamics(**kw)
+        parts = (yk_particle * self.n_particles)()
+        energy = np.zeros(max(n_steps, 1))
+        infos = (yk_solve_info * max(n_steps, 1))()
+        _check(load().yk_step(self.h, C.byref(d), int(n_steps), C.cast(parts, C.c_void_p),
+                              _ptr(energy), C.cast(infos, C.c_void_p)), "yk_step")
+        out = np.array([[p.shape, p.cx, p.cy, p.phi, p.A, p.B] for p in parts])
+        return out, energy[:n_steps], [infos[k].as_dict() for k in range(n_steps)]
+
     def yk_eval_potential(self, sigma, targets, out=None):
         t = np.ascontiguousarray(targets, dtype=np.float64) if isinstance(targets, (list, np.ndarray)) else targets
         nt = t.shape[0]
@@ -354,6 +385,17 @@ def yk_kernel_launches():
     c = C.c_uint64()
     _check(load().yk_kernel_launches(C.byref(c)), "yk_kernel_launches")
     return c.value
+
+
+def default_dynamics(**kw):
+    """yk_dynamics with the library defaults, overridden by keyword."""
+    d = yk_dynamics()
+    _check(load().yk_default_dynamics(C.byref(d)), "yk_default_dynamics")
+    for k, v in kw.items():
+        if not hasattr(d, k):
+            raise AttributeError(k)
+        setattr(d, k, v)
+    return d
 
 
 def params_for(workload, **kw):

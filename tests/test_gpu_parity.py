@@ -361,6 +361,60 @@ def test_fmm_without_admissible_leaf_falls_back_to_cutoff(yk, ctx):
     assert np.array_equal(g.yk_matvec(sig, yk.YK_MIXED), gc.yk_matvec(sig, yk.YK_MIXED))
 
 
+def test_repulsion_matches_oracle(yk, ctx):
+    """Eq. repul with the circle decomposition of Section S1 (ellipses and
+    disks together): force, torque and potential against the oracle."""
+    p = np.array([[1, 0.0, 0.0, 0.3, 1.0, 0.5], [0, 2.5, 0.4, 0.0, 1.0, 1.0],
+                  [1, 0.5, 2.2, 1.2, 1.0, 0.5], [0, -2.4, 1.1, 0.5, 1.0, 1.0]])
+    wl = W.Workload("rep4", p, rho=1.0, n_panels=8, n_gl=16)
+    g = yk.Geometry(ctx, p, _params(yk, wl))
+    F, tau, phi = g.yk_repulsion(0.01, 3)
+    Fr, taur, phir = yo.repulsion(p, 0.01, 3)
+    sc = np.abs(Fr).max()
+    assert np.abs(F - Fr).max() < 1e-14 * sc
+    assert np.abs(tau - taur).max() < 1e-14 * sc
+    assert np.abs(phi - phir).max() < 1e-14 * np.abs(phir).max()
+
+
+def test_dynamics_steps_match_oracle(yk, ctx):
+    """Algorithm 1 with constant drag (Eq. euler): three steps of yk_step on
+    three close ellipses (mixed solves to 1e-12, warm-started) against the
+    oracle's exact discrete solve, forces, repulsion and Euler update; the
+    step energies (Eq. main plus the repulsion potential) as well."""
+    parts = W.make_particles(3, 7.0, 0.3, seed=11, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
+    wl = W.Workload("dyn3", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
+    g = yk.Geometry(ctx, parts, _params(yk, wl, gmres_tol=1e-12))
+    dyn = dict(dt=0.5, c0=0.01, q=3, label_kind=1, label_param=2.0)
+    d = yk.default_dynamics(**dyn)
+    ref = parts.copy()
+    for step in range(3):
+        got, energy, info = g.yk_step(1, **dyn)
+        o = yo.Oracle(ref, 16, 16, 1.0, yo.QBXParams(order=10))
+        f = yo.label(o.geom, 1, 2.0)
+        res = yo.solve_dense(o, f)
+        Fr, taur, phir = yo.repulsion(ref, d.c0, d.q)
+        e_ref = o.energy(f, res["un"]).sum() + phir.sum()
+        assert abs(energy[0] - e_ref) < 1e-10 * abs(e_ref)
+        ref = yo.euler_step(ref, res["F"] + Fr, res["tau"] + taur, d.dt, d.xi_x, d.xi_theta)
+        assert np.abs(got[:, 1:4] - ref[:, 1:4]).max() < 1e-10
+    assert np.abs(ref[:, 1:4] - parts[:, 1:4]).max() > 1e-3       # the particles moved
+
+
+def test_dynamics_warm_start_saves_iterations(yk, ctx):
+    """The previous step's density as the initial guess (Algorithm 1 marching
+    in time) needs fewer GMRES iterations than a cold start, and ends at the
+    same configuration to the solve tolerance."""
+    wl = W.small_system(24, 61, n_panels=12, n_gl=16, rho=1.0, qbx_order=10, gap=0.4)
+    runs = {}
+    for warm in (1, 0):
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl))
+        parts, energy, infos = g.yk_step(5, dt=0.05, warm_start=warm)
+        runs[warm] = (parts, [i["iterations"] for i in infos])
+        g.close()
+    assert sum(runs[1][1][1:]) < sum(runs[0][1][1:])
+    assert np.abs(runs[1][0][:, 1:4] - runs[0][0][:, 1:4]).max() < 1e-8
+
+
 def test_device_pointers_match_host(yk, ctx):
     import torch
     wl = SMALL["disks5_pan9"]()

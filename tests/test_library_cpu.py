@@ -49,6 +49,7 @@ def test_struct_layout_matches_c(tmp_path):
         "yk_particle": [f for f, _ in yk.yk_particle._fields_],
         "yk_params": [f for f, _ in yk.yk_params._fields_],
         "yk_solve_info": [f for f, _ in yk.yk_solve_info._fields_],
+        "yk_dynamics": [f for f, _ in yk.yk_dynamics._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "yk.h"', "int main(void){"]
     for s, fs in fields.items():
