@@ -8,6 +8,7 @@
 #include <tuple>
 
 #include "p2p_kernels.cuh"
+#include "yk_internal.cuh"
 
 namespace yk {
 

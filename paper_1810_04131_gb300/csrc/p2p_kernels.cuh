@@ -29,7 +29,7 @@
 #include <math.h>
 
 #include "bessel.cuh"
-#include "yk_internal.cuh"
+#include "geom_view.cuh"
 
 namespace yk {
 
