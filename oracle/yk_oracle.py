@@ -486,6 +486,123 @@ class Oracle:
         return out
 
 
+def closest_point(prt, tb, s0):
+    """Parameter s of the boundary point of particle prt closest to tb, both
+    in the particle's body frame (x(s) = (A cos s, B sin s)), by Newton's
+    method on (x(s) - tb) . x'(s) = 0 started at s0."""
+    A, B = prt[4], prt[5]
+    s_ = s0
+    for _ in range(50):
+        x = np.array([A * math.cos(s_), B * math.sin(s_)])
+        dx = np.array([-A * math.sin(s_), B * math.cos(s_)])
+        f = (x - tb) @ dx
+        fp = dx @ dx - (x - tb) @ x
+        step = f / fp
+        s_ -= step
+        if abs(step) < 1e-15:
+            break
+    return s_
+
+
+def _oracle_potential_near(self, sigma, targets, near_factor=1.0):
+    """Eq. intrep, u = D[sigma](t), at targets anywhere in the water, also
+    close to a boundary, by QBX (Section 5) for the panels near the target.
+
+    For each particle P and target t:
+      * t inside P: nan;
+      * p = the boundary point of P closest to t, d = |t - p|;
+      * d >= near_factor x (P's largest panel arclength): plain quadrature over
+        P's nodes;
+      * otherwise P's panels near p (the panel holding p +- near_width):
+          - d <= 2r (r = r_factor x that panel's arclength): the local
+            expansion at the target's own centre c = p + r nu(p), on the
+            normal through p (so |t - c| = |d - r| <= r), with coefficients
+            alpha_n from the oversampled near panels as for on-surface targets;
+          - else quadrature on their oversampled nodes (sigma interpolated);
+        and P's other panels by plain quadrature.
+    Positions near P are taken relative to P's centre (same axes), as for the
+    on-surface expansions; p itself is found in P's body frame.
+    """
+    g = self.geom
+    rho, pq = self.rho, self.qbx.order
+    t = np.asarray(targets, dtype=np.float64)
+    out = np.zeros(len(t))
+    ws = g.w * sigma
+    ng = g.n_gl
+    nn = np.arange(pq + 1)
+    mult = np.where(nn == 0, 1.0, 2.0)
+    dt = TWO_PI / g.n_panels
+    for a in range(len(t)):
+        acc = 0.0
+        for P in range(g.n_particles):
+            sl = np.flatnonzero(g.part == P)
+            prt = g.particles[P]
+            c, s_ = math.cos(prt[3]), math.sin(prt[3])
+            tr = t[a] - prt[1:3]                                   # relative to the centre
+            tb = np.array([c * tr[0] + s_ * tr[1], -s_ * tr[0] + c * tr[1]])   # body frame
+            if (tb[0] / prt[4]) ** 2 + (tb[1] / prt[5]) ** 2 < 1.0:
+                acc = np.nan
+                break
+            hmax = g.h[P].max()
+            d2 = ((g.x[sl] - t[a]) ** 2).sum(1)
+            b = int(sl[np.argmin(d2)])
+            if math.sqrt(d2.min()) >= (near_factor + 1.0) * hmax:
+                acc += (dl_kernel(t[a][None, :], g.x[sl], g.nu[sl], rho) * ws[sl]).sum()
+                continue
+            sp_ = closest_point(prt, tb, g.t[b]) % TWO_PI
+            pb = np.array([prt[4] * math.cos(sp_), prt[5] * math.sin(sp_)])
+            tg = np.array([-prt[4] * math.sin(sp_), prt[5] * math.cos(sp_)])
+            nb = np.array([tg[1], -tg[0]]) / math.hypot(*tg)
+            rot = lambda v: np.array([c * v[0] - s_ * v[1], s_ * v[0] + c * v[1]])
+            pt, nup = rot(pb), rot(nb)
+            d = math.hypot(*(tr - pt))
+            if d >= near_factor * hmax:
+                acc += (dl_kernel(t[a][None, :], g.x[sl], g.nu[sl], rho) * ws[sl]).sum()
+                continue
+            kp = int(sp_ // dt) % g.n_panels
+            m = g.n_panels
+            w_ = self.qbx.near_width
+            panels = (list(range(m)) if 2 * w_ + 1 >= m
+                      else [(kp + dd) % m for dd in range(-w_, w_ + 1)])
+            near = np.isin(g.panel[sl], panels)
+            far = sl[~near]
+            acc += (dl_kernel(t[a][None, :], g.x[far], g.nu[far], rho) * ws[far]).sum()
+            sig_near = np.concatenate([sigma[sl[0] + k * ng: sl[0] + (k + 1) * ng]
+                                       for k in panels])
+            r = self.qbx.r_factor * g.h[P, kp]
+            if d <= 2.0 * r:
+                cl = pt + r * nup
+                alpha = np.zeros(pq + 1, dtype=np.complex128)
+                for q, k in enumerate(panels):
+                    y, nu, w = self.fine_nodes(P, k, local=True)
+                    sf = self.interp @ sig_near[q * ng:(q + 1) * ng]
+                    dy = y - cl
+                    sd = np.hypot(dy[:, 0], dy[:, 1])
+                    ph = np.arctan2(dy[:, 1], dy[:, 0])
+                    es = dy / sd[:, None]
+                    ephi = np.stack([-es[:, 1], es[:, 0]], axis=-1)
+                    nus = (nu * es).sum(-1)
+                    nuphi = (nu * ephi).sum(-1)
+                    Kn = sp.kv(nn[:, None], (sd / rho)[None, :])
+                    Knp = sp.kvp(nn[:, None], (sd / rho)[None, :])
+                    dK = (nus[None, :] * Knp / rho - 1j * nn[:, None] * nuphi[None, :] * Kn
+                          / sd[None, :]) * np.exp(-1j * nn[:, None] * ph[None, :])
+                    alpha += (dK * (w * sf)[None, :]).sum(1) / TWO_PI
+                dx = tr - cl
+                rr, th = math.hypot(*dx), math.atan2(dx[1], dx[0])
+                acc += (mult * alpha * sp.iv(nn, rr / rho) * np.exp(1j * nn * th)).real.sum()
+            else:
+                for q, k in enumerate(panels):
+                    y, nu, w = self.fine_nodes(P, k, local=True)
+                    sf = self.interp @ sig_near[q * ng:(q + 1) * ng]
+                    acc += (dl_kernel(tr[None, :], y, nu, rho) * w * sf).sum()
+        out[a] = acc
+    return out
+
+
+Oracle.potential_near = _oracle_potential_near
+
+
 def solve_dense(orc, f, want_grad=True):
     """Exact discrete solution of Eq. (bie) plus u_nu, F and tau (small N)."""
     if want_grad:

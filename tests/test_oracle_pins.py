@@ -483,3 +483,62 @@ def test_repulsion_is_minus_gradient_of_its_potential():
     L = (p[:, 1] * F[:, 1] - p[:, 2] * F[:, 0] + tau).sum()
     assert abs(L) < 1e-15
     assert abs(tau[1]) < 1e-18               # a disk feels no repulsive torque
+
+
+# --------------------------------------------------------------------------
+# the potential near the boundaries (QBX for off-surface targets, Section 5)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho", [4.0, 0.5])
+def test_near_potential_single_disk_full_grid(rho):
+    """Table 1's setting on every kind of target: the 200 x 200 grid of the
+    5 x 5 box outside the disk (every fifth point) plus rings at 1e-9 to 0.4
+    from the boundary, against Eq. true_soln. Plain quadrature is off by
+    O(1) next to the boundary; the near evaluation holds 1e-10."""
+    o = yo.Oracle(_disk(phi=0.4), 16, 16, rho, yo.QBXParams(order=10))
+    s = np.linalg.solve(o.dense(), yo.label(o.geom, 2))
+    xs = np.linspace(-2.5, 2.5, 200)
+    X, Y = np.meshgrid(xs, xs)
+    T = np.stack([X.ravel(), Y.ravel()], 1)
+    T = T[np.hypot(T[:, 0], T[:, 1]) > 1.0][::5]
+    ang = np.linspace(0, 2 * np.pi, 49)[:-1] + 0.013
+    rings = [np.stack([(1 + d) * np.cos(ang), (1 + d) * np.sin(ang)], 1)
+             for d in (1e-9, 1e-6, 1e-3, 0.02, 0.05, 0.1, 0.2, 0.4)]
+    T = np.concatenate([T] + rings)
+    # the label turns with the particle: rotate the analytic field by phi
+    c, s_ = math.cos(0.4), math.sin(0.4)
+    Tb = np.stack([c * T[:, 0] + s_ * T[:, 1], -s_ * T[:, 0] + c * T[:, 1]], 1)
+    ue, _, _ = _true_soln(Tb, rho)
+    u = o.potential_near(s, T)
+    assert np.abs(u - ue).max() < 1e-10
+    near = np.hypot(T[:, 0], T[:, 1]) < 1.01
+    assert np.abs(o.potential(s, T[near]) - ue[near]).max() > 1e-3
+    assert np.isnan(o.potential_near(s, np.array([[0.3, -0.2]])))[0]     # inside
+
+
+def test_near_potential_green_identity_ellipses():
+    """Three close ellipses with point sources inside: the density that
+    reproduces sum q_k G(., x_k) on the boundaries reproduces it at targets
+    1e-8 to 0.3 off the boundaries along the normals at points between the
+    nodes, including targets in the gaps between particles."""
+    wl, u, grad = _green_setup(box=7.0)
+    o = yo.Oracle(wl.particles, 16, 16, 1.0, yo.QBXParams(order=10))
+    s = np.linalg.solve(o.dense(), u(o.geom.x))
+    rng = np.random.default_rng(21)
+    T = []
+    for prt in wl.particles:
+        for tt in rng.uniform(0, 2 * np.pi, 12):
+            x, dx = yo.curve(prt, np.array([tt]))
+            nu = np.array([dx[0, 1], -dx[0, 0]]) / np.hypot(*dx[0])
+            for d in (1e-8, 1e-4, 0.01, 0.05, 0.3):
+                T.append(x[0] + d * nu)
+    T = np.array(T)
+    inside = np.zeros(len(T), bool)
+    for prt in wl.particles:       # drop targets that fell inside a neighbour
+        c, s_ = math.cos(prt[3]), math.sin(prt[3])
+        dv = T - prt[1:3]
+        lx, ly = c * dv[:, 0] + s_ * dv[:, 1], -s_ * dv[:, 0] + c * dv[:, 1]
+        inside |= (lx / prt[4]) ** 2 + (ly / prt[5]) ** 2 < 1.0
+    T = T[~inside]
+    ue = u(T)
+    assert np.abs(o.potential_near(s, T) - ue).max() < 1e-9 * np.abs(ue).max()
