@@ -300,6 +300,19 @@ int yk_step(yk_geom* g, const yk_dynamics* d, int n_steps, yk_particle* particle
 int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets,
                       int64_t nt, double* u);
 
+/* u = D[sigma] (Eq. intrep) at nt targets (nt x 2) anywhere in the water,
+ * including targets arbitrarily close to a boundary (the paper's Table 1
+ * samples such targets on a grid), FP64. Panels next to a target (within one
+ * largest panel arclength of its closest boundary point, found by Newton's
+ * method on the curve parameter) are evaluated by QBX (Section 5) about a
+ * centre on the normal through that closest point (target within twice the
+ * expansion radius of the boundary) or by quadrature on their oversampled
+ * nodes (farther); all other panels by plain quadrature. A target inside a
+ * particle gets NaN. YK_ERR_TOO_LARGE when a target lies in the near zone of
+ * more than four particles.                                                 */
+int yk_eval_potential_near(yk_geom* g, const double* sigma, const double* targets,
+                           int64_t nt, double* u);
+
 /* Allocation-free variant of yk_eval_potential. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory when they evaluate the potential (inside a CUDA stream

@@ -691,6 +691,20 @@ int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets, in
     return sync(g);
 }
 
+int yk_eval_potential_near(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
+                           double* u) {
+    if (!g || !sigma || nt < 0 || (nt > 0 && (!targets || !u))) return YK_ERR_ARG;
+    if (nt == 0) return YK_OK;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    Arg a, t, o;
+    YK_TRY(a.init(g, sigma, (size_t)g->n * sizeof(double), false));
+    YK_TRY(t.init(g, targets, (size_t)nt * 2 * sizeof(double), false));
+    YK_TRY(o.init(g, u, (size_t)nt * sizeof(double), true));
+    YK_TRY(potential_near(g, a.d(), t.d(), nt, o.d()));
+    YK_TRY(o.finish());
+    return sync(g);
+}
+
 int yk_eval_potential_noalloc(yk_geom* g, const double* sigma, const double* targets,
                               int64_t nt, double* u) {
     if (!g || !sigma || nt < 0 || (nt > 0 && (!targets || !u))) return YK_ERR_ARG;

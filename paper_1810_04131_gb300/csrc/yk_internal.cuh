@@ -207,6 +207,9 @@ enum class Prec { F64 = 0, F32 = 1, SPLIT = 2 };
 int matvec(yk_geom* g, const double* sigma, double* y, Prec prec);
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec);
 int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u);
+// near.cu
+int potential_near(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
+                   double* u);
 int potential_noalloc(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
                       double* u);
 

@@ -52,7 +52,7 @@ EXPORTS = [
     "yk_default_params", "yk_create", "yk_destroy", "yk_create_geometry",
     "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
     "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_energy", "yk_eval_potential",
-    "yk_eval_potential_noalloc", "yk_repulsion", "yk_default_dynamics", "yk_step",
+    "yk_eval_potential_noalloc", "yk_eval_potential_near", "yk_repulsion", "yk_default_dynamics", "yk_step",
     "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_strerror",
 ]
 
@@ -128,6 +128,7 @@ def load(path=LIB_PATH):
         "yk_default_dynamics": [C.POINTER(yk_dynamics)],
         "yk_step": [P, C.POINTER(yk_dynamics), I, P, P, P],
         "yk_eval_potential": [P, P, P, I64, P],
+        "yk_eval_potential_near": [P, P, P, I64, P],
         "yk_eval_potential_noalloc": [P, P, P, I64, P],
         "yk_solve_forces": [P, P, P, P, P, C.POINTER(yk_solve_info)],
         "yk_submit": [P, C.POINTER(yk_particle), I, C.POINTER(yk_params), I, D,
@@ -352,6 +353,16 @@ class Geometry:
                               _ptr(energy), C.cast(infos, C.c_void_p)), "yk_step")
         out = np.array([[p.shape, p.cx, p.cy, p.phi, p.A, p.B] for p in parts])
         return out, energy[:n_steps], [infos[k].as_dict() for k in range(n_steps)]
+
+    def yk_eval_potential_near(self, sigma, targets, out=None):
+        """Potential at targets anywhere in the water, also next to a boundary
+        (QBX near the boundary); NaN inside particles."""
+        t = np.ascontiguousarray(targets, dtype=np.float64) if isinstance(targets, (list, np.ndarray)) else targets
+        nt = t.shape[0]
+        u = np.zeros(nt) if out is None else out
+        _check(load().yk_eval_potential_near(self.h, _ptr(sigma), _ptr(t), C.c_int64(nt), _ptr(u)),
+               "yk_eval_potential_near")
+        return u
 
     def yk_eval_potential(self, sigma, targets, out=None):
         t = np.ascontiguousarray(targets, dtype=np.float64) if isinstance(targets, (list, np.ndarray)) else targets

@@ -415,6 +415,79 @@ def test_dynamics_warm_start_saves_iterations(yk, ctx):
     assert np.abs(runs[1][0][:, 1:4] - runs[0][0][:, 1:4]).max() < 1e-8
 
 
+def _near_targets_disk():
+    xs = np.linspace(-2.5, 2.5, 200)
+    X, Y = np.meshgrid(xs, xs)
+    T = np.stack([X.ravel(), Y.ravel()], 1)
+    T = T[np.hypot(T[:, 0], T[:, 1]) > 1.0][::7]
+    ang = np.linspace(0, 2 * np.pi, 49)[:-1] + 0.013
+    rings = [np.stack([(1 + d) * np.cos(ang), (1 + d) * np.sin(ang)], 1)
+             for d in (1e-9, 1e-6, 1e-3, 0.02, 0.05, 0.1, 0.2, 0.4)]
+    return np.concatenate([T] + rings + [np.array([[0.3, -0.2]])])   # last one inside
+
+
+def test_potential_near_boundary_single_disk(yk, ctx):
+    """yk_eval_potential_near (QBX next to the boundary) on Table 1's grid
+    and on rings 1e-9 to 0.4 off a rotated disk (rho = 4): against the
+    oracle's near evaluation of the same density and against Eq. true_soln;
+    NaN inside the particle."""
+    parts = np.array([[0, 0.0, 0.0, 0.4, 1.0, 1.0]])
+    wl = W.Workload("disk_near", parts, rho=4.0, n_panels=16, n_gl=16, qbx_order=10)
+    o = yo.Oracle(parts, 16, 16, 4.0, yo.QBXParams(order=10))
+    s = np.linalg.solve(o.dense(), yo.label(o.geom, 2))
+    g = yk.Geometry(ctx, parts, _params(yk, wl))
+    T = _near_targets_disk()
+    u = g.yk_eval_potential_near(s, T)
+    assert np.isnan(u[-1]) and np.isfinite(u[:-1]).all()
+    ref = o.potential_near(s, T[:-1])
+    assert np.abs(u[:-1] - ref).max() < 1e-12
+    c, s_ = np.cos(0.4), np.sin(0.4)
+    Tb = np.stack([c * T[:-1, 0] + s_ * T[:-1, 1], -s_ * T[:-1, 0] + c * T[:-1, 1]], 1)
+    import scipy.special as sp
+    r = np.hypot(Tb[:, 0], Tb[:, 1])
+    ue = 0.5 * (sp.k0(r / 4.0) / sp.k0(0.25) + sp.k1(r / 4.0) / sp.k1(0.25) * Tb[:, 0] / r)  # Eq. true_soln
+    assert np.abs(u[:-1] - ue).max() < 1e-10
+
+
+def test_potential_near_boundary_close_ellipses(yk, ctx):
+    """Three close ellipses (one target can be near two of them): the GPU
+    near evaluation against the oracle's on targets 1e-8 to 0.3 off the
+    boundaries along the normals, and against the far-field path where the
+    targets are far from every boundary."""
+    parts = W.make_particles(3, 7.0, 0.3, seed=11, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
+    wl = W.Workload("ell_near", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
+    o = yo.Oracle(parts, 16, 16, 1.0, yo.QBXParams(order=10))
+    f = yo.label(o.geom, 0, 10.0)
+    s = np.linalg.solve(o.dense(), f)
+    rng = np.random.default_rng(23)
+    T = []
+    for prt in parts:
+        for tt in rng.uniform(0, 2 * np.pi, 10):
+            x, dx = yo.curve(prt, np.array([tt]))
+            nu = np.array([dx[0, 1], -dx[0, 0]]) / np.hypot(*dx[0])
+            for d in (1e-8, 1e-4, 0.01, 0.05, 0.15, 0.3):
+                T.append(x[0] + d * nu)
+    T = np.array(T)
+    inside = np.zeros(len(T), bool)
+    for prt in parts:
+        c, s_ = np.cos(prt[3]), np.sin(prt[3])
+        dv = T - prt[1:3]
+        lx, ly = c * dv[:, 0] + s_ * dv[:, 1], -s_ * dv[:, 0] + c * dv[:, 1]
+        inside |= (lx / prt[4]) ** 2 + (ly / prt[5]) ** 2 < 1.0
+    g = yk.Geometry(ctx, parts, _params(yk, wl))
+    u = g.yk_eval_potential_near(s, T)
+    assert (np.isnan(u) == inside).all()
+    ref = o.potential_near(s, T[~inside])
+    assert np.abs(u[~inside] - ref).max() < 1e-12 * np.abs(ref).max()
+    xs = np.linspace(-4.0, 11.0, 16)
+    X, Y = np.meshgrid(xs, xs)
+    far = np.stack([X.ravel(), Y.ravel()], 1)
+    dmin = np.min(np.hypot(far[:, None, 0] - parts[None, :, 1], far[:, None, 1] - parts[None, :, 2]), 1)
+    far = far[dmin > 2.5]
+    uf = g.yk_eval_potential(s, far)
+    assert np.abs(g.yk_eval_potential_near(s, far) - uf).max() < 1e-14 * np.abs(uf).max()
+
+
 def test_device_pointers_match_host(yk, ctx):
     import torch
     wl = SMALL["disks5_pan9"]()
