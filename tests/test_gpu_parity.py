@@ -488,6 +488,40 @@ def test_potential_near_boundary_close_ellipses(yk, ctx):
     assert np.abs(g.yk_eval_potential_near(s, far) - uf).max() < 1e-14 * np.abs(uf).max()
 
 
+def test_forces_are_not_pairwise(yk, ctx):
+    """Section 'Pairwise potentials': the force on each particle of a
+    six-particle cluster, F_i (all particles in the fluid), against the sum
+    of its two-particle forces f_i = sum_j f_ij (only P_i and P_j in the
+    fluid). Every f_ij matches the oracle's exact two-particle solve (to 1e-9
+    of the cluster's largest force); F_i and f_i differ by well over the
+    solver tolerance, as the paper reports."""
+    parts = W.make_particles(6, 9.0, 0.3, seed=31, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
+    wl = W.Workload("pair6", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
+    g = yk.Geometry(ctx, parts, _params(yk, wl, gmres_tol=1e-12))
+    f = g.yk_label(0, 10.0)
+    sig, F, tau, info = g.yk_solve_forces(f)
+    F = F.reshape(-1, 2)
+    fp = np.zeros_like(F)
+    for i in range(6):
+        for j in range(i + 1, 6):
+            pair = parts[[i, j]]
+            g2 = yk.Geometry(ctx, pair, _params(yk, wl, gmres_tol=1e-12))
+            f2 = g2.yk_label(0, 10.0)
+            _, F2, _, _ = g2.yk_solve_forces(f2)
+            F2 = F2.reshape(-1, 2)
+            o = yo.Oracle(pair, 16, 16, 1.0, yo.QBXParams(order=10))
+            r = yo.solve_dense(o, yo.label(o.geom, 0, 10.0))
+            # a far pair's net force is small (its stress integrand cancels), so
+            # the bar is relative to the cluster's force scale
+            assert np.abs(F2 - r["F"]).max() < 1e-9 * np.abs(F).max()
+            fp[i] += F2[0]
+            fp[j] += F2[1]
+            g2.close()
+    rel = np.hypot(*(F - fp).T) / np.hypot(*F.T)
+    assert rel.max() > 1e-2             # not pairwise additive
+    assert np.isfinite(rel).all()
+
+
 def test_device_pointers_match_host(yk, ctx):
     import torch
     wl = SMALL["disks5_pan9"]()
