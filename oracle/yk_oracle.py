@@ -193,6 +193,8 @@ class QBXParams:
     r_factor: float = 0.125  # expansion radius r = r_factor * h
     oversample: int = 8      # sub-panels per near panel
     near_width: int = 1      # neighbours on each side
+    contact_factor: float = 0.5   # another particle's panel closer than this x its
+                                  # arclength is integrated on its oversampled nodes
 
 
 def near_panels(geom, i, near_width):
@@ -346,6 +348,39 @@ class Oracle:
         m[self.near_index(i)] = False
         return m
 
+    # ---- near contact: other particles' panels next to a target ----------
+    def contact_panels(self, i):
+        """Panels (P, k) of particles other than the target's whose nearest node
+        is closer to target i than contact_factor x the panel's arclength:
+        plain Gauss-Legendre quadrature on such a panel loses accuracy as the
+        gap closes, so they are integrated on their oversampled nodes (the
+        same 8 sub-panels and interpolation of sigma as the QBX coefficients)."""
+        g = self.geom
+        out = []
+        cf = self.qbx.contact_factor
+        if cf <= 0.0:
+            return out
+        ng = g.n_gl
+        d = np.hypot(g.x[:, 0] - g.x[i, 0], g.x[:, 1] - g.x[i, 1])
+        dmin = d.reshape(g.n_particles, g.n_panels, ng).min(-1)
+        for P, k in zip(*np.nonzero(dmin < cf * g.h)):
+            if P != g.part[i]:
+                out.append((int(P), int(k)))
+        return out
+
+    def contact_row(self, i, P, k, want_grad=False):
+        """Row entries of target i on the n_gl nodes of panel k of particle P
+        by oversampled quadrature: sum_f kernel(x_i, y_f) w_f L_f(node)."""
+        g = self.geom
+        y, nu, w = self.fine_nodes(P, k)
+        xi = g.x[i][None, :]
+        kv = dl_kernel(xi, y, nu, self.rho) * w
+        row = kv @ self.interp
+        if not want_grad:
+            return row
+        kg = (dl_kernel_grad(xi, y, nu, self.rho) @ g.nu[i]) * w
+        return row, kg @ self.interp
+
     # ---- the matvec, row by row ------------------------------------------
     def apply_rows(self, sigma, rows, want_grad=False):
         """((1/2 I + D) sigma)_i for target indices ``rows`` (and, with
@@ -358,12 +393,21 @@ class Oracle:
         for a, i in enumerate(rows):
             m = self.far_mask(i)
             xi = g.x[i][None, :]
+            for P, k in self.contact_panels(i):      # oversampled instead of plain
+                cols = P * g.n_panels * g.n_gl + k * g.n_gl + np.arange(g.n_gl)
+                m[cols] = False
+                if want_grad:
+                    rv, rg = self.contact_row(i, P, k, True)
+                    y[a] += rv @ sigma[cols]
+                    yn[a] += rg @ sigma[cols]
+                else:
+                    y[a] += self.contact_row(i, P, k) @ sigma[cols]
             ws = g.w[m] * sigma[m]
-            y[a] = (dl_kernel(xi, g.x[m], g.nu[m], self.rho) * ws).sum()
+            y[a] += (dl_kernel(xi, g.x[m], g.nu[m], self.rho) * ws).sum()
             idx = self.near_index(i)
             if want_grad:
                 gr = dl_kernel_grad(xi, g.x[m], g.nu[m], self.rho)
-                yn[a] = ((gr @ g.nu[i]) * ws).sum()
+                yn[a] += ((gr @ g.nu[i]) * ws).sum()
                 u, un = self.qbx_eval(i, sigma[idx][:, None], want_grad=True)
                 y[a] += u[0]
                 yn[a] += un[0]
@@ -389,6 +433,13 @@ class Oracle:
             eye = np.eye(len(idx))
             if want_grad:
                 Gn[i, m] = (dl_kernel_grad(xi, g.x[m], g.nu[m], self.rho) @ g.nu[i]) * g.w[m]
+            for P, k in self.contact_panels(i):      # oversampled instead of plain
+                cols = P * g.n_panels * g.n_gl + k * g.n_gl + np.arange(g.n_gl)
+                if want_grad:
+                    A[i, cols], Gn[i, cols] = self.contact_row(i, P, k, True)
+                else:
+                    A[i, cols] = self.contact_row(i, P, k)
+            if want_grad:
                 u, un = self.qbx_eval(i, eye, want_grad=True)
                 A[i, idx] = u
                 Gn[i, idx] = un
