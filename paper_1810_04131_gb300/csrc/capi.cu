@@ -294,6 +294,7 @@ int yk_destroy_geometry(yk_geom* g) {
     dev_free(g->nbr, st);
     fmm_free(g);
     dyn_free(g);
+    contact_free(g);
     for (auto& B : g->bands) {
         dev_free(B.off, st);
         dev_free(B.idx, st);
@@ -304,7 +305,7 @@ int yk_destroy_geometry(yk_geom* g) {
     void* bufs[] = {g->d_part, g->d_c32, g->d_r32, g->d_counter, g->d_shape_of, g->d_shape_ab, g->d_x, g->d_y, g->d_nx, g->d_ny,
                     g->d_w, g->d_speed, g->d_xi, g->d_cval, g->d_cgrad, g->d_glx, g->d_glw,
                     g->d_interp, g->d_diff, g->d_fine_x, g->d_fine_w, g->d_minv, g->d_minv32,
-                    g->d_self, g->d_self_grad, g->d_self32};
+                    g->d_self, g->d_self_grad, g->d_self32, g->d_particles};
     for (void* b : bufs) dev_free(b, st);
     cudaStreamSynchronize(st);
     delete g;
@@ -408,6 +409,7 @@ int yk_create_geometry(yk_ctx* ctx, const yk_particle* particles, int n_particle
 #define ALLOC(ptr, count) \
     if (rc == YK_OK) rc = dev_alloc((void**)&g->ptr, sizeof(*g->ptr) * (size_t)(count), ctx->stream)
     ALLOC(d_part, n_particles);
+    ALLOC(d_particles, n_particles);
     ALLOC(d_c32, n_particles);
     ALLOC(d_r32, n_particles);
     ALLOC(d_counter, 1);

@@ -651,8 +651,7 @@ int apply_preconditioner(yk_geom* g, const double* x, double* y, bool fp32) {
 // Node arrays and per-particle data from the current particle list.
 int update_nodes(yk_geom* g) {
     cudaStream_t st = g->ctx->stream;
-    yk_particle* d_parts = nullptr;
-    YK_TRY(dev_alloc((void**)&d_parts, sizeof(yk_particle) * g->np, st));
+    yk_particle* d_parts = g->d_particles;   // the geometry's device copy of the particles
     YK_TRY_CUDA(cudaMemcpyAsync(d_parts, g->parts.data(), sizeof(yk_particle) * g->np,
                                 cudaMemcpyHostToDevice, st));
     YK_LAUNCH(k_nodes, ceil_div(g->n, 256), 256, 0, st, g->n, g->npan, g->ngl, d_parts, g->d_glx,
@@ -663,9 +662,9 @@ int update_nodes(yk_geom* g) {
     g->nbr_valid = false;
     g->fmm.valid = false;                       // the quadtree follows the particles
     for (auto& B : g->bands) B.valid = false;
+    g->contact.valid = false;                   // so do the near-contact lists
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
-    dev_free(d_parts, st);
     return YK_OK;
 }
 

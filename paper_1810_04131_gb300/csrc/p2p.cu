@@ -271,7 +271,7 @@ static int matvec_fmm(yk_geom* g, const double* sigma, double* y) {
     return fmm_apply(g, sigma, y);
 }
 
-int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
+static int matvec_body(yk_geom* g, const double* sigma, double* y, Prec prec) {
     if (g->prm.farfield == YK_FARFIELD_FMM && prec == Prec::F32) return matvec_fmm(g, sigma, y);
     if (g->prm.farfield != YK_FARFIELD_DENSE) return matvec_cutoff(g, sigma, y, prec, false);
     cudaStream_t st = g->ctx->stream;
@@ -313,7 +313,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
     return YK_OK;
 }
 
-int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
+static int normal_derivative_body(yk_geom* g, const double* sigma, double* un, Prec prec) {
     if (g->prm.farfield != YK_FARFIELD_DENSE) return matvec_cutoff(g, sigma, un, prec, true);
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
@@ -339,6 +339,18 @@ int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
               G.cgrad, sigma, un);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
+}
+
+// The operators, with the near-contact correction (contact.cu) on top of
+// every far-field mode and precision.
+int matvec(yk_geom* g, const double* sigma, double* y, Prec prec) {
+    YK_TRY(matvec_body(g, sigma, y, prec));
+    return contact_apply(g, sigma, y, false);
+}
+
+int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec) {
+    YK_TRY(normal_derivative_body(g, sigma, un, prec));
+    return contact_apply(g, sigma, un, true);
 }
 
 int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u) {

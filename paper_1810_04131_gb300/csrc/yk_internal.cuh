@@ -121,6 +121,20 @@ struct FmmTree {
 }  // namespace yk
 
 namespace yk {
+// Near-contact lists (contact.cu): for every boundary node, the panels of
+// other particles close enough to need oversampled quadrature (CSR).
+struct Contact {
+    bool valid = false;
+    int ntgt = 0;                  // nodes with at least one entry
+    int* partners = nullptr;       // [np][CONTACT_MAX_PARTNERS] particles within reach
+    int* npartners = nullptr;      // [np]
+    int* off = nullptr;            // [n + 1] entries of node i: ent[off[i] .. off[i+1])
+    int* tgt = nullptr;            // [n] nodes with entries
+    int* flag = nullptr;           // [2] overflow flag, node counter
+    int2* ent = nullptr;           // (particle, panel)
+    int64_t cap = 0;
+};
+
 // Device state of the particle dynamics (dynamics.cu).
 struct Dynamics {
     yk_particle* parts = nullptr;  // [np] device copy of the particles
@@ -158,6 +172,8 @@ struct yk_geom {
     bool nbr_valid = false;
     yk::FmmTree fmm;                       // FMM far field (YK_FARFIELD_FMM)
     yk::Dynamics dyn;                      // particle dynamics (yk_step)
+    yk::Contact contact;                   // near-contact lists
+    yk_particle* d_particles = nullptr;    // device copy of the particles
     // device allocations
     yk::d4* d_part = nullptr;
     float4* d_c32 = nullptr;
@@ -238,6 +254,11 @@ void free_workspace(yk_geom* g);
 int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,
                    double* F, double* tau, double* net);
 int energy(yk_geom* g, const double* f, const double* un, double* phi, double* total);
+
+// contact.cu
+constexpr int CONTACT_MAX_PARTNERS = 16;   // particles within reach of one particle
+int contact_apply(yk_geom* g, const double* sigma, double* y, bool grad);
+void contact_free(yk_geom* g);
 
 // dynamics.cu
 int repulsion(yk_geom* g, const yk_particle* d_parts, double c0, int q, double* F, double* tau,

@@ -522,6 +522,43 @@ def test_forces_are_not_pairwise(yk, ctx):
     assert np.isfinite(rel).all()
 
 
+@pytest.mark.parametrize("shape,gap", [(W.SHAPE_DISK, 0.05), (W.SHAPE_ELLIPSE, 0.02)])
+def test_near_contact_matches_oracle(yk, ctx, shape, gap):
+    """Particles closer than the configurations' gaps: another particle's
+    panels next to a target are integrated on their oversampled nodes, in
+    every operator. FP64 and mixed operators and their normal derivatives
+    against the oracle's (same rule), and a mixed solve with forces."""
+    A, B = (1.0, 1.0) if shape == W.SHAPE_DISK else (1.0, 0.5)
+    parts = np.array([[shape, 0.0, 0.0, 0.3 * (shape == 0), A, B],
+                      [shape, 2.0 + gap, 0.0, 1.1 * (shape == 0), A, B],
+                      [shape, 0.7, 3.1, 0.5, A, B]])
+    wl = W.Workload("contact", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
+    o = yo.Oracle(parts, 16, 16, 1.0, yo.QBXParams(order=10))
+    A_, Gn = o.dense(want_grad=True)
+    assert sum(len(o.contact_panels(i)) for i in range(o.geom.n)) > 0     # the rule is in play
+    rng = np.random.default_rng(29)
+    sig = rng.standard_normal(A_.shape[0])
+    cond = (np.abs(Gn) @ np.abs(sig)).max()
+    for prec in ("fp64", "mixed"):
+        p_ = yk.YK_FP64 if prec == "fp64" else yk.YK_MIXED
+        g = yk.Geometry(ctx, parts, _params(yk, wl, precision=p_, gmres_tol=1e-12))
+        y64 = g.yk_matvec(sig, yk.YK_FP64)
+        assert rel(y64, A_ @ sig) < 1e-12
+        assert rel(g.yk_matvec(sig, yk.YK_MIXED), A_ @ sig) < 1e-6
+        un = g.yk_normal_derivative(sig, p_)
+        assert np.abs(un - Gn @ sig).max() < 1e-12 * cond
+        f = g.yk_label(0, 10.0)
+        s, info = g.yk_solve(f)
+        s_ref = np.linalg.solve(A_, f)
+        assert info["converged"] and rel(s, s_ref) < 1e-9
+        F, tau, _ = g.yk_forces_torques(s, f)
+        F_ref, tau_ref, _ = o.forces_torques(f, Gn @ s_ref)
+        sc = np.abs(F_ref).max()
+        assert np.abs(F.reshape(-1, 2) - F_ref).max() < 1e-9 * sc
+        assert np.abs(tau - tau_ref).max() < 1e-9 * max(sc, np.abs(tau_ref).max())
+        g.close()
+
+
 def test_device_pointers_match_host(yk, ctx):
     import torch
     wl = SMALL["disks5_pan9"]()
