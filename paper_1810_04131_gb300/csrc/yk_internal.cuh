@@ -231,7 +231,7 @@ int potential_noalloc(yk_geom* g, const double* sigma, const double* targets, in
 
 // expansions.cu
 constexpr int EXPANSION_TERMS = 41;        // orders 0..40 of the particle expansions
-constexpr double EXPANSION_GAP_RADII = 4.0;  // band starts at a gap of 4 bounding radii
+constexpr double EXPANSION_GAP_RADII = 2.0;  // band starts at a gap of 2 bounding radii
 int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad);
 
 // fmm.cu

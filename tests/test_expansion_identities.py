@@ -7,12 +7,13 @@ checked in numpy/scipy against direct summation (no GPU).
   centre (multipole moments M_n), translated to another particle's centre
   (local coefficients L_m) and evaluated at that particle's nodes, matches
   the direct sum of dG/dnu_y at the truncation order and band start used by
-  the library (order 40, gap >= 4 bounding radii), for the value and the
-  normal derivative.
+  the library (order 40, gap >= 2 bounding radii), for the value and the
+  normal derivative, for smooth and for white-noise densities.
 """
 import math
 
 import numpy as np
+import pytest
 import scipy.special as sp
 
 from oracle import yk_oracle as yo
@@ -78,16 +79,21 @@ def _expand(src, tgt, sig, rho, p):
     return u, un
 
 
-def test_particle_expansion_matches_direct_sum():
+@pytest.mark.parametrize("rough", [False, True])
+def test_particle_expansion_matches_direct_sum(rough):
+    """At the band's start (a gap of 2 bounding radii) and order 40, for a
+    smooth density and for white noise on the nodes (the roughest the
+    discretisation carries, whose moments decay slowest)."""
     rng = np.random.default_rng(5)
     for rho, shape in ((1.0, 0), (0.25, 1), (4.0, 1)):
         A, B = (1.0, 0.5) if shape else (1.0, 1.0)
-        gap = 4.0 * max(A, B) + 0.01          # the band starts at 4 bounding radii
+        gap = 2.0 * max(A, B) + 0.01          # the band starts at 2 bounding radii
         src = yo.make_geometry(np.array([[shape, 0.0, 0.0, 0.7, A, B]]), 16, 16)
         ang = rng.uniform(0, 2 * np.pi)
         c = (2 * max(A, B) + gap) * np.array([np.cos(ang), np.sin(ang)])
         tgt = yo.make_geometry(np.array([[shape, c[0], c[1], 2.1, A, B]]), 16, 16)
-        sig = 1.0 + 0.3 * np.cos(3 * src.t) + 0.2 * np.sin(src.t)
+        sig = (rng.standard_normal(src.t.shape) if rough
+               else 1.0 + 0.3 * np.cos(3 * src.t) + 0.2 * np.sin(src.t))
         u, un = _expand(src, tgt, sig, rho, 40)
         ws = src.w * sig
         ud = np.array([(yo.dl_kernel(x[None], src.x, src.nu, rho) * ws).sum() for x in tgt.x])
