@@ -31,10 +31,21 @@ sys.path.insert(0, ROOT)
 METRIC = "Yukawa-QBX solves/s mixed vs FP64 @1e-9 rel err; P2P %FMA peak; p50/p99 latency"
 WORKLOAD = "disks512"
 # FP32 operations per far-field pair in the P2P inner loop (FMA counted as 2,
-# each MUFU op as 1): 2 sub, |d|^2 (3), 1/z' (1), z' (1), s (2), K1 poly
-# degree 7 (14), exp2 (1), z'^{-1/2} (1), (d.g) (3), 4 products (4), accumulate (1)
-FLOPS_PER_PAIR = 34
+# FADD/FMUL and each MUFU op as 1): d = x - y (2), |d|^2 (3), 1/z' (1 MUFU),
+# z' (1), K1 polynomial in 1/z' (6 FMA = 12 with the full fit, 3 FMA = 6 with
+# the short fit for z >= 10), exp2 (1 MUFU), z'^{-1/2} (1 MUFU), (d.g) (3),
+# three products (3), accumulate (2).
+FLOPS_PER_PAIR = 29
+FLOPS_PER_PAIR_SHORT = 23
+# FMA-pipe lane operations per pair (the same list without the MUFU ops)
+LANE_OPS_PER_PAIR = 17
+LANE_OPS_PER_PAIR_SHORT = 14
 SMS, FP32_LANES = 152, 128
+# the classes of the FP32 far-field kernel (bounding-circle gap in units of rho)
+Z_SHORT = 10.0
+ZP_ZERO = 128.0
+LOG2E = 1.4426950408889634
+TARGETS_PER_BLOCK = 256
 
 
 KERNEL_SOURCES = ("p2p_kernels.cuh", "bessel.cuh", "bessel_tables.h", "geom_view.cuh")
@@ -61,6 +72,36 @@ def stored_traffic():
     if d.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return d.get("dram_bytes_per_launch")
+
+
+def p2p_pair_classes(particles, rho, npp, n, own_by_block=True):
+    """Node pairs of one FP32 far-field matvec by how the kernel treats them.
+
+    The kernel decides per block of 256 consecutive targets and source
+    particle from the smallest bounding-circle gap between the block's target
+    particles and the source: gap >= 128 rho / log2(e) adds exactly zero in
+    FP32 and is skipped, gap >= 10 rho takes the short K1 fit, the rest the
+    full fit; the own particle is left to the self block. Returns
+    (full-fit pairs, short-fit pairs, zero pairs), from the particles in
+    float64 (the kernel compares in FP32; pairs at a class boundary can differ).
+    """
+    c = particles[:, 1:3]
+    R = np.maximum(particles[:, 4], particles[:, 5])
+    counts = np.zeros(3, dtype=np.int64)
+    for b0 in range(0, n, TARGETS_PER_BLOCK):
+        b1 = min(n, b0 + TARGETS_PER_BLOCK)
+        pa, pb = b0 // npp, (b1 - 1) // npp
+        d = np.sqrt(((c[pa:pb + 1, None, :] - c[None, :, :]) ** 2).sum(-1))
+        gap = (d - R[pa:pb + 1, None] - R[None, :]).min(axis=0)
+        nt = b1 - b0
+        cls = np.where(gap >= ZP_ZERO * rho / LOG2E, 2, np.where(gap >= Z_SHORT * rho, 1, 0))
+        if own_by_block and pa == pb:
+            cls[pa] = 3                                       # the self block's pairs
+        for k in range(3):
+            counts[k] += nt * npp * int((cls == k).sum())
+        if not (own_by_block and pa == pb):                   # near panels are QBX rows
+            counts[0] -= nt * 3 * 16
+    return tuple(int(v) for v in counts)
 
 
 def parse():
@@ -346,14 +387,25 @@ def main():
     e1.record(stream)
     e1.synchronize()
     t_p2p = e0.elapsed_time(e1) / 1e3 / reps
-    pairs = n * (n - 3 * 16)
-    achieved = pairs * FLOPS_PER_PAIR / t_p2p / 1e12
+    n_full, n_short, n_zero = p2p_pair_classes(parts, 1.0, n // npart, n)
+    interactions = n * (n - 3 * 16)          # every far (target, source) pair of the operator
+    flops = n_full * FLOPS_PER_PAIR + n_short * FLOPS_PER_PAIR_SHORT
+    lane_ops = n_full * LANE_OPS_PER_PAIR + n_short * LANE_OPS_PER_PAIR_SHORT
+    achieved = flops / t_p2p / 1e12
     peak = SMS * FP32_LANES * 2 * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": stored_traffic(),
-                "kernel": "k_p2p_f32 (+k_assemble)", "pairs_per_s": pairs / t_p2p,
-                "flops_per_pair": FLOPS_PER_PAIR,
-                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max SM clock"}
+                "kernel": "k_p2p_f32 (+k_assemble)",
+                "pairs_evaluated_per_launch": n_full + n_short,
+                "pairs_full_fit": n_full, "pairs_short_fit": n_short,
+                "pairs_exact_zero_skipped": n_zero,
+                "pairs_evaluated_per_s": (n_full + n_short) / t_p2p,
+                "interactions_per_s": interactions / t_p2p,
+                "flops_per_pair": {"full fit": FLOPS_PER_PAIR, "short fit": FLOPS_PER_PAIR_SHORT},
+                "fma_pipe_frac": lane_ops / t_p2p / (SMS * FP32_LANES * 2.070e9),
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max SM clock; "
+                             "achieved counts evaluated pairs only (a pair whose exp2 "
+                             "underflows adds exactly 0 in FP32 and is skipped by particle)"}
 
     # ---- plain FP64 path: one matvec and (optionally) one full solve -------
     fp64 = {}

@@ -118,32 +118,70 @@ def main():
     return finish(out, kmax)
 
 
-def emit_rz(out, nu, name):
+def rz_monomials(nu, deg, tmax):
+    """Fit of P_nu on t in [0, tmax] as monomials in rz = t / (2 log2 e)."""
+    from math import comb
+    c = fit(nu, deg, 0.0, tmax)                    # monomial in s = (2/tmax) t - 1
+    al = 2.0 / tmax
+    t_mono = [0.0] * (deg + 1)
+    for k, ck in enumerate(c):
+        for j in range(k + 1):
+            t_mono[j] += ck * comb(k, j) * (al ** j) * ((-1.0) ** (k - j))
+    a = 2.0 * float(mp.log(2) ** -1)               # 2 log2(e)
+    return [v * a ** j for j, v in enumerate(t_mono)], a
+
+
+def rz_error(nu, rz_mono, a, tmax):
+    worst = 0.0
+    for t in np.linspace(1e-6, tmax, 800):
+        rz = np.float32(t / a)
+        acc = np.float32(rz_mono[-1])
+        for cf in reversed(rz_mono[:-1]):
+            acc = np.float32(acc * rz + np.float32(cf))
+        worst = max(worst, abs(float(acc) / float(p_nu(nu, t)) - 1))
+    return worst
+
+
+def long_rz(nu):
     for deg in (6, 7):
-        c = fit(nu, deg, 0.0, 1.0)                     # monomial in s = 2t - 1
-        t_mono = [0.0] * (deg + 1)                     # expand in t: s = 2t - 1
-        from math import comb
-        for k, ck in enumerate(c):
-            for j in range(k + 1):
-                t_mono[j] += ck * comb(k, j) * (2.0 ** j) * ((-1.0) ** (k - j))
-        a = 2.0 * float(mp.log(2) ** -1)               # 2 log2(e)
-        rz_mono = [v * a ** j for j, v in enumerate(t_mono)]
-        worst = 0.0
-        for t in np.linspace(1e-6, 1.0, 800):
-            rz = np.float32(t / a)
-            acc = np.float32(rz_mono[-1])
-            for cf in reversed(rz_mono[:-1]):
-                acc = np.float32(acc * rz + np.float32(cf))
-            worst = max(worst, abs(float(acc) / float(p_nu(nu, t)) - 1))
+        rz_mono, a = rz_monomials(nu, deg, 1.0)
+        worst = rz_error(nu, rz_mono, a, 1.0)
         if deg == 6 and worst > 1.5e-7:
             continue
         if worst > 2e-7:
             sys.exit("rz-monomial fit error %.3e" % worst)
-        out.append("// nu=%d in rz = 1/z' (z' = z log2 e), t = 2 log2(e) rz in [0, 1], degree %d, "
-                   "max rel. error %.2e (FP32 Horner)" % (nu, deg, worst))
-        out.append(arr(name, rz_mono, "float", "f"))
-        return
+        return rz_mono, worst
     sys.exit("no rz-monomial fit for nu=%d" % nu)
+
+
+# Short fit for particle pairs whose every node pair has z >= 10: fitted
+# down to z = 9.5 (t <= 2/9.5), so that FP32 rounding of the bounding-circle
+# gap that selects it stays inside the fitted range.
+Z_SHORT_FIT = 9.5
+
+
+def short_rz(nu):
+    tmax = 2.0 / Z_SHORT_FIT
+    rz_mono, a = rz_monomials(nu, 3, tmax)
+    worst = rz_error(nu, rz_mono, a, tmax)
+    if worst > 2e-7:
+        sys.exit("short rz-monomial fit error %.3e" % worst)
+    return rz_mono, worst, tmax
+
+
+def emit_rz(out, nu, name):
+    """One array per nu: the fit for every z > 2 (7 terms), then the short
+    fit for z >= 9.5 (4 terms), so that a kernel picks either by an offset."""
+    lng, e_long = long_rz(nu)
+    if len(lng) != 7:
+        sys.exit("the FP32 kernels expect a 7-term fit for z > 2")
+    sht, e_short, tmax = short_rz(nu)
+    out.append("// nu=%d in rz = 1/z' (z' = z log2 e), monomials, coefficient of rz^0 first:" % nu)
+    out.append("//   [0, 7): t = 2 log2(e) rz in [0, 1] (z >= 2), degree 6, max rel. error %.2e;"
+               % e_long)
+    out.append("//   [7, 11): z >= %g (t in [0, %.6f]), degree 3, max rel. error %.2e (FP32 Horner)"
+               % (Z_SHORT_FIT, tmax, e_short))
+    out.append(arr(name, lng + sht, "float", "f"))
 
 
 def finish(out, kmax):

@@ -39,6 +39,8 @@ constexpr int STILE = 256;       // source nodes staged per pass
 constexpr int F32_TPB = 128;     // FP32 kernels: two targets per thread
 constexpr int TILE_TPB = 256;    // FP64 pair tiles
 constexpr float LOG2E_F = 1.4426950408889634f;
+constexpr float Z_SHORT = 10.0f;   // z at or above which the short FP32 fit applies
+constexpr float ZP_ZERO = 128.0f;  // z' = z log2 e at or above which exp2(-z') flushes to 0
 constexpr double LOG2E = 1.4426950408889634;
 
 __device__ __forceinline__ bool is_near_panel(int pt_panel, int ps_panel, int npan, int w) {
@@ -147,19 +149,58 @@ __device__ __forceinline__ void target_setup(TargetF32& T, const GeomView& G, in
     T.pan = pan;
 }
 
+// Smallest bounding-circle gap between target particles [pa, pb] and source
+// particle s, in FP32 from the hi/lo centres. Every thread of a block that
+// passes the same arguments gets the same value, so decisions taken on it
+// are block-uniform.
+__device__ __forceinline__ float block_gap(const GeomView& G, int pa, int pb, int s) {
+    const float4 cs = G.c32[s];
+    const float rs = G.r32[s];
+    float gmin = 3.0e38f;
+    for (int p = pa; p <= pb; ++p) {
+        const float4 ct = G.c32[p];
+        const float dX = (ct.x - cs.x) + (ct.z - cs.z);
+        const float dY = (ct.y - cs.y) + (ct.w - cs.w);
+        gmin = fminf(gmin, sqrtf(dX * dX + dY * dY) - G.r32[p] - rs);
+    }
+    return gmin;
+}
+
 // Packed FP32 evaluation of two far pairs at once (one target, two sources)
 // with the f32x2 FMA/ADD/MUL instructions of sm_100+: lanes .x/.y are the
 // two sources. Sources are staged as pairs: A = (-X0, -X1, -Y0, -Y1) in
 // scaled coordinates, B = (gx0, gx1, gy0, gy1). Returns the two terms in the
-// units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))) added to acc, z > 2 only.
+// units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))) added to acc.
+// NC = 7 evaluates the fit of P1 for every z > 2, NC = 4 the short fit,
+// valid for z >= 9.5 (both within 1.5e-7 relative).
+//
+// Two source-particle classes, decided per block from the bounding-circle
+// gap between the block's target particles and the source particle (the
+// same FP32 arithmetic in every thread, hence block-uniform):
+//  * gap >= Z_SHORT rho: the short fit (three FMA fewer per pair);
+//  * gap >= ZP_ZERO / kappa' (z' >= 128 for every pair): exp2(-z') is below
+//    2^-127, which ex2.approx.ftz flushes to +0, so every pair adds exactly
+//    zero to the FP32 sum; the source particle is skipped, with a result
+//    identical to evaluating it.
+
+// Coefficients of one fit, each in both lanes of a float2: the fit for every
+// z > 2 (7 terms) or the short fit (the first 4 of c), picked at run time so
+// that both use the same registers.
+constexpr int FIT_LONG = 7, FIT_SHORT = 4;
 struct PolyRZ {
-    float2 c[7];
-    __device__ __forceinline__ PolyRZ() {
+    float2 c[FIT_LONG];
+    __device__ __forceinline__ explicit PolyRZ(bool short_fit) {
+        const int off = short_fit ? FIT_LONG : 0;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) c[k] = make_float2(YK_P1_F32_RZ[k], YK_P1_F32_RZ[k]);
+        for (int k = 0; k < FIT_LONG; ++k) {
+            const float v = YK_P1_F32_RZ[min(off + k, FIT_LONG + FIT_SHORT - 1)];
+            c[k] = make_float2(v, v);
+        }
     }
 };
+static_assert(sizeof(YK_P1_F32_RZ) == (FIT_LONG + FIT_SHORT) * sizeof(float), "fit lengths");
 
+template <int NC>
 __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, const float4& B,
                                        const PolyRZ& P, float2 acc) {
     const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
@@ -167,9 +208,9 @@ __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, co
     const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
     const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));   // 1/z'
     const float2 zp = __fmul2_rn(z2, rz);                                 // z'
-    float2 p = P.c[6];
+    float2 p = P.c[NC - 1];
 #pragma unroll
-    for (int k = 5; k >= 0; --k) p = __ffma2_rn(p, rz, P.c[k]);          // P1 in rz
+    for (int k = NC - 2; k >= 0; --k) p = __ffma2_rn(p, rz, P.c[k]);     // P1 in rz
     const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
     const float2 sq = make_float2(rsqrt_fast(zp.x), rsqrt_fast(zp.y));   // z'^{-1/2}
     const float2 dot = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
@@ -191,7 +232,7 @@ __device__ __forceinline__ float2 close2(float2 TX, float2 TY, const float4& A, 
     const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
     const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
     const float z2x = fmaf(dX.x, dX.x, dY.x * dY.x), z2y = fmaf(dX.y, dX.y, dY.y * dY.y);
-    if (z2x > ZCUT2 && z2y > ZCUT2) return far2(TX, TY, A, B, P, acc);
+    if (z2x > ZCUT2 && z2y > ZCUT2) return far2<FIT_LONG>(TX, TY, A, B, P, acc);
     acc.x += PairF32::any(dX.x, dY.x, B.x, B.z);
     acc.y += PairF32::any(dX.y, dY.y, B.y, B.w);
     return acc;
@@ -205,16 +246,21 @@ __device__ __forceinline__ float2 close2(float2 TX, float2 TY, const float4& A, 
 // (kappa = 1/rho, kappa' = log2(e)/rho, kappa/kappa' = ln 2); the constant
 // sqrt(log2 e) kappa kappa' is applied by the caller.
 struct PolyRZ2 {
-    float2 c0[7], c1[7];
-    __device__ __forceinline__ PolyRZ2() {
+    float2 c0[FIT_LONG], c1[FIT_LONG];
+    __device__ __forceinline__ explicit PolyRZ2(bool short_fit) {
+        const int off = short_fit ? FIT_LONG : 0;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            c0[k] = make_float2(YK_P0_F32_RZ[k], YK_P0_F32_RZ[k]);
-            c1[k] = make_float2(YK_P1_F32_RZ[k], YK_P1_F32_RZ[k]);
+        for (int k = 0; k < FIT_LONG; ++k) {
+            const int i = min(off + k, FIT_LONG + FIT_SHORT - 1);
+            const float v0 = YK_P0_F32_RZ[i], v1 = YK_P1_F32_RZ[i];
+            c0[k] = make_float2(v0, v0);
+            c1[k] = make_float2(v1, v1);
         }
     }
 };
+static_assert(sizeof(YK_P0_F32_RZ) == (FIT_LONG + FIT_SHORT) * sizeof(float), "fit lengths");
 
+template <int NC>
 __device__ __forceinline__ float2 grad2(float2 TX, float2 TY, float2 NX, float2 NY, const float4& A,
                                         const float4& B, const PolyRZ2& P, float2 acc) {
     const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
@@ -222,9 +268,9 @@ __device__ __forceinline__ float2 grad2(float2 TX, float2 TY, float2 NX, float2 
     const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
     const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));
     const float2 zp = __fmul2_rn(z2, rz);
-    float2 p0 = P.c0[6], p1 = P.c1[6];
+    float2 p0 = P.c0[NC - 1], p1 = P.c1[NC - 1];
 #pragma unroll
-    for (int k = 5; k >= 0; --k) {
+    for (int k = NC - 2; k >= 0; --k) {
         p0 = __ffma2_rn(p0, rz, P.c0[k]);
         p1 = __ffma2_rn(p1, rz, P.c1[k]);
     }
@@ -272,7 +318,9 @@ __device__ __forceinline__ void stage_pairs(const GeomView& G, const double* __r
 }
 
 // One staged tile of the normal derivative for two targets: packed far
-// pairs into f0/f1 (scaled units), near/own pairs (scalar) into s0/s1.
+// pairs into f0/f1 (scaled units; NC selects the fit), near/own pairs
+// (scalar) into s0/s1.
+template <int NC>
 __device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB, int jb, int cnt,
                                           const GeomView& G, const TargetF32& T0,
                                           const TargetF32& T1, bool use0, bool use1, float nx0,
@@ -288,8 +336,8 @@ __device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB
         float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
         for (int m = 0; m < npair; ++m) {
             const float4 A = srcA[m], B = srcB[m];
-            a0 = grad2(TX0, TY0, NX0, NY0, A, B, P, a0);
-            a1 = grad2(TX1, TY1, NX1, NY1, A, B, P, a1);
+            a0 = grad2<NC>(TX0, TY0, NX0, NY0, A, B, P, a0);
+            a1 = grad2<NC>(TX1, TY1, NX1, NY1, A, B, P, a1);
         }
         f0 += a0.x + a0.y;
         f1 += a1.x + a1.y;
@@ -307,6 +355,24 @@ __device__ __forceinline__ void grad_tile(const float4* srcA, const float4* srcB
     }
 }
 
+// Packed far pairs of one staged tile for two targets (NC selects the fit).
+template <int NC>
+__device__ __forceinline__ void far_tile(const float4* srcA, const float4* srcB, int npair,
+                                         const TargetF32& T0, const TargetF32& T1,
+                                         const PolyRZ& P, float& r0, float& r1) {
+    const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+    const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
+    float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+#pragma unroll 2
+    for (int m = 0; m < npair; ++m) {
+        const float4 A = srcA[m], B = srcB[m];
+        a0 = far2<NC>(TX0, TY0, A, B, P, a0);
+        a1 = far2<NC>(TX1, TY1, A, B, P, a1);
+    }
+    r0 = a0.x + a0.y;
+    r1 = a1.x + a1.y;
+}
+
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
                                                      int ppc, float kscale, double skip_gap,
@@ -322,11 +388,17 @@ __global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const doubl
     const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
     const float kpf = (float)(LOG2E / G.rho);          // log2(e) / rho
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;  // z <= 2 possible below
+    const float short_gap = Z_SHORT * (float)G.rho, zero_gap = ZP_ZERO / kpf;
+    const int pa = (int)(blockIdx.x * (int64_t)TPB / G.npp);
+    const int pb = (int)((min((int64_t)G.n, (blockIdx.x + 1) * (int64_t)TPB) - 1) / G.npp);
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
-    const PolyRZ P;
     double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
+        const float bg = block_gap(G, pa, pb, s);
+        if (bg >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
+        const bool short_fit = bg >= short_gap;
+        const PolyRZ P(short_fit);
         const int64_t base = (int64_t)s * G.npp;
         TargetF32 T0, T1;
         target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
@@ -370,17 +442,8 @@ __global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const doubl
             __syncthreads();
             float r0 = 0.0f, r1 = 0.0f;
             if (!T0.close && !T1.close && !skip0 && !skip1) {
-                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
-                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
-                float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-#pragma unroll 2
-                for (int m = 0; m < npair; ++m) {
-                    const float4 A = srcA[m], B = srcB[m];
-                    a0 = far2(TX0, TY0, A, B, P, a0);
-                    a1 = far2(TX1, TY1, A, B, P, a1);
-                }
-                r0 = a0.x + a0.y;
-                r1 = a1.x + a1.y;
+                if (short_fit) far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                else far_tile<FIT_LONG>(srcA, srcB, npair, T0, T1, P, r0, r1);
             } else {
                 for (int q = 0; q < cnt; ++q) {
                     const float4 S = src_scalar(srcA, srcB, q);
@@ -419,11 +482,17 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
     const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
     const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const PolyRZ2 P;
+    const float short_gap = Z_SHORT * (float)G.rho, zero_gap = ZP_ZERO / kpf;
+    const int pa = (int)(blockIdx.x * (int64_t)TPB / G.npp);
+    const int pb = (int)((min((int64_t)G.n, (blockIdx.x + 1) * (int64_t)TPB) - 1) / G.npp);
     const int s0 = blockIdx.y * ppc;
     const int s1 = min(G.np, s0 + ppc);
     double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
     for (int s = s0; s < s1; ++s) {
+        const float bg = block_gap(G, pa, pb, s);
+        if (bg >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
+        const PolyRZ2 P(bg >= short_gap);
+        const bool short_fit = bg >= short_gap;
         const int64_t base = (int64_t)s * G.npp;
         TargetF32 T0, T1;
         target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
@@ -437,8 +506,12 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
             stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
             __syncthreads();
             float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-            grad_tile(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1, inv_kp,
-                      kappa, rho, P, a0, a1, b0, b1);
+            if (short_fit)
+                grad_tile<FIT_SHORT>(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1,
+                             inv_kp, kappa, rho, P, a0, a1, b0, b1);
+            else
+                grad_tile<FIT_LONG>(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1,
+                             inv_kp, kappa, rho, P, a0, a1, b0, b1);
             fast0 += (double)a0;
             fast1 += (double)a1;
             slow0 += (double)b0;
@@ -468,7 +541,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
     const int pt = blockIdx.x;
     const float kpf = (float)(LOG2E / G.rho);
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const PolyRZ P;
+    const float short_gap = Z_SHORT * (float)G.rho, zero_gap = ZP_ZERO / kpf;
     const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
     for (int ib = 0; ib < G.npp; ib += TPB) {
         const int l0 = ib + threadIdx.x, l1 = l0 + F32_TPB;
@@ -480,6 +553,10 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
         double acc0 = 0.0, acc1 = 0.0;
         for (int k = n0; k < n1; ++k) {
             const int s = nbr[k];
+            const float bg = block_gap(G, pt, pt, s);
+            if (bg >= zero_gap) continue;   // every pair adds +0 in FP32
+            const bool short_fit = bg >= short_gap;
+            const PolyRZ P(short_fit);
             TargetF32 T0, T1;
             target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
             target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
@@ -515,19 +592,12 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
                 }
                 __syncthreads();
                 float r0 = 0.0f, r1 = 0.0f;
-                const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
-                const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
                 if (!T0.close) {
-                    float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-#pragma unroll 2
-                    for (int m = 0; m < npair; ++m) {
-                        const float4 A = srcA[m], B = srcB[m];
-                        a0 = far2(TX0, TY0, A, B, P, a0);
-                        a1 = far2(TX1, TY1, A, B, P, a1);
-                    }
-                    r0 = a0.x + a0.y;
-                    r1 = a1.x + a1.y;
+                    if (short_fit) far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                    else far_tile<FIT_LONG>(srcA, srcB, npair, T0, T1, P, r0, r1);
                 } else if (!T0.own) {
+                    const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
+                    const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
                     float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
                     for (int m = 0; m < npair; ++m) {
                         const float4 A = srcA[m], B = srcB[m];
@@ -567,7 +637,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
     const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
     const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const PolyRZ2 P;
+    const float short_gap = Z_SHORT * (float)G.rho, zero_gap = ZP_ZERO / kpf;
     const double cf = sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho);
     const int n0 = nbr_off[pt], n1 = nbr_off[pt + 1];
     for (int ib = 0; ib < G.npp; ib += TPB) {
@@ -582,6 +652,10 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
         double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
         for (int k = n0; k < n1; ++k) {
             const int s = nbr[k];
+            const float bg = block_gap(G, pt, pt, s);
+            if (bg >= zero_gap) continue;   // every pair adds +0 in FP32
+            const bool short_fit = bg >= short_gap;
+            const PolyRZ2 P(short_fit);
             TargetF32 T0, T1;
             target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
             target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
@@ -593,8 +667,12 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
                 stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
                 __syncthreads();
                 float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-                grad_tile(srcA, srcB, jb, cnt, G, T0, T1, true, true, nx0, ny0, nx1, ny1, inv_kp,
-                          kappa, rho, P, a0, a1, b0, b1);
+                if (short_fit)
+                    grad_tile<FIT_SHORT>(srcA, srcB, jb, cnt, G, T0, T1, true, true, nx0, ny0, nx1, ny1,
+                                 inv_kp, kappa, rho, P, a0, a1, b0, b1);
+                else
+                    grad_tile<FIT_LONG>(srcA, srcB, jb, cnt, G, T0, T1, true, true, nx0, ny0, nx1, ny1,
+                                 inv_kp, kappa, rho, P, a0, a1, b0, b1);
                 fast0 += (double)a0;
                 fast1 += (double)a1;
                 slow0 += (double)b0;
