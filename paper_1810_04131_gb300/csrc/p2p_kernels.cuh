@@ -149,21 +149,27 @@ __device__ __forceinline__ void target_setup(TargetF32& T, const GeomView& G, in
     T.pan = pan;
 }
 
-// Smallest bounding-circle gap between target particles [pa, pb] and source
-// particle s, in FP32 from the hi/lo centres. Every thread of a block that
-// passes the same arguments gets the same value, so decisions taken on it
-// are block-uniform.
-__device__ __forceinline__ float block_gap(const GeomView& G, int pa, int pb, int s) {
+// Smallest bounding-circle gap, and largest centre distance plus both radii,
+// between target particles [pa, pb] and source particle s, in FP32 from the
+// hi/lo centres: every node pair's distance lies in [gap, far]. Every thread
+// of a block that passes the same arguments gets the same values, so
+// decisions taken on them are block-uniform.
+struct PairRange {
+    float gap, far;
+};
+__device__ __forceinline__ PairRange block_range(const GeomView& G, int pa, int pb, int s) {
     const float4 cs = G.c32[s];
     const float rs = G.r32[s];
-    float gmin = 3.0e38f;
+    PairRange r{3.0e38f, 0.0f};
     for (int p = pa; p <= pb; ++p) {
         const float4 ct = G.c32[p];
         const float dX = (ct.x - cs.x) + (ct.z - cs.z);
         const float dY = (ct.y - cs.y) + (ct.w - cs.w);
-        gmin = fminf(gmin, sqrtf(dX * dX + dY * dY) - G.r32[p] - rs);
+        const float d = sqrtf(dX * dX + dY * dY), rsum = G.r32[p] + rs;
+        r.gap = fminf(r.gap, d - rsum);
+        r.far = fmaxf(r.far, d + rsum);
     }
-    return gmin;
+    return r;
 }
 
 // Packed FP32 evaluation of two far pairs at once (one target, two sources)
@@ -172,7 +178,9 @@ __device__ __forceinline__ float block_gap(const GeomView& G, int pa, int pb, in
 // scaled coordinates, B = (gx0, gx1, gy0, gy1). Returns the two terms in the
 // units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))) added to acc.
 // NC = 7 evaluates the fit of P1 for every z > 2, NC = 4 the short fit,
-// valid for z >= 9.5 (both within 1.5e-7 relative).
+// valid for z >= 9.5 (both within 1.5e-7 relative), NC = NARROW the
+// expansion about the source particle's 1/z' (two MUFU operations a pair
+// instead of three).
 //
 // Two source-particle classes, decided per block from the bounding-circle
 // gap between the block's target particles and the source particle (the
@@ -183,14 +191,51 @@ __device__ __forceinline__ float block_gap(const GeomView& G, int pa, int pb, in
 //    zero to the FP32 sum; the source particle is skipped, with a result
 //    identical to evaluating it.
 
-// Coefficients of one fit, each in both lanes of a float2: the fit for every
-// z > 2 (7 terms) or the short fit (the first 4 of c), picked at run time so
-// that both use the same registers.
-constexpr int FIT_LONG = 7, FIT_SHORT = 4;
+// Coefficients of one source particle's evaluation, each in both lanes of a
+// float2, picked at run time so that all modes use the same registers:
+//  * FIT_LONG: the fit of P1 for every z > 2 (7 terms);
+//  * FIT_SHORT: the short fit (the first 4 of c);
+//  * NARROW: every pair has 1/z' within a factor 1 +- eps of rc (eps <=
+//    EPS_NARROW). Then g(rz) = rz^{1/2} P1(rz), with P1 the short fit
+//    sum_j p_j rz^j, is sum_k a_k u^k with u = rz/rc - 1 and
+//    a_k = sum_j p_j rc^{j+1/2} binom(j + 1/2, k), cut after k = 4 (the
+//    binomial series of (1 + u)^{j+1/2}; the first term left out is below
+//    0.03 eps^5 = 5e-8 relative). c[0..4] = a_k, c[5] = 1/rc, c[6] = -1.
+//    This replaces the z'^{-1/2} MUFU operation with one FMA.
+constexpr int FIT_LONG = 7, FIT_SHORT = 4, NARROW = 5;
+constexpr float EPS_NARROW = 0.07f;
+
+__host__ __device__ constexpr float binom_half(int j, int k) {   // binom(j + 1/2, k)
+    float b = 1.0f;
+    for (int i = 0; i < k; ++i) b = b * ((float)j + 0.5f - (float)i) / (float)(i + 1);
+    return b;
+}
+
 struct PolyRZ {
     float2 c[FIT_LONG];
-    __device__ __forceinline__ explicit PolyRZ(bool short_fit) {
-        const int off = short_fit ? FIT_LONG : 0;
+    __device__ __forceinline__ PolyRZ(int mode, float rc) {
+        if (mode == NARROW) {
+            const float sr = sqrtf(rc);
+            float pj[FIT_SHORT];
+            float pw = sr;
+#pragma unroll
+            for (int j = 0; j < FIT_SHORT; ++j) {
+                pj[j] = YK_P1_F32_RZ[FIT_LONG + j] * pw;   // p_j rc^{j+1/2}
+                pw *= rc;
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                float a = 0.0f;
+#pragma unroll
+                for (int j = FIT_SHORT - 1; j >= 0; --j) a = fmaf(pj[j], binom_half(j, k), a);
+                c[k] = make_float2(a, a);
+            }
+            const float ir = 1.0f / rc;
+            c[5] = make_float2(ir, ir);
+            c[6] = make_float2(-1.0f, -1.0f);
+            return;
+        }
+        const int off = (mode == FIT_SHORT) ? FIT_LONG : 0;
 #pragma unroll
         for (int k = 0; k < FIT_LONG; ++k) {
             const float v = YK_P1_F32_RZ[min(off + k, FIT_LONG + FIT_SHORT - 1)];
@@ -200,6 +245,18 @@ struct PolyRZ {
 };
 static_assert(sizeof(YK_P1_F32_RZ) == (FIT_LONG + FIT_SHORT) * sizeof(float), "fit lengths");
 
+// The mode of a source particle from its pair range (block-uniform).
+__device__ __forceinline__ int far_mode(const PairRange& r, float short_gap, float kpf, float& rc) {
+    rc = 0.0f;
+    if (!(r.gap >= short_gap)) return FIT_LONG;
+    const float lo = 1.0f / (kpf * r.far), hi = 1.0f / (kpf * r.gap);   // range of 1/z'
+    if (hi - lo <= EPS_NARROW * (hi + lo)) {
+        rc = 0.5f * (hi + lo);
+        return NARROW;
+    }
+    return FIT_SHORT;
+}
+
 template <int NC>
 __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, const float4& B,
                                        const PolyRZ& P, float2 acc) {
@@ -208,6 +265,15 @@ __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, co
     const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
     const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));   // 1/z'
     const float2 zp = __fmul2_rn(z2, rz);                                 // z'
+    if constexpr (NC == NARROW) {
+        const float2 u = __ffma2_rn(rz, P.c[5], P.c[6]);                  // rz/rc - 1
+        float2 q = P.c[4];
+#pragma unroll
+        for (int k = 3; k >= 0; --k) q = __ffma2_rn(q, u, P.c[k]);       // rz^{1/2} P1(rz)
+        const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
+        const float2 dot = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
+        return __ffma2_rn(__fmul2_rn(e, q), __fmul2_rn(rz, dot), acc);
+    }
     float2 p = P.c[NC - 1];
 #pragma unroll
     for (int k = NC - 2; k >= 0; --k) p = __ffma2_rn(p, rz, P.c[k]);     // P1 in rz
@@ -395,10 +461,11 @@ __global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const doubl
     const int s1 = min(G.np, s0 + ppc);
     double acc0 = 0.0, acc1 = 0.0;
     for (int s = s0; s < s1; ++s) {
-        const float bg = block_gap(G, pa, pb, s);
-        if (bg >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
-        const bool short_fit = bg >= short_gap;
-        const PolyRZ P(short_fit);
+        const PairRange rg = block_range(G, pa, pb, s);
+        if (rg.gap >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
+        float rc;
+        const int mode = far_mode(rg, short_gap, kpf, rc);
+        const PolyRZ P(mode, rc);
         const int64_t base = (int64_t)s * G.npp;
         TargetF32 T0, T1;
         target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
@@ -442,7 +509,8 @@ __global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const doubl
             __syncthreads();
             float r0 = 0.0f, r1 = 0.0f;
             if (!T0.close && !T1.close && !skip0 && !skip1) {
-                if (short_fit) far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                if (mode == NARROW) far_tile<NARROW>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                else if (mode == FIT_SHORT) far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
                 else far_tile<FIT_LONG>(srcA, srcB, npair, T0, T1, P, r0, r1);
             } else {
                 for (int q = 0; q < cnt; ++q) {
@@ -489,7 +557,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
     const int s1 = min(G.np, s0 + ppc);
     double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
     for (int s = s0; s < s1; ++s) {
-        const float bg = block_gap(G, pa, pb, s);
+        const float bg = block_range(G, pa, pb, s).gap;
         if (bg >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
         const PolyRZ2 P(bg >= short_gap);
         const bool short_fit = bg >= short_gap;
@@ -553,10 +621,11 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
         double acc0 = 0.0, acc1 = 0.0;
         for (int k = n0; k < n1; ++k) {
             const int s = nbr[k];
-            const float bg = block_gap(G, pt, pt, s);
-            if (bg >= zero_gap) continue;   // every pair adds +0 in FP32
-            const bool short_fit = bg >= short_gap;
-            const PolyRZ P(short_fit);
+            const PairRange rg = block_range(G, pt, pt, s);
+            if (rg.gap >= zero_gap) continue;   // every pair adds +0 in FP32
+            float rc;
+            const int mode = far_mode(rg, short_gap, kpf, rc);
+            const PolyRZ P(mode, rc);
             TargetF32 T0, T1;
             target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
             target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
@@ -593,9 +662,12 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
                 __syncthreads();
                 float r0 = 0.0f, r1 = 0.0f;
                 if (!T0.close) {
-                    if (short_fit) far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                    if (mode == NARROW) far_tile<NARROW>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                    else if (mode == FIT_SHORT)
+                        far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
                     else far_tile<FIT_LONG>(srcA, srcB, npair, T0, T1, P, r0, r1);
                 } else if (!T0.own) {
+                    // close (gap <= 2 rho) implies mode FIT_LONG (gap < 10 rho)
                     const float2 TX0 = make_float2(T0.TX, T0.TX), TY0 = make_float2(T0.TY, T0.TY);
                     const float2 TX1 = make_float2(T1.TX, T1.TX), TY1 = make_float2(T1.TY, T1.TY);
                     float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
@@ -652,7 +724,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
         double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
         for (int k = n0; k < n1; ++k) {
             const int s = nbr[k];
-            const float bg = block_gap(G, pt, pt, s);
+            const float bg = block_range(G, pt, pt, s).gap;
             if (bg >= zero_gap) continue;   // every pair adds +0 in FP32
             const bool short_fit = bg >= short_gap;
             const PolyRZ2 P(short_fit);

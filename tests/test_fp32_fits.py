@@ -1,0 +1,113 @@
+"""Host-side checks of the FP32 far-field kernels' constants, against scipy's
+exponentially scaled Bessel function (an independent implementation):
+
+* the K1/K0 fits the packed FP32 loops read from bessel_tables.h, in FP32
+  Horner order, over the ranges the kernels use them on;
+* the narrow expansion of rz^{1/2} P1(rz) about the source particle's 1/z'
+  (binomial series of (1 + u)^{j+1/2}, cut after u^4) for every range the
+  kernel admits (relative width up to 0.07);
+* the exact-zero skip: at z' >= 128 the largest possible pair value is below
+  the smallest normal FP32 number, so ex2.approx.ftz gives +0 for every pair.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+scipy_special = pytest.importorskip("scipy.special")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLES = os.path.join(ROOT, "paper_1810_04131_gb300", "csrc", "bessel_tables.h")
+KERNELS = os.path.join(ROOT, "paper_1810_04131_gb300", "csrc", "p2p_kernels.cuh")
+LOG2E = 1.4426950408889634
+
+
+def table(name):
+    txt = open(TABLES).read()
+    m = re.search(r"%s\[(\d+)\] = \{([^}]*)\}" % name, txt)
+    vals = [float(v.strip().rstrip("f")) for v in m.group(2).split(",")]
+    assert len(vals) == int(m.group(1))
+    return np.array(vals, dtype=np.float32)
+
+
+def kernel_constant(name):
+    m = re.search(r"constexpr float %s = ([0-9.e+-]+)f;" % name, open(KERNELS).read())
+    return float(m.group(1))
+
+
+def horner32(coef, x):
+    acc = np.full_like(x, coef[-1], dtype=np.float32)
+    for c in coef[-2::-1]:
+        acc = (acc * x + np.float32(c)).astype(np.float32)
+    return acc
+
+
+def p_nu(nu, rz):
+    """e^z z^{1/2} K_nu(z) at z = 1/(rz log2 e) (the fitted function)."""
+    z = 1.0 / (rz * LOG2E)
+    return scipy_special.kve(nu, z) * np.sqrt(z)
+
+
+@pytest.mark.parametrize("name,nu", [("YK_P1_F32_RZ", 1), ("YK_P0_F32_RZ", 0)])
+def test_packed_fits_against_scipy(name, nu):
+    c = table(name)
+    assert len(c) == 11
+    # full fit: z >= 2 (t = 2/z in (0, 1])
+    rz = np.linspace(1e-6, 1.0 / (2.0 * LOG2E), 2000).astype(np.float32)
+    err = np.abs(horner32(c[:7], rz) / p_nu(nu, rz.astype(np.float64)) - 1).max()
+    assert err < 2e-7, err
+    # short fit: z >= 9.5
+    rz = np.linspace(1e-6, 1.0 / (9.5 * LOG2E), 2000).astype(np.float32)
+    err = np.abs(horner32(c[7:], rz) / p_nu(nu, rz.astype(np.float64)) - 1).max()
+    assert err < 2e-7, err
+    # the short fit is not good for the full range (the tables are not swapped)
+    rz = np.linspace(1.0 / (4.0 * LOG2E), 1.0 / (2.0 * LOG2E), 200).astype(np.float32)
+    assert np.abs(horner32(c[7:], rz) / p_nu(nu, rz.astype(np.float64)) - 1).max() > 1e-5
+
+
+def binom_half(j, k):
+    b = 1.0
+    for i in range(k):
+        b = b * (j + 0.5 - i) / (i + 1)
+    return b
+
+
+def test_binomial_coefficients_match_series():
+    # (1 + u)^{j+1/2} = sum_k binom(j + 1/2, k) u^k, checked at small u
+    for j in range(4):
+        u = np.linspace(-0.07, 0.07, 41)
+        series = sum(binom_half(j, k) * u ** k for k in range(30))
+        assert np.allclose(series, (1 + u) ** (j + 0.5), rtol=1e-14, atol=0)
+
+
+def test_narrow_expansion_truncation():
+    eps = kernel_constant("EPS_NARROW")
+    assert 0.0 < eps <= 0.07
+    p = table("YK_P1_F32_RZ")[7:].astype(np.float64)
+    zshort = kernel_constant("Z_SHORT")
+    worst_trunc = worst_total = 0.0
+    for rc in np.geomspace(1.0 / (128 * (1 + eps)), 1.0 / (zshort * LOG2E * (1 + eps)), 300):
+        a = [sum(p[j] * rc ** (j + 0.5) * binom_half(j, k) for j in range(4)) for k in range(5)]
+        rz = np.linspace(rc * (1 - eps), rc * (1 + eps), 200)
+        u = rz / rc - 1
+        q = sum(a[k] * u ** k for k in range(5))
+        fit = np.sqrt(rz) * np.polyval(p[::-1], rz)
+        worst_trunc = max(worst_trunc, np.abs(q / fit - 1).max())
+        worst_total = max(worst_total, np.abs(q / (np.sqrt(rz) * p_nu(1, rz)) - 1).max())
+    assert worst_trunc < 6e-8, worst_trunc
+    assert worst_total < 2.5e-7, worst_total
+
+
+def test_exact_zero_threshold():
+    zp0 = kernel_constant("ZP_ZERO")
+    assert zp0 >= 127.0
+    # the true exp2(-z') at the threshold is below 2^-127; an approximation
+    # with relative error 2^-22 stays below the smallest normal number 2^-126,
+    # which ftz flushes to zero
+    assert 2.0 ** (-zp0) * (1 + 2.0 ** -22) < 2.0 ** -126
+    # a particle pair is skipped when its bounding-circle gap g has
+    # g log2(e) / rho >= 128; every node pair is at least g apart
+    rho = 1.0
+    gap = zp0 * rho / LOG2E
+    assert gap * LOG2E / rho >= zp0 - 1e-9
