@@ -37,15 +37,19 @@ WORKLOAD = "disks512"
 # three products (3), accumulate (2).
 # With a source particle whose 1/z' range is within 1 +- 0.07 of its centre
 # (the narrow class), z'^{-1/2} and the polynomial become one degree-4
-# polynomial in u = rz/rc - 1: u (2), polynomial (8), one MUFU fewer.
+# polynomial in u = rz/rc - 1: u (2), polynomial (8), no z'^{-1/2} MUFU and one
+# product fewer.
 FLOPS_PER_PAIR = 29
 FLOPS_PER_PAIR_SHORT = 23
-FLOPS_PER_PAIR_NARROW = 24
+FLOPS_PER_PAIR_NARROW = 25
+FLOPS_PER_PAIR_NARROW3 = 23      # the narrow class within 1 +- 0.03: degree 3
 # FMA-pipe lane operations per pair (the same lists without the MUFU ops)
 LANE_OPS_PER_PAIR = 17
 LANE_OPS_PER_PAIR_SHORT = 14
 LANE_OPS_PER_PAIR_NARROW = 15
+LANE_OPS_PER_PAIR_NARROW3 = 14
 EPS_NARROW = 0.07
+EPS_NARROW3 = 0.03
 SMS, FP32_LANES = 152, 128
 # the classes of the FP32 far-field kernel (bounding-circle gap in units of rho)
 Z_SHORT = 10.0
@@ -88,14 +92,16 @@ def p2p_pair_classes(particles, rho, npp, n, own_by_block=True):
     bounding-circle gap, largest centre distance plus both radii, over the
     block's target particles): gap >= 128 rho / log2(e) adds exactly zero in
     FP32 and is skipped; gap >= 10 rho takes the short K1 fit, and the
-    narrow expansion when also far - gap <= 0.07 (far + gap); the rest the
-    full fit. The own particle is left to the self block. Returns
-    (full-fit, short-fit, narrow, zero) pair counts, from the particles in
-    float64 (the kernel compares in FP32; pairs at a class boundary can differ).
+    narrow expansion when also far - gap <= 0.07 (far + gap), of degree 3
+    when far - gap <= 0.03 (far + gap); the rest the full fit. The own
+    particle is left to the self block. Returns (full-fit, short-fit,
+    narrow degree 4, narrow degree 3, zero) pair counts, from the particles
+    in float64 (the kernel compares in FP32; pairs at a class boundary can
+    differ).
     """
     c = particles[:, 1:3]
     R = np.maximum(particles[:, 4], particles[:, 5])
-    counts = np.zeros(4, dtype=np.int64)
+    counts = np.zeros(5, dtype=np.int64)
     for b0 in range(0, n, TARGETS_PER_BLOCK):
         b1 = min(n, b0 + TARGETS_PER_BLOCK)
         pa, pb = b0 // npp, (b1 - 1) // npp
@@ -106,11 +112,12 @@ def p2p_pair_classes(particles, rho, npp, n, own_by_block=True):
         nt = b1 - b0
         short = gap >= Z_SHORT * rho
         narrow = short & (far - gap <= EPS_NARROW * (far + gap))
-        cls = np.where(gap >= ZP_ZERO * rho / LOG2E, 3,
-                       np.where(narrow, 2, np.where(short, 1, 0)))
+        narrow3 = narrow & (far - gap <= EPS_NARROW3 * (far + gap))
+        cls = np.where(gap >= ZP_ZERO * rho / LOG2E, 4,
+                       np.where(narrow3, 3, np.where(narrow, 2, np.where(short, 1, 0))))
         if own_by_block and pa == pb:
-            cls[pa] = 4                                       # the self block's pairs
-        for k in range(4):
+            cls[pa] = 5                                       # the self block's pairs
+        for k in range(5):
             counts[k] += nt * npp * int((cls == k).sum())
         if not (own_by_block and pa == pb):                   # near panels are QBX rows
             counts[0] -= nt * 3 * 16
@@ -400,13 +407,13 @@ def main():
     e1.record(stream)
     e1.synchronize()
     t_p2p = e0.elapsed_time(e1) / 1e3 / reps
-    n_full, n_short, n_narrow, n_zero = p2p_pair_classes(parts, 1.0, n // npart, n)
-    n_eval = n_full + n_short + n_narrow
+    n_full, n_short, n_narrow, n_narrow3, n_zero = p2p_pair_classes(parts, 1.0, n // npart, n)
+    n_eval = n_full + n_short + n_narrow + n_narrow3
     interactions = n * (n - 3 * 16)          # every far (target, source) pair of the operator
     flops = (n_full * FLOPS_PER_PAIR + n_short * FLOPS_PER_PAIR_SHORT
-             + n_narrow * FLOPS_PER_PAIR_NARROW)
+             + n_narrow * FLOPS_PER_PAIR_NARROW + n_narrow3 * FLOPS_PER_PAIR_NARROW3)
     lane_ops = (n_full * LANE_OPS_PER_PAIR + n_short * LANE_OPS_PER_PAIR_SHORT
-                + n_narrow * LANE_OPS_PER_PAIR_NARROW)
+                + n_narrow * LANE_OPS_PER_PAIR_NARROW + n_narrow3 * LANE_OPS_PER_PAIR_NARROW3)
     achieved = flops / t_p2p / 1e12
     peak = SMS * FP32_LANES * 2 * 2.070e9 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -414,11 +421,13 @@ def main():
                 "kernel": "k_p2p_f32 (+k_assemble)",
                 "pairs_evaluated_per_launch": n_eval,
                 "pairs_full_fit": n_full, "pairs_short_fit": n_short,
-                "pairs_narrow": n_narrow, "pairs_exact_zero_skipped": n_zero,
+                "pairs_narrow": n_narrow, "pairs_narrow3": n_narrow3,
+                "pairs_exact_zero_skipped": n_zero,
                 "pairs_evaluated_per_s": n_eval / t_p2p,
                 "interactions_per_s": interactions / t_p2p,
                 "flops_per_pair": {"full fit": FLOPS_PER_PAIR, "short fit": FLOPS_PER_PAIR_SHORT,
-                                   "narrow": FLOPS_PER_PAIR_NARROW},
+                                   "narrow": FLOPS_PER_PAIR_NARROW,
+                                   "narrow3": FLOPS_PER_PAIR_NARROW3},
                 "fma_pipe_frac": lane_ops / t_p2p / (SMS * FP32_LANES * 2.070e9),
                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max SM clock; "
                              "achieved counts evaluated pairs only (a pair whose exp2 "

@@ -178,8 +178,8 @@ __device__ __forceinline__ PairRange block_range(const GeomView& G, int pa, int 
 // scaled coordinates, B = (gx0, gx1, gy0, gy1). Returns the two terms in the
 // units of PairF32::far (K1(z) (D'.g) / (z' sqrt(log2 e))) added to acc.
 // NC = 7 evaluates the fit of P1 for every z > 2, NC = 4 the short fit,
-// valid for z >= 9.5 (both within 1.5e-7 relative), NC = NARROW the
-// expansion about the source particle's 1/z' (two MUFU operations a pair
+// valid for z >= 9.5 (both within 1.5e-7 relative), NC = NARROW or NARROW3
+// the expansion about the source particle's 1/z' (two MUFU operations a pair
 // instead of three).
 //
 // Two source-particle classes, decided per block from the bounding-circle
@@ -201,9 +201,12 @@ __device__ __forceinline__ PairRange block_range(const GeomView& G, int pa, int 
 //    a_k = sum_j p_j rc^{j+1/2} binom(j + 1/2, k), cut after k = 4 (the
 //    binomial series of (1 + u)^{j+1/2}; the first term left out is below
 //    0.03 eps^5 = 5e-8 relative). c[0..4] = a_k, c[5] = 1/rc, c[6] = -1.
-//    This replaces the z'^{-1/2} MUFU operation with one FMA.
-constexpr int FIT_LONG = 7, FIT_SHORT = 4, NARROW = 5;
+//    This replaces the z'^{-1/2} MUFU operation with one FMA;
+//  * NARROW3: the same, cut after k = 3 for eps <= EPS_NARROW3 (the first
+//    term left out is below 0.04 eps^4 = 3e-8 relative), c[4] unused.
+constexpr int FIT_LONG = 7, FIT_SHORT = 4, NARROW = 5, NARROW3 = 6;
 constexpr float EPS_NARROW = 0.07f;
+constexpr float EPS_NARROW3 = 0.03f;
 
 __host__ __device__ constexpr float binom_half(int j, int k) {   // binom(j + 1/2, k)
     float b = 1.0f;
@@ -214,7 +217,7 @@ __host__ __device__ constexpr float binom_half(int j, int k) {   // binom(j + 1/
 struct PolyRZ {
     float2 c[FIT_LONG];
     __device__ __forceinline__ PolyRZ(int mode, float rc) {
-        if (mode == NARROW) {
+        if (mode == NARROW || mode == NARROW3) {
             const float sr = sqrtf(rc);
             float pj[FIT_SHORT];
             float pw = sr;
@@ -252,7 +255,7 @@ __device__ __forceinline__ int far_mode(const PairRange& r, float short_gap, flo
     const float lo = 1.0f / (kpf * r.far), hi = 1.0f / (kpf * r.gap);   // range of 1/z'
     if (hi - lo <= EPS_NARROW * (hi + lo)) {
         rc = 0.5f * (hi + lo);
-        return NARROW;
+        return (hi - lo <= EPS_NARROW3 * (hi + lo)) ? NARROW3 : NARROW;
     }
     return FIT_SHORT;
 }
@@ -265,11 +268,12 @@ __device__ __forceinline__ float2 far2(float2 TX, float2 TY, const float4& A, co
     const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
     const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));   // 1/z'
     const float2 zp = __fmul2_rn(z2, rz);                                 // z'
-    if constexpr (NC == NARROW) {
+    if constexpr (NC == NARROW || NC == NARROW3) {
         const float2 u = __ffma2_rn(rz, P.c[5], P.c[6]);                  // rz/rc - 1
-        float2 q = P.c[4];
+        constexpr int top = (NC == NARROW) ? 4 : 3;
+        float2 q = P.c[top];
 #pragma unroll
-        for (int k = 3; k >= 0; --k) q = __ffma2_rn(q, u, P.c[k]);       // rz^{1/2} P1(rz)
+        for (int k = top - 1; k >= 0; --k) q = __ffma2_rn(q, u, P.c[k]); // rz^{1/2} P1(rz)
         const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
         const float2 dot = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
         return __ffma2_rn(__fmul2_rn(e, q), __fmul2_rn(rz, dot), acc);
@@ -440,7 +444,7 @@ __device__ __forceinline__ void far_tile(const float4* srcA, const float4* srcB,
 }
 
 template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
+__global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
                                                      int ppc, float kscale, double skip_gap,
                                                      bool own_by_block,
                                                      double* __restrict__ partial) {
@@ -509,7 +513,8 @@ __global__ void __launch_bounds__(F32_TPB, 10) k_p2p_f32(GeomView G, const doubl
             __syncthreads();
             float r0 = 0.0f, r1 = 0.0f;
             if (!T0.close && !T1.close && !skip0 && !skip1) {
-                if (mode == NARROW) far_tile<NARROW>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                if (mode == NARROW3) far_tile<NARROW3>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                else if (mode == NARROW) far_tile<NARROW>(srcA, srcB, npair, T0, T1, P, r0, r1);
                 else if (mode == FIT_SHORT) far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
                 else far_tile<FIT_LONG>(srcA, srcB, npair, T0, T1, P, r0, r1);
             } else {
@@ -662,7 +667,8 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
                 __syncthreads();
                 float r0 = 0.0f, r1 = 0.0f;
                 if (!T0.close) {
-                    if (mode == NARROW) far_tile<NARROW>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                    if (mode == NARROW3) far_tile<NARROW3>(srcA, srcB, npair, T0, T1, P, r0, r1);
+                else if (mode == NARROW) far_tile<NARROW>(srcA, srcB, npair, T0, T1, P, r0, r1);
                     else if (mode == FIT_SHORT)
                         far_tile<FIT_SHORT>(srcA, srcB, npair, T0, T1, P, r0, r1);
                     else far_tile<FIT_LONG>(srcA, srcB, npair, T0, T1, P, r0, r1);

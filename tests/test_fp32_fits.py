@@ -3,9 +3,9 @@ exponentially scaled Bessel function (an independent implementation):
 
 * the K1/K0 fits the packed FP32 loops read from bessel_tables.h, in FP32
   Horner order, over the ranges the kernels use them on;
-* the narrow expansion of rz^{1/2} P1(rz) about the source particle's 1/z'
-  (binomial series of (1 + u)^{j+1/2}, cut after u^4) for every range the
-  kernel admits (relative width up to 0.07);
+* the narrow expansions of rz^{1/2} P1(rz) about the source particle's 1/z'
+  (binomial series of (1 + u)^{j+1/2}, cut after u^4 for a relative width
+  up to 0.07 and after u^3 up to 0.03);
 * the exact-zero skip: at z' >= 128 the largest possible pair value is below
   the smallest normal FP32 number, so ex2.approx.ftz gives +0 for every pair.
 """
@@ -81,17 +81,19 @@ def test_binomial_coefficients_match_series():
         assert np.allclose(series, (1 + u) ** (j + 0.5), rtol=1e-14, atol=0)
 
 
-def test_narrow_expansion_truncation():
-    eps = kernel_constant("EPS_NARROW")
+@pytest.mark.parametrize("name,degree", [("EPS_NARROW", 4), ("EPS_NARROW3", 3)])
+def test_narrow_expansion_truncation(name, degree):
+    eps = kernel_constant(name)
     assert 0.0 < eps <= 0.07
     p = table("YK_P1_F32_RZ")[7:].astype(np.float64)
     zshort = kernel_constant("Z_SHORT")
     worst_trunc = worst_total = 0.0
     for rc in np.geomspace(1.0 / (128 * (1 + eps)), 1.0 / (zshort * LOG2E * (1 + eps)), 300):
-        a = [sum(p[j] * rc ** (j + 0.5) * binom_half(j, k) for j in range(4)) for k in range(5)]
+        a = [sum(p[j] * rc ** (j + 0.5) * binom_half(j, k) for j in range(4))
+             for k in range(degree + 1)]
         rz = np.linspace(rc * (1 - eps), rc * (1 + eps), 200)
         u = rz / rc - 1
-        q = sum(a[k] * u ** k for k in range(5))
+        q = sum(a[k] * u ** k for k in range(degree + 1))
         fit = np.sqrt(rz) * np.polyval(p[::-1], rz)
         worst_trunc = max(worst_trunc, np.abs(q / fit - 1).max())
         worst_total = max(worst_total, np.abs(q / (np.sqrt(rz) * p_nu(1, rz)) - 1).max())
