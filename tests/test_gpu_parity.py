@@ -699,6 +699,51 @@ def test_serving_alone_and_in_mix(yk):
 
 
 # --------------------------------------------------------------------------
+# FP32 far field, one source particle at a time: every evaluation mode of
+# the FP32 kernels (close pairs, the full and the short K1 fit, the narrow
+# expansions of degree 4 and 3, the exact-zero skip) against the oracle.
+# The density is zero on the target disk, so its rows hold the far field of
+# the source disk alone, which in a full system would be hidden under the
+# near field by many orders of magnitude. The tolerance allows for FP32
+# rounding of the scaled positions (about 1.2e-7 z' in the exponent).
+# --------------------------------------------------------------------------
+
+LOG2E = 1.4426950408889634
+
+
+@pytest.mark.parametrize("rho,D,mode", [
+    (1.0, 3.0, "close"), (1.0, 8.0, "full fit"), (1.0, 20.0, "short fit"),
+    (1.0, 40.0, "narrow"), (1.0, 80.0, "narrow3"), (1.0, 95.0, "zero"),
+    (4.0, 30.0, "full fit"), (4.0, 50.0, "narrow"), (4.0, 80.0, "narrow3"),
+    (0.25, 12.0, "short fit"), (0.25, 30.0, "zero")])
+def test_far_field_modes_one_source(yk, ctx, rho, D, mode):
+    a = 0.7
+    parts = np.array([[0, 0.0, 0.0, 0.3, 1.0, 1.0],
+                      [0, D * np.cos(a), D * np.sin(a), 1.1, 1.0, 1.0]])
+    wl = W.Workload("two_disks", parts, rho=rho, n_panels=16, n_gl=16, qbx_order=10)
+    g = yk.Geometry(ctx, parts, _params(yk, wl))
+    o = yo.Oracle(parts, 16, 16, rho, yo.QBXParams(order=10))
+    rng = np.random.default_rng(int(D * 10 + rho * 100))
+    sig = np.zeros(g.n)
+    sig[256:] = rng.standard_normal(256)
+    rows = np.arange(256)
+    y32 = g.yk_matvec(sig, yk.YK_MIXED)[rows]
+    y64 = g.yk_matvec(sig, yk.YK_FP64)[rows]
+    ref = o.apply_rows(sig, rows)
+    assert np.abs(y64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    gap = D - 2.0
+    if mode == "zero":
+        # every pair's exp2(-z') flushes to zero in FP32: exactly nothing
+        assert gap * LOG2E / rho >= 128
+        assert np.all(y32 == 0.0)
+        assert np.abs(ref).max() < 1e-37
+        return
+    zmax = (D + 2.0) * LOG2E / rho
+    tol = 5e-7 + 1.5e-7 * zmax
+    assert np.abs(y32 - ref).max() <= tol * np.abs(ref).max(), (mode, tol)
+
+
+# --------------------------------------------------------------------------
 # full size (512 disks, N = 131072): sampled rows and properties
 # --------------------------------------------------------------------------
 
