@@ -9,7 +9,10 @@ Tolerances (relative 2-norm unless stated):
     discrete operator is about 100), and forces/torques (max-norm relative
     to max |F|): 1e-9;
   * normal derivative: its rows cancel (entries ~10x the result), so the
-    difference is bounded by 1e-12 |G| |sigma| and 1e-11 relative.
+    difference is bounded by 1e-12 |G| |sigma| and 1e-11 relative;
+  * the FP32 far field of one distant source disk, row by row: 1e-6 +
+    3e-7 z'_max of the sum of absolute pair contributions (the FP32 error
+    of the exponent grows with the scaled distance z').
 Small systems span several 256-target tiles with a ragged tail; the
 512-disk system is checked on sampled rows and through properties that
 hold at any size (the oracle's residual of the GPU density).
@@ -704,8 +707,11 @@ def test_serving_alone_and_in_mix(yk):
 # expansions of degree 4 and 3, the exact-zero skip) against the oracle.
 # The density is zero on the target disk, so its rows hold the far field of
 # the source disk alone, which in a full system would be hidden under the
-# near field by many orders of magnitude. The tolerance allows for FP32
-# rounding of the scaled positions (about 1.2e-7 z' in the exponent).
+# near field by many orders of magnitude. Each pair carries an FP32 error
+# of about 2e-7 z' relative (the rounding of the scaled positions and of
+# 1/z' enters the exponent), so the bound is taken against the sum of the
+# absolute pair contributions, |A| |sigma|, which a random density makes
+# far larger than the cancelling sum itself.
 # --------------------------------------------------------------------------
 
 LOG2E = 1.4426950408889634
@@ -723,24 +729,27 @@ def test_far_field_modes_one_source(yk, ctx, rho, D, mode):
     wl = W.Workload("two_disks", parts, rho=rho, n_panels=16, n_gl=16, qbx_order=10)
     g = yk.Geometry(ctx, parts, _params(yk, wl))
     o = yo.Oracle(parts, 16, 16, rho, yo.QBXParams(order=10))
+    A = o.dense()
     rng = np.random.default_rng(int(D * 10 + rho * 100))
     sig = np.zeros(g.n)
     sig[256:] = rng.standard_normal(256)
     rows = np.arange(256)
     y32 = g.yk_matvec(sig, yk.YK_MIXED)[rows]
     y64 = g.yk_matvec(sig, yk.YK_FP64)[rows]
-    ref = o.apply_rows(sig, rows)
-    assert np.abs(y64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    ref = A[rows] @ sig
+    absum = np.abs(A[rows]) @ np.abs(sig)
+    assert np.all(np.abs(y64 - ref) <= 1e-13 * absum)
     gap = D - 2.0
     if mode == "zero":
         # every pair's exp2(-z') flushes to zero in FP32: exactly nothing
         assert gap * LOG2E / rho >= 128
         assert np.all(y32 == 0.0)
-        assert np.abs(ref).max() < 1e-37
+        assert absum.max() < 1e-37
         return
     zmax = (D + 2.0) * LOG2E / rho
-    tol = 5e-7 + 1.5e-7 * zmax
-    assert np.abs(y32 - ref).max() <= tol * np.abs(ref).max(), (mode, tol)
+    tol = 1e-6 + 3e-7 * zmax
+    err = np.abs(y32 - ref) / absum
+    assert err.max() <= tol, (mode, err.max(), tol)
 
 
 # --------------------------------------------------------------------------
