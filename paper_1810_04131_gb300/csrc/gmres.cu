@@ -162,6 +162,7 @@ int alloc_workspace(yk_geom* g) {
     w.nchunk = ceil_div(g->np, ppc);
     w.dot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(296, (n + 2047) / 2048));
     YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n, st));
+    YK_TRY(dev_alloc((void**)&w.src4, sizeof(float4) * 2 * (size_t)g->np * ((g->npp + 1) / 2), st));
     YK_TRY(dev_alloc((void**)&w.V, sizeof(double) * (m + 1) * n, st));
     YK_TRY(dev_alloc((void**)&w.H, sizeof(double) * (m + 1) * m, st));
     YK_TRY(dev_alloc((void**)&w.gvec, sizeof(double) * (m + 1), st));
@@ -180,6 +181,7 @@ void free_workspace(yk_geom* g) {
     Workspace& w = g->ws;
     cudaStream_t st = g->ctx->stream;
     dev_free(w.partial, st);
+    dev_free(w.src4, st);
     dev_free(w.V, st);
     dev_free(w.H, st);
     dev_free(w.gvec, st);

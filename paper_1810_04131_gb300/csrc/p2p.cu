@@ -69,6 +69,14 @@ static int self_blocks(yk_geom* g, const double* sigma, double* extra, bool grad
     return YK_OK;
 }
 
+// The FP32 source records of sigma (k_src_pairs), before any FP32 far-field kernel.
+static int stage_sources(yk_geom* g, const double* sigma) {
+    const int64_t npairs = (int64_t)g->np * ((g->npp + 1) / 2);
+    YK_LAUNCH(k_src_pairs, (unsigned)((npairs + 255) / 256), 256, 0, g->ctx->stream, g->view(),
+              sigma, (float)(LOG2E / g->prm.rho), g->ws.src4);
+    return YK_OK;
+}
+
 // Cut-off neighbour lists (CSR), built on first use and after the particles move.
 static int neighbours(yk_geom* g) {
     if (g->nbr_valid) return YK_OK;
@@ -106,11 +114,12 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
     double* extra = nullptr;
     int used = 1;
     if (prec == Prec::F32) {
+        YK_TRY(stage_sources(g, sigma));
         if (grad)
-            YK_LAUNCH(k_p2p_f32_grad_cut<false>, g->np, F32_TPB, 0, st, G, sigma, 0.0, g->nbr_off,
-                      g->nbr, g->ws.partial);
+            YK_LAUNCH(k_p2p_f32_grad_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, 0.0,
+                      g->nbr_off, g->nbr, g->ws.partial);
         else
-            YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, 0.0,
+            YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,
                       g->use_self, g->nbr_off, g->nbr, g->ws.partial);
         if (!grad && g->use_self) {
             extra = g->ws.vec[5];
@@ -126,12 +135,13 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
         YK_TRY(self_blocks(g, sigma, extra, grad));
         if (prec == Prec::SPLIT) {
             const double gap = grad ? g->split_gap_grad : g->split_gap;
+            YK_TRY(stage_sources(g, sigma));
             if (grad)
-                YK_LAUNCH(k_p2p_f32_grad_cut<true>, g->np, F32_TPB, 0, st, G, sigma, gap,
+                YK_LAUNCH(k_p2p_f32_grad_cut<true>, g->np, F32_TPB, 0, st, G, g->ws.src4, gap,
                           g->nbr_off, g->nbr, g->ws.partial);
             else
-                YK_LAUNCH(k_p2p_f32_cut<true>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, gap,
-                          false, g->nbr_off, g->nbr, g->ws.partial);
+                YK_LAUNCH(k_p2p_f32_cut<true>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks,
+                          gap, false, g->nbr_off, g->nbr, g->ws.partial);
         } else {
             used = 0;
         }
@@ -158,7 +168,8 @@ static int fmm_apply(yk_geom* g, const double* sigma, double* y) {
     YK_TRY(fmm_far(g, sigma, extra));
     YK_TRY(self_blocks_f32(g, sigma, extra, true));
     const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
-    YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, sigma, (float)ks, 0.0,
+    YK_TRY(stage_sources(g, sigma));
+    YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,
               g->use_self, g->fmm.near_off, g->fmm.near, g->ws.partial);
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, 1, g->ws.partial, extra, G.cval,
               sigma, y);
@@ -283,7 +294,8 @@ static int matvec_body(yk_geom* g, const double* sigma, double* y, Prec prec) {
     double* extra = nullptr;
     int used_chunks = nchunk;
     if (prec == Prec::F32) {
-        YK_LAUNCH(k_p2p_f32<false>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks, 0.0,
+        YK_TRY(stage_sources(g, sigma));
+        YK_LAUNCH(k_p2p_f32<false>, grid, F32_TPB, 0, st, G, g->ws.src4, ppc, (float)ks, 0.0,
                   g->use_self, g->ws.partial);
         if (g->use_self) {
             extra = g->ws.vec[5];
@@ -298,7 +310,8 @@ static int matvec_body(yk_geom* g, const double* sigma, double* y, Prec prec) {
         YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
         YK_TRY(self_blocks(g, sigma, extra, false));
         if (prec == Prec::SPLIT) {
-            YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, sigma, ppc, (float)ks,
+            YK_TRY(stage_sources(g, sigma));
+            YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, g->ws.src4, ppc, (float)ks,
                       g->split_gap, false, g->ws.partial);
         } else {
             used_chunks = 0;
@@ -329,8 +342,9 @@ static int normal_derivative_body(yk_geom* g, const double* sigma, double* un, P
     YK_TRY(self_blocks(g, sigma, extra, true));
     int used_chunks = 0;
     if (prec != Prec::F64) {
-        YK_LAUNCH(k_p2p_f32_grad<true>, grid, F32_TPB, 0, st, G, sigma, ppc, g->split_gap_grad,
-                  g->ws.partial);
+        YK_TRY(stage_sources(g, sigma));
+        YK_LAUNCH(k_p2p_f32_grad<true>, grid, F32_TPB, 0, st, G, g->ws.src4, ppc,
+                  g->split_gap_grad, g->ws.partial);
         used_chunks = nchunk;
     }
     YK_LAUNCH(k_tiles_f64<true>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles, extra);

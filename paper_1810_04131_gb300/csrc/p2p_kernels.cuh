@@ -13,7 +13,9 @@
 // Sources that are the target's own near panels are skipped: the QBX rows
 // replace them.
 //
-// Three evaluators share the work:
+// The kernels:
+//  * k_src_pairs: the pair-packed FP32 source records of the density, once
+//    per operator application (read by every block of the FP32 kernels).
 //  * k_p2p_f32 / k_p2p_f32_grad: FP32 evaluation with FP64 accumulation per
 //    source particle; blockIdx.x = 256 consecutive targets (two per thread),
 //    blockIdx.y = a chunk of source particles, partial sums per chunk.
@@ -356,34 +358,53 @@ __device__ __forceinline__ float2 grad2(float2 TX, float2 TY, float2 NX, float2 
     return __ffma2_rn(__fmul2_rn(E, rz), br, acc);
 }
 
-// Stage sources [jb, jb + cnt) of the particle at `base` in pair-packed form
-// (scaled coordinates negated, g = w sigma nu); pads with a far weightless source.
-__device__ __forceinline__ void stage_pairs(const GeomView& G, const double* __restrict__ sigma,
-                                            int64_t base, int jb, int cnt, float kpf,
-                                            float4* srcA, float4* srcB) {
-    const int npair = (cnt + 1) >> 1;
-    for (int m = threadIdx.x; m < npair; m += blockDim.x) {
-        float xs[2], ys[2], gx[2], gy[2];
+// Pair-packed FP32 source records of one density, written once per operator
+// application and read by every block of the FP32 far-field kernels: for
+// source particle s and pair m (its nodes 2m, 2m + 1),
+//   rec[2 (s hp + m)]     = A = (-X0, -X1, -Y0, -Y1)   (scaled offsets from
+//                                                      the particle's centre)
+//   rec[2 (s hp + m) + 1] = B = (g0x, g1x, g0y, g1y),  g = w sigma nu,
+// hp = ceil(npp / 2); a particle with an odd node count pads its last pair
+// with a far, weightless source.
+__global__ void k_src_pairs(GeomView G, const double* __restrict__ sigma, float kpf,
+                            float4* __restrict__ rec) {
+    const int hp = (G.npp + 1) >> 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)G.np * hp) return;
+    const int s = (int)(idx / hp), m = (int)(idx % hp);
+    float xs[2], ys[2], gx[2], gy[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = 2 * m + h;
-            if (q < cnt) {
-                const int64_t j = base + jb + q;
-                const float2 x = G.xi[j];
-                const double ws = G.w[j] * sigma[j];
-                xs[h] = -kpf * x.x;
-                ys[h] = -kpf * x.y;
-                gx[h] = (float)(ws * G.nx[j]);
-                gy[h] = (float)(ws * G.ny[j]);
-            } else {
-                xs[h] = 1.0e6f;
-                ys[h] = 0.0f;
-                gx[h] = 0.0f;
-                gy[h] = 0.0f;
-            }
+    for (int h = 0; h < 2; ++h) {
+        const int q = 2 * m + h;
+        if (q < G.npp) {
+            const int64_t j = (int64_t)s * G.npp + q;
+            const float2 x = G.xi[j];
+            const double ws = G.w[j] * sigma[j];
+            xs[h] = -kpf * x.x;
+            ys[h] = -kpf * x.y;
+            gx[h] = (float)(ws * G.nx[j]);
+            gy[h] = (float)(ws * G.ny[j]);
+        } else {
+            xs[h] = 1.0e6f;
+            ys[h] = 0.0f;
+            gx[h] = 0.0f;
+            gy[h] = 0.0f;
         }
-        srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
-        srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
+    }
+    rec[2 * idx] = make_float4(xs[0], xs[1], ys[0], ys[1]);
+    rec[2 * idx + 1] = make_float4(gx[0], gx[1], gy[0], gy[1]);
+}
+
+// Stage the source pairs of nodes [jb, jb + cnt) of particle s into shared
+// memory (jb even): plain 16-byte loads of the pre-packed records.
+__device__ __forceinline__ void stage_rec(const float4* __restrict__ rec, int npp, int s, int jb,
+                                          int cnt, float4* srcA, float4* srcB) {
+    const int hp = (npp + 1) >> 1;
+    const int npair = (cnt + 1) >> 1;
+    const float4* r = rec + 2 * ((int64_t)s * hp + (jb >> 1));
+    for (int m = threadIdx.x; m < npair; m += blockDim.x) {
+        srcA[m] = r[2 * m];
+        srcB[m] = r[2 * m + 1];
     }
 }
 
@@ -444,7 +465,7 @@ __device__ __forceinline__ void far_tile(const float4* srcA, const float4* srcB,
 }
 
 template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const double* __restrict__ sigma,
+__global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const float4* __restrict__ rec,
                                                      int ppc, float kscale, double skip_gap,
                                                      bool own_by_block,
                                                      double* __restrict__ partial) {
@@ -470,7 +491,6 @@ __global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const double
         float rc;
         const int mode = far_mode(rg, short_gap, kpf, rc);
         const PolyRZ P(mode, rc);
-        const int64_t base = (int64_t)s * G.npp;
         TargetF32 T0, T1;
         target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
         target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
@@ -487,29 +507,7 @@ __global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const double
             const int cnt = min(STILE, G.npp - jb);
             const int npair = (cnt + 1) >> 1;
             __syncthreads();
-            for (int m = threadIdx.x; m < npair; m += F32_TPB) {
-                float xs[2], ys[2], gx[2], gy[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = 2 * m + h;
-                    if (q < cnt) {
-                        const int64_t j = base + jb + q;
-                        const float2 x = G.xi[j];
-                        const double ws = G.w[j] * sigma[j];
-                        xs[h] = -kpf * x.x;
-                        ys[h] = -kpf * x.y;
-                        gx[h] = (float)(ws * G.nx[j]);
-                        gy[h] = (float)(ws * G.ny[j]);
-                    } else {       // padding: a far, weightless source
-                        xs[h] = 1.0e6f;
-                        ys[h] = 0.0f;
-                        gx[h] = 0.0f;
-                        gy[h] = 0.0f;
-                    }
-                }
-                srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
-                srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
-            }
+            stage_rec(rec, G.npp, s, jb, cnt, srcA, srcB);
             __syncthreads();
             float r0 = 0.0f, r1 = 0.0f;
             if (!T0.close && !T1.close && !skip0 && !skip1) {
@@ -539,7 +537,7 @@ __global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const double
 // pairs (same staging and masking as k_p2p_f32).
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
-                                                          const double* __restrict__ sigma,
+                                                          const float4* __restrict__ rec,
                                                           int ppc, double skip_gap,
                                                           double* __restrict__ partial) {
     __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
@@ -566,7 +564,6 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
         if (bg >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
         const PolyRZ2 P(bg >= short_gap);
         const bool short_fit = bg >= short_gap;
-        const int64_t base = (int64_t)s * G.npp;
         TargetF32 T0, T1;
         target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
         target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
@@ -576,7 +573,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
         for (int jb = 0; jb < G.npp; jb += STILE) {
             const int cnt = min(STILE, G.npp - jb);
             __syncthreads();
-            stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
+            stage_rec(rec, G.npp, s, jb, cnt, srcA, srcB);
             __syncthreads();
             float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
             if (short_fit)
@@ -604,7 +601,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
 // evaluation and masking as the chunked kernels.
 // ---------------------------------------------------------------------------
 template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const double* __restrict__ sigma,
+__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const float4* __restrict__ rec,
                                                          float kscale, double skip_gap,
                                                          bool own_by_block,
                                                          const int* __restrict__ nbr_off,
@@ -636,34 +633,11 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
             target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
             // uniform: one target particle per block
             if ((MASK && T0.skip) || (own_by_block && T0.own)) continue;
-            const int64_t base = (int64_t)s * G.npp;
-            for (int jb = 0; jb < G.npp; jb += STILE) {
+                for (int jb = 0; jb < G.npp; jb += STILE) {
                 const int cnt = min(STILE, G.npp - jb);
                 const int npair = (cnt + 1) >> 1;
                 __syncthreads();
-                for (int m = threadIdx.x; m < npair; m += F32_TPB) {
-                    float xs[2], ys[2], gx[2], gy[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int q = 2 * m + h;
-                        if (q < cnt) {
-                            const int64_t j = base + jb + q;
-                            const float2 x = G.xi[j];
-                            const double ws = G.w[j] * sigma[j];
-                            xs[h] = -kpf * x.x;
-                            ys[h] = -kpf * x.y;
-                            gx[h] = (float)(ws * G.nx[j]);
-                            gy[h] = (float)(ws * G.ny[j]);
-                        } else {
-                            xs[h] = 1.0e6f;
-                            ys[h] = 0.0f;
-                            gx[h] = 0.0f;
-                            gy[h] = 0.0f;
-                        }
-                    }
-                    srcA[m] = make_float4(xs[0], xs[1], ys[0], ys[1]);
-                    srcB[m] = make_float4(gx[0], gx[1], gy[0], gy[1]);
-                }
+                stage_rec(rec, G.npp, s, jb, cnt, srcA, srcB);
                 __syncthreads();
                 float r0 = 0.0f, r1 = 0.0f;
                 if (!T0.close) {
@@ -705,7 +679,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const doubl
 
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
-                                                              const double* __restrict__ sigma,
+                                                              const float4* __restrict__ rec,
                                                               double skip_gap,
                                                               const int* __restrict__ nbr_off,
                                                               const int* __restrict__ nbr,
@@ -738,11 +712,10 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
             target_setup(T0, G, pt, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
             target_setup(T1, G, pt, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
             if (MASK && T0.skip) continue;   // uniform: one target particle per block
-            const int64_t base = (int64_t)s * G.npp;
-            for (int jb = 0; jb < G.npp; jb += STILE) {
+                for (int jb = 0; jb < G.npp; jb += STILE) {
                 const int cnt = min(STILE, G.npp - jb);
                 __syncthreads();
-                stage_pairs(G, sigma, base, jb, cnt, kpf, srcA, srcB);
+                stage_rec(rec, G.npp, s, jb, cnt, srcA, srcB);
                 __syncthreads();
                 float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
                 if (short_fit)

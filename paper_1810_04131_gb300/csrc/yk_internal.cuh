@@ -41,6 +41,7 @@ void note_launch();
 struct Workspace {
     double* partial = nullptr;   // [nchunk][n]
     int nchunk = 0;
+    float4* src4 = nullptr;      // pair-packed FP32 source records [np][ceil(npp/2)][2]
     double* V = nullptr;         // Krylov basis [(m+1)][n]
     double* H = nullptr;         // Hessenberg (m+1) x m, column-major
     double* gvec = nullptr;      // rotated rhs, m+1
