@@ -74,17 +74,22 @@ __global__ void k_p2m(GeomView G, const double* __restrict__ sigma, double2* __r
 
 // M2L from the band neighbours of each target particle Q into its local
 // coefficients L[Q][m], m = 0..EXP_ORDER (written; zero without neighbours).
-// One warp per target particle; lane t handles m = t and m = t + 32.
-__global__ void __launch_bounds__(128) k_band_m2l(GeomView G, const double2* __restrict__ M,
-                                                  const int* __restrict__ off,
-                                                  const int* __restrict__ nbr,
-                                                  double2* __restrict__ Lout) {
-    __shared__ double Ksh[4][2 * EXP_ORDER + 1];       // K_k(|D|/rho), k = 0..2p
-    __shared__ double2 Esh[4][3 * EXP_ORDER + 1];      // e^{i k psi}, k = -p..2p
-    __shared__ double2 Msh[4][EXP_N];
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// One block of four warps per target particle: warp w takes neighbours
+// w, w + 4, ... of the list, lane t handles m = t and m = t + 32, and the
+// four partial expansions are summed in a fixed order at the end.
+constexpr int M2L_WARPS = 4;
+__global__ void __launch_bounds__(32 * M2L_WARPS) k_band_m2l(GeomView G,
+                                                             const double2* __restrict__ M,
+                                                             const int* __restrict__ off,
+                                                             const int* __restrict__ nbr,
+                                                             double2* __restrict__ Lout) {
+    __shared__ double Ksh[M2L_WARPS][2 * EXP_ORDER + 1];    // K_k(|D|/rho), k = 0..2p
+    __shared__ double2 Esh[M2L_WARPS][3 * EXP_ORDER + 1];   // e^{i k psi}, k = -p..2p
+    __shared__ double2 Msh[M2L_WARPS][EXP_N];
+    __shared__ double2 Lsh[M2L_WARPS][EXP_N];
+    const int q = blockIdx.x;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (q >= G.np) return;                                // warp-uniform
+    if (q >= G.np) return;                                // block-uniform
     double* Kr = Ksh[wib];
     double2* eps = Esh[wib];
     double2* Ms = Msh[wib];
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(128) k_band_m2l(GeomView G, const double2* __r
     const double rho = G.rho;
     const d4 cq = G.part[q];
     double lr0 = 0.0, li0 = 0.0, lr1 = 0.0, li1 = 0.0;   // m = lane, lane + 32
-    for (int k = k0; k < k1; ++k) {
+    for (int k = k0 + wib; k < k1; k += M2L_WARPS) {
         const int p = nbr[k];
         const d4 cp = G.part[p];
         const double Dx = cq.x - cp.x, Dy = cq.y - cp.y;
@@ -131,8 +136,18 @@ __global__ void __launch_bounds__(128) k_band_m2l(GeomView G, const double2* __r
             else lr1 += sg * lr, li1 += sg * li;
         }
     }
-    Lout[(int64_t)q * EXP_N + lane] = make_double2(lr0, li0);
-    if (lane + 32 <= EXP_ORDER) Lout[(int64_t)q * EXP_N + lane + 32] = make_double2(lr1, li1);
+    Lsh[wib][lane] = make_double2(lr0, li0);
+    if (lane + 32 < EXP_N) Lsh[wib][lane + 32] = make_double2(lr1, li1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < EXP_N; t += blockDim.x) {
+        double2 a = Lsh[0][t];
+#pragma unroll
+        for (int w = 1; w < M2L_WARPS; ++w) {
+            a.x += Lsh[w][t].x;
+            a.y += Lsh[w][t].y;
+        }
+        Lout[(int64_t)q * EXP_N + t] = a;
+    }
 }
 
 // L2P: value or normal derivative of each node's particle local expansion,
@@ -271,8 +286,8 @@ int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad) {
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
     YK_LAUNCH(k_p2m, ceil_div((int64_t)g->np * 32, 128), 128, 0, st, G, sigma, g->d_mpole);
-    YK_LAUNCH(k_band_m2l, ceil_div((int64_t)g->np * 32, 128), 128, 0, st, G, g->d_mpole,
-              g->bands[kind].off, g->bands[kind].idx, g->d_local);
+    YK_LAUNCH(k_band_m2l, g->np, 32 * M2L_WARPS, 0, st, G, g->d_mpole, g->bands[kind].off,
+              g->bands[kind].idx, g->d_local);
     if (grad)
         YK_LAUNCH(k_band_l2p<true>, ceil_div(g->n, 128), 128, 0, st, G, g->d_local,
                   g->bands[kind].off, out);

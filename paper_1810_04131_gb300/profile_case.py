@@ -1,11 +1,13 @@
 """Run one kernel case of the yk library on a named workload, for profilers.
 
     python -m paper_1810_04131_gb300.profile_case --case p2p_f32 --workload disks512 --reps 2
-        [--farfield dense|cutoff|fmm]
+        [--farfield dense|cutoff|fmm] [--particles K]
 
 Cases: p2p_f32 (mixed matvec: FP32 far field + near rows), p2p_f64 (FP64
 matvec), grad (precision-split normal derivative), qbx (geometry + QBX rows), solve (one mixed solve +
 forces). The geometry is built first; then the case runs --reps times.
+--particles K keeps the first K particles of the workload (a smaller case of
+the same kernels, for captures that replay each launch many times).
 """
 import argparse
 import os
@@ -22,11 +24,14 @@ def main():
     ap.add_argument("--workload", default="disks512")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--farfield", default="dense", choices=["dense", "cutoff", "fmm"])
+    ap.add_argument("--particles", type=int, default=0)
     a = ap.parse_args()
     import torch
     from paper_1810_04131_gb300 import workloads as W
     from paper_1810_04131_gb300 import yk
     wl = W.WORKLOADS[a.workload]()
+    if a.particles > 0:
+        wl.particles = wl.particles[:a.particles]
     ctx = yk.Context(0, torch.cuda.current_stream().cuda_stream)
     prm = yk.params_for(wl, farfield={"dense": yk.YK_FARFIELD_DENSE,
                                       "cutoff": yk.YK_FARFIELD_CUTOFF,
