@@ -113,3 +113,23 @@ def test_exact_zero_threshold():
     rho = 1.0
     gap = zp0 * rho / LOG2E
     assert gap * LOG2E / rho >= zp0 - 1e-9
+
+
+def test_bench_pair_classes_partition_the_interactions():
+    """The bench's count of evaluated pairs by kernel mode (its roofline
+    numerator) covers every far interaction between different particles
+    exactly once, and uses the kernel's own thresholds."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1810_04131_gb300 import workloads as W
+    assert bench.Z_SHORT == kernel_constant("Z_SHORT")
+    assert bench.ZP_ZERO == kernel_constant("ZP_ZERO")
+    assert np.isclose(bench.EPS_NARROW, kernel_constant("EPS_NARROW"))
+    assert np.isclose(bench.EPS_NARROW3, kernel_constant("EPS_NARROW3"))
+    wl = W.disks512()
+    n, npp = wl.n_nodes, 256
+    counts = bench.p2p_pair_classes(wl.particles, wl.rho, npp, n)
+    assert sum(counts) == n * n - wl.n_particles * npp * npp
+    full, short, narrow, narrow3, zero = counts
+    assert min(counts) > 0 and zero > 0.5 * sum(counts)
