@@ -4,12 +4,14 @@ the 512-ellipse system (semi-axes 1.0 x 0.5, 200 x 200 box, gap >= 0.2,
 {0.25, 1, 4}.
 
 For each rho: one FP64 solve to a 1e-12 residual (the reference), one mixed
-solve to 1e-10, and the relative errors of the mixed density, off-surface
+solve to --mixed-tol (default 1e-11: forces and torques carry about 60 times
+the density error at rho = 4, so this keeps them a factor of ten inside the
+1e-9 bar), and the relative errors of the mixed density, off-surface
 potential (200 targets at least 0.25 from every boundary), forces and
 torques against it. The FP64 oracle recomputes the residual of both
 densities at sampled rows, an independent check at full size.
 
-    python -m paper_1810_04131_gb300.accuracy_report [--rhos 0.25 1 4] [--json out.json]
+    python -m paper_1810_04131_gb300.accuracy_report [--rhos 0.25 1 4] [--mixed-tol 1e-11] [--json out.json]
 """
 import argparse
 import json
@@ -27,6 +29,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--rhos", type=float, nargs="+", default=[0.25, 1.0, 4.0])
     ap.add_argument("--oracle-rows", type=int, default=24)
+    ap.add_argument("--mixed-tol", type=float, default=1e-11)
     ap.add_argument("--json", default=None)
     a = ap.parse_args()
     import torch
@@ -41,7 +44,7 @@ def main():
         wl = W.ellipses512(rho)
         res = {"rho": rho}
         out = {}
-        for name, prec, tol in (("fp64", yk.YK_FP64, 1e-12), ("mixed", yk.YK_MIXED, 1e-10)):
+        for name, prec, tol in (("fp64", yk.YK_FP64, 1e-12), ("mixed", yk.YK_MIXED, a.mixed_tol)):
             g = yk.Geometry(ctx, wl.particles, yk.params_for(wl, precision=prec, gmres_tol=tol,
                                                              max_iter=400))
             f = g.yk_label(yk.YK_LABEL_TANH, 10.0)
