@@ -20,7 +20,12 @@
 //    source particle; blockIdx.x = 256 consecutive targets (two per thread),
 //    blockIdx.y = a chunk of source particles, partial sums per chunk.
 //    With a skip distance they leave out the particle pairs that the FP64
-//    tiles handle (same FP64 predicate in both places).
+//    tiles handle (same FP64 predicate in both places). Per block and source
+//    particle, the range of node-pair distances picks the evaluation: none
+//    (every pair underflows to an exact FP32 zero), the full or the short K1
+//    fit, or (value kernels) an expansion about the particle's 1/z'.
+//  * k_p2p_f32_cut / k_p2p_f32_grad_cut: the same per target particle over
+//    a neighbour list (cut-off and FMM near fields).
 //  * k_tiles_f64<GRAD>: one block per listed particle pair (P, Q), P <= Q,
 //    all in FP64. The pair kernels are symmetric in (i, j) up to the sign of
 //    d (value) or exactly (gradient), so each kernel evaluation feeds both
