@@ -157,6 +157,34 @@ __device__ inline double bessel_i_series(int n, double z) {
 
 // ---- FP32 ------------------------------------------------------------------
 
+// I_0..I_T(x) in FP32 for a fixed top order T (so that I stays in
+// registers): I_T and I_{T-1} from the ascending series (DLMF 10.25.2) as in
+// bessel_i_pair, then the downward recurrence I_{k-1} = I_{k+1} + (2k/x) I_k.
+// For T <= 13 and x >= BESSEL_I_F32_XMIN the series' first term
+// (x/2)^T / T! stays above 1e-30, inside the FP32 normal range.
+constexpr float BESSEL_I_F32_XMIN = 0.06f;
+template <int T>
+__device__ __forceinline__ void bessel_i_down_f(float x, float (&I)[T + 1]) {
+    static_assert(T >= 1 && T <= 13, "order range of the FP32 series");
+    const float h = 0.5f * x, q = h * h;
+    float hn = 1.0f;
+#pragma unroll
+    for (int k = 0; k < T; ++k) hn *= h;
+    float t = hn * (float)c_inv_fact[T];
+    float s1 = t, s2 = (float)T * t;
+    for (int k = 1; k < 100; ++k) {
+        t *= q / ((float)k * (float)(T + k));
+        s1 += t;
+        s2 = fmaf((float)(T + k), t, s2);
+        if (t < 1e-8f * s1) break;
+    }
+    I[T] = s1;
+    I[T - 1] = s2 / h;
+    const float xi2 = 2.0f / x;
+#pragma unroll
+    for (int k = T - 1; k >= 1; --k) I[k - 1] = fmaf((float)k * xi2, I[k], I[k + 1]);
+}
+
 // K1(z) in FP32; rinv_rho2 = t = 2/z supplied by the caller (it has 1/r).
 __device__ __forceinline__ float k1f(float z, float t) {
     if (z > 2.0f) {

@@ -154,12 +154,17 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 
 // P2M about each leaf centre (leaf level slice M). The moments feed only
 // the FP32 inner operator, so the sums run in FP32; I_n comes from the FP64
-// series and recurrence (FP32 would underflow at high orders).
+// series and recurrence (FP32 would underflow at high orders). With a fixed
+// order PF (the default 12) the moments stay in registers and I_n is taken
+// in FP32 (bessel_i_down_f) wherever s/rho >= BESSEL_I_F32_XMIN.
+template <int PF>
 __global__ void __launch_bounds__(128) k_fmm_p2m(GeomView G, const double* __restrict__ sigma,
-                                                 int p, int nb, double x0, double y0, double b,
+                                                 int p_rt, int nb, double x0, double y0, double b,
                                                  const int* __restrict__ leaf_off,
                                                  const int* __restrict__ leaf_part,
                                                  double2* __restrict__ M) {
+    constexpr int NP = PF > 0 ? PF : FMM_PMAX;            // array bound, loop bound if fixed
+    const int p = PF > 0 ? PF : p_rt;
     const int leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (leaf >= nb * nb) return;
@@ -168,9 +173,10 @@ __global__ void __launch_bounds__(128) k_fmm_p2m(GeomView G, const double* __res
     const double cx = x0 + (leaf % nb + 0.5) * b, cy = y0 + (leaf / nb + 0.5) * b;
     const double rho = G.rho, rinv = 1.0 / rho;
     const float rinvf = (float)rinv;
-    float mre[FMM_PMAX + 1], mim[FMM_PMAX + 1];
+    float mre[NP + 1], mim[NP + 1];
     double I[FMM_PMAX + 2];
-    for (int n = 0; n <= p; ++n) mre[n] = mim[n] = 0.0f;
+#pragma unroll
+    for (int n = 0; n <= NP; ++n) mre[n] = mim[n] = 0.0f;
     for (int t = t0; t < t1; ++t) {
         const int P = leaf_part[t];
         for (int l = lane; l < G.npp; l += 32) {
@@ -190,11 +196,20 @@ __global__ void __launch_bounds__(128) k_fmm_p2m(GeomView G, const double* __res
             const float a_s = nx * esx + ny * esy;             // nu . e_s
             const float a_p = -nx * esy + ny * esx;            // nu . e_phi
             const float sinvf = (float)sinv;
-            bessel_i_down(p + 1, s * rinv, I);
+            float If[NP + 2];
+            if (PF > 0 && s * rinv >= (double)BESSEL_I_F32_XMIN) {
+                if constexpr (PF > 0) bessel_i_down_f<PF + 1>((float)(s * rinv), If);
+            } else {
+                bessel_i_down(p + 1, s * rinv, I);
+#pragma unroll
+                for (int n = 0; n <= NP + 1; ++n) If[n] = (n <= p + 1) ? (float)I[n] : 0.0f;
+            }
             float cn = 1.0f, sn = 0.0f;                        // e^{i n phi}
-            float Iprev = (float)I[1], Icur = (float)I[0];     // I_{n-1} (I_1 at n = 0), I_n
-            for (int n = 0; n <= p; ++n) {
-                const float Inext = (float)I[n + 1];
+            float Iprev = If[1], Icur = If[0];                 // I_{n-1} (I_1 at n = 0), I_n
+#pragma unroll
+            for (int n = 0; n <= NP; ++n) {
+                if (PF == 0 && n > p) break;
+                const float Inext = If[n + 1];
                 const float ip = (n == 0) ? Inext : 0.5f * (Iprev + Inext);
                 const float ar = a_s * ip * rinvf;
                 const float ai = -(float)n * a_p * Icur * sinvf;
@@ -208,7 +223,9 @@ __global__ void __launch_bounds__(128) k_fmm_p2m(GeomView G, const double* __res
             }
         }
     }
-    for (int n = 0; n <= p; ++n) {
+#pragma unroll
+    for (int n = 0; n <= NP; ++n) {
+        if (PF == 0 && n > p) break;
         float a = mre[n], c = mim[n];
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -465,12 +482,15 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(int lc, int p, double rho, doub
 
 // L2P: value of the leaf's local expansion at every node (written to out),
 // summed in R (FP32 when every level's coefficients fit its range); I_m
-// from the FP64 series and recurrence.
-template <typename R>
-__global__ void __launch_bounds__(128) k_fmm_l2p(GeomView G, int p, int nb, double x0, double y0,
+// from the FP64 series and recurrence, or, with a fixed order PF and R =
+// float, from the FP32 series wherever r/rho >= BESSEL_I_F32_XMIN.
+template <typename R, int PF>
+__global__ void __launch_bounds__(128) k_fmm_l2p(GeomView G, int p_rt, int nb, double x0, double y0,
                                                  double b, const int* __restrict__ leaf_of,
                                                  const double2* __restrict__ Lleaf,
                                                  double* __restrict__ out) {
+    constexpr int NP = PF > 0 ? PF : FMM_PMAX;
+    const int p = PF > 0 ? PF : p_rt;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= G.n) return;
     const int leaf = leaf_of[i / G.npp];
@@ -482,16 +502,31 @@ __global__ void __launch_bounds__(128) k_fmm_l2p(GeomView G, int p, int nb, doub
         out[i] = L[0].x / (2.0 * PI);
         return;
     }
-    double I[FMM_PMAX + 2];
-    bessel_i_down(p + 1, r / G.rho, I);
+    R Ir[NP + 2];
+    const double x = r / G.rho;
+    if (PF > 0 && sizeof(R) == sizeof(float) && x >= (double)BESSEL_I_F32_XMIN) {
+        if constexpr (PF > 0) {
+            float If[PF + 2];
+            bessel_i_down_f<PF + 1>((float)x, If);
+#pragma unroll
+            for (int n = 0; n <= PF + 1; ++n) Ir[n] = (R)If[n];
+        }
+    } else {
+        double I[FMM_PMAX + 2];
+        bessel_i_down(p + 1, x, I);
+#pragma unroll
+        for (int n = 0; n <= NP + 1; ++n) Ir[n] = (n <= p + 1) ? (R)I[n] : (R)0;
+    }
     const double rinv = 1.0 / r;
     const R erx = (R)(vx * rinv), ery = (R)(vy * rinv);
-    R acc = (R)L[0].x * (R)I[0];
+    R acc = (R)L[0].x * Ir[0];
     R cm = erx, sm = ery;                                   // (cos, sin)(m theta), m = 1
-    for (int m = 1; m <= p; ++m) {
+#pragma unroll
+    for (int m = 1; m <= NP; ++m) {
+        if (PF == 0 && m > p) break;
         const double2 Lm = L[m];
         // 2 Re[L_m e^{-i m theta}] I_m
-        acc = fma((R)2 * (R)I[m], (R)Lm.x * cm + (R)Lm.y * sm, acc);
+        acc = fma((R)2 * Ir[m], (R)Lm.x * cm + (R)Lm.y * sm, acc);
         const R c2 = cm * erx - sm * ery;
         sm = sm * erx + cm * ery;
         cm = c2;
@@ -664,8 +699,12 @@ int fmm_far(yk_geom* g, const double* sigma, double* out) {
                                 sizeof(double2) * (F.nbox - o0) * (p + 1), st));
     auto lvl = [&](int l) { return (int64_t)level_offset(l); };
     auto side = [&](int l) { return F.side / (double)(1 << l); };
-    YK_LAUNCH(k_fmm_p2m, ceil_div((int64_t)nb * nb * 32, 128), 128, 0, st, G, sigma, p, nb, F.x0,
-              F.y0, F.leaf, F.leaf_off, F.leaf_part, F.M + lvl(L) * (p + 1));
+    if (p == FMM_FIXED_ORDER)
+        YK_LAUNCH(k_fmm_p2m<FMM_FIXED_ORDER>, ceil_div((int64_t)nb * nb * 32, 128), 128, 0, st, G,
+                  sigma, p, nb, F.x0, F.y0, F.leaf, F.leaf_off, F.leaf_part, F.M + lvl(L) * (p + 1));
+    else
+        YK_LAUNCH(k_fmm_p2m<0>, ceil_div((int64_t)nb * nb * 32, 128), 128, 0, st, G, sigma, p, nb,
+                  F.x0, F.y0, F.leaf, F.leaf_off, F.leaf_part, F.M + lvl(L) * (p + 1));
     for (int l = L - 1; l >= F.lmin; --l)
         YK_LAUNCH(k_fmm_m2m, ceil_div((int64_t(1) << (2 * l)) * 32, 128), 128, 0, st, l, p, rho,
                   side(l + 1), F.box_count + lvl(l + 1), F.M + lvl(l + 1) * (p + 1),
@@ -686,12 +725,11 @@ int fmm_far(yk_geom* g, const double* sigma, double* out) {
                       l + 1, p, rho, side(l + 1), F.box_count + lvl(l + 1),
                       F.Lc + lvl(l) * (p + 1), F.Lc + lvl(l + 1) * (p + 1));
     }
-    if (F.all32)
-        YK_LAUNCH(k_fmm_l2p<float>, ceil_div(g->n, 128), 128, 0, st, G, p, nb, F.x0, F.y0, F.leaf,
-                  F.leaf_of, F.Lc + lvl(L) * (p + 1), out);
-    else
-        YK_LAUNCH(k_fmm_l2p<double>, ceil_div(g->n, 128), 128, 0, st, G, p, nb, F.x0, F.y0,
-                  F.leaf, F.leaf_of, F.Lc + lvl(L) * (p + 1), out);
+    auto l2p = F.all32 ? (p == FMM_FIXED_ORDER ? &k_fmm_l2p<float, FMM_FIXED_ORDER>
+                                               : &k_fmm_l2p<float, 0>)
+                       : &k_fmm_l2p<double, 0>;
+    YK_LAUNCH(l2p, ceil_div(g->n, 128), 128, 0, st, G, p, nb, F.x0, F.y0, F.leaf, F.leaf_of,
+              F.Lc + lvl(L) * (p + 1), out);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

@@ -237,6 +237,7 @@ int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad);
 
 // fmm.cu
 constexpr int FMM_PMAX = 30;      // largest expansion order (one warp lane per order)
+constexpr int FMM_FIXED_ORDER = 12;   // the default order, with register-resident P2M/L2P
 constexpr int FMM_SEP = 2;        // near field: leaves at most FMM_SEP boxes apart
 constexpr int FMM_LMAX = 10;      // deepest leaf level
 constexpr double FMM_REACH_TOL = 1e-10;   // FMM interactions bounded below this x max|sigma| are left out
