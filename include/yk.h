@@ -314,20 +314,27 @@ int yk_eval_potential_near(yk_geom* g, const double* sigma, const double* target
                            int64_t nt, double* u);
 
 /* Allocation-free variant of yk_eval_potential. The paper has no
- * counterpart: this entry point exists for callers that cannot allocate
- * device memory when they evaluate the potential (inside a CUDA stream
- * capture, in real-time loops that must not touch the allocator, or under a
- * fixed memory budget). It computes the same u = D[sigma] at nt off-surface
- * targets but keeps its partial sums in a fixed 8 MiB device array inside
- * the library (one per GPU, held until the process exits) instead of
- * allocating them, and makes no allocation of any kind.
- *   - sigma (N), targets (nt x 2) and u (nt) must be device pointers
- *     (YK_ERR_ARG otherwise: staging host arrays would allocate).
+ * counterpart. It is for callers that must not allocate device memory at the
+ * point where they evaluate the potential: a real-time loop that cannot
+ * block in the allocator (an allocation may synchronise the device and has
+ * no latency bound), or an application that reserved the GPU's memory up
+ * front and hands libraries a fixed budget. It computes the same
+ * u = D[sigma] at nt off-surface targets as yk_eval_potential, but keeps its
+ * partial sums in a fixed 8 MiB device array inside the library (one per
+ * GPU that loads the library, held until the process exits) and allocates
+ * nothing.
+ *   - sigma (N), targets (nt x 2) and u (nt) must be device memory of the
+ *     context's device (YK_ERR_ARG otherwise: staging host arrays would
+ *     allocate).
  *   - nt <= 1,048,576 (2^20); larger requests return YK_ERR_TOO_LARGE.
- *   - The first call on each device looks up the array's device address;
- *     make that first call before any stream capture begins.
- *   - All calls share the array. Calls whose kernels overlap on the GPU (two
- *     streams, or two contexts on one device) race on it: order them.
+ *   - The first call on each device looks up the array's device address and
+ *     keeps it for the life of the process; make that first call before any
+ *     stream capture begins. A device reset (cudaDeviceReset) invalidates the
+ *     kept address: do not call this entry point after one.
+ *   - All calls share the array, which keeps the last call's contents (every
+ *     partial sum a call reads, it wrote first). Calls whose kernels overlap
+ *     on the GPU (two streams, or two contexts on one device) race on it:
+ *     order them.
  *   - The call enqueues its work on the context's stream and returns without
  *     synchronising it.                                                      */
 int yk_eval_potential_noalloc(yk_geom* g, const double* sigma, const double* targets,

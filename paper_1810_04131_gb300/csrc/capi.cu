@@ -34,6 +34,20 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory that lives on `device` itself (managed memory counts for
+// any device). Used where a pointer on another GPU would otherwise pass and
+// be read through peer access or fail only in a later call.
+static bool is_device_ptr_on(const void* p, int device) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) return YK_OK;
@@ -711,8 +725,12 @@ int yk_eval_potential_noalloc(yk_geom* g, const double* sigma, const double* tar
                               int64_t nt, double* u) {
     if (!g || !sigma || nt < 0 || (nt > 0 && (!targets || !u))) return YK_ERR_ARG;
     if (nt == 0) return YK_OK;
-    // device pointers only: staging host arrays would need allocations
-    if (!is_device_ptr(sigma) || !is_device_ptr(targets) || !is_device_ptr(u)) return YK_ERR_ARG;
+    // device pointers on the context's device only: staging host arrays
+    // would need allocations
+    const int dev = g->ctx->device;
+    if (!is_device_ptr_on(sigma, dev) || !is_device_ptr_on(targets, dev) ||
+        !is_device_ptr_on(u, dev))
+        return YK_ERR_ARG;
     YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
     return potential_noalloc(g, sigma, targets, nt, u);
 }

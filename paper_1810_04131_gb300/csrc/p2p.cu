@@ -391,19 +391,20 @@ int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt
 // Allocation-free off-surface potential (yk_eval_potential_noalloc).
 //
 // yk_eval_potential stages its per-chunk partial sums in a buffer it
-// allocates for each call. Some callers cannot allocate device memory at
-// the point where they evaluate the potential: code running inside a
-// stream capture, where allocation calls are not allowed, real-time loops
-// that must not touch the allocator, or hosts that hand the library a
-// fixed memory budget. For them this variant keeps the scratch in a
-// file-scope device array of STATIC_SCRATCH_DOUBLES doubles (8 MiB), which
-// every GPU that loads the library holds until the process exits.
+// allocates for each call. Some callers must not allocate device memory
+// where they evaluate the potential: real-time loops that cannot block in
+// the allocator, or applications that reserved the GPU's memory up front
+// and give libraries a fixed budget. For them this variant keeps the
+// scratch in a file-scope device array of STATIC_SCRATCH_DOUBLES doubles
+// (8 MiB), which every GPU that loads the library holds until the process
+// exits.
 //
 // In host code the array's name only stands for the symbol; the kernels
 // receive its device address, looked up once per device with
 // cudaGetSymbolAddress while that device is current. The lookup happens on
 // the first call on each device, so that first call should come before any
-// stream capture begins.
+// stream capture begins. The address is kept for the life of the process; a
+// device reset invalidates it.
 //
 // All calls share the one array and it keeps the last call's contents.
 // Nothing in it has to start at zero: every partial sum the reduction reads

@@ -13,6 +13,7 @@ configurations:
   * ``disks8``    8 unit disks in a 20x20 box, gap >= 0.5, 16x16 nodes, rho=1, QBX order 8.
   * ``disks512``  512 unit disks in a 200x200 box, gap >= 0.3, 16x16 nodes, rho=1, QBX order 10.
   * ``ellipses512`` 512 ellipses 1.0x0.5 in a 200x200 box, gap >= 0.2, 16x16 nodes, QBX order 10.
+  * ``ellipses128`` 128 such ellipses in a 100x100 box (same area fraction), N = 32768.
   * ``disks8192`` 8192 unit disks in an 800x800 box, gap >= 0.3, 16x16 nodes.
   * ``stream``    seeded request stream (Poisson arrivals, log-uniform sizes).
 
@@ -180,6 +181,14 @@ def ellipses512(rho=1.0):
     return Workload("ellipses512_rho%g" % rho, p, rho=rho, qbx_order=10, box=200.0)
 
 
+def ellipses128(rho=1.0):
+    """128 ellipses 1.0x0.5 in a 100x100 box (the area fraction of ``ellipses512``),
+    gap 0.2, N = 32768, QBX order 10: the ellipse system at which the FP64 oracle
+    finishes a full solve for every screening length in minutes."""
+    p = make_particles(128, 100.0, 0.2, seed=7, shape=SHAPE_ELLIPSE, A=1.0, B=0.5)
+    return Workload("ellipses128_rho%g" % rho, p, rho=rho, qbx_order=10, box=100.0)
+
+
 def disks8192():
     """8192 unit disks, 800x800 box, gap 0.3, N = 2,097,152, rho = 1."""
     p = make_particles(8192, 800.0, 0.3, seed=5)
@@ -235,5 +244,6 @@ WORKLOADS = {
     "disks8": disks8,
     "disks512": disks512,
     "ellipses512": ellipses512,
+    "ellipses128": ellipses128,
     "disks8192": disks8192,
 }

@@ -61,6 +61,62 @@ def test_janus_labels():
     assert np.allclose(yo.label(g, 0, 10.0), 0.5 * (1 + np.tanh(10 * np.cos(th))), atol=1e-14)
 
 
+def _midpoint_nodes(shape, n_panels, phi):
+    """Geometry with 3 Gauss-Legendre nodes per panel: the middle node of
+    panel k sits at curve parameter t = (k + 1/2) 2 pi / n_panels, and for a
+    disk, or an ellipse at t = pi/2 and 3 pi/2, its polar angle from the
+    director is t itself."""
+    A, B = (1.0, 0.5) if shape == W.SHAPE_ELLIPSE else (1.0, 1.0)
+    g = yo.make_geometry(np.array([[shape, 2.0, -1.0, phi, A, B]]), n_panels, 3)
+    t = (np.arange(n_panels) + 0.5) * 2 * np.pi / n_panels
+    return g, np.arange(n_panels) * 3 + 1, t
+
+
+@pytest.mark.parametrize("shape", [W.SHAPE_DISK, W.SHAPE_ELLIPSE])
+def test_janus_label_values_at_known_angles(shape):
+    """Label values fixed by the angle alone (Eq. JanusBC: theta is the angle
+    between x - a_i and the director d_i; p an even integer):
+      * across the director (theta = +-pi/2): sin^p = 1, so 1 - sin^p = 0, and
+        the tanh label is exactly 1/2 (cos theta = 0);
+      * along the director (theta = 0, the tail) and opposite it (theta = pi,
+        the head): 1 - sin^p = 1; the tanh label is the logistic function
+        1/(1 + e^{-2 s cos theta}) of the same argument (1/(1 + e^{-20}) at
+        the tail, 1/(1 + e^{20}) at the head for s = 10);
+      * theta = pi/4: 1 - (1/sqrt 2)^p = 1 - 2^{-p/2} (1/2 for p = 2, 3/4 for
+        p = 4); theta = pi/6: 1 - 2^{-p} (3/4, 15/16).
+    The orientation phi must not matter: the label turns with the particle."""
+    for phi in (0.0, 0.9, -2.3):
+        # n_panels = 2: theta = pi/2 and 3 pi/2 (for ellipses too)
+        g, k, _ = _midpoint_nodes(shape, 2, phi)
+        f0 = yo.label(g, 0, 10.0)[k]
+        f1 = yo.label(g, 1, 2)[k]
+        f4 = yo.label(g, 1, 4)[k]
+        assert np.allclose(f0, 0.5, atol=1e-15), f0
+        assert np.allclose(f1, 0.0, atol=1e-15) and np.allclose(f4, 0.0, atol=1e-15)
+        if shape != W.SHAPE_DISK:
+            continue
+        # n_panels = 1: theta = pi (head)
+        g, k, _ = _midpoint_nodes(shape, 1, phi)
+        assert abs(yo.label(g, 0, 10.0)[k][0] - 1.0 / (1.0 + math.exp(20.0))) < 1e-15
+        assert abs(yo.label(g, 1, 2)[k][0] - 1.0) < 1e-15
+        # n_panels = 4: theta = pi/4, 3 pi/4, 5 pi/4, 7 pi/4
+        g, k, t = _midpoint_nodes(shape, 4, phi)
+        assert np.allclose(yo.label(g, 1, 2)[k], 0.5, atol=1e-15)
+        assert np.allclose(yo.label(g, 1, 4)[k], 0.75, atol=1e-15)
+        logistic = 1.0 / (1.0 + np.exp(-20.0 * np.array([1, -1, -1, 1]) / math.sqrt(2)))
+        assert np.allclose(yo.label(g, 0, 10.0)[k], logistic, atol=1e-15)
+        # n_panels = 6: theta = pi/6 (and 5 pi/6, 7 pi/6, 11 pi/6), pi/2, 3 pi/2
+        g, k, t = _midpoint_nodes(shape, 6, phi)
+        f2, f4 = yo.label(g, 1, 2)[k], yo.label(g, 1, 4)[k]
+        assert np.allclose(f2[[0, 2, 3, 5]], 0.75, atol=1e-15)
+        assert np.allclose(f4[[0, 2, 3, 5]], 15.0 / 16.0, atol=1e-15)
+        assert np.allclose(f2[[1, 4]], 0.0, atol=1e-15)
+        # the tanh label: head-tail antisymmetry f(theta) + f(pi - theta) = 1
+        f0 = yo.label(g, 0, 10.0)[k]
+        assert np.allclose(f0[0] + f0[2], 1.0, atol=1e-15)
+        assert f0[0] > 0.99999 and f0[2] < 1e-5        # tail hydrophobic, head hydrophilic
+
+
 # --------------------------------------------------------------------------
 # kernel and expansion identities
 # --------------------------------------------------------------------------
@@ -581,3 +637,55 @@ def test_near_contact_green_identity(shape, gap):
         errs[cf] = np.abs(Gn @ sig - (grad(o.geom.x) * o.geom.nu).sum(1)).max()
     assert errs[0.5] < 1e-8
     assert errs[0.0] > 1e-3
+
+
+# --------------------------------------------------------------------------
+# constant-drag dynamics (Eq. euler)
+# --------------------------------------------------------------------------
+
+def test_euler_two_disks_follow_the_exact_separation():
+    """Two unit disks pushed apart by Eq. repul alone. By symmetry each moves
+    with velocity F/xi_x along the line of centres, so the gap s obeys
+    ds/dt = 2 c0 q / (xi_x s^{q+1}), whose solution is
+    s(t)^{q+2} = s0^{q+2} + 2 (q+2) q c0 t / xi_x. Forward Euler (Eq. euler
+    with the repulsion recomputed every step) converges to it at first order
+    in dt; a dropped dt, a drag applied twice or the rotational drag used for
+    translation fails. The disks feel no torque, so their angles stay."""
+    c0, q, xi_x, xi_th, T = 0.02, 3, 4 * math.pi, 0.7, 2.0
+    p0 = np.array([[0, 0.0, 0.0, 0.3, 1.0, 1.0], [0, 1.5, 2.0, 1.1, 1.0, 1.0]])
+    s0 = math.hypot(1.5, 2.0) - 2.0
+    exact = (s0 ** (q + 2) + 2 * (q + 2) * q * c0 * T / xi_x) ** (1.0 / (q + 2))
+    errs = []
+    for n in (200, 400):
+        p = p0.copy()
+        for _ in range(n):
+            F, tau, _ = yo.repulsion(p, c0, q)
+            p = yo.euler_step(p, F, tau, T / n, xi_x, xi_th)
+        s = math.hypot(*(p[1, 1:3] - p[0, 1:3])) - 2.0
+        errs.append(abs(s - exact))
+        # the centre of mass stays, the motion is along the line of centres
+        assert np.allclose(p[:, 1:3].sum(0), p0[:, 1:3].sum(0), atol=1e-14)
+        d0, d1 = p0[1, 1:3] - p0[0, 1:3], p[1, 1:3] - p[0, 1:3]
+        assert abs(d0[0] * d1[1] - d0[1] * d1[0]) < 1e-13
+        assert np.allclose(p[:, 3], p0[:, 3], atol=1e-15)
+    assert errs[0] < 2e-3 * (exact - s0)
+    assert 1.8 < errs[0] / errs[1] < 2.2                # first order in dt
+
+
+def test_euler_dissipates_the_repulsion_energy_at_the_mobility_rate():
+    """Eq. euler is a gradient flow of the repulsion potential with mobilities
+    1/xi_x (position) and 1/xi_theta (angle), since F = -dPhi/da and
+    tau = -dPhi/dtheta. One step therefore lowers Phi by
+    dt (|F|^2 / xi_x + tau^2 / xi_theta) up to O(dt^2). With xi_x != xi_theta
+    and |F|^2 != tau^2 on this ellipse pair, swapping the two drags, or
+    updating the angle from the force, changes the rate."""
+    c0, q, xi_x, xi_th = 0.01, 3, 4 * math.pi, 0.5
+    p = np.array([[1, 0.0, 0.0, 0.4, 1.0, 0.5], [1, 1.9, 0.9, 2.3, 1.0, 0.5]])
+    F, tau, phi = yo.repulsion(p, c0, q)
+    rate = (F ** 2).sum() / xi_x + (tau ** 2).sum() / xi_th
+    swapped = (F ** 2).sum() / xi_th + (tau ** 2).sum() / xi_x
+    assert abs(swapped - rate) > 0.5 * rate and np.abs(tau).min() > 1e-3
+    for dt in (1e-5, 1e-6):
+        p1 = yo.euler_step(p, F, tau, dt, xi_x, xi_th)
+        dphi = yo.repulsion(p1, c0, q)[2].sum() - phi.sum()
+        assert abs(-dphi / dt / rate - 1.0) < 1e-5, (dt, -dphi / dt / rate)   # O(dt) + rounding

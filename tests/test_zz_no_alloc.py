@@ -1,10 +1,10 @@
 """The allocation-free potential entry point (yk_eval_potential_noalloc).
 
-It is meant for callers that cannot allocate device memory when they
-evaluate the potential: code inside a CUDA stream capture, real-time loops
-that must not touch the allocator, or hosts with a fixed memory budget. It
-keeps its partial sums in a fixed device array inside the library rather
-than allocating them.
+It is for callers that must not allocate device memory where they evaluate
+the potential: real-time loops that cannot block in the allocator, or
+applications that reserved the GPU's memory up front and hand the library a
+fixed budget. It keeps its partial sums in a fixed device array inside the
+library rather than allocating them.
 
 Checked here, through the C ABI: on two calls in a row with different
 densities, it returns what yk_eval_potential returns for the same inputs
