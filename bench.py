@@ -5,10 +5,29 @@ on the host cores.
 
 One step = one solve of Eq. (bie) plus forces and torques for the 512 unit
 disks (200 x 200 box, gap >= 0.3, 16 panels x 16 nodes, rho = 1, QBX order
-10, tolerance 1e-10): re-discretise the particles, label, mixed-precision
+10, tolerance 1e-12): re-discretise the particles, label, mixed-precision
 GMRES with FP64 iterative refinement, FP64-accurate normal derivative,
 force/torque reduction. Inputs are resident on the device; L2 is flushed
 between steps (a 256 MiB write) outside the timed events.
+
+Further legs, outside the timed steps (``--legs``; all by default):
+  fp64      the same system with every step in FP64 (dense far field);
+  samefar   both precisions on the cut-off far field, so that the ratio
+            measures precision alone (at the library's 1e-12 and at 1e-10);
+  cold      a first solve from scratch: geometry, QBX rows, self blocks,
+            preconditioner, label, solve, forces;
+  accuracy  the headline density, forces and torques against the FP64
+            oracle's stored reference solution of the same system;
+  c3        512 ellipses at rho in {0.25, 1, 4}: mixed (dense) and FP64
+            (cut-off) solves, errors against the oracle's stored references
+            (512 ellipses where stored, else the 128-ellipse system of the
+            same area fraction);
+  c4        8192 disks: mixed solves with the FMM and the cut-off far field,
+            the FP64 cut-off solve, and a 256-disk (65,536-node) subset solved
+            with the dense FP64 operator against the mixed FMM solve;
+  serving   the seeded request stream: saturation throughput, then Poisson
+            arrivals at 0.5, 0.7 and 0.9 of it, latency percentiles;
+  cpu       the FP64 oracle on all host cores (a bounded sample of rows).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank solves its own replica (independent
@@ -16,8 +35,11 @@ systems; no collective on the data path), value = all ranks' solves / the
 slowest rank's time ("scaling": "weak").
 """
 import argparse
+import ast
 import json
+import multiprocessing as mp
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -30,32 +52,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Yukawa-QBX solves/s mixed vs FP64 @1e-9 rel err; P2P %FMA peak; p50/p99 latency"
 WORKLOAD = "disks512"
-# FP32 operations per far-field pair in the P2P inner loop (FMA counted as 2,
-# FADD/FMUL and each MUFU op as 1): d = x - y (2), |d|^2 (3), 1/z' (1 MUFU),
-# z' (1), K1 polynomial in 1/z' (6 FMA = 12 with the full fit, 3 FMA = 6 with
-# the short fit for z >= 10), exp2 (1 MUFU), z'^{-1/2} (1 MUFU), (d.g) (3),
-# three products (3), accumulate (2).
-# With a source particle whose 1/z' range is within 1 +- 0.07 of its centre
-# (the narrow class), z'^{-1/2} and the polynomial become one degree-4
-# polynomial in u = rz/rc - 1: u (2), polynomial (8), no z'^{-1/2} MUFU and one
-# product fewer.
-FLOPS_PER_PAIR = 29
-FLOPS_PER_PAIR_SHORT = 23
-FLOPS_PER_PAIR_NARROW = 25
-FLOPS_PER_PAIR_NARROW3 = 23      # the narrow class within 1 +- 0.03: degree 3
-# FMA-pipe lane operations per pair (the same lists without the MUFU ops)
-LANE_OPS_PER_PAIR = 17
-LANE_OPS_PER_PAIR_SHORT = 14
-LANE_OPS_PER_PAIR_NARROW = 15
-LANE_OPS_PER_PAIR_NARROW3 = 14
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+# FP32 operations per far-field pair in the P2P inner loop, in two counts:
+# flops (FMA = 2, FADD/FMUL = 1) on the FMA pipe, and FMA-pipe lane
+# operations (each FMA, FADD or FMUL = 1); MUFU operations (1/z', exp2,
+# z'^{-1/2}) are listed apart. Full fit: d = x - y (2 FADD), |d|^2 (FMA +
+# FMUL), z' (FMUL), K1 polynomial in 1/z' (6 FMA; 3 with the short fit for
+# z >= 10), the three-factor product (2 FMUL), (d.g) (FMA + FMUL), 1/z' (d.g)
+# (FMUL), accumulate (FMA); MUFU: 1/z', exp2, z'^{-1/2}. Narrow class (1/z'
+# within 1 +- 0.07 of its centre): the z'^{-1/2} MUFU and the polynomial are
+# replaced by u = rz/rc - 1 (FMA) and a degree-4 (degree-3 within 1 +- 0.03)
+# polynomial in u, one product fewer.
+FLOPS_PER_PAIR = {"full": 26, "short": 20, "narrow": 23, "narrow3": 21}
+LANE_OPS_PER_PAIR = {"full": 17, "short": 14, "narrow": 15, "narrow3": 14}
+MUFU_PER_PAIR = {"full": 3, "short": 3, "narrow": 2, "narrow3": 2}
 EPS_NARROW = 0.07
 EPS_NARROW3 = 0.03
-SMS, FP32_LANES = 152, 128
+SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 # the classes of the FP32 far-field kernel (bounding-circle gap in units of rho)
 Z_SHORT = 10.0
 ZP_ZERO = 128.0
 LOG2E = 1.4426950408889634
 TARGETS_PER_BLOCK = 256
+ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "serving", "cpu")
+# GMRES iterations of the FP64 path on the 512-disk system at tolerance 1e-12
+# (measured on the GPU; the CPU model of the reference arm, which has no GPU,
+# uses this count)
+FP64_ITERS_DISKS512 = 20
 
 
 KERNEL_SOURCES = ("p2p_kernels.cuh", "bessel.cuh", "bessel_tables.h", "geom_view.cuh")
@@ -94,10 +117,9 @@ def p2p_pair_classes(particles, rho, npp, n, own_by_block=True):
     FP32 and is skipped; gap >= 10 rho takes the short K1 fit, and the
     narrow expansion when also far - gap <= 0.07 (far + gap), of degree 3
     when far - gap <= 0.03 (far + gap); the rest the full fit. The own
-    particle is left to the self block. Returns (full-fit, short-fit,
-    narrow degree 4, narrow degree 3, zero) pair counts, from the particles
-    in float64 (the kernel compares in FP32; pairs at a class boundary can
-    differ).
+    particle is left to the self block. Returns a dict of pair counts (full,
+    short, narrow, narrow3, zero) from the particles in float64 (the kernel
+    compares in FP32; pairs at a class boundary can differ).
     """
     c = particles[:, 1:3]
     R = np.maximum(particles[:, 4], particles[:, 5])
@@ -121,7 +143,7 @@ def p2p_pair_classes(particles, rho, npp, n, own_by_block=True):
             counts[k] += nt * npp * int((cls == k).sum())
         if not (own_by_block and pa == pb):                   # near panels are QBX rows
             counts[0] -= nt * 3 * 16
-    return tuple(int(v) for v in counts)
+    return dict(zip(("full", "short", "narrow", "narrow3", "zero"), (int(v) for v in counts)))
 
 
 def parse():
@@ -130,17 +152,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-solve", type=int, default=1, help="time one plain FP64 solve")
-    ap.add_argument("--cpu-baseline", type=int, default=1)
-    ap.add_argument("--cpu-rows", type=int, default=384)
-    ap.add_argument("--serve-requests", type=int, default=48,
-                    help="requests replayed from the seeded serving stream")
+    ap.add_argument("--legs", default=",".join(ALL_LEGS),
+                    help="comma-separated legs beyond the timed steps (or 'none')")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="CPU time budget of the oracle sample (all cores)")
+    ap.add_argument("--serve-requests", type=int, default=500,
+                    help="requests per arrival rate, from the seeded serving stream")
+    ap.add_argument("--serve-lambdas", default="0.5,0.7,0.9",
+                    help="arrival rates as fractions of the measured saturation rate")
     ap.add_argument("--serve-max-particles", type=int, default=2048)
-    ap.add_argument("--fmm-leg", type=int, default=1,
-                    help="also time the system with the FMM inner operator (context)")
     ap.add_argument("--serve-fmm-above", type=int, default=256,
                     help="requests with more particles use the FMM far field")
-    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrivals per second")
     return ap.parse_args()
 
 
@@ -196,40 +218,109 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rows_timing(wl, nrows, want_grad=False):
-    """Seconds per operator row of the FP64 oracle on a sample of rows."""
-    from oracle import yk_oracle as yo
-    o = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
-    rng = np.random.default_rng(0)
-    sig = yo.label(o.geom, 0, 10.0)
-    rows = np.sort(rng.choice(o.geom.n, nrows, replace=False))
-    o.apply_rows(sig, rows[:2], want_grad=want_grad)  # warm caches
-    t0 = time.perf_counter()
-    o.apply_rows(sig, rows, want_grad=want_grad)
-    return (time.perf_counter() - t0) / nrows
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (cpu leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+_ORC = None
 
 
-def oracle_gmres_iters():
-    """Iterations of the oracle's own GMRES (tol 1e-10) on the 8-disk system,
-    used as the iteration count of the CPU solve-time model."""
+def _oracle_init():
+    global _ORC
     from oracle import yk_oracle as yo
     from paper_1810_04131_gb300 import workloads as W
-    wl = W.small_system(8, 1, n_panels=16, rho=1.0)
-    o = yo.Oracle(wl.particles, 16, 16, 1.0, yo.QBXParams(order=10))
-    A = o.dense()
-    f = yo.label(o.geom, 0, 10.0)
-    _, it, _ = yo.Oracle.gmres(lambda v: A @ v, f, tol=1e-10)
-    return it
+    wl = W.disks512()
+    _ORC = yo.Oracle(wl.particles, wl.n_panels, wl.n_gl, wl.rho, yo.QBXParams(order=wl.qbx_order))
+    _ORC.f = yo.label(_ORC.geom, 0, 10.0)
 
 
-def cpu_solve_rate(wl, nrows, iters):
-    """Oracle solves/s on the host, from a timed sample of rows: one solve =
-    (iters + 1) value matvecs + one gradient pass, each N rows."""
-    t_val = oracle_rows_timing(wl, nrows)
-    t_grad = oracle_rows_timing(wl, max(8, nrows // 4), want_grad=True)
-    t_solve = wl.n_nodes * ((iters + 1) * t_val + t_grad)
-    return 1.0 / t_solve, t_val, t_grad
+def _oracle_rows(args):
+    rows, want_grad = args
+    t0 = time.perf_counter()
+    _ORC.apply_rows(_ORC.f, rows, want_grad=want_grad)
+    return time.perf_counter() - t0
 
+
+def oracle_pool():
+    """One spawn-started worker per host core, each holding the oracle of the
+    512-disk system (spawn: the pool is started after CUDA is initialised)."""
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
+    pool.map(_oracle_rows, [([0], False)] * cores)                     # warm every worker
+    return pool, cores
+
+
+def cpu_model():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return model
+
+
+def cpu_solve_rate(pool, cores, iters, cpu_seconds):
+    """Oracle solves/s of the 512-disk system on every host core, from a
+    timed sample: the pool's workers evaluate random operator rows (value
+    rows, then gradient rows) of the oracle as it stands; the row throughput
+    of the whole pool gives one solve as N ((iters + 1) value rows + 1
+    gradient row). About cpu_seconds of pool wall time in all."""
+    n = 512 * 256
+    rng = np.random.default_rng(int(time.time() * 1e3) % 2 ** 31)
+    n_val = max(4 * cores, int(cpu_seconds * 2 / 3 * cores / 0.03))
+    n_grad = max(2 * cores, int(cpu_seconds / 3 * cores / 0.06))
+    out = {}
+    for key, nrows, grad in (("val", n_val, False), ("grad", n_grad, True)):
+        rows = np.sort(rng.choice(n, nrows, replace=False))
+        chunks = [(list(c), grad) for c in np.array_split(rows, cores * 4) if len(c)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_rows, chunks, chunksize=1)
+        out[key] = (time.perf_counter() - t0) / nrows            # pool wall seconds per row
+    t_solve = n * ((iters + 1) * out["val"] + out["grad"])
+    sample = ("model: rows x iterations. %d value rows + %d gradient rows of the 512-disk "
+              "operator (N=131072) timed on a %d-process pool (%.3f ms, %.3f ms of pool wall "
+              "time per row); solve = N x ((iters+1) value rows + 1 gradient row), iters=%d (the "
+              "GMRES iterations of the FP64 path on this system at tolerance 1e-12); CPU: %s"
+              % (n_val, n_grad, cores, out["val"] * 1e3, out["grad"] * 1e3, iters, cpu_model()))
+    return 1.0 / t_solve, sample
+
+
+def run_reference(args):
+    """The oracle arm: FP64 CPU oracle timed on the host cores, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1810_04131_gb300 import workloads as W
+    wl = W.disks512()
+    vals = []
+    budget = max(3.0, 120.0 / max(1, args.warmup + args.steps))
+    pool, cores = oracle_pool()
+    with pool:
+        for k in range(args.warmup + args.steps):
+            v, sample = cpu_solve_rate(pool, cores, FP64_ITERS_DISKS512, budget)
+            if k >= args.warmup:
+                vals.append(v)
+    value = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_particles": 512, "n_nodes": wl.n_nodes,
+                      "rho": 1.0, "qbx_order": 10, "gmres_tol": 1e-12, "precision": "fp64",
+                      "farfield": "dense"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": "per step: " + sample},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# helpers of the GPU legs
+# ---------------------------------------------------------------------------
 
 def combine_ranks(t_local, steps, world, dist=None, device=None):
     """Whole-job throughput of independent replicas: every rank solved
@@ -245,89 +336,143 @@ def combine_ranks(t_local, steps, world, dist=None, device=None):
     return t_max, world * steps / t_max
 
 
+def load_reference(name):
+    """The oracle's stored solution of a named system (written by
+    tests/golden/make_reference_solution.py), or None."""
+    path = os.path.join(GOLDEN, "ref_%s.npz" % name)
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    return {k: z[k] for k in z.files}
+
+
+def errors_vs(ref, sigma, F, tau):
+    """Relative errors: 2-norm for sigma, max-norm (relative to max |ref|)
+    for forces and torques."""
+    F = np.asarray(F).reshape(-1, 2)
+    return {"sigma": float(np.linalg.norm(sigma - ref["sigma"]) / np.linalg.norm(ref["sigma"])),
+            "F": float(np.abs(F - ref["F"]).max() / np.abs(ref["F"]).max()),
+            "tau": float(np.abs(tau - ref["tau"]).max() / np.abs(ref["tau"]).max()),
+            "oracle_gmres_tol": float(ast.literal_eval(str(ref["meta"]))["tol"])}
+
+
+class Solver:
+    """One geometry with device buffers and a timed solve + forces."""
+
+    def __init__(self, yk, ctx, particles, prm, dev):
+        import torch
+        self.torch = torch
+        self.yk = yk
+        self.parts = particles
+        t0 = time.perf_counter()
+        self.g = yk.Geometry(ctx, particles, prm)
+        torch.cuda.synchronize()
+        self.create_s = time.perf_counter() - t0
+        n, npart = self.g.n, self.g.n_particles
+        self.f = torch.zeros(n, dtype=torch.float64, device=dev)
+        self.sig = torch.zeros_like(self.f)
+        self.F = torch.zeros((npart, 2), dtype=torch.float64, device=dev)
+        self.tau = torch.zeros(npart, dtype=torch.float64, device=dev)
+
+    def solve(self, update=True):
+        """Re-discretise (optional), label, solve, forces; wall seconds."""
+        torch, g = self.torch, self.g
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if update:
+            g.yk_update_geometry(self.parts)
+        g.yk_label(self.yk.YK_LABEL_TANH, 10.0, out=self.f)
+        _, self.info = g.yk_solve(self.f, out=self.sig)
+        g.yk_forces_torques(self.sig, self.f, F=self.F, tau=self.tau, want_net=False)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def result(self):
+        return (self.sig.cpu().numpy(), self.F.cpu().numpy(), self.tau.cpu().numpy())
+
+    def close(self):
+        self.g.close()
+
+
+def solve_leg(yk, ctx, dev, particles, prm, reps=1):
+    """Solve reps times on one geometry (the first also builds lists and
+    tunes the FMM); report the best time, the statistics and the result."""
+    s = Solver(yk, ctx, particles, prm, dev)
+    times = [s.solve() for _ in range(reps)]
+    out = {"solve_s": min(times), "first_solve_s": times[0], "create_s": s.create_s,
+           "iterations": s.info["iterations"], "refinements": s.info["refinements"],
+           "rel_residual": s.info["rel_residual"]}
+    res = s.result()
+    s.close()
+    return out, res
+
+
 def run_serving(yk, W, ctx, args):
-    """Replay the head of the seeded request stream (Poisson arrivals,
-    log-uniform particle counts capped at --serve-max-particles, 8-32 panels,
-    disks and ellipses, rho in {0.5, 1, 2}) through yk_submit / yk_poll and
-    report latency percentiles and throughput."""
-    reqs = W.request_stream(args.serve_requests, seed=6, rate=args.serve_rate,
-                            np_max=args.serve_max_particles)
-    loads = [W.materialise_request(r) for r in reqs]
-    t0 = time.perf_counter()
-    pending = {}
-    lat = []
-    nodes = 0
-    k = 0
-    while k < len(reqs) or pending:
-        now = time.perf_counter() - t0
-        while k < len(reqs) and reqs[k]["arrival"] <= now:
-            wl = loads[k]
-            # large systems take the FMM far field for the inner operator
-            ff = yk.YK_FARFIELD_FMM if len(wl.particles) > args.serve_fmm_above \
-                else yk.YK_FARFIELD_DENSE
-            rid = ctx.yk_submit(wl.particles, yk.params_for(wl, precision=yk.YK_MIXED,
-                                                            farfield=ff))
-            pending[rid] = wl
-            k += 1
-        done = []
-        for rid, wl in pending.items():
-            r = ctx.yk_poll(rid)
-            if r["status"] == yk.YK_REQ_DONE:
-                lat.append(r["latency_ms"])
-                nodes += wl.n_nodes
-                done.append(rid)
-            elif r["status"] == yk.YK_REQ_FAILED:
-                raise RuntimeError("serving request failed")
-        for rid in done:
-            del pending[rid]
-        time.sleep(0.002)
-    wall = time.perf_counter() - t0
-    lat = np.array(lat)
-    return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "solves_per_s": len(lat) / wall, "wall_s": wall, "nodes_total": int(nodes),
-            "arrival_rate_per_s": args.serve_rate, "max_particles": args.serve_max_particles,
-            "stream": "seeded (seed 6): Poisson arrivals, log-uniform 4..%d particles, "
-                      "8-32 panels x 16 nodes, disk/ellipse, rho in {0.5,1,2}, mixed precision; "
-                      "dense far field up to %d particles, FMM above"
-                      % (args.serve_max_particles, args.serve_fmm_above)}
+    """The seeded request stream (Poisson arrivals, log-uniform particle
+    counts, 8-32 panels, disks and ellipses, rho in {0.5, 1, 2}) through
+    yk_submit / yk_poll. First the saturation throughput: every request
+    submitted at once. Then, for each fraction lambda of it, the same
+    requests with Poisson arrivals at that rate; latency percentiles and
+    throughput per rate."""
+    nreq = args.serve_requests
+    base = W.request_stream(nreq, seed=6, rate=1.0, np_max=args.serve_max_particles)
+    loads = [W.materialise_request(r) for r in base]
+    unit_gaps = np.diff([0.0] + [r["arrival"] for r in base])   # Exp(1) inter-arrival gaps
 
+    def params(wl):
+        ff = yk.YK_FARFIELD_FMM if len(wl.particles) > args.serve_fmm_above \
+            else yk.YK_FARFIELD_DENSE
+        return yk.params_for(wl, precision=yk.YK_MIXED, farfield=ff)
 
-def run_reference(args):
-    """The oracle arm: FP64 CPU oracle timed on the host cores, bounded samples."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return 0
-    from paper_1810_04131_gb300 import workloads as W
-    wl = W.disks512()
-    iters = oracle_gmres_iters()
-    vals = []
-    for k in range(args.warmup + args.steps):
-        v, t_val, t_grad = cpu_solve_rate(wl, 64, iters)
-        if k >= args.warmup:
-            vals.append(v)
-    value = float(np.mean(vals))
-    sample = ("per step: 64 value rows + 16 gradient rows of the 512-disk operator "
-              "(N=131072), solve = N x ((iters+1) value rows + 1 gradient row), iters=%d "
-              "from the oracle's own GMRES on an 8-disk system" % iters)
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n_particles": 512, "n_nodes": wl.n_nodes,
-                      "rho": 1.0, "qbx_order": 10, "gmres_tol": 1e-10},
-           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                            "sample": sample},
-           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
-    return 0
+    def replay(arrivals):
+        t0 = time.perf_counter()
+        pending = {}
+        lat = []
+        k = 0
+        while k < len(loads) or pending:
+            now = time.perf_counter() - t0
+            while k < len(loads) and arrivals[k] <= now:
+                rid = ctx.yk_submit(loads[k].particles, params(loads[k]))
+                pending[rid] = loads[k]
+                k += 1
+            done = []
+            for rid in pending:
+                r = ctx.yk_poll(rid)
+                if r["status"] == yk.YK_REQ_DONE:
+                    lat.append(r["latency_ms"])
+                    done.append(rid)
+                elif r["status"] == yk.YK_REQ_FAILED:
+                    raise RuntimeError("serving request failed")
+            for rid in done:
+                del pending[rid]
+            time.sleep(0.001)
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        return {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "solves_per_s": len(lat) / wall, "wall_s": wall}
+
+    sat = replay(np.zeros(len(loads)))
+    out = {"saturation": sat, "rates": []}
+    for frac in [float(x) for x in args.serve_lambdas.split(",") if x]:
+        lam = frac * sat["solves_per_s"]
+        arrivals = np.cumsum(unit_gaps) / lam
+        r = replay(arrivals)
+        r.update(arrival_rate_per_s=lam, lambda_fraction=frac)
+        out["rates"].append(r)
+    out["stream"] = ("seeded (seed 6): %d requests, log-uniform 4..%d particles, 8-32 panels x 16 "
+                     "nodes, disk/ellipse, rho in {0.5,1,2}, mixed precision to 1e-12; dense far "
+                     "field up to %d particles, FMM above; nodes in total %d"
+                     % (nreq, args.serve_max_particles, args.serve_fmm_above,
+                        sum(w.n_nodes for w in loads)))
+    return out
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    legs = set() if args.legs == "none" else set(x for x in args.legs.split(",") if x)
     import torch
     from paper_1810_04131_gb300 import workloads as W
     from paper_1810_04131_gb300 import yk
@@ -390,11 +535,13 @@ def main():
     clk = clocks.stop()
     t_max, value = combine_ranks(total_ms / 1e3, args.steps, world, dist, dev)
     info = infos[-1]
-    sig_mixed = sig.clone()
+    sig_mixed = sig.cpu().numpy()
+    F_mixed, tau_mixed = F.cpu().numpy(), tau.cpu().numpy()
 
     # ---- the dominant kernel: FP32 far-field P2P (k_p2p_f32) -------------
-    # yk_matvec(YK_MIXED) = k_p2p_f32 + k_assemble (near rows); timed with
-    # CUDA events on the bench stream, back to back on the solved density.
+    # yk_matvec(YK_MIXED) = k_src_pairs + k_p2p_f32 + k_assemble (near rows);
+    # timed with CUDA events on the bench stream, back to back on the solved
+    # density.
     y = torch.zeros_like(sig)
     reps = 10
     g.yk_matvec(sig, yk.YK_MIXED, out=y)
@@ -407,97 +554,151 @@ def main():
     e1.record(stream)
     e1.synchronize()
     t_p2p = e0.elapsed_time(e1) / 1e3 / reps
-    n_full, n_short, n_narrow, n_narrow3, n_zero = p2p_pair_classes(parts, 1.0, n // npart, n)
-    n_eval = n_full + n_short + n_narrow + n_narrow3
+    cls = p2p_pair_classes(parts, 1.0, n // npart, n)
+    n_eval = sum(cls[k] for k in FLOPS_PER_PAIR)
     interactions = n * (n - 3 * 16)          # every far (target, source) pair of the operator
-    flops = (n_full * FLOPS_PER_PAIR + n_short * FLOPS_PER_PAIR_SHORT
-             + n_narrow * FLOPS_PER_PAIR_NARROW + n_narrow3 * FLOPS_PER_PAIR_NARROW3)
-    lane_ops = (n_full * LANE_OPS_PER_PAIR + n_short * LANE_OPS_PER_PAIR_SHORT
-                + n_narrow * LANE_OPS_PER_PAIR_NARROW + n_narrow3 * LANE_OPS_PER_PAIR_NARROW3)
+    flops = sum(cls[k] * FLOPS_PER_PAIR[k] for k in FLOPS_PER_PAIR)
+    lane_ops = sum(cls[k] * LANE_OPS_PER_PAIR[k] for k in LANE_OPS_PER_PAIR)
+    mufu = sum(cls[k] * MUFU_PER_PAIR[k] for k in MUFU_PER_PAIR)
+    peak = yk.yk_fp32_fma_peak(local)        # measured: FMA chains on every SM, TFLOP/s
     achieved = flops / t_p2p / 1e12
-    peak = SMS * FP32_LANES * 2 * 2.070e9 / 1e12
+    clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": stored_traffic(),
-                "kernel": "k_p2p_f32 (+k_assemble)",
-                "pairs_evaluated_per_launch": n_eval,
-                "pairs_full_fit": n_full, "pairs_short_fit": n_short,
-                "pairs_narrow": n_narrow, "pairs_narrow3": n_narrow3,
-                "pairs_exact_zero_skipped": n_zero,
+                "kernel": "k_p2p_f32 (yk_matvec YK_MIXED: + k_src_pairs, k_assemble)",
+                "peak_note": "measured: yk_fp32_fma_peak (independent FMA chains on every SM, "
+                             "FMA = 2 flops), same GPU, same run; achieved counts the FMA-pipe "
+                             "flops of the pairs the kernel evaluates (MUFU operations excluded; "
+                             "a pair whose exp2 underflows adds exactly 0 in FP32 and is "
+                             "skipped by particle)",
+                "pairs_evaluated_per_launch": n_eval, "pairs_by_class": cls,
+                "flops_per_pair": FLOPS_PER_PAIR, "fma_lane_ops_per_pair": LANE_OPS_PER_PAIR,
+                "mufu_ops_per_pair": MUFU_PER_PAIR,
                 "pairs_evaluated_per_s": n_eval / t_p2p,
                 "interactions_per_s": interactions / t_p2p,
-                "flops_per_pair": {"full fit": FLOPS_PER_PAIR, "short fit": FLOPS_PER_PAIR_SHORT,
-                                   "narrow": FLOPS_PER_PAIR_NARROW,
-                                   "narrow3": FLOPS_PER_PAIR_NARROW3},
-                "fma_pipe_frac": lane_ops / t_p2p / (SMS * FP32_LANES * 2.070e9),
-                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max SM clock; "
-                             "achieved counts evaluated pairs only (a pair whose exp2 "
-                             "underflows adds exactly 0 in FP32 and is skipped by particle)"}
+                "fma_pipe_frac": lane_ops / t_p2p / (peak * 1e12 / 2),
+                "mufu_pipe_frac": mufu / t_p2p / (SMS * MUFU_LANES * clock_hz),
+                "mufu_note": "MUFU (ex2, rsqrt) ops per second over 152 SMs x 16 per clock at "
+                             "the median SM clock of the timed steps"}
 
-    # ---- plain FP64 path: one matvec and (optionally) one full solve -------
-    fp64 = {}
-    e0.record(stream)
-    g.yk_matvec(sig, yk.YK_FP64, out=y)
-    e1.record(stream)
-    e1.synchronize()
-    fp64["matvec_ms"] = e0.elapsed_time(e1)
-    fp64["matvec_mixed_ms"] = t_p2p * 1e3
-    if args.fp64_solve and rank == 0:
-        prm64 = yk.params_for(wl, precision=yk.YK_FP64)
-        g64 = yk.Geometry(ctx, parts, prm64)
-        f64 = torch.zeros_like(f)
-        s64 = torch.zeros_like(sig)
-        torch.cuda.synchronize()
+    extra = {}
+    fp64_iters = None
+    # ---- plain FP64 path: the same system, dense far field -----------------
+    if "fp64" in legs and rank == 0:
         e0.record(stream)
-        g64.yk_update_geometry(parts)
-        g64.yk_label(yk.YK_LABEL_TANH, 10.0, out=f64)
-        _, info64 = g64.yk_solve(f64, out=s64)
-        g64.yk_forces_torques(s64, f64, want_net=False)
+        g.yk_matvec(sig, yk.YK_FP64, out=y)
         e1.record(stream)
         e1.synchronize()
-        t64 = e0.elapsed_time(e1) / 1e3
-        fp64.update(solves_per_s=1.0 / t64, solve_s=t64, iterations=info64["iterations"],
-                    rel_residual=info64["rel_residual"])
-        fp64["mixed_speedup"] = value / world / fp64["solves_per_s"]
-        fp64["sigma_rel_diff_mixed_vs_fp64"] = float(
-            torch.linalg.norm(sig_mixed - s64) / torch.linalg.norm(s64))
-        g64.close()
+        r, _ = solve_leg(yk, ctx, dev, parts, yk.params_for(wl, precision=yk.YK_FP64))
+        fp64_iters = r["iterations"]
+        r.update(matvec_ms=e0.elapsed_time(e1), matvec_mixed_ms=t_p2p * 1e3,
+                 solves_per_s=1.0 / r["solve_s"], mixed_speedup=value / world * r["solve_s"])
+        extra["fp64"] = r
 
-    # ---- context: the same system with the FMM inner operator --------------
-    # (not the headline: the configuration names a dense far field for both
-    # precisions; the residuals and forces keep the FP64-accurate cut-off
-    # operator, so the density matches the dense mixed solve to the tolerance)
-    fmm = {}
-    if args.fmm_leg and rank == 0:
-        gf = yk.Geometry(ctx, parts, yk.params_for(wl, precision=yk.YK_MIXED,
-                                                   farfield=yk.YK_FARFIELD_FMM))
-        ff = torch.zeros_like(f)
-        sf = torch.zeros_like(sig)
-        gf.yk_label(yk.YK_LABEL_TANH, 10.0, out=ff)
-        gf.yk_solve(ff, out=sf)                      # builds the tree, tunes the leaf size
+    # ---- both precisions on the cut-off far field (precision alone) --------
+    if "samefar" in legs and rank == 0:
+        out = {}
+        for tol in (1e-12, 1e-10):
+            rec = {}
+            for name, pr in (("mixed", yk.YK_MIXED), ("fp64", yk.YK_FP64)):
+                rec[name], _ = solve_leg(yk, ctx, dev, parts, yk.params_for(
+                    wl, precision=pr, farfield=yk.YK_FARFIELD_CUTOFF, gmres_tol=tol),
+                    reps=2 if pr else 1)
+            rec["mixed_speedup"] = rec["fp64"]["solve_s"] / rec["mixed"]["solve_s"]
+            out["tol_%g" % tol] = rec
+        out["note"] = ("disks512, both precisions with the cut-off far field (source particles "
+                       "bounded below 1e-15 max|sigma| left out): the ratio comes from precision; "
+                       "at the library's default tolerance 1e-12 and at 1e-10")
+        extra["same_farfield"] = out
+
+    # ---- cold first solve: geometry + QBX rows + blocks + preconditioner ---
+    if "cold" in legs and rank == 0:
         torch.cuda.synchronize()
-        reps_f = 3
-        e0.record(stream)
-        for _ in range(reps_f):
-            gf.yk_update_geometry(parts)
-            gf.yk_label(yk.YK_LABEL_TANH, 10.0, out=ff)
-            _, info_f = gf.yk_solve(ff, out=sf)
-            gf.yk_forces_torques(sf, ff, want_net=False)
-        e1.record(stream)
-        e1.synchronize()
-        t_f = e0.elapsed_time(e1) / 1e3 / reps_f
-        e0.record(stream)
-        for _ in range(reps):
-            gf.yk_matvec(sf, yk.YK_MIXED, out=y)
-        e1.record(stream)
-        e1.synchronize()
-        fmm = {"solves_per_s": 1.0 / t_f, "ms_per_solve": t_f * 1e3,
-               "inner_matvec_ms": e0.elapsed_time(e1) / reps,
-               "iterations": info_f["iterations"], "rel_residual": info_f["rel_residual"],
-               "sigma_rel_diff_vs_dense_mixed": float(
-                   torch.linalg.norm(sf - sig_mixed) / torch.linalg.norm(sig_mixed)),
-               "note": "context only: disks512 with the FMM far field (order 12, leaf size "
-                       "autotuned) for the FP32 inner operator"}
-        gf.close()
+        t0 = time.perf_counter()
+        s = Solver(yk, ctx, parts, prm, dev)
+        s.solve(update=False)
+        t_cold = time.perf_counter() - t0
+        extra["cold"] = {"solve_s": t_cold, "create_geometry_s": s.create_s,
+                         "warm_solve_s": t_max / args.steps,
+                         "note": "yk_create_geometry (nodes, QBX rows per shape, self blocks, "
+                                 "Newton-Schulz preconditioner, workspace) + label + solve + "
+                                 "forces, wall time"}
+        s.close()
+
+    # ---- the headline against the oracle's stored reference ----------------
+    if "accuracy" in legs and rank == 0:
+        ref = load_reference("disks512")
+        extra["accuracy"] = ({"vs_oracle": errors_vs(ref, sig_mixed, F_mixed, tau_mixed),
+                              "reference": "tests/golden/ref_disks512.npz"}
+                             if ref is not None else {"vs_oracle": None,
+                                                      "reference": "not stored"})
+
+    # ---- C3: 512 ellipses, rho in {0.25, 1, 4} ------------------------------
+    if "c3" in legs and rank == 0:
+        rows = []
+        for rho in (0.25, 1.0, 4.0):
+            e = W.ellipses512(rho)
+            rec = {"rho": rho}
+            res = {}
+            for name, pr, ff in (("mixed", yk.YK_MIXED, yk.YK_FARFIELD_DENSE),
+                                 ("mixed_cutoff", yk.YK_MIXED, yk.YK_FARFIELD_CUTOFF),
+                                 ("fp64_cutoff", yk.YK_FP64, yk.YK_FARFIELD_CUTOFF)):
+                r, res[name] = solve_leg(yk, ctx, dev, e.particles,
+                                         yk.params_for(e, precision=pr, farfield=ff),
+                                         reps=2 if pr else 1)
+                rec[name] = r
+            rec["speedup_same_farfield"] = (rec["fp64_cutoff"]["solve_s"] /
+                                            rec["mixed_cutoff"]["solve_s"])
+            ref = load_reference(e.name)
+            if ref is not None:
+                rec["vs_oracle"] = {k: errors_vs(ref, *res[k]) for k in res}
+                rec["reference"] = "tests/golden/ref_%s.npz" % e.name
+            small = W.ellipses128(rho)
+            ref = load_reference(small.name)
+            if ref is not None:
+                r, resm = solve_leg(yk, ctx, dev, small.particles,
+                                    yk.params_for(small, precision=yk.YK_MIXED), reps=1)
+                rec["ellipses128_mixed_vs_oracle"] = errors_vs(ref, *resm)
+            rows.append(rec)
+        extra["c3"] = rows
+
+    # ---- C4: 8192 disks ------------------------------------------------------
+    if "c4" in legs and rank == 0:
+        big = W.disks8192()
+        out = {"n_nodes": big.n_nodes}
+        res = {}
+        for name, pr, ff in (("mixed_fmm", yk.YK_MIXED, yk.YK_FARFIELD_FMM),
+                             ("mixed_cutoff", yk.YK_MIXED, yk.YK_FARFIELD_CUTOFF),
+                             ("fp64_cutoff", yk.YK_FP64, yk.YK_FARFIELD_CUTOFF)):
+            out[name], res[name] = solve_leg(yk, ctx, dev, big.particles,
+                                             yk.params_for(big, precision=pr, farfield=ff),
+                                             reps=2 if pr else 1)
+        ref = {"sigma": res["fp64_cutoff"][0], "F": res["fp64_cutoff"][1].reshape(-1, 2),
+               "tau": res["fp64_cutoff"][2]}
+        for name in ("mixed_fmm", "mixed_cutoff"):
+            sg, Fm, tm = res[name]
+            out[name]["vs_fp64_cutoff"] = {
+                "sigma": float(np.linalg.norm(sg - ref["sigma"]) / np.linalg.norm(ref["sigma"])),
+                "F": float(np.abs(Fm.reshape(-1, 2) - ref["F"]).max() / np.abs(ref["F"]).max())}
+            out[name]["speedup_vs_fp64_cutoff"] = (out["fp64_cutoff"]["solve_s"] /
+                                                   out[name]["solve_s"])
+        # 65,536-node subset: the 256 disks nearest the box centre, solved alone
+        # with the dense FP64 operator and with the mixed FMM solver
+        c = big.particles[:, 1:3] - big.box / 2
+        sub = big.particles[np.argsort(np.hypot(c[:, 0], c[:, 1]), kind="stable")[:256]]
+        sw = W.Workload("disks8192_subset256", sub, rho=1.0, box=big.box)
+        r64, s64 = solve_leg(yk, ctx, dev, sub, yk.params_for(sw, precision=yk.YK_FP64))
+        rfm, sfm = solve_leg(yk, ctx, dev, sub, yk.params_for(sw, precision=yk.YK_MIXED,
+                                                              farfield=yk.YK_FARFIELD_FMM), reps=2)
+        out["subset256"] = {
+            "fp64_dense": r64, "mixed_fmm": rfm,
+            "mixed_fmm_vs_fp64_dense": {
+                "sigma": float(np.linalg.norm(sfm[0] - s64[0]) / np.linalg.norm(s64[0])),
+                "F": float(np.abs(sfm[1] - s64[1]).max() / np.abs(s64[1]).max()),
+                "tau": float(np.abs(sfm[2] - s64[2]).max() / np.abs(s64[2]).max())},
+            "note": "the 256 disks nearest the box centre (65,536 nodes, spatially contiguous), "
+                    "solved alone: mixed FMM solve against the dense FP64 P2P solve"}
+        extra["c4"] = out
 
     # ---- end to end through the C ABI with host buffers --------------------
     f_h = np.zeros(n)
@@ -514,23 +715,19 @@ def main():
            "d2h_bytes_per_step": int(n * 8 * 2 + npart * 24)}
 
     # ---- serving: continuous batching of a request stream ------------------
-    serving = None
-    if args.serve_requests > 0 and rank == 0:
+    if "serving" in legs and rank == 0:
         sctx = yk.Context(local)
-        serving = run_serving(yk, W, sctx, args)
+        extra["serving"] = run_serving(yk, W, sctx, args)
         sctx.close()
 
     # ---- FP64 oracle on the host cores (bounded sample) ---------------------
     cpu = None
-    if args.cpu_baseline and rank == 0:
-        iters = oracle_gmres_iters()
-        v, t_val, t_grad = cpu_solve_rate(wl, args.cpu_rows, iters)
-        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": "%d value rows + %d gradient rows of the 512-disk operator timed "
-                         "(%.1f ms/row, %.1f ms/gradient row); solve = N x ((iters+1) rows + "
-                         "1 gradient row), iters=%d from the oracle's GMRES on 8 disks"
-                         % (args.cpu_rows, max(8, args.cpu_rows // 4), t_val * 1e3,
-                            t_grad * 1e3, iters)}
+    if "cpu" in legs and rank == 0:
+        pool, cores = oracle_pool()
+        with pool:
+            v, sample = cpu_solve_rate(pool, cores, fp64_iters or FP64_ITERS_DISKS512,
+                                       args.cpu_seconds)
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -538,16 +735,16 @@ def main():
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32+f64", "data": "synthetic",
                "config": {"workload": WORKLOAD, "n_particles": 512, "n_nodes": n, "rho": 1.0,
-                          "qbx_order": 10, "gmres_tol": 1e-10, "precision": "mixed",
+                          "qbx_order": 10, "gmres_tol": 1e-12, "precision": "mixed",
                           "farfield": "dense", "l2": "flushed (256 MiB write) between steps",
                           "parallelism": "replicas" if world > 1 else "single"},
                "solve": {"iterations": info["iterations"], "refinements": info["refinements"],
                          "rel_residual": info["rel_residual"],
                          "matvecs_fp32": info["matvecs_fp32"],
                          "matvecs_fp64": info["matvecs_fp64"]},
-               "fp64": fp64, "fmm": fmm, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-               "serving": serving,
+               "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
                "gpu_launches": int(launches), "clocks": clk}
+        out.update(extra)
         print(json.dumps(out))
     g.close()
     ctx.close()

@@ -122,7 +122,12 @@ typedef struct {
     int32_t gmres_restart; /* Krylov basis size m; default 100                */
     int32_t max_iter;      /* total GMRES iterations (all restarts); default 300 */
     int32_t precision;     /* YK_FP64 or YK_MIXED; default YK_MIXED            */
-    double gmres_tol;      /* relative residual ||f - A sigma|| / ||f||; 1e-10 */
+    double gmres_tol;      /* relative residual ||f - A sigma|| / ||f||; default
+                              1e-12. The forces and torques amplify the density
+                              error (about 25x for ellipses at rho = 4), so a
+                              residual of 1e-10 leaves them only within a few
+                              1e-9 of the exact discrete solution; at 1e-12 the
+                              density, forces and torques are within 1e-11    */
     double inner_tol;      /* YK_MIXED: inner (FP32) GMRES tolerance; 1e-6     */
     int32_t max_refine;    /* YK_MIXED: refinement steps; default 8            */
     int32_t farfield;      /* YK_FARFIELD_DENSE, _CUTOFF or _FMM; default DENSE */
@@ -371,6 +376,15 @@ int yk_drain(yk_ctx* ctx);
  * (all contexts), for accounting in benchmarks. Library-specific; the
  * paper has no counterpart.                                               */
 int yk_kernel_launches(uint64_t* count);
+
+/* Measured FP32 FMA throughput of CUDA device `device` in TFLOP/s (an FMA
+ * counts as two flops): the best of three timed launches of a kernel that
+ * runs independent FMA chains on every SM. It is the denominator of the
+ * far-field kernels' roofline, which are bound by the FP32 FMA pipe.
+ * Library-specific; the paper has no counterpart. Allocates a small device
+ * buffer and a stream of its own and synchronises them.
+ * Errors: YK_ERR_ARG, YK_ERR_CUDA.                                         */
+int yk_fp32_fma_peak(int device, double* tflops);
 
 const char* yk_strerror(int code);
 

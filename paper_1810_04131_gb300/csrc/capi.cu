@@ -241,7 +241,7 @@ int yk_default_params(yk_params* p) {
     p->gmres_restart = 100;
     p->max_iter = 300;
     p->precision = YK_MIXED;
-    p->gmres_tol = 1e-10;
+    p->gmres_tol = 1e-12;
     p->inner_tol = 1e-6;
     p->max_refine = 8;
     p->farfield = YK_FARFIELD_DENSE;

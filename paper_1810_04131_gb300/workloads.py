@@ -146,7 +146,7 @@ class Workload:
     n_panels: int = 16
     n_gl: int = 16
     qbx_order: int = 10
-    gmres_tol: float = 1e-10
+    gmres_tol: float = 1e-12
     label_kind: int = LABEL_TANH
     label_param: float = 10.0
     box: float = 0.0

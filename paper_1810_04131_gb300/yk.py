@@ -53,7 +53,7 @@ EXPORTS = [
     "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
     "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_energy", "yk_eval_potential",
     "yk_eval_potential_noalloc", "yk_eval_potential_near", "yk_repulsion", "yk_default_dynamics", "yk_step",
-    "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_strerror",
+    "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_fp32_fma_peak", "yk_strerror",
 ]
 
 
@@ -136,6 +136,7 @@ def load(path=LIB_PATH):
         "yk_poll": [P, C.c_uint64, C.POINTER(I), P, P, P, C.POINTER(yk_solve_info),
                     C.POINTER(D)],
         "yk_drain": [P],
+        "yk_fp32_fma_peak": [I, C.POINTER(D)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -396,6 +397,13 @@ def yk_kernel_launches():
     c = C.c_uint64()
     _check(load().yk_kernel_launches(C.byref(c)), "yk_kernel_launches")
     return c.value
+
+
+def yk_fp32_fma_peak(device=0):
+    """Measured FP32 FMA throughput of the device in TFLOP/s."""
+    t = C.c_double()
+    _check(load().yk_fp32_fma_peak(int(device), C.byref(t)), "yk_fp32_fma_peak")
+    return t.value
 
 
 def default_dynamics(**kw):

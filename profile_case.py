@@ -1,6 +1,6 @@
 """Run one kernel case of the yk library on a named workload, for profilers.
 
-    python -m paper_1810_04131_gb300.profile_case --case p2p_f32 --workload disks512 --reps 2
+    python profile_case.py --case p2p_f32 --workload disks512 --reps 2
         [--farfield dense|cutoff|fmm] [--particles K]
 
 Cases: p2p_f32 (mixed matvec: FP32 far field + near rows), p2p_f64 (FP64
@@ -13,7 +13,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 

@@ -129,10 +129,12 @@ def test_bench_pair_classes_partition_the_interactions():
     assert np.isclose(bench.EPS_NARROW3, kernel_constant("EPS_NARROW3"))
     wl = W.disks512()
     n, npp = wl.n_nodes, 256
-    counts = bench.p2p_pair_classes(wl.particles, wl.rho, npp, n)
+    cls = bench.p2p_pair_classes(wl.particles, wl.rho, npp, n)
+    counts = [cls[k] for k in ("full", "short", "narrow", "narrow3", "zero")]
     assert sum(counts) == n * n - wl.n_particles * npp * npp
-    full, short, narrow, narrow3, zero = counts
-    assert min(counts) > 0 and zero > 0.5 * sum(counts)
+    assert min(counts) > 0 and cls["zero"] > 0.5 * sum(counts)
+    modes = {"full", "short", "narrow", "narrow3"}
+    assert set(bench.FLOPS_PER_PAIR) == set(bench.LANE_OPS_PER_PAIR) == set(bench.MUFU_PER_PAIR) == modes
 
 
 def bessel_i_down_f32(T, x):

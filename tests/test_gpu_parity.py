@@ -4,10 +4,10 @@ the same seeded inputs.
 Tolerances (relative 2-norm unless stated):
   * FP64 matvec: 1e-12;
   * mixed (FP32 far field) matvec: 1e-6;
-  * density after a solve (run to a 1e-12 residual, so that the GMRES
-    error itself stays far below the bar; the condition number of the
-    discrete operator is about 100), and forces/torques (max-norm relative
-    to max |F|): 1e-9;
+  * density after a solve at the library's default tolerance (residual
+    1e-12; forces amplify the density error about 25x at rho = 4, which is
+    why the default is not 1e-10), and forces/torques (max-norm relative to
+    max |F|): 1e-9;
   * normal derivative: its rows cancel (entries ~10x the result), so the
     difference is bounded by 1e-12 |G| |sigma| and 1e-11 relative;
   * the FP32 far field of one distant source disk, row by row: 1e-6 +
@@ -120,7 +120,7 @@ def test_solve_forces_small(yk, ctx, dense_cache, name, precision):
     o, A, Gn = _oracle(wl, dense_cache)
     prec = yk.YK_FP64 if precision == "fp64" else yk.YK_MIXED
     # a 1e-12 residual keeps the solver's own error well inside the 1e-9 bar
-    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec, gmres_tol=1e-12))
+    g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec))
     f = g.yk_label(0, 10.0)
     sig, info = g.yk_solve(f)
     s_ref = np.linalg.solve(A, f)
@@ -158,7 +158,7 @@ def test_forces_are_minus_energy_gradient_gpu(yk, ctx):
     solves to 1e-12) against yk_forces_torques, as in the oracle's pin."""
     parts = W.make_particles(3, 7.0, 0.3, seed=11, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
     wl = W.Workload("fd3", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
-    g = yk.Geometry(ctx, parts, _params(yk, wl, gmres_tol=1e-12))
+    g = yk.Geometry(ctx, parts, _params(yk, wl))
 
     def solve(P):
         g.yk_update_geometry(P)
@@ -201,8 +201,7 @@ def test_block_preconditioner(yk, ctx, dense_cache, precision):
     s_ref = None
     its = {}
     for pc in (yk.YK_PRECOND_NONE, yk.YK_PRECOND_BLOCK):
-        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec, precond=pc,
-                                                   gmres_tol=1e-12))
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec, precond=pc))
         f = g.yk_label(0, 10.0)
         s, info = g.yk_solve(f)
         s_ref = np.linalg.solve(A, f) if s_ref is None else s_ref
@@ -222,7 +221,7 @@ def test_disks8_end_to_end(yk, ctx, dense_cache):
     F_ref, tau_ref, _ = o.forces_torques(f_ref, Gn @ s_ref)
     u_ref = o.potential(s_ref, wl.targets)
     for prec in (yk.YK_FP64, yk.YK_MIXED):
-        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec, gmres_tol=1e-12))
+        g = yk.Geometry(ctx, wl.particles, _params(yk, wl, precision=prec))
         f = g.yk_label(0, 10.0)
         assert np.abs(f - f_ref).max() < 1e-13
         sig, info = g.yk_solve(f)
@@ -263,7 +262,7 @@ def test_cutoff_far_field(yk, ctx, dense_cache):
             assert np.abs(un - Gn @ sig).max() <= 1e-12 * cond + 40 * tol * np.abs(sig).max() / wl.rho
         g.close()
     g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF,
-                                               precision=yk.YK_MIXED, gmres_tol=1e-12))
+                                               precision=yk.YK_MIXED))
     f = g.yk_label(0, 10.0)
     s, info = g.yk_solve(f)
     assert info["converged"] and rel(s, np.linalg.solve(A, f)) < 1e-9
@@ -330,7 +329,7 @@ def test_fmm_operator_and_solve(yk, ctx):
         assert np.abs(y64 - A @ sig).max() <= 20 * 1e-15 * np.abs(sig).max() + 1e-13
         g.close()
     g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_FMM, fmm_leaf=6.0,
-                                               precision=yk.YK_MIXED, gmres_tol=1e-12))
+                                               precision=yk.YK_MIXED))
     f = g.yk_label(0, 10.0)
     s, info = g.yk_solve(f)
     s_ref = np.linalg.solve(A, f)
@@ -386,7 +385,7 @@ def test_dynamics_steps_match_oracle(yk, ctx):
     step energies (Eq. main plus the repulsion potential) as well."""
     parts = W.make_particles(3, 7.0, 0.3, seed=11, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
     wl = W.Workload("dyn3", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
-    g = yk.Geometry(ctx, parts, _params(yk, wl, gmres_tol=1e-12))
+    g = yk.Geometry(ctx, parts, _params(yk, wl))
     dyn = dict(dt=0.5, c0=0.01, q=3, label_kind=1, label_param=2.0)
     d = yk.default_dynamics(**dyn)
     ref = parts.copy()
@@ -500,7 +499,7 @@ def test_forces_are_not_pairwise(yk, ctx):
     solver tolerance, as the paper reports."""
     parts = W.make_particles(6, 9.0, 0.3, seed=31, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
     wl = W.Workload("pair6", parts, rho=1.0, n_panels=16, n_gl=16, qbx_order=10)
-    g = yk.Geometry(ctx, parts, _params(yk, wl, gmres_tol=1e-12))
+    g = yk.Geometry(ctx, parts, _params(yk, wl))
     f = g.yk_label(0, 10.0)
     sig, F, tau, info = g.yk_solve_forces(f)
     F = F.reshape(-1, 2)
@@ -508,7 +507,7 @@ def test_forces_are_not_pairwise(yk, ctx):
     for i in range(6):
         for j in range(i + 1, 6):
             pair = parts[[i, j]]
-            g2 = yk.Geometry(ctx, pair, _params(yk, wl, gmres_tol=1e-12))
+            g2 = yk.Geometry(ctx, pair, _params(yk, wl))
             f2 = g2.yk_label(0, 10.0)
             _, F2, _, _ = g2.yk_solve_forces(f2)
             F2 = F2.reshape(-1, 2)
@@ -544,7 +543,7 @@ def test_near_contact_matches_oracle(yk, ctx, shape, gap):
     cond = (np.abs(Gn) @ np.abs(sig)).max()
     for prec in ("fp64", "mixed"):
         p_ = yk.YK_FP64 if prec == "fp64" else yk.YK_MIXED
-        g = yk.Geometry(ctx, parts, _params(yk, wl, precision=p_, gmres_tol=1e-12))
+        g = yk.Geometry(ctx, parts, _params(yk, wl, precision=p_))
         y64 = g.yk_matvec(sig, yk.YK_FP64)
         assert rel(y64, A_ @ sig) < 1e-12
         assert rel(g.yk_matvec(sig, yk.YK_MIXED), A_ @ sig) < 1e-6
