@@ -156,7 +156,7 @@ def parse():
                     help="comma-separated legs beyond the timed steps (or 'none')")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="CPU time budget of the oracle sample (all cores)")
-    ap.add_argument("--serve-requests", type=int, default=500,
+    ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests per arrival rate, from the seeded serving stream")
     ap.add_argument("--serve-lambdas", default="0.5,0.7,0.9",
                     help="arrival rates as fractions of the measured saturation rate")
@@ -336,6 +336,20 @@ def combine_ranks(t_local, steps, world, dist=None, device=None):
     return t_max, world * steps / t_max
 
 
+class LegTimer:
+    """Wall time of each leg, reported in the JSON line and on stderr."""
+
+    def __init__(self):
+        self.t = {}
+        self.t0 = time.perf_counter()
+
+    def done(self, name):
+        now = time.perf_counter()
+        self.t[name] = round(now - self.t0, 1)
+        print("bench: %s done (%.1f s)" % (name, now - self.t0), file=sys.stderr, flush=True)
+        self.t0 = now
+
+
 def load_reference(name):
     """The oracle's stored solution of a named system (written by
     tests/golden/make_reference_solution.py), or None."""
@@ -473,6 +487,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     legs = set() if args.legs == "none" else set(x for x in args.legs.split(",") if x)
+    legt = LegTimer()
     import torch
     from paper_1810_04131_gb300 import workloads as W
     from paper_1810_04131_gb300 import yk
@@ -494,7 +509,13 @@ def main():
     if world > 1 and rank > 0:  # an independent replica per rank
         parts = W.make_particles(512, 200.0, 0.3, seed=1000 + rank)
     prm = yk.params_for(wl, precision=yk.YK_MIXED)
+    # the first geometry of these shapes in the process: a cold set-up (QBX
+    # rows, self blocks and preconditioner formed, not taken from the cache)
+    torch.cuda.synchronize()
+    t_create0 = time.perf_counter()
     g = yk.Geometry(ctx, parts, prm)
+    torch.cuda.synchronize()
+    t_create_cold = time.perf_counter() - t_create0
     n, npart = g.n, g.n_particles
     f = torch.zeros(n, dtype=torch.float64, device=dev)
     sig = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -583,6 +604,7 @@ def main():
 
     extra = {}
     fp64_iters = None
+    legt.done("timed steps + roofline")
     # ---- plain FP64 path: the same system, dense far field -----------------
     if "fp64" in legs and rank == 0:
         e0.record(stream)
@@ -595,6 +617,8 @@ def main():
                  solves_per_s=1.0 / r["solve_s"], mixed_speedup=value / world * r["solve_s"])
         extra["fp64"] = r
 
+    if "fp64" in legs:
+        legt.done("fp64")
     # ---- both precisions on the cut-off far field (precision alone) --------
     if "samefar" in legs and rank == 0:
         out = {}
@@ -611,20 +635,25 @@ def main():
                        "at the library's default tolerance 1e-12 and at 1e-10")
         extra["same_farfield"] = out
 
+    if "samefar" in legs:
+        legt.done("samefar")
     # ---- cold first solve: geometry + QBX rows + blocks + preconditioner ---
     if "cold" in legs and rank == 0:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s = Solver(yk, ctx, parts, prm, dev)
-        s.solve(update=False)
-        t_cold = time.perf_counter() - t0
-        extra["cold"] = {"solve_s": t_cold, "create_geometry_s": s.create_s,
-                         "warm_solve_s": t_max / args.steps,
-                         "note": "yk_create_geometry (nodes, QBX rows per shape, self blocks, "
-                                 "Newton-Schulz preconditioner, workspace) + label + solve + "
-                                 "forces, wall time"}
+        s = Solver(yk, ctx, parts, prm, dev)      # the shapes' set-up now comes from the cache
+        t_solve = s.solve(update=False)
+        extra["cold"] = {"solve_s": t_create_cold + t_solve,
+                         "create_geometry_cold_s": t_create_cold,
+                         "create_geometry_cached_shapes_s": s.create_s,
+                         "first_solve_s": t_solve, "warm_solve_s": t_max / args.steps,
+                         "note": "cold = the process's first yk_create_geometry of these shapes "
+                                 "(nodes, QBX rows, self blocks, Newton-Schulz preconditioner, "
+                                 "workspace) + label + solve + forces on a new geometry, wall time; "
+                                 "a later geometry of the same shapes copies the per-shape arrays "
+                                 "from the library's shape cache"}
         s.close()
 
+    if "cold" in legs:
+        legt.done("cold")
     # ---- the headline against the oracle's stored reference ----------------
     if "accuracy" in legs and rank == 0:
         ref = load_reference("disks512")
@@ -633,6 +662,8 @@ def main():
                              if ref is not None else {"vs_oracle": None,
                                                       "reference": "not stored"})
 
+    if "accuracy" in legs:
+        legt.done("accuracy")
     # ---- C3: 512 ellipses, rho in {0.25, 1, 4} ------------------------------
     if "c3" in legs and rank == 0:
         rows = []
@@ -662,6 +693,8 @@ def main():
             rows.append(rec)
         extra["c3"] = rows
 
+    if "c3" in legs:
+        legt.done("c3")
     # ---- C4: 8192 disks ------------------------------------------------------
     if "c4" in legs and rank == 0:
         big = W.disks8192()
@@ -700,6 +733,8 @@ def main():
                     "solved alone: mixed FMM solve against the dense FP64 P2P solve"}
         extra["c4"] = out
 
+    if "c4" in legs:
+        legt.done("c4")
     # ---- end to end through the C ABI with host buffers --------------------
     f_h = np.zeros(n)
     torch.cuda.synchronize()
@@ -714,12 +749,15 @@ def main():
            "h2d_bytes_per_step": int(parts.shape[0] * 48 + n * 8),
            "d2h_bytes_per_step": int(n * 8 * 2 + npart * 24)}
 
+    legt.done("e2e")
     # ---- serving: continuous batching of a request stream ------------------
     if "serving" in legs and rank == 0:
         sctx = yk.Context(local)
         extra["serving"] = run_serving(yk, W, sctx, args)
         sctx.close()
 
+    if "serving" in legs:
+        legt.done("serving")
     # ---- FP64 oracle on the host cores (bounded sample) ---------------------
     cpu = None
     if "cpu" in legs and rank == 0:
@@ -728,6 +766,7 @@ def main():
             v, sample = cpu_solve_rate(pool, cores, fp64_iters or FP64_ITERS_DISKS512,
                                        args.cpu_seconds)
         cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+        legt.done("cpu")
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -743,7 +782,7 @@ def main():
                          "matvecs_fp32": info["matvecs_fp32"],
                          "matvecs_fp64": info["matvecs_fp64"]},
                "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-               "gpu_launches": int(launches), "clocks": clk}
+               "gpu_launches": int(launches), "clocks": clk, "leg_seconds": legt.t}
         out.update(extra)
         print(json.dumps(out))
     g.close()

@@ -47,25 +47,55 @@ def _boundary_samples(p, m=4096):
     return np.stack([p[1] + c * u - s * v, p[2] + s * u + c * v], axis=1)
 
 
-def _gap(p, q):
-    """Minimum distance between two particle boundaries (disks exact, ellipses sampled)."""
+def _gap_at_least(p, q, gap):
+    """Whether the surface gap of two particles (disks exact; ellipses as the
+    smallest distance between 4096 samples of p's boundary and every fourth of
+    4096 samples of q's) is at least ``gap``.
+
+    Bounding circles at least gap apart accept at once (every sampled
+    distance is at least theirs). Otherwise the samples are grouped around
+    every 16th one: a sample lies within 8 sample steps, so within
+    8 (2 pi max(A, B) / 4096) of its group's centre, and a pair of groups
+    whose centres are d apart holds no sampled pair closer than d minus both
+    bounds. Only the groups that could hold a pair closer than gap are
+    compared sample by sample, which gives exactly the answer of comparing
+    all of them."""
     d = math.hypot(p[1] - q[1], p[2] - q[2])
     if p[0] == SHAPE_DISK and q[0] == SHAPE_DISK:
-        return d - p[4] - q[4]
-    # conservative pre-check: bounding circles already far apart
+        return d - p[4] - q[4] >= gap
     ra, rb = max(p[4], p[5]), max(q[4], q[5])
-    if d - ra - rb > 0.0:
-        lo = d - ra - rb
-        if lo >= 1.0:  # far beyond any gap used here; exact value not needed
-            return lo
-    a = _boundary_samples(p)
-    b = _boundary_samples(q)
-    diff = a[:, None, :] - b[None, ::4, :]
-    return float(np.sqrt((diff ** 2).sum(-1)).min())
+    if d - ra - rb >= gap:   # bounding circles: every boundary distance is at least this
+        return True
+    a, b = _boundary_samples(p), _boundary_samples(q)
+    m = a.shape[0]
+    dc = np.sqrt(((a[::16, None, :] - b[None, ::16, :]) ** 2).sum(-1))
+    if dc.min() < gap:       # group centres are samples themselves
+        return False
+    slack = 8.0 * 2.0 * math.pi * (ra + rb) / m
+    gi, gj = np.nonzero(dc - slack < gap)
+    if gi.size == 0:
+        return True
+    ia = (16 * gi[:, None] + np.arange(-8, 9)[None, :]) % m          # p's samples
+    jb = (16 * gj[:, None] + np.arange(-8, 9, 4)[None, :]) % m       # q's, every fourth
+    diff = a[ia][:, :, None, :] - b[jb][:, None, :, :]
+    return bool(np.sqrt((diff ** 2).sum(-1)).min() >= gap)
+
+
+_PLACED = {}
 
 
 def make_particles(n, box, gap, seed, shape=SHAPE_DISK, A=1.0, B=1.0,
                    shapes=None, max_tries=2_000_000):
+    """Rejection-sample ``n`` non-overlapping particles in ``[0, box]^2``
+    (memoised per process: the same arguments return a copy of the same
+    array)."""
+    key = (n, box, gap, seed, shape, A, B, None if shapes is None else tuple(shapes), max_tries)
+    if key not in _PLACED:
+        _PLACED[key] = _place(n, box, gap, seed, shape, A, B, shapes, max_tries)
+    return _PLACED[key].copy()
+
+
+def _place(n, box, gap, seed, shape, A, B, shapes, max_tries):
     """Rejection-sample ``n`` non-overlapping particles in ``[0, box]^2``.
 
     Centres are uniform in ``[R, box - R]^2`` (R = max semi-axis) and a
@@ -95,7 +125,7 @@ def make_particles(n, box, gap, seed, shape=SHAPE_DISK, A=1.0, B=1.0,
         for ix in range(gx - 1, gx + 2):
             for iy in range(gy - 1, gy + 2):
                 for j in grid.get((ix, iy), ()):
-                    if _gap(cand, out[j]) < gap:
+                    if not _gap_at_least(cand, out[j], gap):
                         ok = False
                         break
                 if not ok:
