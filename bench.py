@@ -40,6 +40,7 @@ import json
 import multiprocessing as mp
 import os
 import platform
+import re
 import subprocess
 import sys
 import threading
@@ -156,7 +157,7 @@ def parse():
                     help="comma-separated legs beyond the timed steps (or 'none')")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="CPU time budget of the oracle sample (all cores)")
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests per arrival rate, from the seeded serving stream")
     ap.add_argument("--serve-lambdas", default="0.5,0.7,0.9",
                     help="arrival rates as fractions of the measured saturation rate")
@@ -360,6 +361,16 @@ def load_reference(name):
     return {k: z[k] for k in z.files}
 
 
+def reference_meta(ref):
+    """Metadata of a stored reference: JSON, or (older files) a Python repr
+    whose numpy scalars are printed as np.float64(...)."""
+    text = str(ref["meta"])
+    try:
+        return json.loads(text)
+    except ValueError:
+        return ast.literal_eval(re.sub(r"np\.float64\(([^)]*)\)", r"\1", text))
+
+
 def errors_vs(ref, sigma, F, tau):
     """Relative errors: 2-norm for sigma, max-norm (relative to max |ref|)
     for forces and torques."""
@@ -367,7 +378,7 @@ def errors_vs(ref, sigma, F, tau):
     return {"sigma": float(np.linalg.norm(sigma - ref["sigma"]) / np.linalg.norm(ref["sigma"])),
             "F": float(np.abs(F - ref["F"]).max() / np.abs(ref["F"]).max()),
             "tau": float(np.abs(tau - ref["tau"]).max() / np.abs(ref["tau"]).max()),
-            "oracle_gmres_tol": float(ast.literal_eval(str(ref["meta"]))["tol"])}
+            "oracle_gmres_tol": float(reference_meta(ref)["tol"])}
 
 
 class Solver:

@@ -304,6 +304,7 @@ int yk_destroy_geometry(yk_geom* g) {
     free_workspace(g);
     cudaStream_t st = g->ctx->stream;
     for (auto& L : g->lists) dev_free(L.d, st);
+    for (auto& L : g->sym) dev_free(L.d, st);
     dev_free(g->nbr_off, st);
     dev_free(g->nbr, st);
     fmm_free(g);

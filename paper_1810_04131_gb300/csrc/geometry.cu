@@ -6,7 +6,11 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <utility>
+#include <vector>
 
 #include "bessel.cuh"
 #include "yk_internal.cuh"
@@ -659,6 +663,7 @@ int update_nodes(yk_geom* g) {
     YK_LAUNCH(k_particle_info, g->np, 256, 0, st, g->np, g->npp, d_parts, g->d_w, g->d_part,
               g->d_c32, g->d_r32);
     for (auto& L : g->lists) L.valid = false;   // particle pairs change when particles move
+    for (auto& L : g->sym) L.valid = false;
     g->nbr_valid = false;
     g->fmm.valid = false;                       // the quadtree follows the particles
     for (auto& B : g->bands) B.valid = false;
@@ -666,6 +671,153 @@ int update_nodes(yk_geom* g) {
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     return YK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Per-shape precomputation shared across geometries. A rigid shape's QBX
+// rows (value and normal derivative), its self blocks and the inverse of its
+// self-interaction block depend on the shape, the discretisation and rho,
+// not on where the particle sits or how it is turned. A process-wide cache,
+// per device, keeps them keyed by every parameter they depend on, so that a
+// geometry whose shapes were seen before (the same shapes solved again, a
+// stream of requests drawn from a few shapes) copies them instead of forming
+// the QBX coefficients and running the Newton-Schulz inversion again. The
+// first geometry of a shape computes and inserts it. Entries are device
+// buffers of their own (cudaMalloc), evicted least recently used beyond
+// SHAPE_CACHE_BYTES; they live until evicted or the process exits.
+// ---------------------------------------------------------------------------
+constexpr size_t SHAPE_CACHE_BYTES = (size_t)4 << 30;
+
+struct ShapeKey {
+    int device, npan, ngl, near_w, os, order, precond, use_self;
+    double A, B, r_factor, rho;
+    bool operator<(const ShapeKey& o) const {
+        return std::tie(device, npan, ngl, near_w, os, order, precond, use_self, A, B, r_factor,
+                        rho) < std::tie(o.device, o.npan, o.ngl, o.near_w, o.os, o.order,
+                                        o.precond, o.use_self, o.A, o.B, o.r_factor, o.rho);
+    }
+};
+
+struct ShapeEntry {
+    void* buf = nullptr;     // rows (cval, cgrad), blocks (self, self_grad, minv), FP32 blocks
+    size_t bytes = 0;
+    uint64_t last_use = 0;
+};
+
+static std::mutex g_shape_mutex;
+static std::map<ShapeKey, ShapeEntry> g_shape_cache;
+static size_t g_shape_bytes = 0;
+static uint64_t g_shape_clock = 0;
+
+// Byte offsets of one shape's arrays inside an entry's buffer.
+struct ShapeLayout {
+    size_t rows, blk, cval, cgrad, self, self_grad, minv, self32, minv32, total;
+    explicit ShapeLayout(const yk_geom* g) {
+        const bool has_self = g->use_self, has_pc = g->prm.precond == YK_PRECOND_BLOCK;
+        rows = (size_t)g->npp * g->n_near * g->ngl * sizeof(double);
+        blk = (size_t)g->npp * g->npp;
+        cval = 0;
+        cgrad = cval + rows;
+        self = cgrad + rows;
+        self_grad = self + (has_self ? blk * sizeof(double) : 0);
+        minv = self_grad + (has_self ? blk * sizeof(double) : 0);
+        self32 = minv + (has_pc ? blk * sizeof(double) : 0);
+        minv32 = self32 + (has_self ? blk * sizeof(float) : 0);
+        total = minv32 + (has_pc ? blk * sizeof(float) : 0);
+    }
+};
+
+static ShapeKey shape_key(const yk_geom* g, int s) {
+    ShapeKey k;
+    k.device = g->ctx->device;
+    k.npan = g->npan;
+    k.ngl = g->ngl;
+    k.near_w = g->prm.near_width;
+    k.os = g->prm.oversample;
+    k.order = g->prm.qbx_order;
+    k.precond = g->prm.precond;
+    k.use_self = g->use_self ? 1 : 0;
+    k.A = g->shape_ab[s].x;
+    k.B = g->shape_ab[s].y;
+    k.r_factor = g->prm.qbx_r_factor;
+    k.rho = g->prm.rho;
+    return k;
+}
+
+// Copy shape s's arrays between the geometry and a cache buffer (to_cache:
+// geometry -> buffer), on the geometry's stream.
+static int shape_copy(yk_geom* g, int s, char* buf, bool to_cache) {
+    const ShapeLayout L(g);
+    cudaStream_t st = g->ctx->stream;
+    const size_t rs = L.rows / sizeof(double), bs = L.blk;
+    struct Part {
+        void* geom;
+        size_t off, bytes;
+    } parts[] = {
+        {g->d_cval + s * rs, L.cval, L.rows},
+        {g->d_cgrad + s * rs, L.cgrad, L.rows},
+        {g->use_self ? (void*)(g->d_self + s * bs) : nullptr, L.self, bs * sizeof(double)},
+        {g->use_self ? (void*)(g->d_self_grad + s * bs) : nullptr, L.self_grad, bs * sizeof(double)},
+        {g->d_minv ? (void*)(g->d_minv + s * bs) : nullptr, L.minv, bs * sizeof(double)},
+        {g->use_self ? (void*)(g->d_self32 + s * bs) : nullptr, L.self32, bs * sizeof(float)},
+        {g->d_minv32 ? (void*)(g->d_minv32 + s * bs) : nullptr, L.minv32, bs * sizeof(float)},
+    };
+    for (const Part& p : parts) {
+        if (!p.geom) continue;
+        void* dst = to_cache ? (void*)(buf + p.off) : p.geom;
+        const void* src = to_cache ? (const void*)p.geom : (const void*)(buf + p.off);
+        YK_TRY_CUDA(cudaMemcpyAsync(dst, src, p.bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    return YK_OK;
+}
+
+// Fill every shape's arrays from the cache; true if all shapes were there.
+static bool shapes_from_cache(yk_geom* g) {
+    std::lock_guard<std::mutex> lk(g_shape_mutex);
+    std::vector<ShapeEntry*> hit;
+    for (int s = 0; s < g->nshape; ++s) {
+        auto it = g_shape_cache.find(shape_key(g, s));
+        if (it == g_shape_cache.end()) return false;
+        hit.push_back(&it->second);
+    }
+    for (int s = 0; s < g->nshape; ++s) {
+        hit[s]->last_use = ++g_shape_clock;
+        if (shape_copy(g, s, (char*)hit[s]->buf, false) != YK_OK) return false;
+    }
+    // the copies are stream-ordered; an entry is freed only after a device
+    // synchronisation (cudaFree), so it outlives them
+    return true;
+}
+
+static void shapes_to_cache(yk_geom* g) {
+    const ShapeLayout L(g);
+    std::lock_guard<std::mutex> lk(g_shape_mutex);
+    for (int s = 0; s < g->nshape; ++s) {
+        const ShapeKey k = shape_key(g, s);
+        if (g_shape_cache.count(k)) continue;
+        while (g_shape_bytes + L.total > SHAPE_CACHE_BYTES && !g_shape_cache.empty()) {
+            auto lru = g_shape_cache.begin();
+            for (auto it = g_shape_cache.begin(); it != g_shape_cache.end(); ++it)
+                if (it->second.last_use < lru->second.last_use) lru = it;
+            cudaFree(lru->second.buf);   // synchronises the device: no copy from it is pending
+            g_shape_bytes -= lru->second.bytes;
+            g_shape_cache.erase(lru);
+        }
+        if (L.total > SHAPE_CACHE_BYTES) return;
+        ShapeEntry e;
+        if (cudaMalloc(&e.buf, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            return;   // no room: the geometry keeps its own copy, nothing is cached
+        }
+        if (shape_copy(g, s, (char*)e.buf, true) != YK_OK) {
+            cudaFree(e.buf);
+            return;
+        }
+        e.bytes = L.total;
+        e.last_use = ++g_shape_clock;
+        g_shape_bytes += e.bytes;
+        g_shape_cache[k] = e;
+    }
 }
 
 int build_geometry(yk_geom* g) {
@@ -676,6 +828,11 @@ int build_geometry(yk_geom* g) {
     YK_LAUNCH(k_ref_matrices, 1, 256, 0, st, g->ngl, os, g->d_glx, g->d_glw, g->d_fine_x,
               g->d_fine_w, g->d_interp, g->d_diff);
     YK_TRY(update_nodes(g));
+    if (shapes_from_cache(g)) {
+        YK_TRY_CUDA(cudaGetLastError());
+        YK_TRY_CUDA(cudaStreamSynchronize(st));
+        return YK_OK;
+    }
     const int nf = g->n_near * os * g->ngl;
     const size_t smem = 2 * sizeof(double) * nf;
     if (smem > 48 * 1024)
@@ -695,6 +852,8 @@ int build_geometry(yk_geom* g) {
     }
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY(build_preconditioner(g));
+    YK_TRY_CUDA(cudaStreamSynchronize(st));
+    shapes_to_cache(g);
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     return YK_OK;
 }

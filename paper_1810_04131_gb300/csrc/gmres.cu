@@ -4,8 +4,13 @@
 // GMRES: Arnoldi with classical Gram-Schmidt applied twice (CGS2) on an
 // FP64 Krylov basis, Givens rotations on the Hessenberg matrix, restart
 // after m steps. Every vector operation, the rotations and the small
-// triangular solve run on the device; the host reads one residual estimate
-// per iteration to decide whether to stop.
+// triangular solve run on the device. The host enqueues up to
+// GMRES_BATCH Arnoldi steps at a time, as many as the residual's recent
+// rate of decrease says are still needed, and then reads the residual
+// estimates those steps left in a device history. Steps after the first
+// one that met the tolerance only write later Hessenberg columns and
+// right-hand-side entries, so the solution is formed from the steps up to
+// that one, exactly as if the host had stopped there.
 //
 // Mixed: sigma <- sigma + GMRES_32(r), r = f - A_64 sigma, where A_32 is
 // the FP32-far-field operator (accurate to about 1e-6) and A_64 the
@@ -63,10 +68,11 @@ __global__ void k_sub_proj(double* __restrict__ w, const double* __restrict__ V,
 
 // One Arnoldi column: H[:, j] = h1 + h2, H[j+1, j] = ||w||, previous
 // rotations, a new rotation, and the residual estimate |g[j+1]|.
-// status[0] = residual estimate, status[1] = ||w|| (before normalisation).
+// status[0] = residual estimate, status[1] = ||w|| (before normalisation);
+// hist[2 j], hist[2 j + 1] keep the same two numbers for step j.
 __global__ void k_arnoldi_col(int j, int ldh, double* H, const double* h1, const double* h2,
                               const double* wn2, double* cs, double* sn, double* g,
-                              double* status) {
+                              double* status, double* hist) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double* col = H + (int64_t)j * ldh;
     for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];
@@ -92,14 +98,17 @@ __global__ void k_arnoldi_col(int j, int ldh, double* H, const double* h1, const
     g[j + 1] = -s * g[j];
     g[j] = c * g[j];
     status[0] = fabs(g[j + 1]);
+    hist[2 * j] = status[0];
+    hist[2 * j + 1] = hn;
 }
 
-// dst = src / s[0]  (s[0] > 0), or dst = src * scale when s == nullptr
+// dst = src / s[0] (unchanged when s[0] = 0, an exact breakdown), or
+// dst = src * scale when s == nullptr
 __global__ void k_scale(double* dst, const double* src, int64_t n, const double* s,
                         double scale) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double f = s ? 1.0 / s[0] : scale;
+    const double f = s ? (s[0] > 0.0 ? 1.0 / s[0] : 1.0) : scale;
     dst[i] = src[i] * f;
 }
 
@@ -172,6 +181,7 @@ int alloc_workspace(yk_geom* g) {
     YK_TRY(dev_alloc((void**)&w.ybuf, sizeof(double) * (m + 1), st));
     YK_TRY(dev_alloc((void**)&w.dotpart, sizeof(double) * (m + 2) * w.dot_blocks, st));
     YK_TRY(dev_alloc((void**)&w.status, sizeof(double) * 8, st));
+    YK_TRY(dev_alloc((void**)&w.hist, sizeof(double) * 2 * (m + 1), st));
     for (int k = 0; k < 8; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n, st));
     if (!host_status(g->ctx)) return YK_ERR_NO_MEMORY;
     return YK_OK;
@@ -191,6 +201,7 @@ void free_workspace(yk_geom* g) {
     dev_free(w.ybuf, st);
     dev_free(w.dotpart, st);
     dev_free(w.status, st);
+    dev_free(w.hist, st);
     for (int k = 0; k < 8; ++k) dev_free(w.vec[k], st);
     w = Workspace{};
 }
@@ -211,6 +222,33 @@ static int read_status(yk_geom* g, double* s0, double* s1) {
     *s0 = hs[0];
     *s1 = hs[1];
     return YK_OK;
+}
+
+// Arnoldi steps enqueued before the host looks at the residuals (at most
+// four (residual, norm) pairs fit the pinned status mirror).
+constexpr int GMRES_BATCH = 4;
+
+// Reads the history of steps [j0, j0 + k) into res[], hn[].
+static int read_hist(yk_geom* g, int j0, int k, double* res, double* hn) {
+    cudaStream_t st = g->ctx->stream;
+    double* hs = g->ctx->h_status;
+    YK_TRY_CUDA(cudaMemcpyAsync(hs, g->ws.hist + 2 * j0, 2 * k * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+    YK_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < k; ++i) {
+        res[i] = hs[2 * i];
+        hn[i] = hs[2 * i + 1];
+    }
+    return YK_OK;
+}
+
+// Steps to enqueue next: as many as a geometric decrease at the last
+// observed rate needs to reach tol_abs, less one, within [1, GMRES_BATCH].
+static int next_batch(double res, double prev, double tol_abs) {
+    if (!(prev > 0.0) || !(res > 0.0) || !(res < prev)) return 1;
+    const double need = log(tol_abs / res) / log(res / prev);
+    if (!(need > 2.0)) return 1;
+    return (int)std::min<double>(GMRES_BATCH, floor(need - 1.0));
 }
 
 // GMRES on A(prec) x = b with initial guess x (x_zero: x is taken as 0).
@@ -249,32 +287,46 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
         YK_LAUNCH(k_scale, nb, 256, 0, st, w.V, r, n, w.status + 1, 0.0);
         int j = 0;
         bool done = false;
-        for (; j < m && total < max_iter; ++j) {
-            double* vj = w.V + (int64_t)j * n;
-            double* wv = w.V + (int64_t)(j + 1) * n;
-            if (pc) {   // right preconditioning: w = A M^{-1} v_j
-                YK_TRY(apply_preconditioner(g, vj, w.vec[6], prec == Prec::F32));
-                vj = w.vec[6];
+        double prev = beta;
+        int batch = 1;
+        while (j < m && total < max_iter && !done) {
+            const int k = std::min(batch, std::min(m - j, max_iter - total));
+            for (int b = 0; b < k; ++b) {
+                const int jj = j + b;
+                double* vj = w.V + (int64_t)jj * n;
+                double* wv = w.V + (int64_t)(jj + 1) * n;
+                if (pc) {   // right preconditioning: w = A M^{-1} v_j
+                    YK_TRY(apply_preconditioner(g, vj, w.vec[6], prec == Prec::F32));
+                    vj = w.vec[6];
+                }
+                YK_TRY(matvec(g, vj, wv, prec));
+                ++*matvecs;
+                // CGS2
+                dots(g, w.V, jj + 1, wv, h1);
+                YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, jj + 1, h1);
+                dots(g, w.V, jj + 1, wv, h2);
+                YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, jj + 1, h2);
+                dots(g, wv, 1, wv, w.status + 2);
+                YK_LAUNCH(k_arnoldi_col, 1, 32, 0, st, jj, ldh, w.H, h1, h2, w.status + 2, w.cs,
+                          w.sn, w.gvec, w.status, w.hist);
+                YK_LAUNCH(k_scale, nb, 256, 0, st, wv, wv, n, w.status + 1, 0.0);
             }
-            YK_TRY(matvec(g, vj, wv, prec));
-            ++*matvecs;
-            // CGS2
-            dots(g, w.V, j + 1, wv, h1);
-            YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, j + 1, h1);
-            dots(g, w.V, j + 1, wv, h2);
-            YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, j + 1, h2);
-            dots(g, wv, 1, wv, w.status + 2);
-            YK_LAUNCH(k_arnoldi_col, 1, 32, 0, st, j, ldh, w.H, h1, h2, w.status + 2, w.cs, w.sn,
-                                            w.gvec, w.status);
-            double hn;
-            YK_TRY(read_status(g, &res, &hn));
-            ++total;
-            if (hn > 0.0) YK_LAUNCH(k_scale, nb, 256, 0, st, wv, wv, n, w.status + 1, 0.0);
-            if (res <= tol_abs || hn == 0.0 || !isfinite(res)) {
-                done = true;
-                ++j;
-                break;
+            double rs[GMRES_BATCH], hs[GMRES_BATCH];
+            YK_TRY(read_hist(g, j, k, rs, hs));
+            int used = k;   // steps kept: up to the first that stops the cycle
+            for (int b = 0; b < k; ++b) {
+                if (rs[b] <= tol_abs || hs[b] == 0.0 || !isfinite(rs[b])) {
+                    used = b + 1;
+                    done = true;
+                    break;
+                }
             }
+            res = rs[used - 1];
+            const double before = used >= 2 ? rs[used - 2] : prev;
+            prev = rs[used - 1];
+            j += used;
+            total += used;
+            batch = done ? 1 : next_batch(res, before, tol_abs);
         }
         // x += V y
         YK_LAUNCH(k_tri_solve, 1, 32, 0, st, j, ldh, w.H, w.gvec, w.ybuf);

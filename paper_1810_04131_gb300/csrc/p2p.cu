@@ -47,6 +47,53 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
     return YK_OK;
 }
 
+// The particle pairs of the symmetric FP32 far field (k_p2p_f32_sym), sorted
+// by P: kind 0 for the inner operator, kind 1 for the precision-split
+// residual (pairs of the FP64 tiles left out). Built on first use and after
+// the particles move.
+static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
+    PairList& L = g->sym[kind];
+    if (!L.valid) {
+        cudaStream_t st = g->ctx->stream;
+        GeomView G = g->view();
+        const bool mask = kind == 1;
+        const double gap = mask ? g->split_gap : 0.0;
+        int* counts = (int*)g->ws.partial;   // 2 np + 1 ints of scratch (partial holds >= n doubles)
+        int* off = counts + g->np;
+        YK_LAUNCH(k_sym_count, ceil_div(g->np, 128), 128, 0, st, G, mask, gap, counts);
+        YK_LAUNCH(k_scan_offsets, 1, 1024, 0, st, g->np, counts, off);
+        int n = 0;
+        YK_TRY_CUDA(cudaMemcpyAsync(&n, off + g->np, sizeof(int), cudaMemcpyDeviceToHost, st));
+        YK_TRY_CUDA(cudaStreamSynchronize(st));
+        if (n > L.cap) {
+            dev_free(L.d, st);
+            L.d = nullptr;
+            L.cap = 0;
+            YK_TRY(dev_alloc((void**)&L.d, sizeof(int2) * (size_t)n, st));
+            L.cap = n;
+        }
+        if (n > 0) YK_LAUNCH(k_sym_fill, ceil_div(g->np, 128), 128, 0, st, G, mask, gap, off, L.d);
+        YK_TRY_CUDA(cudaGetLastError());
+        L.n = n;
+        L.valid = true;
+    }
+    *list = L.d;
+    *count = L.n;
+    return YK_OK;
+}
+
+// FP32 far field of the dense operator by the symmetric kernel, added to out.
+static int far_sym(yk_geom* g, int kind, double* out) {
+    const int2* list;
+    int ntasks;
+    YK_TRY(sym_list(g, kind, &list, &ntasks));
+    if (ntasks == 0) return YK_OK;
+    const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);   // units of PairF32
+    YK_LAUNCH(k_p2p_f32_sym, ceil_div(ntasks, SYM_TASKS), F32_TPB, 0, g->ctx->stream, g->view(),
+              g->ws.src4, list, ntasks, ks, out);
+    return YK_OK;
+}
+
 static int tiles_grid(int ntiles) { return std::max(1, std::min(ntiles, 152 * 16)); }
 
 // Own-particle far pairs of the FP64 operators: the precomputed self blocks
@@ -293,14 +340,18 @@ static int matvec_body(yk_geom* g, const double* sigma, double* y, Prec prec) {
     const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);   // units of PairF32
     double* extra = nullptr;
     int used_chunks = nchunk;
-    if (prec == Prec::F32) {
+    if (prec == Prec::F32 && g->use_self) {
+        // own-particle far pairs by the FP32 self block, all other pairs by
+        // the symmetric kernel
+        YK_TRY(stage_sources(g, sigma));
+        extra = g->ws.vec[5];
+        YK_TRY(self_blocks_f32(g, sigma, extra, false));
+        YK_TRY(far_sym(g, 0, extra));
+        used_chunks = 0;
+    } else if (prec == Prec::F32) {
         YK_TRY(stage_sources(g, sigma));
         YK_LAUNCH(k_p2p_f32<false>, grid, F32_TPB, 0, st, G, g->ws.src4, ppc, (float)ks, 0.0,
                   g->use_self, g->ws.partial);
-        if (g->use_self) {
-            extra = g->ws.vec[5];
-            YK_TRY(self_blocks_f32(g, sigma, extra, false));
-        }
     } else {
         const int kind = (prec == Prec::F64) ? 2 : 0;
         const int2* list;
@@ -309,13 +360,11 @@ static int matvec_body(yk_geom* g, const double* sigma, double* y, Prec prec) {
         extra = g->ws.vec[5];
         YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
         YK_TRY(self_blocks(g, sigma, extra, false));
-        if (prec == Prec::SPLIT) {
+        if (prec == Prec::SPLIT) {   // pairs beyond the split distance in FP32
             YK_TRY(stage_sources(g, sigma));
-            YK_LAUNCH(k_p2p_f32<true>, grid, F32_TPB, 0, st, G, g->ws.src4, ppc, (float)ks,
-                      g->split_gap, false, g->ws.partial);
-        } else {
-            used_chunks = 0;
+            YK_TRY(far_sym(g, 1, extra));
         }
+        used_chunks = 0;
         YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
                   extra);
         if (prec == Prec::SPLIT) YK_TRY(band_expansions(g, sigma, extra, false));

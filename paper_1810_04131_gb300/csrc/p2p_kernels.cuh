@@ -600,6 +600,273 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
 }
 
 // ---------------------------------------------------------------------------
+// Symmetric FP32 far field of the dense operator (k_p2p_f32_sym).
+//
+// For nodes i of particle P and j of particle Q, d = x_i - y_j and
+// g = w sigma nu, the two double-layer terms (Eq. double-layer-def) are
+//   K(x_i, y_j) g_j = c(r) (d . g_j),   K(y_j, x_i) g_i = c(r) (-d . g_i),
+// with the same radial factor c(r) = K1(r/rho) / (2 pi rho r), which carries
+// all the special-function work (1/z', exp2, the K1 fit or expansion). The
+// kernel takes a list of particle pairs (P, Q), P < Q, sorted by P, and
+// evaluates c once per node pair for both directions: about 10 FMA-pipe lane
+// operations and 1.5 MUFU operations per interaction instead of 17 and 3.
+//
+// Per block: 128 threads, SYM_TASKS consecutive pairs of the list. P's nodes
+// sit in registers (warp w holds nodes 64 w + l and 64 w + 32 + l of the
+// chunk in lane l), Q's nodes in shared memory as the packed source records
+// (two nodes per record). Q's side rotates: in group b of 32 records, at
+// step k lane l evaluates record 32 b + ((l + k) mod 32), so the 32 lanes
+// read 32 distinct records (no bank conflicts) and each record's reverse
+// sums are held by exactly one lane. After every step each lane passes its
+// reverse sums to lane l - 1 (a warp shuffle); after 32 steps every record's
+// sums are back in lane (record mod 32), complete over the warp's 64 nodes
+// of P. The four warps' sums are added in shared memory and go to Q's nodes;
+// P's sums stay in FP64 registers while consecutive pairs share P. Both go
+// to an FP64 buffer by atomic adds (the order of those adds, and so the last
+// bits of the result, vary from run to run).
+//
+// Particle-pair classes as in k_p2p_f32 (same FP32 arithmetic on the pair's
+// range [gap, far]): pairs whose every term is an exact FP32 zero are not
+// listed; close pairs (gap <= 2 rho) evaluate pairs with z <= 2 by the K1
+// series; otherwise the full or short fit or the narrow expansions.
+// ---------------------------------------------------------------------------
+constexpr int SYM_TASKS = 8;     // particle pairs per block
+constexpr int CLOSE = 8;         // pair mode: some node pairs may have z <= 2
+
+// The radial factor of two packed pairs (one target, two sources) in the
+// units of PairF32::far without the dot product, and the scaled separations.
+template <int NC>
+__device__ __forceinline__ float2 coef2(float2 TX, float2 TY, const float4& A, const PolyRZ& P,
+                                        float2& dX, float2& dY) {
+    dX = __fadd2_rn(TX, make_float2(A.x, A.y));
+    dY = __fadd2_rn(TY, make_float2(A.z, A.w));
+    const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
+    const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));   // 1/z'
+    const float2 zp = __fmul2_rn(z2, rz);                                 // z'
+    if constexpr (NC == NARROW || NC == NARROW3) {
+        const float2 u = __ffma2_rn(rz, P.c[5], P.c[6]);                  // rz/rc - 1
+        constexpr int top = (NC == NARROW) ? 4 : 3;
+        float2 q = P.c[top];
+#pragma unroll
+        for (int k = top - 1; k >= 0; --k) q = __ffma2_rn(q, u, P.c[k]); // rz^{1/2} P1(rz)
+        const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
+        return __fmul2_rn(__fmul2_rn(e, q), rz);
+    } else {
+        float2 p = P.c[NC - 1];
+#pragma unroll
+        for (int k = NC - 2; k >= 0; --k) p = __ffma2_rn(p, rz, P.c[k]); // P1 in rz
+        const float2 e = make_float2(ex2_fast(-zp.x), ex2_fast(-zp.y));
+        const float2 sq = make_float2(rsqrt_fast(zp.x), rsqrt_fast(zp.y));   // z'^{-1/2}
+        return __fmul2_rn(__fmul2_rn(__fmul2_rn(e, p), sq), rz);
+    }
+}
+
+// The radial factor of one pair for any z (the series of PairF32::any for
+// z <= 2), same units as coef2.
+__device__ __forceinline__ float coef_any(float dX, float dY) {
+    const float z2 = fmaf(dX, dX, dY * dY);
+    const float rz = rsqrt_fast(z2);
+    const float zp = z2 * rz;
+    const float z = zp * (1.0f / LOG2E_F);
+    if (z > 2.0f) {
+        const float s = fmaf(4.0f * LOG2E_F, rz, -1.0f);     // 2t - 1
+        const float P = hornerf(YK_P1_F32, s);
+        return (ex2_fast(-zp) * P * rsqrt_fast(zp)) * rz;
+    }
+    return k1f(z, 2.0f / z) * rsqrtf(LOG2E_F) * rz;
+}
+
+// One target against one packed record (two sources): forward sums into fw
+// (one lane per source), reverse sums of the two sources into rv. NG = -g of
+// the target, in both lanes.
+template <int NC>
+__device__ __forceinline__ void sym_pair(float2 TX, float2 TY, float2 NGX, float2 NGY,
+                                         const float4& A, const float4& B, const PolyRZ& P,
+                                         float2& fw, float2& rv) {
+    float2 dX, dY, c;
+    if constexpr (NC == CLOSE) {
+        dX = __fadd2_rn(TX, make_float2(A.x, A.y));
+        dY = __fadd2_rn(TY, make_float2(A.z, A.w));
+        const float z2x = fmaf(dX.x, dX.x, dY.x * dY.x), z2y = fmaf(dX.y, dX.y, dY.y * dY.y);
+        if (z2x > ZCUT2 && z2y > ZCUT2) c = coef2<FIT_LONG>(TX, TY, A, P, dX, dY);
+        else c = make_float2(coef_any(dX.x, dY.x), coef_any(dX.y, dY.y));
+    } else {
+        c = coef2<NC>(TX, TY, A, P, dX, dY);
+    }
+    const float2 dj = __ffma2_rn(dX, make_float2(B.x, B.y), __fmul2_rn(dY, make_float2(B.z, B.w)));
+    const float2 di = __ffma2_rn(dX, NGX, __fmul2_rn(dY, NGY));
+    fw = __ffma2_rn(c, dj, fw);
+    rv = __ffma2_rn(c, di, rv);
+}
+
+// All rotation groups of one staged chunk of Q for the lane's two targets.
+template <int NC>
+__device__ __forceinline__ void sym_chunk(const float4* qA, const float4* qB, int ngrp, int lane,
+                                          float TX0, float TY0, float TX1, float TY1, float NGX0,
+                                          float NGY0, float NGX1, float NGY1, const PolyRZ& P,
+                                          float2& fw0, float2& fw1, float* rsum_w) {
+    const float2 tx0 = make_float2(TX0, TX0), ty0 = make_float2(TY0, TY0);
+    const float2 tx1 = make_float2(TX1, TX1), ty1 = make_float2(TY1, TY1);
+    const float2 ngx0 = make_float2(NGX0, NGX0), ngy0 = make_float2(NGY0, NGY0);
+    const float2 ngx1 = make_float2(NGX1, NGX1), ngy1 = make_float2(NGY1, NGY1);
+    const int next = (lane + 1) & 31;
+    for (int b = 0; b < ngrp; ++b) {
+        float2 rv = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+            const int m = 32 * b + ((lane + k) & 31);
+            const float4 A = qA[m], B = qB[m];
+            sym_pair<NC>(tx0, ty0, ngx0, ngy0, A, B, P, fw0, rv);
+            sym_pair<NC>(tx1, ty1, ngx1, ngy1, A, B, P, fw1, rv);
+            rv.x = __shfl_sync(0xffffffffu, rv.x, next);
+            rv.y = __shfl_sync(0xffffffffu, rv.y, next);
+        }
+        // record 32 b + lane: Q nodes 64 b + 2 lane and 64 b + 2 lane + 1 of the chunk
+        rsum_w[64 * b + 2 * lane] = rv.x;
+        rsum_w[64 * b + 2 * lane + 1] = rv.y;
+    }
+}
+
+__global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const float4* __restrict__ rec,
+                                                           const int2* __restrict__ tasks,
+                                                           int ntasks, double kscale,
+                                                           double* __restrict__ out) {
+    __shared__ float4 qA[STILE / 2], qB[STILE / 2];
+    __shared__ float rsum[F32_TPB / 32][STILE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float kpf = (float)(LOG2E / G.rho);
+    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
+    const float short_gap = Z_SHORT * (float)G.rho;
+    const int hp = (G.npp + 1) >> 1;
+    const int t0 = blockIdx.x * SYM_TASKS, t1 = min(ntasks, t0 + SYM_TASKS);
+    const int lt0 = 64 * warp + lane, lt1 = lt0 + 32;   // the lane's targets in a chunk
+    int curP = -1, curC = 0;                            // owner of the FP64 forward sums
+    double f0 = 0.0, f1 = 0.0;
+    for (int t = t0; t < t1; ++t) {
+        const int2 pq = tasks[t];
+        const int P = pq.x, Q = pq.y;
+        const PairRange rg = block_range(G, P, P, Q);   // block-uniform
+        float rc = 0.0f;
+        const int mode = (rg.gap <= near_gap) ? CLOSE : far_mode(rg, short_gap, kpf, rc);
+        const PolyRZ Pz(mode == CLOSE ? FIT_LONG : mode, rc);
+        const float4 cp = G.c32[P], cq = G.c32[Q];
+        const float oX = kpf * ((cp.x - cq.x) + (cp.z - cq.z));
+        const float oY = kpf * ((cp.y - cq.y) + (cp.w - cq.w));
+        for (int pc = 0; pc < G.npp; pc += STILE) {
+            if (P != curP || pc != curC) {
+                if (curP >= 0) {
+                    const int64_t b = (int64_t)curP * G.npp + curC;
+                    if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+                    if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+                }
+                curP = P;
+                curC = pc;
+                f0 = f1 = 0.0;
+            }
+            // the lane's two targets of P: scaled position relative to Q's centre, -g
+            float TX[2], TY[2], NGX[2], NGY[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int li = pc + (h ? lt1 : lt0);
+                if (li < G.npp) {
+                    const int64_t r = 2 * ((int64_t)P * hp + (li >> 1));
+                    const float4 A = rec[r], B = rec[r + 1];
+                    const bool odd = li & 1;
+                    TX[h] = oX - (odd ? A.y : A.x);
+                    TY[h] = oY - (odd ? A.w : A.z);
+                    NGX[h] = -(odd ? B.y : B.x);
+                    NGY[h] = -(odd ? B.w : B.z);
+                } else {   // no node: far away and weightless
+                    TX[h] = 3.0e6f;
+                    TY[h] = 0.0f;
+                    NGX[h] = NGY[h] = 0.0f;
+                }
+            }
+            for (int qc = 0; qc < G.npp; qc += STILE) {
+                const int cnt = min(STILE, G.npp - qc);
+                const int npair = (cnt + 1) >> 1;
+                const int ngrp = (npair + 31) >> 5;
+                __syncthreads();   // previous chunk's shared data fully used
+                const float4* rq = rec + 2 * ((int64_t)Q * hp + (qc >> 1));
+                for (int m = threadIdx.x; m < 32 * ngrp; m += blockDim.x) {
+                    if (m < npair) {
+                        qA[m] = rq[2 * m];
+                        qB[m] = rq[2 * m + 1];
+                    } else {       // padding records: far away and weightless
+                        qA[m] = make_float4(1.0e6f, 1.0e6f, 0.0f, 0.0f);
+                        qB[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+                }
+                __syncthreads();
+                float2 fw0 = make_float2(0.0f, 0.0f), fw1 = fw0;
+                float* rw = rsum[warp];
+                switch (mode) {
+                    case NARROW3:
+                        sym_chunk<NARROW3>(qA, qB, ngrp, lane, TX[0], TY[0], TX[1], TY[1], NGX[0],
+                                           NGY[0], NGX[1], NGY[1], Pz, fw0, fw1, rw);
+                        break;
+                    case NARROW:
+                        sym_chunk<NARROW>(qA, qB, ngrp, lane, TX[0], TY[0], TX[1], TY[1], NGX[0],
+                                          NGY[0], NGX[1], NGY[1], Pz, fw0, fw1, rw);
+                        break;
+                    case FIT_SHORT:
+                        sym_chunk<FIT_SHORT>(qA, qB, ngrp, lane, TX[0], TY[0], TX[1], TY[1],
+                                             NGX[0], NGY[0], NGX[1], NGY[1], Pz, fw0, fw1, rw);
+                        break;
+                    case CLOSE:
+                        sym_chunk<CLOSE>(qA, qB, ngrp, lane, TX[0], TY[0], TX[1], TY[1], NGX[0],
+                                         NGY[0], NGX[1], NGY[1], Pz, fw0, fw1, rw);
+                        break;
+                    default:
+                        sym_chunk<FIT_LONG>(qA, qB, ngrp, lane, TX[0], TY[0], TX[1], TY[1],
+                                            NGX[0], NGY[0], NGX[1], NGY[1], Pz, fw0, fw1, rw);
+                }
+                f0 += (double)(fw0.x + fw0.y);
+                f1 += (double)(fw1.x + fw1.y);
+                __syncthreads();   // every warp's reverse sums are in rsum
+                for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+                    const float v = (rsum[0][j] + rsum[1][j]) + (rsum[2][j] + rsum[3][j]);
+                    atomicAdd(&out[(int64_t)Q * G.npp + qc + j], (double)v * kscale);
+                }
+            }
+        }
+    }
+    if (curP >= 0) {
+        const int64_t b = (int64_t)curP * G.npp + curC;
+        if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+        if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+    }
+}
+
+// Particle pairs of the symmetric far field: P < Q, not every term an exact
+// FP32 zero (the kernels' FP32 gap test), and, with a skip distance, not a
+// pair of the FP64 tiles. Counted per P, then listed in order of Q.
+__device__ __forceinline__ bool sym_pair_listed(const GeomView& G, int P, int Q, float zero_gap,
+                                                bool mask, double skip_gap) {
+    if (block_range(G, P, P, Q).gap >= zero_gap) return false;
+    return !(mask && pair_in_tiles(G.part[P], G.part[Q], skip_gap));
+}
+
+__global__ void k_sym_count(GeomView G, bool mask, double skip_gap, int* __restrict__ counts) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= G.np) return;
+    const float zero_gap = ZP_ZERO / (float)(LOG2E / G.rho);
+    int c = 0;
+    for (int Q = P + 1; Q < G.np; ++Q) c += sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap);
+    counts[P] = c;
+}
+
+__global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __restrict__ off,
+                           int2* __restrict__ tasks) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= G.np) return;
+    const float zero_gap = ZP_ZERO / (float)(LOG2E / G.rho);
+    int k = off[P];
+    for (int Q = P + 1; Q < G.np; ++Q)
+        if (sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap)) tasks[k++] = make_int2(P, Q);
+}
+
+// ---------------------------------------------------------------------------
 // Cut-off far field: one block per target particle, sweeping only the source
 // particles in its neighbour list (bounding-circle gap below the cut-off);
 // the block owns all its targets, so it writes complete sums. Same pair

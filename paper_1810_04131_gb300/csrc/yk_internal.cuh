@@ -51,6 +51,7 @@ struct Workspace {
     double* ybuf = nullptr;      // m+1 least-squares coefficients
     double* dotpart = nullptr;   // partial dots [(m+2)][nblk]
     double* status = nullptr;    // [0] residual estimate, [1] norm, [2..] scratch
+    double* hist = nullptr;      // (residual estimate, norm) of every Arnoldi step, 2 (m+1)
     double* vec[8] = {};         // N-length scratch vectors
     int m = 0;
     int dot_blocks = 0;
@@ -181,6 +182,7 @@ struct yk_geom {
     float* d_r32 = nullptr;
     int* d_counter = nullptr;
     yk::PairList lists[4];                 // residual split, gradient split, all, cut-off
+    yk::PairList sym[2];                   // symmetric FP32 far field: inner operator, split
     int* d_shape_of = nullptr;
     double2* d_shape_ab = nullptr;
     double* d_x = nullptr;

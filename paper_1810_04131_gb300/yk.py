@@ -12,6 +12,7 @@ library detects which per pointer.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 import weakref
@@ -97,6 +98,17 @@ class YKError(RuntimeError):
 
 
 _lib = None
+_exiting = False
+
+
+@atexit.register
+def _stop_calls_at_exit():
+    """From interpreter exit on, handles dropped during teardown make no
+    library call: the CUDA runtime may already be shut down by then (atexit
+    handlers run before the objects still alive are finalised). The driver
+    releases what such handles held when the process ends."""
+    global _exiting
+    _exiting = True
 
 
 def load(path=LIB_PATH):
@@ -218,6 +230,8 @@ class Context:
             self.h = None
 
     def __del__(self):
+        if _exiting:
+            return
         try:
             self.close()
         except Exception:
@@ -271,6 +285,8 @@ class Geometry:
             self.h = None
 
     def __del__(self):
+        if _exiting:
+            return
         try:
             self.close()
         except Exception:

@@ -35,8 +35,11 @@ Usage (hours of CPU at N = 131,072):
 from __future__ import annotations
 
 import argparse
+import ast
 import hashlib
+import json
 import multiprocessing as mp
+import re
 import os
 import platform
 import sys
@@ -71,6 +74,16 @@ def _self_block(args):
     row, n_panels, n_gl, rho, order = args
     o = yo.Oracle(row[None, :], n_panels, n_gl, rho, yo.QBXParams(order=order))
     return np.linalg.inv(o.dense())
+
+
+def read_meta(z):
+    """The metadata dictionary of a stored reference (JSON; files written
+    before the switch to JSON hold a Python repr with numpy scalars)."""
+    text = str(z["meta"])
+    try:
+        return json.loads(text)
+    except ValueError:
+        return ast.literal_eval(re.sub(r"np\.float64\(([^)]*)\)", r"\1", text))
 
 
 class PooledOperator:
@@ -164,7 +177,7 @@ def main():
                 particles_sha256=hashlib.sha256(np.ascontiguousarray(wl.particles).tobytes()).hexdigest(),
                 script="tests/golden/make_reference_solution.py")
     np.savez_compressed(out, particles=wl.particles, f=f, sigma=sigma, u_nu=un, F=F, tau=tau,
-                        tau0=tau0, meta=np.array(repr(meta)))
+                        tau0=tau0, meta=np.array(json.dumps(meta)))
     print("wrote %s (%s)" % (out, meta), flush=True)
 
 
