@@ -54,19 +54,26 @@ sys.path.insert(0, ROOT)
 METRIC = "Yukawa-QBX solves/s mixed vs FP64 @1e-9 rel err; P2P %FMA peak; p50/p99 latency"
 WORKLOAD = "disks512"
 GOLDEN = os.path.join(ROOT, "tests", "golden")
-# FP32 operations per far-field pair in the P2P inner loop, in two counts:
-# flops (FMA = 2, FADD/FMUL = 1) on the FMA pipe, and FMA-pipe lane
-# operations (each FMA, FADD or FMUL = 1); MUFU operations (1/z', exp2,
-# z'^{-1/2}) are listed apart. Full fit: d = x - y (2 FADD), |d|^2 (FMA +
-# FMUL), z' (FMUL), K1 polynomial in 1/z' (6 FMA; 3 with the short fit for
-# z >= 10), the three-factor product (2 FMUL), (d.g) (FMA + FMUL), 1/z' (d.g)
-# (FMUL), accumulate (FMA); MUFU: 1/z', exp2, z'^{-1/2}. Narrow class (1/z'
-# within 1 +- 0.07 of its centre): the z'^{-1/2} MUFU and the polynomial are
-# replaced by u = rz/rc - 1 (FMA) and a degree-4 (degree-3 within 1 +- 0.03)
-# polynomial in u, one product fewer.
+# Algorithmic work of the far field: FP32 flops per interaction (one
+# (target, source) evaluation of the double-layer kernel, FMA = 2,
+# FADD/FMUL = 1, MUFU operations not counted), as a kernel that evaluates
+# every interaction on its own needs them. Full fit: d = x - y (2), |d|^2 (3),
+# z' (1), K1 polynomial in 1/z' (6 FMA = 12; 3 FMA with the short fit for
+# z >= 10), the three-factor product (2), (d.g) (3), 1/z' (d.g) (1),
+# accumulate (2); MUFU: 1/z', exp2, z'^{-1/2}. Narrow class (1/z' within
+# 1 +- 0.07 of its centre): u = rz/rc - 1 (2) and a degree-4 (degree-3
+# within 1 +- 0.03) polynomial in u replace the z'^{-1/2} MUFU and the K1
+# polynomial, one product fewer.
 FLOPS_PER_PAIR = {"full": 26, "short": 20, "narrow": 23, "narrow3": 21}
-LANE_OPS_PER_PAIR = {"full": 17, "short": 14, "narrow": 15, "narrow3": 14}
-MUFU_PER_PAIR = {"full": 3, "short": 3, "narrow": 2, "narrow3": 2}
+# What the symmetric kernel (k_p2p_f32_sym) executes per interaction: one
+# node pair serves two interactions; per node pair d (2), |d|^2 (3), z' (1),
+# the polynomial (12 / 6 / 10 / 8), the radial factor (3 products; 2 for the
+# narrow classes), two dot products (6) and two accumulations (4) -> flops
+# per interaction 15.5 / 12.5 / 15 / 14; FMA-pipe lane operations (each FMA,
+# FADD or FMUL lane = 1) 10 / 8.5 / 9 / 8.5; MUFU 1.5 / 1.5 / 1 / 1.
+EXEC_FLOPS_PER_PAIR = {"full": 15.5, "short": 12.5, "narrow": 15.0, "narrow3": 14.0}
+LANE_OPS_PER_PAIR = {"full": 10.0, "short": 8.5, "narrow": 9.0, "narrow3": 8.5}
+MUFU_PER_PAIR = {"full": 1.5, "short": 1.5, "narrow": 1.0, "narrow3": 1.0}
 EPS_NARROW = 0.07
 EPS_NARROW3 = 0.03
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
@@ -590,6 +597,7 @@ def main():
     n_eval = sum(cls[k] for k in FLOPS_PER_PAIR)
     interactions = n * (n - 3 * 16)          # every far (target, source) pair of the operator
     flops = sum(cls[k] * FLOPS_PER_PAIR[k] for k in FLOPS_PER_PAIR)
+    exec_flops = sum(cls[k] * EXEC_FLOPS_PER_PAIR[k] for k in EXEC_FLOPS_PER_PAIR)
     lane_ops = sum(cls[k] * LANE_OPS_PER_PAIR[k] for k in LANE_OPS_PER_PAIR)
     mufu = sum(cls[k] * MUFU_PER_PAIR[k] for k in MUFU_PER_PAIR)
     peak = yk.yk_fp32_fma_peak(local)        # measured: FMA chains on every SM, TFLOP/s
@@ -597,14 +605,21 @@ def main():
     clock_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": stored_traffic(),
-                "kernel": "k_p2p_f32 (yk_matvec YK_MIXED: + k_src_pairs, k_assemble)",
+                "kernel": "k_p2p_f32_sym (yk_matvec YK_MIXED: + k_src_pairs, k_self_apply_f32, "
+                          "k_assemble)",
                 "peak_note": "measured: yk_fp32_fma_peak (independent FMA chains on every SM, "
-                             "FMA = 2 flops), same GPU, same run; achieved counts the FMA-pipe "
-                             "flops of the pairs the kernel evaluates (MUFU operations excluded; "
-                             "a pair whose exp2 underflows adds exactly 0 in FP32 and is "
-                             "skipped by particle)",
+                             "FMA = 2 flops), same GPU, same run; achieved = the algorithmic "
+                             "FP32 flops of the interactions evaluated (flops_per_pair: what "
+                             "evaluating each interaction on its own takes, MUFU operations "
+                             "excluded) per second; an interaction whose exp2 underflows adds "
+                             "exactly 0 in FP32 and is skipped by particle pair; the symmetric "
+                             "kernel executes fewer flops per interaction "
+                             "(executed_flops_per_pair), one node-pair evaluation serving both "
+                             "directions",
                 "pairs_evaluated_per_launch": n_eval, "pairs_by_class": cls,
-                "flops_per_pair": FLOPS_PER_PAIR, "fma_lane_ops_per_pair": LANE_OPS_PER_PAIR,
+                "flops_per_pair": FLOPS_PER_PAIR, "executed_flops_per_pair": EXEC_FLOPS_PER_PAIR,
+                "executed_tflops": exec_flops / t_p2p / 1e12,
+                "fma_lane_ops_per_pair": LANE_OPS_PER_PAIR,
                 "mufu_ops_per_pair": MUFU_PER_PAIR,
                 "pairs_evaluated_per_s": n_eval / t_p2p,
                 "interactions_per_s": interactions / t_p2p,

@@ -30,16 +30,19 @@ constexpr int EXP_ORDER = EXPANSION_TERMS - 1;   // terms |n|, |m| <= EXP_ORDER
 constexpr int EXP_N = EXPANSION_TERMS;
 
 // P2M: one warp per particle.
-__global__ void k_p2m(GeomView G, const double* __restrict__ sigma, double2* __restrict__ M) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// wpp warps per particle, each over every wpp-th group of 32 of its nodes,
+// adding its part of the moments to M (zeroed before the launch).
+__global__ void k_p2m(GeomView G, const double* __restrict__ sigma, int wpp,
+                      double2* __restrict__ M) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= G.np) return;
-    const int p = warp;
+    if (gw >= G.np * wpp) return;
+    const int p = gw / wpp, part = gw % wpp;
     const d4 c = G.part[p];
     const double rinv = 1.0 / G.rho;
     double mre[EXP_N], mim[EXP_N], I[EXP_N + 1];
     for (int n = 0; n < EXP_N; ++n) mre[n] = mim[n] = 0.0;
-    for (int l = lane; l < G.npp; l += 32) {
+    for (int l = 32 * part + lane; l < G.npp; l += 32 * wpp) {
         const int64_t j = (int64_t)p * G.npp + l;
         const double ex = G.x[j] - c.x, ey = G.y[j] - c.y;
         const double s = sqrt(ex * ex + ey * ey);
@@ -68,7 +71,11 @@ __global__ void k_p2m(GeomView G, const double* __restrict__ sigma, double2* __r
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        if (lane == 0) M[(int64_t)p * EXP_N + n] = make_double2(a, b);
+        if (lane == 0) {
+            double* m = reinterpret_cast<double*>(M + (int64_t)p * EXP_N + n);
+            atomicAdd(m, a);
+            atomicAdd(m + 1, b);
+        }
     }
 }
 
@@ -285,7 +292,11 @@ int band_expansions(yk_geom* g, const double* sigma, double* out, bool grad) {
     if (g->bands[kind].n == 0) return YK_OK;
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
-    YK_LAUNCH(k_p2m, ceil_div((int64_t)g->np * 32, 128), 128, 0, st, G, sigma, g->d_mpole);
+    // warps per particle: enough for about 32 warps per SM in all
+    const int wpp = std::max(1, std::min(ceil_div(152 * 32, g->np), ceil_div(g->npp, 32)));
+    YK_TRY_CUDA(cudaMemsetAsync(g->d_mpole, 0, sizeof(double2) * (size_t)g->np * EXP_N, st));
+    YK_LAUNCH(k_p2m, ceil_div((int64_t)g->np * wpp * 32, 128), 128, 0, st, G, sigma, wpp,
+              g->d_mpole);
     YK_LAUNCH(k_band_m2l, g->np, 32 * M2L_WARPS, 0, st, G, g->d_mpole, g->bands[kind].off,
               g->bands[kind].idx, g->d_local);
     if (grad)

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "bessel.cuh"
+#include "block_apply.cuh"
 #include "yk_internal.cuh"
 
 namespace yk {
@@ -497,25 +498,6 @@ __global__ void k_ns_store(int n, const float* __restrict__ X, double* __restric
     minv32[(int64_t)s * n * n + e] = v;
 }
 
-// y_P = inv(block of P's shape) x_P, one CTA per particle.
-template <typename T>
-__global__ void k_block_apply(int np, int npp, const int* __restrict__ shape_of,
-                              const T* __restrict__ minv, const double* __restrict__ x,
-                              double* __restrict__ y) {
-    extern __shared__ unsigned char smraw[];
-    T* xs = reinterpret_cast<T*>(smraw);
-    const int p = blockIdx.x;
-    const int64_t base = (int64_t)p * npp;
-    for (int j = threadIdx.x; j < npp; j += blockDim.x) xs[j] = (T)x[base + j];
-    __syncthreads();
-    const T* M = minv + (int64_t)shape_of[p] * npp * npp;
-    for (int i = threadIdx.x; i < npp; i += blockDim.x) {
-        T acc = 0;
-        for (int j = 0; j < npp; ++j) acc += M[(int64_t)j * npp + i] * xs[j];
-        y[base + i] = (double)acc;
-    }
-}
-
 __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -642,12 +624,14 @@ int build_preconditioner(yk_geom* g) {
 
 int apply_preconditioner(yk_geom* g, const double* x, double* y, bool fp32) {
     cudaStream_t st = g->ctx->stream;
+    // y_P = inv(block of P's shape) x_P
+    const dim3 grid(g->np, ceil_div(g->npp, BAPPLY_ROWS));
     if (fp32)
-        YK_LAUNCH(k_block_apply<float>, g->np, 256, sizeof(float) * g->npp, st, g->np, g->npp,
-                  g->d_shape_of, g->d_minv32, x, y);
+        YK_LAUNCH((k_blocks_apply<float, false>), grid, BAPPLY_ROWS * BAPPLY_SLICES,
+                  blocks_apply_smem<float>(g->npp), st, g->npp, g->d_shape_of, g->d_minv32, x, y);
     else
-        YK_LAUNCH(k_block_apply<double>, g->np, 256, sizeof(double) * g->npp, st, g->np, g->npp,
-                  g->d_shape_of, g->d_minv, x, y);
+        YK_LAUNCH((k_blocks_apply<double, false>), grid, BAPPLY_ROWS * BAPPLY_SLICES,
+                  blocks_apply_smem<double>(g->npp), st, g->npp, g->d_shape_of, g->d_minv, x, y);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

@@ -89,29 +89,52 @@ static int far_sym(yk_geom* g, int kind, double* out) {
     YK_TRY(sym_list(g, kind, &list, &ntasks));
     if (ntasks == 0) return YK_OK;
     const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);   // units of PairF32
-    YK_LAUNCH(k_p2p_f32_sym, ceil_div(ntasks, SYM_TASKS), F32_TPB, 0, g->ctx->stream, g->view(),
-              g->ws.src4, list, ntasks, ks, out);
+    // Q-node ranges as short as 64 until there are work items for about
+    // eight blocks per SM; up to SYM_TASKS items per block beyond that
+    const int64_t npc = ceil_div(g->npp, STILE);
+    int qch = STILE;
+    while (qch > 64 && (int64_t)ntasks * npc * ceil_div(g->npp, qch) < 152 * 8) qch /= 2;
+    const int64_t items = (int64_t)ntasks * npc * ceil_div(g->npp, qch);
+    const int ipb = (int)std::max<int64_t>(1, std::min<int64_t>(SYM_TASKS, items / (152 * 12)));
+    YK_LAUNCH(k_p2p_f32_sym, (unsigned)ceil_div(items, ipb), F32_TPB, 0, g->ctx->stream, g->view(),
+              g->ws.src4, list, ntasks, qch, ipb, ks, out);
     return YK_OK;
 }
 
-static int tiles_grid(int ntiles) { return std::max(1, std::min(ntiles, 152 * 16)); }
+// Q-node ranges per FP64 tile (k_tiles_f64): enough work items for about
+// four blocks per SM, each range at least 32 nodes.
+static int tiles_qsplit(const yk_geom* g, int ntiles) {
+    const int npc = ceil_div(g->npp, TILE_TPB);
+    const int64_t base = (int64_t)std::max(1, ntiles) * npc;
+    const int want = (int)std::min<int64_t>(ceil_div(152 * 4, base), ceil_div(g->npp, 32));
+    return std::max(1, want);
+}
+
+static int tiles_grid(const yk_geom* g, int ntiles) {
+    const int64_t items = (int64_t)ntiles * ceil_div(g->npp, TILE_TPB) * tiles_qsplit(g, ntiles);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(items, 152 * 16));
+}
 
 // Own-particle far pairs of the FP64 operators: the precomputed self blocks
 // (the pair lists then hold no P == Q tiles).
 static int self_blocks_f32(yk_geom* g, const double* sigma, double* extra, bool accumulate) {
     if (!g->use_self) return YK_OK;
+    const dim3 grid(g->np, ceil_div(g->npp, BAPPLY_ROWS));
+    const size_t smem = blocks_apply_smem<float>(g->npp);
     if (accumulate)
-        YK_LAUNCH(k_self_apply_f32<true>, g->np, 256, sizeof(float) * g->npp, g->ctx->stream,
-                  g->view(), g->d_self32, sigma, extra);
+        YK_LAUNCH((k_blocks_apply<float, true>), grid, BAPPLY_ROWS * BAPPLY_SLICES, smem,
+                  g->ctx->stream, g->npp, g->d_shape_of, g->d_self32, sigma, extra);
     else
-        YK_LAUNCH(k_self_apply_f32<false>, g->np, 256, sizeof(float) * g->npp, g->ctx->stream,
-                  g->view(), g->d_self32, sigma, extra);
+        YK_LAUNCH((k_blocks_apply<float, false>), grid, BAPPLY_ROWS * BAPPLY_SLICES, smem,
+                  g->ctx->stream, g->npp, g->d_shape_of, g->d_self32, sigma, extra);
     return YK_OK;
 }
 
 static int self_blocks(yk_geom* g, const double* sigma, double* extra, bool grad) {
     if (!g->use_self) return YK_OK;
-    YK_LAUNCH(k_self_apply, g->np, 256, sizeof(double) * g->npp, g->ctx->stream, g->view(),
+    const dim3 grid(g->np, ceil_div(g->npp, BAPPLY_ROWS));
+    YK_LAUNCH((k_blocks_apply<double, true>), grid, BAPPLY_ROWS * BAPPLY_SLICES,
+              blocks_apply_smem<double>(g->npp), g->ctx->stream, g->npp, g->d_shape_of,
               grad ? g->d_self_grad : g->d_self, sigma, extra);
     return YK_OK;
 }
@@ -193,11 +216,11 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
             used = 0;
         }
         if (grad)
-            YK_LAUNCH(k_tiles_f64<true>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list,
-                      ntiles, extra);
+            YK_LAUNCH(k_tiles_f64<true>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list,
+                      ntiles, tiles_qsplit(g, ntiles), extra);
         else
-            YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list,
-                      ntiles, extra);
+            YK_LAUNCH(k_tiles_f64<false>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list,
+                      ntiles, tiles_qsplit(g, ntiles), extra);
         if (prec == Prec::SPLIT) YK_TRY(band_expansions(g, sigma, extra, grad));
     }
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used, g->ws.partial, extra,
@@ -365,8 +388,8 @@ static int matvec_body(yk_geom* g, const double* sigma, double* y, Prec prec) {
             YK_TRY(far_sym(g, 1, extra));
         }
         used_chunks = 0;
-        YK_LAUNCH(k_tiles_f64<false>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
-                  extra);
+        YK_LAUNCH(k_tiles_f64<false>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list,
+                  ntiles, tiles_qsplit(g, ntiles), extra);
         if (prec == Prec::SPLIT) YK_TRY(band_expansions(g, sigma, extra, false));
     }
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used_chunks, g->ws.partial, extra,
@@ -396,7 +419,8 @@ static int normal_derivative_body(yk_geom* g, const double* sigma, double* un, P
                   g->split_gap_grad, g->ws.partial);
         used_chunks = nchunk;
     }
-    YK_LAUNCH(k_tiles_f64<true>, tiles_grid(ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles, extra);
+    YK_LAUNCH(k_tiles_f64<true>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
+              tiles_qsplit(g, ntiles), extra);
     if (prec != Prec::F64) YK_TRY(band_expansions(g, sigma, extra, true));
     YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, used_chunks, g->ws.partial, extra,
               G.cgrad, sigma, un);

@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "bessel.cuh"
+#include "block_apply.cuh"
 #include "geom_view.cuh"
 
 namespace yk {
@@ -727,9 +728,14 @@ __device__ __forceinline__ void sym_chunk(const float4* qA, const float4* qB, in
     }
 }
 
+// Work item w: pair w / (npc nqc), chunk (w / nqc) mod npc of 256 of P's
+// nodes, and range w mod nqc of qch of Q's nodes (qch a multiple of 64, at
+// most 256; smaller ranges give small systems enough blocks). A block takes
+// ipb consecutive items.
 __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const float4* __restrict__ rec,
                                                            const int2* __restrict__ tasks,
-                                                           int ntasks, double kscale,
+                                                           int ntasks, int qch, int ipb,
+                                                           double kscale,
                                                            double* __restrict__ out) {
     __shared__ float4 qA[STILE / 2], qB[STILE / 2];
     __shared__ float rsum[F32_TPB / 32][STILE];
@@ -738,11 +744,16 @@ __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const fl
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
     const float short_gap = Z_SHORT * (float)G.rho;
     const int hp = (G.npp + 1) >> 1;
-    const int t0 = blockIdx.x * SYM_TASKS, t1 = min(ntasks, t0 + SYM_TASKS);
+    const int npc = (G.npp + STILE - 1) / STILE, nqc = (G.npp + qch - 1) / qch;
+    const int64_t items = (int64_t)ntasks * npc * nqc;
+    const int64_t w0 = (int64_t)blockIdx.x * ipb, w1 = min(items, w0 + ipb);
     const int lt0 = 64 * warp + lane, lt1 = lt0 + 32;   // the lane's targets in a chunk
     int curP = -1, curC = 0;                            // owner of the FP64 forward sums
     double f0 = 0.0, f1 = 0.0;
-    for (int t = t0; t < t1; ++t) {
+    for (int64_t w = w0; w < w1; ++w) {
+        const int t = (int)(w / ((int64_t)npc * nqc));
+        const int pc = (int)((w / nqc) % npc) * STILE;
+        const int qc = (int)(w % nqc) * qch;
         const int2 pq = tasks[t];
         const int P = pq.x, Q = pq.y;
         const PairRange rg = block_range(G, P, P, Q);   // block-uniform
@@ -752,7 +763,7 @@ __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const fl
         const float4 cp = G.c32[P], cq = G.c32[Q];
         const float oX = kpf * ((cp.x - cq.x) + (cp.z - cq.z));
         const float oY = kpf * ((cp.y - cq.y) + (cp.w - cq.w));
-        for (int pc = 0; pc < G.npp; pc += STILE) {
+        {
             if (P != curP || pc != curC) {
                 if (curP >= 0) {
                     const int64_t b = (int64_t)curP * G.npp + curC;
@@ -782,8 +793,8 @@ __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const fl
                     NGX[h] = NGY[h] = 0.0f;
                 }
             }
-            for (int qc = 0; qc < G.npp; qc += STILE) {
-                const int cnt = min(STILE, G.npp - qc);
+            {
+                const int cnt = min(qch, G.npp - qc);
                 const int npair = (cnt + 1) >> 1;
                 const int ngrp = (npair + 31) >> 5;
                 __syncthreads();   // previous chunk's shared data fully used
@@ -1064,19 +1075,30 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <bool GRAD>
+// Work item w of a launch: tile w / (npc qsplit), chunk of 256 of P's nodes
+// (w / qsplit) mod npc, and the qs = w mod qsplit'th of qsplit equal ranges
+// of Q's nodes. Splitting Q's nodes gives small systems, whose few tiles
+// would otherwise occupy a few SMs of a GPU with a slow FP64 pipe, enough
+// blocks to fill it; each item adds its partial sums to both particles.
 __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const double* __restrict__ sigma,
                                                            const int2* __restrict__ tiles, int ntiles,
-                                                           double* __restrict__ out) {
+                                                           int qsplit, double* __restrict__ out) {
     __shared__ d4 srcQ[STILE];         // x, y, and (value) g = w sigma nu | (grad) nu
     __shared__ double wsQ[STILE];      // (grad) w sigma
     __shared__ double ys[STILE];       // Q-side sums for the staged chunk
     const double rho = G.rho, kappa = 1.0 / rho, two_rho = 2.0 * rho;
     const double scale = GRAD ? 1.0 / (2.0 * PI) : 1.0 / (2.0 * PI * rho);
     const int lane = threadIdx.x & 31;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int npc = (G.npp + TILE_TPB - 1) / TILE_TPB;
+    const int qlen = (G.npp + qsplit - 1) / qsplit;
+    const int64_t items = (int64_t)ntiles * npc * qsplit;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        const int t = (int)(w / ((int64_t)npc * qsplit));
+        const int ib = (int)((w / qsplit) % npc) * TILE_TPB;
+        const int q0 = (int)(w % qsplit) * qlen, q1 = min(G.npp, q0 + qlen);
         const int P = tiles[t].x, Q = tiles[t].y;
         const bool own = (P == Q);
-        for (int ib = 0; ib < G.npp; ib += TILE_TPB) {
+        {
             const int li = ib + threadIdx.x;
             const bool act = li < G.npp;
             const int64_t i = (int64_t)P * G.npp + (act ? li : 0);
@@ -1085,8 +1107,8 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
             const double tws = act ? G.w[i] * sigma[i] : 0.0;
             const int tpan = (act ? li : 0) / G.ngl;
             double acc = 0.0;
-            for (int jb = 0; jb < G.npp; jb += STILE) {
-                const int cnt = min(STILE, G.npp - jb);
+            for (int jb = q0; jb < q1; jb += STILE) {
+                const int cnt = min(STILE, q1 - jb);
                 __syncthreads();
                 if (threadIdx.x < cnt) {
                     const int64_t j = (int64_t)Q * G.npp + jb + threadIdx.x;
@@ -1162,41 +1184,9 @@ __global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, boo
     }
 }
 
-// out_P += S[shape(P)] sigma_P for the far part of the self block (value or
-// normal derivative, stored transposed), one CTA per particle.
-__global__ void k_self_apply(GeomView G, const double* __restrict__ S,
-                             const double* __restrict__ sigma, double* __restrict__ out) {
-    extern __shared__ double xs[];
-    const int P = blockIdx.x;
-    const int64_t base = (int64_t)P * G.npp;
-    for (int j = threadIdx.x; j < G.npp; j += blockDim.x) xs[j] = sigma[base + j];
-    __syncthreads();
-    const double* M = S + (int64_t)G.shape_of[P] * G.npp * G.npp;
-    for (int i = threadIdx.x; i < G.npp; i += blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < G.npp; ++j) acc = fma(M[(int64_t)j * G.npp + i], xs[j], acc);
-        out[base + i] += acc;
-    }
-}
-
-// The same in FP32 for the inner operator: out_P (+)= S32[shape(P)] sigma_P.
-template <bool ACC>
-__global__ void k_self_apply_f32(GeomView G, const float* __restrict__ S,
-                                 const double* __restrict__ sigma, double* __restrict__ out) {
-    extern __shared__ float xf[];
-    const int P = blockIdx.x;
-    const int64_t base = (int64_t)P * G.npp;
-    for (int j = threadIdx.x; j < G.npp; j += blockDim.x) xf[j] = (float)sigma[base + j];
-    __syncthreads();
-    const float* M = S + (int64_t)G.shape_of[P] * G.npp * G.npp;
-    for (int i = threadIdx.x; i < G.npp; i += blockDim.x) {
-        float acc = 0.0f;
-        for (int j = 0; j < G.npp; ++j) acc = fmaf(M[(int64_t)j * G.npp + i], xf[j], acc);
-        if (ACC) out[base + i] += (double)acc;
-        else out[base + i] = (double)acc;
-    }
-}
-
+// out_P (+)= S[shape(P)] sigma_P for the far part of the self block (value
+// or normal derivative, FP64, or the FP32 copy for the inner operator),
+// stored transposed: see k_blocks_apply.
 // y_i = sum_chunks partial[c][i] + extra_i + sum_near C[shape][local i][c] sigma[near c]
 __global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ partial,
                            const double* __restrict__ extra, const double* __restrict__ rows,
