@@ -103,9 +103,9 @@ def kernel_source_hash():
 
 
 def stored_traffic():
-    """DRAM bytes per launch of k_p2p_f32 from the committed ncu summary, if
+    """DRAM bytes per launch of k_p2p_f32_sym from the committed ncu summary, if
     it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_p2p_f32_disks512.json")
+    path = os.path.join(ROOT, "profiles", "k_p2p_f32_sym_disks512.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):

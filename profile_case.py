@@ -5,7 +5,10 @@
 
 Cases: p2p_f32 (mixed matvec: FP32 far field + near rows), p2p_f64 (FP64
 matvec), grad (precision-split normal derivative), qbx (geometry + QBX rows), solve (one mixed solve +
-forces). The geometry is built first; then the case runs --reps times.
+forces). The geometry is built first; then the case runs --reps times. The case
+requests instead solves single requests of the seeded serving stream alone (one
+of about 4, 6, 13, 34, 68 and 156 particles), twice each, and prints the wall
+time of geometry creation and of the second solve.
 --particles K keeps the first K particles of the workload (a smaller case of
 the same kernels, for captures that replay each launch many times).
 """
@@ -20,7 +23,7 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="p2p_f32",
-                    choices=["p2p_f32", "p2p_f64", "grad", "qbx", "solve"])
+                    choices=["p2p_f32", "p2p_f64", "grad", "qbx", "solve", "requests"])
     ap.add_argument("--workload", default="disks512")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--farfield", default="dense", choices=["dense", "cutoff", "fmm"])
@@ -29,6 +32,8 @@ def main():
     import torch
     from paper_1810_04131_gb300 import workloads as W
     from paper_1810_04131_gb300 import yk
+    if a.case == "requests":
+        return requests(torch, W, yk)
     wl = W.WORKLOADS[a.workload]()
     if a.particles > 0:
         wl.particles = wl.particles[:a.particles]
@@ -57,6 +62,32 @@ def main():
     torch.cuda.synchronize()
     print("ok", a.case, a.workload, g.n)
     g.close()
+    ctx.close()
+
+
+def requests(torch, W, yk):
+    """Single requests of the seeded stream, each solved alone."""
+    import time
+    ctx = yk.Context(0)
+    stream = W.request_stream(200, seed=6, rate=1.0)
+    for target in (4, 6, 13, 34, 68, 156):
+        r = min(stream, key=lambda q: abs(q["n_particles"] - target))
+        wl = W.materialise_request(r)
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = yk.Geometry(ctx, wl.particles, yk.params_for(wl, precision=yk.YK_MIXED))
+            torch.cuda.synchronize()
+            t_create = time.perf_counter() - t0
+            f = g.yk_label(yk.YK_LABEL_TANH, 10.0)
+            g.yk_solve_forces(f)
+            t0 = time.perf_counter()
+            s, F, tau, info = g.yk_solve_forces(f)
+            t_solve = time.perf_counter() - t0
+            g.close()
+        print("particles %d panels %d nodes %d: create %.2f ms, solve %.2f ms (%d iterations, "
+              "%d refinements)" % (wl.n_particles, wl.n_panels, wl.n_nodes, t_create * 1e3,
+                                   t_solve * 1e3, info["iterations"], info["refinements"]))
     ctx.close()
 
 
