@@ -250,6 +250,22 @@ int yk_normal_derivative(yk_geom* g, const double* sigma, double* u_nu, int prec
 int yk_solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
              yk_solve_info* info);
 
+/* Solve 1/2 sigma + D sigma = f (Eq. bie) for count independent
+ * configurations at once, each to its own parameters and tolerance, with the
+ * results of count separate yk_solve calls (from a zero initial guess) up to
+ * the solver tolerance. The inner FP32 GMRES of every mixed-precision,
+ * dense-far-field system with self blocks and the block preconditioner (and
+ * no near-contact pairs) advances in lock step with the others: each step is
+ * one kernel launch per stage for all of them. Other systems are solved one
+ * after another as by yk_solve.
+ *   - geoms (count): distinct geometries of one context;
+ *   - f, sigma (count arrays of N_s each, per pointer host or device);
+ *   - info (count, host, nullable): the statistics of each system.
+ * Returns YK_ERR_NOT_CONVERGED if some system stopped above its tolerance
+ * (its sigma holds the last iterate), another error code if one failed. */
+int yk_solve_batch(yk_geom* const* geoms, int count, const double* const* f,
+                   double* const* sigma, yk_solve_info* info);
+
 /* Forces F (n_particles x 2) and scalar torques tau (n_particles) about the
  * particle centres (Eqs. force_torque, stress, scalar-torque) from the
  * density sigma and the data f, using u_nu from yk_normal_derivative (in

@@ -16,15 +16,16 @@ namespace yk {
 constexpr int BAPPLY_ROWS = 32;
 constexpr int BAPPLY_SLICES = 8;   // 256 threads
 
+// One CTA's tile: rows [r0, r0 + 32) of particle P's block; smem holds npp
+// values of T plus 256 partial sums.
 template <typename T, bool ACC>
-__global__ void __launch_bounds__(BAPPLY_ROWS * BAPPLY_SLICES)
-k_blocks_apply(int npp, const int* __restrict__ shape_of, const T* __restrict__ B,
-               const double* __restrict__ x, double* __restrict__ y) {
-    extern __shared__ unsigned char bapply_smem[];
-    T* xs = reinterpret_cast<T*>(bapply_smem);                   // npp
+__device__ __forceinline__ void blocks_apply_tile(int npp, const int* __restrict__ shape_of,
+                                                  const T* __restrict__ B,
+                                                  const double* __restrict__ x,
+                                                  double* __restrict__ y, int P, int r0,
+                                                  unsigned char* smem) {
+    T* xs = reinterpret_cast<T*>(smem);                         // npp
     T* part = xs + ((npp + 1) & ~1);                             // [slices][rows]
-    const int P = blockIdx.x;
-    const int r0 = blockIdx.y * BAPPLY_ROWS;
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const int64_t base = (int64_t)P * npp;
     for (int j = threadIdx.x; j < npp; j += blockDim.x) xs[j] = (T)x[base + j];
@@ -44,6 +45,15 @@ k_blocks_apply(int npp, const int* __restrict__ shape_of, const T* __restrict__ 
         if (ACC) y[base + i] += (double)s;
         else y[base + i] = (double)s;
     }
+}
+
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(BAPPLY_ROWS * BAPPLY_SLICES)
+k_blocks_apply(int npp, const int* __restrict__ shape_of, const T* __restrict__ B,
+               const double* __restrict__ x, double* __restrict__ y) {
+    extern __shared__ unsigned char bapply_smem[];
+    blocks_apply_tile<T, ACC>(npp, shape_of, B, x, y, blockIdx.x, blockIdx.y * BAPPLY_ROWS,
+                              bapply_smem);
 }
 
 template <typename T>

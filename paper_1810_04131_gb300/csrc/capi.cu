@@ -10,6 +10,8 @@
 #include <map>
 #include <tuple>
 
+#include <vector>
+
 #include "yk_internal.cuh"
 
 namespace yk {
@@ -292,6 +294,7 @@ int yk_destroy(yk_ctx* ctx) {
     destroy_server(ctx);
     while (!ctx->geoms.empty()) yk_destroy_geometry(*ctx->geoms.begin());
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
     delete ctx;
     return YK_OK;
 }
@@ -595,6 +598,33 @@ int yk_solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
     if (rc != YK_OK && rc != YK_ERR_NOT_CONVERGED) return rc;
     YK_TRY(o.finish());
     YK_TRY(sync(g));
+    return rc;
+}
+
+int yk_solve_batch(yk_geom* const* geoms, int count, const double* const* f,
+                   double* const* sigma, yk_solve_info* info) {
+    if (!geoms || !f || !sigma || count < 0) return YK_ERR_ARG;
+    if (count == 0) return YK_OK;
+    for (int s = 0; s < count; ++s)
+        if (!geoms[s] || !f[s] || !sigma[s] || geoms[s]->ctx != geoms[0]->ctx) return YK_ERR_ARG;
+    for (int s = 0; s < count; ++s)
+        for (int t = 0; t < s; ++t)
+            if (geoms[s] == geoms[t]) return YK_ERR_ARG;   // one workspace per system
+    YK_TRY_CUDA(cudaSetDevice(geoms[0]->ctx->device));
+    std::vector<Arg> a(count), o(count);
+    std::vector<const double*> fd(count);
+    std::vector<double*> sd(count);
+    for (int s = 0; s < count; ++s) {
+        const size_t bytes = (size_t)geoms[s]->n * sizeof(double);
+        YK_TRY(a[s].init(geoms[s], f[s], bytes, false));
+        YK_TRY(o[s].init(geoms[s], sigma[s], bytes, true));
+        fd[s] = a[s].d();
+        sd[s] = o[s].d();
+    }
+    const int rc = solve_batch(geoms, count, fd.data(), sd.data(), info);
+    if (rc != YK_OK && rc != YK_ERR_NOT_CONVERGED) return rc;
+    for (int s = 0; s < count; ++s) YK_TRY(o[s].finish());
+    YK_TRY(sync(geoms[0]));
     return rc;
 }
 

@@ -258,6 +258,13 @@ int contact_apply(yk_geom* g, const double* sigma, double* y, bool grad) {
     return YK_OK;
 }
 
+int contact_targets(yk_geom* g, int* ntgt) {
+    Contact& C = g->contact;
+    if (!C.valid) YK_TRY(contact_build(g));
+    *ntgt = C.ntgt;
+    return YK_OK;
+}
+
 void contact_free(yk_geom* g) {
     Contact& C = g->contact;
     cudaStream_t st = g->ctx->stream;

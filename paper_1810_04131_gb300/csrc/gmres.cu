@@ -348,6 +348,13 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
     return YK_OK;
 }
 
+// The inner (FP32) solve's relative tolerance in a refinement step taken at
+// relative residual rel: no tighter than what brings rel to gmres_tol with a
+// 10x margin, no looser than 0.1, and not below inner_tol.
+double inner_tolerance(const yk_params& P, double rel) {
+    return std::max(P.inner_tol, std::min(0.1, 0.1 * P.gmres_tol / rel));
+}
+
 static double norm2(yk_geom* g, const double* v) {
     dots(g, v, 1, v, g->ws.status + 2);
     cudaStream_t st = g->ctx->stream;
@@ -356,6 +363,8 @@ static double norm2(yk_geom* g, const double* v) {
     cudaStreamSynchronize(st);
     return sqrt(hs[2]);
 }
+
+double device_norm2(yk_geom* g, const double* v) { return norm2(g, v); }
 
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
           yk_solve_info* info) {
@@ -399,9 +408,7 @@ int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
         int ref = 0;
         while (rel > P.gmres_tol && ref < P.max_refine && total < P.max_iter) {
             const double rn = rel * fn;
-            // an inner solve need not go below what the remaining factor
-            // (rel -> gmres_tol, with a 10x margin) asks for
-            const double itol = std::max(P.inner_tol, std::min(0.1, 0.1 * P.gmres_tol / rel));
+            const double itol = inner_tolerance(P, rel);
             int it = 0, nmv = 0;
             double res = 0.0;
             YK_TRY(gmres(g, Prec::F32, r, d, true, itol * rn, P.max_iter - total, &it, &res,

@@ -7,6 +7,8 @@
 #include <mutex>
 #include <tuple>
 
+// this translation unit holds the far-field kernels themselves
+#define YK_DEFINE_P2P_KERNELS
 #include "p2p_kernels.cuh"
 #include "yk_internal.cuh"
 
@@ -82,22 +84,29 @@ static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
     return YK_OK;
 }
 
-// FP32 far field of the dense operator by the symmetric kernel, added to out.
-static int far_sym(yk_geom* g, int kind, double* out) {
-    const int2* list;
-    int ntasks;
-    YK_TRY(sym_list(g, kind, &list, &ntasks));
-    if (ntasks == 0) return YK_OK;
-    const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);   // units of PairF32
-    // Q-node ranges as short as 64 until there are work items for about
-    // eight blocks per SM; up to SYM_TASKS items per block beyond that
+// Launch shape of the symmetric kernel for a geometry's pair list kind:
+// Q-node ranges as short as 64 until there are work items for about eight
+// blocks per SM (small systems), up to SYM_TASKS items per block beyond.
+int sym_params(yk_geom* g, int kind, SymParams* p) {
+    YK_TRY(sym_list(g, kind, &p->tasks, &p->ntasks));
     const int64_t npc = ceil_div(g->npp, STILE);
     int qch = STILE;
-    while (qch > 64 && (int64_t)ntasks * npc * ceil_div(g->npp, qch) < 152 * 8) qch /= 2;
-    const int64_t items = (int64_t)ntasks * npc * ceil_div(g->npp, qch);
-    const int ipb = (int)std::max<int64_t>(1, std::min<int64_t>(SYM_TASKS, items / (152 * 12)));
-    YK_LAUNCH(k_p2p_f32_sym, (unsigned)ceil_div(items, ipb), F32_TPB, 0, g->ctx->stream, g->view(),
-              g->ws.src4, list, ntasks, qch, ipb, ks, out);
+    while (qch > 64 && (int64_t)p->ntasks * npc * ceil_div(g->npp, qch) < 152 * 8) qch /= 2;
+    const int64_t items = (int64_t)p->ntasks * npc * ceil_div(g->npp, qch);
+    p->qch = qch;
+    p->ipb = (int)std::max<int64_t>(1, std::min<int64_t>(SYM_TASKS, items / (152 * 12)));
+    p->blocks = items == 0 ? 0 : ceil_div(items, p->ipb);
+    p->kscale = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);   // units of PairF32
+    return YK_OK;
+}
+
+// FP32 far field of the dense operator by the symmetric kernel, added to out.
+static int far_sym(yk_geom* g, int kind, double* out) {
+    SymParams p;
+    YK_TRY(sym_params(g, kind, &p));
+    if (p.blocks == 0) return YK_OK;
+    YK_LAUNCH(k_p2p_f32_sym, (unsigned)p.blocks, F32_TPB, 0, g->ctx->stream, g->view(),
+              g->ws.src4, p.tasks, p.ntasks, p.qch, p.ipb, p.kscale, out);
     return YK_OK;
 }
 

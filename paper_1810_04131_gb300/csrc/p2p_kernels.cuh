@@ -32,6 +32,10 @@
 //    targets: P's nodes through registers, Q's through a warp reduction and
 //    shared-memory atomics. Results go to a FP64 buffer with atomics.
 //  * k_assemble: chunk partials (fixed order) + FP64 tile sums + near rows.
+//
+// The __global__ kernels are compiled only where YK_DEFINE_P2P_KERNELS is
+// defined (p2p.cu); other translation units (batch.cu) include this header
+// for the device functions and constants alone.
 #pragma once
 #include <math.h>
 
@@ -372,10 +376,9 @@ __device__ __forceinline__ float2 grad2(float2 TX, float2 TY, float2 NX, float2 
 //   rec[2 (s hp + m) + 1] = B = (g0x, g1x, g0y, g1y),  g = w sigma nu,
 // hp = ceil(npp / 2); a particle with an odd node count pads its last pair
 // with a far, weightless source.
-__global__ void k_src_pairs(GeomView G, const double* __restrict__ sigma, float kpf,
-                            float4* __restrict__ rec) {
+__device__ __forceinline__ void src_pairs_at(const GeomView& G, const double* __restrict__ sigma,
+                                             float kpf, float4* __restrict__ rec, int64_t idx) {
     const int hp = (G.npp + 1) >> 1;
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)G.np * hp) return;
     const int s = (int)(idx / hp), m = (int)(idx % hp);
     float xs[2], ys[2], gx[2], gy[2];
@@ -400,6 +403,13 @@ __global__ void k_src_pairs(GeomView G, const double* __restrict__ sigma, float 
     rec[2 * idx] = make_float4(xs[0], xs[1], ys[0], ys[1]);
     rec[2 * idx + 1] = make_float4(gx[0], gx[1], gy[0], gy[1]);
 }
+
+#ifdef YK_DEFINE_P2P_KERNELS
+__global__ void k_src_pairs(GeomView G, const double* __restrict__ sigma, float kpf,
+                            float4* __restrict__ rec) {
+    src_pairs_at(G, sigma, kpf, rec, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+#endif
 
 // Stage the source pairs of nodes [jb, jb + cnt) of particle s into shared
 // memory (jb even): plain 16-byte loads of the pre-packed records.
@@ -470,6 +480,7 @@ __device__ __forceinline__ void far_tile(const float4* srcA, const float4* srcB,
     r1 = a1.x + a1.y;
 }
 
+#ifdef YK_DEFINE_P2P_KERNELS
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const float4* __restrict__ rec,
                                                      int ppc, float kscale, double skip_gap,
@@ -538,9 +549,11 @@ __global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const float4
     if (act0) partial[blockIdx.y * G.n + i0] = acc0 * (double)kscale;
     if (act1) partial[blockIdx.y * G.n + i1] = acc1 * (double)kscale;
 }
+#endif
 
 // FP32 normal derivative of the far field, two targets per thread, packed
 // pairs (same staging and masking as k_p2p_f32).
+#ifdef YK_DEFINE_P2P_KERNELS
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
                                                           const float4* __restrict__ rec,
@@ -599,6 +612,7 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
     if (act0) partial[blockIdx.y * G.n + i0] = (fast0 * cf + slow0) * sc;
     if (act1) partial[blockIdx.y * G.n + i1] = (fast1 * cf + slow1) * sc;
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Symmetric FP32 far field of the dense operator (k_p2p_f32_sym).
@@ -732,11 +746,10 @@ __device__ __forceinline__ void sym_chunk(const float4* qA, const float4* qB, in
 // nodes, and range w mod nqc of qch of Q's nodes (qch a multiple of 64, at
 // most 256; smaller ranges give small systems enough blocks). A block takes
 // ipb consecutive items.
-__global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const float4* __restrict__ rec,
-                                                           const int2* __restrict__ tasks,
-                                                           int ntasks, int qch, int ipb,
-                                                           double kscale,
-                                                           double* __restrict__ out) {
+__device__ __forceinline__ void sym_items(const GeomView& G, const float4* __restrict__ rec,
+                                          const int2* __restrict__ tasks, int ntasks, int qch,
+                                          int ipb, double kscale, double* __restrict__ out,
+                                          int block) {
     __shared__ float4 qA[STILE / 2], qB[STILE / 2];
     __shared__ float rsum[F32_TPB / 32][STILE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -746,7 +759,7 @@ __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const fl
     const int hp = (G.npp + 1) >> 1;
     const int npc = (G.npp + STILE - 1) / STILE, nqc = (G.npp + qch - 1) / qch;
     const int64_t items = (int64_t)ntasks * npc * nqc;
-    const int64_t w0 = (int64_t)blockIdx.x * ipb, w1 = min(items, w0 + ipb);
+    const int64_t w0 = (int64_t)block * ipb, w1 = min(items, w0 + ipb);
     const int lt0 = 64 * warp + lane, lt1 = lt0 + 32;   // the lane's targets in a chunk
     int curP = -1, curC = 0;                            // owner of the FP64 forward sums
     double f0 = 0.0, f1 = 0.0;
@@ -849,6 +862,16 @@ __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const fl
     }
 }
 
+#ifdef YK_DEFINE_P2P_KERNELS
+__global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const float4* __restrict__ rec,
+                                                           const int2* __restrict__ tasks,
+                                                           int ntasks, int qch, int ipb,
+                                                           double kscale,
+                                                           double* __restrict__ out) {
+    sym_items(G, rec, tasks, ntasks, qch, ipb, kscale, out, blockIdx.x);
+}
+#endif
+
 // Particle pairs of the symmetric far field: P < Q, not every term an exact
 // FP32 zero (the kernels' FP32 gap test), and, with a skip distance, not a
 // pair of the FP64 tiles. Counted per P, then listed in order of Q.
@@ -858,6 +881,7 @@ __device__ __forceinline__ bool sym_pair_listed(const GeomView& G, int P, int Q,
     return !(mask && pair_in_tiles(G.part[P], G.part[Q], skip_gap));
 }
 
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_sym_count(GeomView G, bool mask, double skip_gap, int* __restrict__ counts) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= G.np) return;
@@ -866,7 +890,9 @@ __global__ void k_sym_count(GeomView G, bool mask, double skip_gap, int* __restr
     for (int Q = P + 1; Q < G.np; ++Q) c += sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap);
     counts[P] = c;
 }
+#endif
 
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __restrict__ off,
                            int2* __restrict__ tasks) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
@@ -876,6 +902,7 @@ __global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __
     for (int Q = P + 1; Q < G.np; ++Q)
         if (sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap)) tasks[k++] = make_int2(P, Q);
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Cut-off far field: one block per target particle, sweeping only the source
@@ -883,6 +910,7 @@ __global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __
 // the block owns all its targets, so it writes complete sums. Same pair
 // evaluation and masking as the chunked kernels.
 // ---------------------------------------------------------------------------
+#ifdef YK_DEFINE_P2P_KERNELS
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const float4* __restrict__ rec,
                                                          float kscale, double skip_gap,
@@ -959,7 +987,9 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_cut(GeomView G, const float
         if (act1) out[ii1] = acc1 * (double)kscale;
     }
 }
+#endif
 
+#ifdef YK_DEFINE_P2P_KERNELS
 template <bool MASK>
 __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
                                                               const float4* __restrict__ rec,
@@ -1018,8 +1048,10 @@ __global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad_cut(GeomView G,
         if (act1) out[ii1] = (fast1 * cf + slow1) * sc;
     }
 }
+#endif
 
 // Cut-off neighbour lists: counts, a single-block exclusive scan, fill.
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_nbr_count(int np, const d4* __restrict__ part, double thr, int* counts) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= np) return;
@@ -1028,7 +1060,9 @@ __global__ void k_nbr_count(int np, const d4* __restrict__ part, double thr, int
     for (int Q = 0; Q < np; ++Q) c += (Q == P || pair_in_tiles(a, part[Q], thr)) ? 1 : 0;
     counts[P] = c;
 }
+#endif
 
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_scan_offsets(int np, const int* __restrict__ counts, int* __restrict__ off) {
     __shared__ int buf[1024];
     __shared__ int carry;
@@ -1051,7 +1085,9 @@ __global__ void k_scan_offsets(int np, const int* __restrict__ counts, int* __re
     }
     if (threadIdx.x == 0) off[0] = 0;
 }
+#endif
 
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_nbr_fill(int np, const d4* __restrict__ part, double thr,
                            const int* __restrict__ off, int* __restrict__ nbr) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1061,6 +1097,7 @@ __global__ void k_nbr_fill(int np, const d4* __restrict__ part, double thr,
     for (int Q = 0; Q < np; ++Q)
         if (Q == P || pair_in_tiles(a, part[Q], thr)) nbr[k++] = Q;
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // FP64 pair tiles. Value: k = K1(z)/r; the (i <- j) term is k (d . g_j) and
@@ -1074,12 +1111,13 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <bool GRAD>
 // Work item w of a launch: tile w / (npc qsplit), chunk of 256 of P's nodes
 // (w / qsplit) mod npc, and the qs = w mod qsplit'th of qsplit equal ranges
 // of Q's nodes. Splitting Q's nodes gives small systems, whose few tiles
 // would otherwise occupy a few SMs of a GPU with a slow FP64 pipe, enough
 // blocks to fill it; each item adds its partial sums to both particles.
+#ifdef YK_DEFINE_P2P_KERNELS
+template <bool GRAD>
 __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const double* __restrict__ sigma,
                                                            const int2* __restrict__ tiles, int ntiles,
                                                            int qsplit, double* __restrict__ out) {
@@ -1167,10 +1205,12 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
         }
     }
 }
+#endif
 
 // List the particle pairs (P <= Q) with pair_in_tiles(P, Q, thr), leaving out
 // P == Q when self_pairs is false (the self blocks cover them). Writes up to
 // cap entries; *count receives the total.
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, bool self_pairs,
                             int* count, int2* __restrict__ out, int cap) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1183,15 +1223,18 @@ __global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, boo
         }
     }
 }
+#endif
 
 // out_P (+)= S[shape(P)] sigma_P for the far part of the self block (value
 // or normal derivative, FP64, or the FP32 copy for the inner operator),
 // stored transposed: see k_blocks_apply.
 // y_i = sum_chunks partial[c][i] + extra_i + sum_near C[shape][local i][c] sigma[near c]
-__global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ partial,
-                           const double* __restrict__ extra, const double* __restrict__ rows,
-                           const double* __restrict__ sigma, double* __restrict__ y) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void assemble_at(const GeomView& G, int nchunk,
+                                            const double* __restrict__ partial,
+                                            const double* __restrict__ extra,
+                                            const double* __restrict__ rows,
+                                            const double* __restrict__ sigma,
+                                            double* __restrict__ y, int64_t i) {
     if (i >= G.n) return;
     double acc = extra ? extra[i] : 0.0;
     for (int c = 0; c < nchunk; ++c) acc += partial[c * G.n + i];
@@ -1212,7 +1255,17 @@ __global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ pa
     y[i] = acc + nr;
 }
 
+#ifdef YK_DEFINE_P2P_KERNELS
+__global__ void k_assemble(GeomView G, int nchunk, const double* __restrict__ partial,
+                           const double* __restrict__ extra, const double* __restrict__ rows,
+                           const double* __restrict__ sigma, double* __restrict__ y) {
+    assemble_at(G, nchunk, partial, extra, rows, sigma, y,
+                blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+#endif
+
 // u(t) = D[sigma](t) at off-surface targets, FP64, all sources.
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __restrict__ sigma,
                                                    const double* __restrict__ tgt, int64_t nt,
                                                    int ppc, double* __restrict__ partial) {
@@ -1251,7 +1304,9 @@ __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __r
     }
     if (active) partial[blockIdx.y * nt + i] = acc / (2.0 * PI * rho);
 }
+#endif
 
+#ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_sum_chunks(int64_t n, int nchunk, const double* __restrict__ partial,
                              double* __restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1260,5 +1315,6 @@ __global__ void k_sum_chunks(int64_t n, int nchunk, const double* __restrict__ p
     for (int c = 0; c < nchunk; ++c) acc += partial[c * n + i];
     out[i] = acc;
 }
+#endif
 
 }  // namespace yk

@@ -2,6 +2,12 @@
 // solved (label, Eq. bie, forces and torques) by the library with
 // continuous batching.
 //
+// A worker that admits a small mixed-precision request (up to
+// SMALL_REQUEST_NODES nodes, dense far field, block preconditioner) also
+// admits the small ones queued right behind it, up to MAX_BATCH, and solves
+// them together: their inner FP32 GMRES advance in lock step, one kernel
+// launch per stage for all of them (batch.cu). Larger requests run alone.
+//
 // A fixed set of worker slots, each with its own CUDA streams (a
 // high-priority one for small requests, a low-priority one for large ones)
 // and internal context, takes requests from the arrival queue. A request is admitted when
@@ -21,6 +27,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <vector>
 
 #include "yk_internal.cuh"
 
@@ -68,6 +75,96 @@ static size_t request_bytes(const Request& r) {
     const size_t blocks = 2 * npp * npp * (8 * 2 + 8 + 4);
     return (size_t)(1.25 * (8.0 * (double)(n * (m + 1 + nchunk + 16) + rows) + (double)blocks)) +
            (8u << 20);
+}
+
+// Requests up to this many nodes run on a high-priority stream, so that
+// their blocks are scheduled ahead of those of large requests sharing the GPU,
+// and, when they are mixed-precision dense-far-field solves, are batched.
+constexpr int64_t SMALL_REQUEST_NODES = 65536;
+constexpr int MAX_BATCH = 16;   // requests solved together by one worker
+
+static int64_t request_nodes(const Request* r) {
+    return (int64_t)r->parts.size() * r->prm.n_panels * r->prm.n_gl;
+}
+
+static bool batchable(const Request* r) {
+    return request_nodes(r) <= SMALL_REQUEST_NODES && r->prm.precision == YK_MIXED &&
+           r->prm.farfield == YK_FARFIELD_DENSE && r->prm.precond == YK_PRECOND_BLOCK;
+}
+
+// Run several requests together: geometries and data per request, one
+// batched solve (lock-step inner GMRES, see batch.cu), forces per request.
+// Returns per request its code in rc[].
+static void run_batch(yk_ctx* ctx, const std::vector<Request*>& rs, std::vector<int>& rc) {
+    const size_t k = rs.size();
+    rc.assign(k, YK_OK);
+    std::vector<yk_geom*> g(k, nullptr);
+    std::vector<double*> f(k, nullptr), sig(k, nullptr), F(k, nullptr), tau(k, nullptr);
+    cudaStream_t st = ctx->stream;
+    std::vector<yk_geom*> ok_g;
+    std::vector<const double*> ok_f;
+    std::vector<double*> ok_s;
+    std::vector<size_t> ok_i;
+    for (size_t q = 0; q < k; ++q) {
+        Request* r = rs[q];
+        int c = yk_create_geometry(ctx, r->parts.data(), (int)r->parts.size(), &r->prm, &g[q]);
+        if (c == YK_OK) {
+            const size_t n = (size_t)g[q]->n, np = (size_t)g[q]->np;
+            if (cudaMallocAsync((void**)&f[q], n * sizeof(double), st) != cudaSuccess ||
+                cudaMallocAsync((void**)&sig[q], n * sizeof(double), st) != cudaSuccess ||
+                cudaMallocAsync((void**)&F[q], 2 * np * sizeof(double), st) != cudaSuccess ||
+                cudaMallocAsync((void**)&tau[q], np * sizeof(double), st) != cudaSuccess) {
+                cudaGetLastError();
+                c = YK_ERR_NO_MEMORY;
+            }
+        }
+        if (c == YK_OK) c = yk_label(g[q], r->label_kind, r->label_param, nullptr, f[q]);
+        rc[q] = c;
+        if (c == YK_OK) {
+            ok_g.push_back(g[q]);
+            ok_f.push_back(f[q]);
+            ok_s.push_back(sig[q]);
+            ok_i.push_back(q);
+        }
+    }
+    std::vector<yk_solve_info> info(ok_g.size());
+    int brc = ok_g.empty() ? YK_OK
+                           : solve_batch(ok_g.data(), (int)ok_g.size(), ok_f.data(), ok_s.data(),
+                                         info.data());
+    for (size_t t = 0; t < ok_i.size(); ++t) {
+        const size_t q = ok_i[t];
+        Request* r = rs[q];
+        r->info = info[t];
+        if (brc != YK_OK && brc != YK_ERR_NOT_CONVERGED) {
+            rc[q] = brc;
+            continue;
+        }
+        if (!(info[t].rel_residual <= r->prm.gmres_tol)) r->error = YK_ERR_NOT_CONVERGED;
+        yk_geom* gg = g[q];
+        double* un = gg->ws.vec[4];
+        int c = normal_derivative(gg, sig[q], un, Prec::SPLIT);
+        if (c == YK_OK) c = forces_torques(gg, sig[q], f[q], un, F[q], tau[q], nullptr);
+        if (c == YK_OK) {
+            const size_t n = (size_t)gg->n, np = (size_t)gg->np;
+            r->sigma.resize(n);
+            r->F.resize(2 * np);
+            r->tau.resize(np);
+            cudaMemcpyAsync(r->sigma.data(), sig[q], n * sizeof(double), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(r->F.data(), F[q], 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(r->tau.data(), tau[q], np * sizeof(double), cudaMemcpyDeviceToHost, st);
+        }
+        rc[q] = c;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        for (auto& c : rc)
+            if (c == YK_OK) c = YK_ERR_CUDA;
+    for (size_t q = 0; q < k; ++q) {
+        if (f[q]) cudaFreeAsync(f[q], st);
+        if (sig[q]) cudaFreeAsync(sig[q], st);
+        if (F[q]) cudaFreeAsync(F[q], st);
+        if (tau[q]) cudaFreeAsync(tau[q], st);
+        if (g[q]) yk_destroy_geometry(g[q]);
+    }
 }
 
 // Run one request to completion on a worker's context.
@@ -120,10 +217,6 @@ static Request* admit(Server* s) {
     return nullptr;
 }
 
-// Requests up to this many nodes run on a high-priority stream, so that
-// their blocks are scheduled ahead of those of large requests sharing the GPU.
-constexpr int64_t SMALL_REQUEST_NODES = 65536;
-
 static void worker_main(Server* s) {
     cudaSetDevice(s->device);
     keep_pool_memory(s->device);
@@ -140,22 +233,47 @@ static void worker_main(Server* s) {
         Request* r = nullptr;
         s->cv_work.wait(lk, [&] { return s->stop || (r = admit(s)) != nullptr; });
         if (!r) break;   // stop requested and nothing admitted
-        r->status = YK_REQ_RUNNING;
-        s->mem_in_flight += r->mem_bytes;
-        s->running++;
+        // a small batchable request takes the batchable ones queued right
+        // behind it along (arrival order kept, memory permitting)
+        std::vector<Request*> batch{r};
+        if (batchable(r)) {
+            while ((int)batch.size() < MAX_BATCH && !s->queue.empty()) {
+                Request* q = s->reqs[s->queue.front()].get();
+                if (!batchable(q)) break;
+                const size_t mem = s->mem_in_flight + r->mem_bytes;
+                size_t extra = 0;
+                for (size_t b = 1; b < batch.size(); ++b) extra += batch[b]->mem_bytes;
+                if (mem + extra + q->mem_bytes > s->mem_budget) break;
+                s->queue.pop_front();
+                batch.push_back(q);
+            }
+        }
+        for (Request* q : batch) {
+            q->status = YK_REQ_RUNNING;
+            s->mem_in_flight += q->mem_bytes;
+            s->running++;
+        }
         lk.unlock();
-        const int64_t nodes = (int64_t)r->parts.size() * r->prm.n_panels * r->prm.n_gl;
-        ctx.stream = nodes <= SMALL_REQUEST_NODES ? st_hi : st_lo;
-        const int rc = run_request(&ctx, r);
-        lk.lock();
-        r->t_done = Clock::now();
-        s->mem_in_flight -= r->mem_bytes;
-        s->running--;
-        if (rc != YK_OK) {
-            r->status = YK_REQ_FAILED;
-            r->error = rc;
+        std::vector<int> rcs(batch.size(), YK_OK);
+        if (batch.size() > 1) {
+            ctx.stream = st_hi;
+            run_batch(&ctx, batch, rcs);
         } else {
-            r->status = YK_REQ_DONE;
+            ctx.stream = request_nodes(r) <= SMALL_REQUEST_NODES ? st_hi : st_lo;
+            rcs[0] = run_request(&ctx, r);
+        }
+        lk.lock();
+        for (size_t b = 0; b < batch.size(); ++b) {
+            Request* q = batch[b];
+            q->t_done = Clock::now();
+            s->mem_in_flight -= q->mem_bytes;
+            s->running--;
+            if (rcs[b] != YK_OK) {
+                q->status = YK_REQ_FAILED;
+                q->error = rcs[b];
+            } else {
+                q->status = YK_REQ_DONE;
+            }
         }
         s->cv_done.notify_all();
         s->cv_work.notify_all();

@@ -82,6 +82,8 @@ struct yk_ctx {
     void* server = nullptr;  // serving state (serve.cu)
     std::set<yk_geom*> geoms;  // live geometries made from this context
     double* h_status = nullptr;  // pinned host mirror of solver status (8 doubles)
+    double* h_batch = nullptr;   // pinned host buffer of batched solves' residuals
+    size_t h_batch_cap = 0;      // its length in doubles
 };
 
 namespace yk {
@@ -224,6 +226,13 @@ int apply_preconditioner(yk_geom* g, const double* x, double* y, bool fp32);
 // p2p.cu
 enum class Prec { F64 = 0, F32 = 1, SPLIT = 2 };
 int matvec(yk_geom* g, const double* sigma, double* y, Prec prec);
+// launch shape of the symmetric FP32 far field (kind 0: inner operator)
+struct SymParams {
+    const int2* tasks = nullptr;
+    int ntasks = 0, qch = 0, ipb = 1, blocks = 0;
+    double kscale = 0.0;
+};
+int sym_params(yk_geom* g, int kind, SymParams* p);
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec);
 int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u);
 // near.cu
@@ -251,6 +260,11 @@ void fmm_free(yk_geom* g);
 
 // gmres.cu
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0, yk_solve_info* info);
+double inner_tolerance(const yk_params& P, double rel);
+double device_norm2(yk_geom* g, const double* v);
+// batch.cu
+int solve_batch(yk_geom* const* g, int count, const double* const* f, double* const* sigma,
+                yk_solve_info* info);
 int alloc_workspace(yk_geom* g);
 void free_workspace(yk_geom* g);
 
@@ -262,6 +276,7 @@ int energy(yk_geom* g, const double* f, const double* un, double* phi, double* t
 // contact.cu
 constexpr int CONTACT_MAX_PARTNERS = 16;   // particles within reach of one particle
 int contact_apply(yk_geom* g, const double* sigma, double* y, bool grad);
+int contact_targets(yk_geom* g, int* ntgt);   // nodes with near-contact entries
 void contact_free(yk_geom* g);
 
 // dynamics.cu

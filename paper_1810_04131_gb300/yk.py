@@ -54,7 +54,8 @@ EXPORTS = [
     "yk_destroy_geometry", "yk_update_geometry", "yk_kernel_launches", "yk_num_nodes", "yk_nodes", "yk_label", "yk_matvec",
     "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_energy", "yk_eval_potential",
     "yk_eval_potential_noalloc", "yk_eval_potential_near", "yk_repulsion", "yk_default_dynamics", "yk_step",
-    "yk_solve_forces", "yk_submit", "yk_poll", "yk_drain", "yk_fp32_fma_peak", "yk_strerror",
+    "yk_solve_forces", "yk_solve_batch", "yk_submit", "yk_poll", "yk_drain", "yk_fp32_fma_peak",
+    "yk_strerror",
 ]
 
 
@@ -149,6 +150,7 @@ def load(path=LIB_PATH):
                     C.POINTER(D)],
         "yk_drain": [P],
         "yk_fp32_fma_peak": [I, C.POINTER(D)],
+        "yk_solve_batch": [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -413,6 +415,26 @@ def yk_kernel_launches():
     c = C.c_uint64()
     _check(load().yk_kernel_launches(C.byref(c)), "yk_kernel_launches")
     return c.value
+
+
+def yk_solve_batch(geoms, fs, sigmas=None, allow_not_converged=False):
+    """Solve several configurations together (lock-step inner GMRES); geoms
+    is a list of Geometry of one context, fs their data (arrays or tensors).
+    Returns (sigmas, infos)."""
+    n = len(geoms)
+    if len(fs) != n:
+        raise ValueError("one f per geometry")
+    sigmas = [np.zeros(g.n) for g in geoms] if sigmas is None else sigmas
+    for g, f, s in zip(geoms, fs, sigmas):
+        _f64(f, g.n, "f")
+        _f64(s, g.n, "sigma")
+    G = (C.c_void_p * n)(*[g.h.value if hasattr(g.h, "value") else g.h for g in geoms])
+    F = (C.c_void_p * n)(*[_ptr(f) for f in fs])
+    S = (C.c_void_p * n)(*[_ptr(s) for s in sigmas])
+    infos = (yk_solve_info * n)()
+    ok = (YK_OK, YK_ERR_NOT_CONVERGED) if allow_not_converged else (YK_OK,)
+    _check(load().yk_solve_batch(G, n, F, S, C.cast(infos, C.c_void_p)), "yk_solve_batch", ok)
+    return sigmas, [infos[k].as_dict() for k in range(n)]
 
 
 def yk_fp32_fma_peak(device=0):

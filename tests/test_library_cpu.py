@@ -105,9 +105,20 @@ def test_workloads_are_seeded_and_separated():
     assert (d - 2.0).min() >= 0.5
     assert a.n_nodes == 2048
     e = W.make_particles(30, 30.0, 0.2, seed=9, shape=W.SHAPE_ELLIPSE, A=1.0, B=0.5)
+    # boundary distance by 2048 samples of each ellipse (the placement samples
+    # 4096 x 1024; both stay within a few 1e-3 of the true distance)
+    t = np.linspace(0.0, 2.0 * np.pi, 2048, endpoint=False)
+    pts = []
+    for row in e:
+        c, s_ = np.cos(row[3]), np.sin(row[3])
+        u, v = row[4] * np.cos(t), row[5] * np.sin(t)
+        pts.append(np.stack([row[1] + c * u - s_ * v, row[2] + s_ * u + c * v], 1))
     for i in range(len(e)):
         for j in range(i):
-            assert W._gap(e[i], e[j]) >= 0.2 - 1e-9
+            if np.hypot(*(e[i, 1:3] - e[j, 1:3])) > 2.0 + 0.2 + 1.0:
+                continue
+            dmin = np.sqrt(((pts[i][:, None] - pts[j][None]) ** 2).sum(-1)).min()
+            assert dmin >= 0.2 - 5e-3, (i, j, dmin)
     s = W.request_stream(50, seed=6)
     assert len(s) == 50 and all(4 <= r["n_particles"] <= 2048 for r in s)
     assert all(8 <= r["n_panels"] <= 32 for r in s)
