@@ -25,8 +25,11 @@ Further legs, outside the timed steps (``--legs``; all by default):
   c4        8192 disks: mixed solves with the FMM and the cut-off far field,
             the FP64 cut-off solve, and a 256-disk (65,536-node) subset solved
             with the dense FP64 operator against the mixed FMM solve;
+  batch     16 small requests solved one by one and as one batch
+            (yk_solve_batch: inner GMRES in lock step);
   serving   the seeded request stream: saturation throughput, then Poisson
-            arrivals at 0.5, 0.7 and 0.9 of it, latency percentiles;
+            arrivals at 0.5, 0.7 and 0.9 of it, latency percentiles (also by
+            request size);
   cpu       the FP64 oracle on all host cores (a bounded sample of rows).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -82,7 +85,7 @@ Z_SHORT = 10.0
 ZP_ZERO = 128.0
 LOG2E = 1.4426950408889634
 TARGETS_PER_BLOCK = 256
-ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "serving", "cpu")
+ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "batch", "serving", "cpu")
 # GMRES iterations of the FP64 path on the 512-disk system at tolerance 1e-12
 # (measured on the GPU; the CPU model of the reference arm, which has no GPU,
 # uses this count)
@@ -459,7 +462,7 @@ def run_serving(yk, W, ctx, args):
     def replay(arrivals):
         t0 = time.perf_counter()
         pending = {}
-        lat = []
+        lat, size = [], []
         k = 0
         while k < len(loads) or pending:
             now = time.perf_counter() - t0
@@ -468,10 +471,11 @@ def run_serving(yk, W, ctx, args):
                 pending[rid] = loads[k]
                 k += 1
             done = []
-            for rid in pending:
+            for rid, wl in pending.items():
                 r = ctx.yk_poll(rid)
                 if r["status"] == yk.YK_REQ_DONE:
                     lat.append(r["latency_ms"])
+                    size.append(wl.n_particles)
                     done.append(rid)
                 elif r["status"] == yk.YK_REQ_FAILED:
                     raise RuntimeError("serving request failed")
@@ -479,10 +483,18 @@ def run_serving(yk, W, ctx, args):
                 del pending[rid]
             time.sleep(0.001)
         wall = time.perf_counter() - t0
-        lat = np.array(lat)
-        return {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                "solves_per_s": len(lat) / wall, "wall_s": wall}
+        lat, size = np.array(lat), np.array(size)
+        out = {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+               "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+               "solves_per_s": len(lat) / wall, "wall_s": wall, "by_size": {}}
+        for name, lo, hi in (("under 64 particles", 0, 64), ("64 to 256", 64, 257),
+                             ("over 256 (FMM)", 257, 1 << 30)):
+            sel = lat[(size >= lo) & (size < hi)]
+            if len(sel):
+                out["by_size"][name] = {"requests": int(len(sel)),
+                                        "p50_ms": float(np.percentile(sel, 50)),
+                                        "p99_ms": float(np.percentile(sel, 99))}
+        return out
 
     sat = replay(np.zeros(len(loads)))
     out = {"saturation": sat, "rates": []}
@@ -776,6 +788,43 @@ def main():
            "d2h_bytes_per_step": int(n * 8 * 2 + npart * 24)}
 
     legt.done("e2e")
+    # ---- batched against one-by-one solves of small requests ---------------
+    if "batch" in legs and rank == 0:
+        reqs = [r for r in W.request_stream(400, seed=6, rate=1.0) if r["n_particles"] < 64][:16]
+        bw = [W.materialise_request(r) for r in reqs]
+        bctx = yk.Context(local, stream.cuda_stream)
+        gs = [yk.Geometry(bctx, w.particles, yk.params_for(w, precision=yk.YK_MIXED)) for w in bw]
+        fs = [torch.from_numpy(g.yk_label(yk.YK_LABEL_TANH, 10.0)).to(dev) for g in gs]
+        ss = [torch.zeros_like(f) for f in fs]
+        for g, f, sg in zip(gs, fs, ss):          # warm: lists built
+            g.yk_solve(f, out=sg)
+        yk.yk_solve_batch(gs, fs, ss)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            for g, f, sg in zip(gs, fs, ss):
+                g.yk_solve(f, out=sg)
+        torch.cuda.synchronize()
+        t_one = (time.perf_counter() - t0) / 3
+        l0 = yk.yk_kernel_launches()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            _, binfo = yk.yk_solve_batch(gs, fs, ss)
+        torch.cuda.synchronize()
+        t_batch = (time.perf_counter() - t0) / 3
+        l_batch = (yk.yk_kernel_launches() - l0) / 3
+        extra["batch"] = {"systems": len(gs), "nodes": [g.n for g in gs],
+                          "one_by_one_s": t_one, "batched_s": t_batch,
+                          "speedup": t_one / t_batch, "launches_batched": l_batch,
+                          "iterations": [i["iterations"] for i in binfo],
+                          "note": "16 requests of the seeded stream with under 64 particles, "
+                                  "mixed solves to 1e-12: yk_solve one after another vs "
+                                  "yk_solve_batch (inner FP32 GMRES in lock step)"}
+        for g in gs:
+            g.close()
+        bctx.close()
+        legt.done("batch")
+
     # ---- serving: continuous batching of a request stream ------------------
     if "serving" in legs and rank == 0:
         sctx = yk.Context(local)
