@@ -27,6 +27,10 @@ What it computes, in the paper's order:
      plain kernel (far); tangential derivative from the data f.
   5. Stress, force and torque (Eqs. stress, force_torque, scalar-torque).
   6. Off-surface potential u = D[sigma] (Eq. intrep) by plain quadrature.
+  7. Optionally the combined representation of the remark on Eq. bwform:
+     u = D[sigma] + eta S[sigma] (S of Eq. single-layer-def), whose
+     boundary equation 1/2 sigma + D sigma + eta S sigma = f stays well
+     conditioned for large rho.
 
 Readings taken where the paper is silent (shared with the CUDA path only as
 a definition, not as code):
@@ -44,6 +48,15 @@ a definition, not as code):
     QBX coefficients from those panels resampled on 8 sub-panels of n_gl
     Gauss-Legendre nodes each, with sigma interpolated panel-wise.
   * QBX order p means |n| <= p.
+  * Eq. bwform writes the combined representation as i S + D for the
+    Helmholtz equation with complex k. For the real screened-Laplace kernel
+    the coupling is taken real and positive, u = D[sigma] + eta S[sigma],
+    eta > 0: with u = 0 outside, the inside field then satisfies
+    du/dnu + eta u = 0 on the boundary (jumps of Eqs. sjump and djump and of
+    dS/dnu), and Green's identity makes it vanish, so the equation is
+    uniquely solvable; the system stays real. The single-layer QBX
+    coefficient is that of Eq. graf-coefficient in its Yukawa form,
+    beta_n = (1/2pi) int sigma K_n(s/rho) e^{-i n phi_y} ds_y.
 """
 from __future__ import annotations
 
@@ -187,6 +200,16 @@ def dl_kernel_grad(x, y, nu_y, rho):
     return np.stack([gx, gy], axis=-1)
 
 
+def sl_kernel_grad(x, y, rho):
+    """grad_x G(x, y) = -K1(r/rho) (x - y) / (2 pi rho r) (for the normal
+    derivative of S[sigma]). Returns (..., 2)."""
+    d0 = x[..., 0] - y[..., 0]
+    d1 = x[..., 1] - y[..., 1]
+    r = np.hypot(d0, d1)
+    c = -sp.k1(r / rho) / (TWO_PI * rho * r)
+    return np.stack([c * d0, c * d1], axis=-1)
+
+
 @dataclass
 class QBXParams:
     order: int = 10          # |n| <= order
@@ -235,10 +258,12 @@ def lagrange_diff_matrix(xc):
 class Oracle:
     """Discrete operator of Eq. (bie) for one geometry."""
 
-    def __init__(self, particles, n_panels=16, n_gl=16, rho=1.0, qbx=None, gamma=1.0):
+    def __init__(self, particles, n_panels=16, n_gl=16, rho=1.0, qbx=None, gamma=1.0, eta=0.0):
         self.geom = make_geometry(particles, n_panels, n_gl)
         self.rho = float(rho)
         self.gamma = float(gamma)
+        # coupling of the single layer in u = D[sigma] + eta S[sigma] (0: Eq. intrep)
+        self.eta = float(eta)
         self.qbx = qbx or QBXParams()
         g = self.geom
         # fine sub-panel nodes in the reference interval [-1, 1] of a panel
@@ -321,6 +346,8 @@ class Oracle:
             # nu . grad_y [K_n(s/rho) e^{-in phi}]
             dK = (nus[None, :] * Knp / rho - 1j * nn * nuphi[None, :] * Kn[:p + 1] / s[None, :]) \
                 * np.exp(-1j * nn * phi[None, :])
+            if self.eta:     # + eta K_n(s/rho) e^{-in phi}: the single layer's coefficient
+                dK = dK + self.eta * Kn[:p + 1] * np.exp(-1j * nn * phi[None, :])
             alpha += (dK * w[None, :]) @ sf / TWO_PI               # (b)
         dx = xl - c
         theta = math.atan2(dx[1], dx[0])
@@ -336,6 +363,21 @@ class Oracle:
         Inp = sp.ivp(nn, z)[:, None]
         un = -(mult * alpha * Inp * e).real.sum(0) / rho
         return u, un
+
+    def far_kernel(self, xi, y, nu_y):
+        """Kernel of the far sources: dG/dnu_y, plus eta G in the combined
+        representation."""
+        k = dl_kernel(xi, y, nu_y, self.rho)
+        if self.eta:
+            k = k + self.eta * green(xi, y, self.rho)
+        return k
+
+    def far_kernel_grad(self, xi, y, nu_y):
+        """grad_x of far_kernel, (..., 2)."""
+        k = dl_kernel_grad(xi, y, nu_y, self.rho)
+        if self.eta:
+            k = k + self.eta * sl_kernel_grad(xi, y, self.rho)
+        return k
 
     def near_index(self, i):
         g = self.geom
@@ -374,11 +416,11 @@ class Oracle:
         g = self.geom
         y, nu, w = self.fine_nodes(P, k)
         xi = g.x[i][None, :]
-        kv = dl_kernel(xi, y, nu, self.rho) * w
+        kv = self.far_kernel(xi, y, nu) * w
         row = kv @ self.interp
         if not want_grad:
             return row
-        kg = (dl_kernel_grad(xi, y, nu, self.rho) @ g.nu[i]) * w
+        kg = (self.far_kernel_grad(xi, y, nu) @ g.nu[i]) * w
         return row, kg @ self.interp
 
     # ---- the matvec, row by row ------------------------------------------
@@ -403,10 +445,10 @@ class Oracle:
                 else:
                     y[a] += self.contact_row(i, P, k) @ sigma[cols]
             ws = g.w[m] * sigma[m]
-            y[a] += (dl_kernel(xi, g.x[m], g.nu[m], self.rho) * ws).sum()
+            y[a] += (self.far_kernel(xi, g.x[m], g.nu[m]) * ws).sum()
             idx = self.near_index(i)
             if want_grad:
-                gr = dl_kernel_grad(xi, g.x[m], g.nu[m], self.rho)
+                gr = self.far_kernel_grad(xi, g.x[m], g.nu[m])
                 yn[a] += ((gr @ g.nu[i]) * ws).sum()
                 u, un = self.qbx_eval(i, sigma[idx][:, None], want_grad=True)
                 y[a] += u[0]
@@ -428,11 +470,11 @@ class Oracle:
         for i in range(N):
             m = self.far_mask(i)
             xi = g.x[i][None, :]
-            A[i, m] = dl_kernel(xi, g.x[m], g.nu[m], self.rho) * g.w[m]
+            A[i, m] = self.far_kernel(xi, g.x[m], g.nu[m]) * g.w[m]
             idx = self.near_index(i)
             eye = np.eye(len(idx))
             if want_grad:
-                Gn[i, m] = (dl_kernel_grad(xi, g.x[m], g.nu[m], self.rho) @ g.nu[i]) * g.w[m]
+                Gn[i, m] = (self.far_kernel_grad(xi, g.x[m], g.nu[m]) @ g.nu[i]) * g.w[m]
             for P, k in self.contact_panels(i):      # oversampled instead of plain
                 cols = P * g.n_panels * g.n_gl + k * g.n_gl + np.arange(g.n_gl)
                 if want_grad:
@@ -533,7 +575,7 @@ class Oracle:
         out = np.zeros(len(t))
         ws = g.w * sigma
         for a in range(len(t)):
-            out[a] = (dl_kernel(t[a][None, :], g.x, g.nu, self.rho) * ws).sum()
+            out[a] = (self.far_kernel(t[a][None, :], g.x, g.nu) * ws).sum()
         return out
 
 
@@ -598,7 +640,7 @@ def _oracle_potential_near(self, sigma, targets, near_factor=1.0):
             d2 = ((g.x[sl] - t[a]) ** 2).sum(1)
             b = int(sl[np.argmin(d2)])
             if math.sqrt(d2.min()) >= (near_factor + 1.0) * hmax:
-                acc += (dl_kernel(t[a][None, :], g.x[sl], g.nu[sl], rho) * ws[sl]).sum()
+                acc += (self.far_kernel(t[a][None, :], g.x[sl], g.nu[sl]) * ws[sl]).sum()
                 continue
             sp_ = closest_point(prt, tb, g.t[b]) % TWO_PI
             pb = np.array([prt[4] * math.cos(sp_), prt[5] * math.sin(sp_)])
@@ -608,7 +650,7 @@ def _oracle_potential_near(self, sigma, targets, near_factor=1.0):
             pt, nup = rot(pb), rot(nb)
             d = math.hypot(*(tr - pt))
             if d >= near_factor * hmax:
-                acc += (dl_kernel(t[a][None, :], g.x[sl], g.nu[sl], rho) * ws[sl]).sum()
+                acc += (self.far_kernel(t[a][None, :], g.x[sl], g.nu[sl]) * ws[sl]).sum()
                 continue
             kp = int(sp_ // dt) % g.n_panels
             m = g.n_panels
@@ -617,7 +659,7 @@ def _oracle_potential_near(self, sigma, targets, near_factor=1.0):
                       else [(kp + dd) % m for dd in range(-w_, w_ + 1)])
             near = np.isin(g.panel[sl], panels)
             far = sl[~near]
-            acc += (dl_kernel(t[a][None, :], g.x[far], g.nu[far], rho) * ws[far]).sum()
+            acc += (self.far_kernel(t[a][None, :], g.x[far], g.nu[far]) * ws[far]).sum()
             sig_near = np.concatenate([sigma[sl[0] + k * ng: sl[0] + (k + 1) * ng]
                                        for k in panels])
             r = self.qbx.r_factor * g.h[P, kp]
@@ -638,6 +680,8 @@ def _oracle_potential_near(self, sigma, targets, near_factor=1.0):
                     Knp = sp.kvp(nn[:, None], (sd / rho)[None, :])
                     dK = (nus[None, :] * Knp / rho - 1j * nn[:, None] * nuphi[None, :] * Kn
                           / sd[None, :]) * np.exp(-1j * nn[:, None] * ph[None, :])
+                    if self.eta:
+                        dK = dK + self.eta * Kn * np.exp(-1j * nn[:, None] * ph[None, :])
                     alpha += (dK * (w * sf)[None, :]).sum(1) / TWO_PI
                 dx = tr - cl
                 rr, th = math.hypot(*dx), math.atan2(dx[1], dx[0])
@@ -646,7 +690,7 @@ def _oracle_potential_near(self, sigma, targets, near_factor=1.0):
                 for q, k in enumerate(panels):
                     y, nu, w = self.fine_nodes(P, k, local=True)
                     sf = self.interp @ sig_near[q * ng:(q + 1) * ng]
-                    acc += (dl_kernel(tr[None, :], y, nu, rho) * w * sf).sum()
+                    acc += (self.far_kernel(tr[None, :], y, nu) * w * sf).sum()
         out[a] = acc
     return out
 

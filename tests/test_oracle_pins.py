@@ -689,3 +689,119 @@ def test_euler_dissipates_the_repulsion_energy_at_the_mobility_rate():
         p1 = yo.euler_step(p, F, tau, dt, xi_x, xi_th)
         dphi = yo.repulsion(p1, c0, q)[2].sum() - phi.sum()
         assert abs(-dphi / dt / rate - 1.0) < 1e-5, (dt, -dphi / dt / rate)   # O(dt) + rounding
+
+
+# --------------------------------------------------------------------------
+# the combined representation u = D[sigma] + eta S[sigma] (remark on Eq. bwform)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho,eta", [(1.0, 1.0), (4.0, 1.0), (8.0, 0.5), (0.25, 2.0)])
+def test_circle_eigenvalues_combined(rho, eta):
+    """On a circle of radius R, S maps cos(n theta) to R I_n(z) K_n(z)
+    cos(n theta) on the boundary and its exterior field is
+    R I_n(z) K_n(r/rho) cos(n theta) (separable Yukawa potentials, z = R/rho),
+    so the exterior limit of D + eta S has the eigenvalue
+    z I_n' K_n + eta R I_n K_n and its normal derivative
+    (z I_n' + eta R I_n) K_n'(z)/rho. Pins the single-layer far kernel, its
+    QBX coefficient (Eq. graf-coefficient, Yukawa form) and gradient row."""
+    R = 1.3
+    o = yo.Oracle(_disk(R, phi=0.4), 16, 16, rho, yo.QBXParams(order=10), eta=eta)
+    g = o.geom
+    th = np.arctan2(g.x[:, 1], g.x[:, 0])
+    rows = list(range(3, g.n, 11))
+    z = R / rho
+    for n in (0, 1, 2, 3, 6):
+        for trig in (np.cos, np.sin):
+            sig = trig(n * th)
+            y, yn = o.apply_rows(sig, rows, want_grad=True)
+            lam = z * sp.ivp(n, z) * sp.kv(n, z) + eta * R * sp.iv(n, z) * sp.kv(n, z)
+            lamn = (z * sp.ivp(n, z) + eta * R * sp.iv(n, z)) * sp.kvp(n, z) / rho
+            assert np.abs(y - lam * sig[rows]).max() < 1e-10 * max(1.0, abs(lam))
+            assert np.abs(yn - lamn * sig[rows]).max() < 1e-7 * max(1.0, abs(lamn))
+
+
+def test_combined_single_layer_brute_force():
+    """The single-layer part alone, (A_combined - A_D) / eta, applied to an
+    analytic density on two particles, against adaptive quadrature of
+    Eq. single-layer-def (the log singularity of K0 at the target split out
+    as a breakpoint)."""
+    parts = np.array([[W.SHAPE_ELLIPSE, 0.0, 0.0, 0.3, 1.0, 0.6],
+                      [W.SHAPE_DISK, 2.9, 0.4, 1.1, 0.8, 0.8]])
+    rho, eta = 0.8, 0.7
+    o = yo.Oracle(parts, 16, 16, rho, yo.QBXParams(order=10))
+    oc = yo.Oracle(parts, 16, 16, rho, yo.QBXParams(order=10), eta=eta)
+    g = o.geom
+
+    def sig_fn(pi, t):
+        return np.cos(2 * t) + 0.3 * np.sin(t) + 0.5 * pi
+
+    sig = sig_fn(g.part, g.t)
+    rows = [0, 10, 74, 128, 200, 260, 400, 510]
+    ys = (oc.apply_rows(sig, rows) - o.apply_rows(sig, rows)) / eta
+    for a, i in enumerate(rows):
+        xi = g.x[i]
+        tot = 0.0
+        for pi, p in enumerate(parts):
+            def integrand(t, pi=pi, p=p):
+                x, dx = yo.curve(p, np.array([t]))
+                r = np.hypot(*(x[0] - xi))
+                if r < 1e-14:
+                    return 0.0
+                return sp.k0(r / rho) / (2 * np.pi) * sig_fn(pi, t) * np.hypot(*dx[0])
+            t0 = g.t[i] if pi == g.part[i] else 0.0
+            for lo, hi in ((t0 - np.pi, t0), (t0, t0 + np.pi)):
+                val, _ = si.quad(integrand, lo, hi, limit=400, epsabs=1e-15, epsrel=1e-13)
+                tot += val
+        assert abs(ys[a] - tot) < 1e-10, (i, ys[a], tot)
+
+
+@pytest.mark.parametrize("rho", [1.0, 4.0])
+def test_combined_single_disk_analytic(rho):
+    """The single Janus disk of Eq. true_soln solved in the combined
+    representation: the field, u_nu and the (zero) force are those of the
+    exact solution, whatever the representation."""
+    o = yo.Oracle(_disk(), 16, 16, rho, yo.QBXParams(order=10), eta=1.0)
+    res = yo.solve_dense(o, yo.label(o.geom, 2))
+    ang = np.linspace(0, 2 * np.pi, 37)[:-1]
+    T = np.concatenate([np.stack([r * np.cos(ang), r * np.sin(ang)], 1) for r in (1.3, 2.0, 4.0)])
+    ue, _, _ = _true_soln(T, rho)
+    assert np.abs(o.potential(res["sigma"], T) - ue).max() < 1e-11
+    _, ur, _ = _true_soln(o.geom.x, rho)
+    assert np.abs(res["un"] - ur).max() < 1e-8
+    assert np.abs(res["F"]).max() < 1e-8
+
+
+def test_combined_matches_double_layer_and_helps_at_large_rho():
+    """Both representations solve the same exterior Dirichlet problem, so on
+    four close ellipses at rho = 4 they give the same u_nu, forces, torques and
+    off-surface field (to the discretisation error of the steep label), with
+    different densities. At large rho the weak n = 0 modes of 1/2 + D (circle
+    eigenvalue z I_1(z) K_0(z) -> 0 as z = R/rho -> 0) are lifted by eta S:
+    on six ellipses at rho = 16 the smallest eigenvalue modulus rises from
+    about 0.002 to the discretisation's own floor (about 0.012, shared by both)
+    and plain GMRES needs markedly fewer iterations."""
+    wl, _, _ = _green_setup(n=4, seed=13, box=6.0)
+    rho = 4.0
+    o = yo.Oracle(wl.particles, 16, 16, rho, yo.QBXParams(order=10))
+    oc = yo.Oracle(wl.particles, 16, 16, rho, yo.QBXParams(order=10), eta=0.25)
+    f = yo.label(o.geom, 0, 10.0)
+    r0, r1 = yo.solve_dense(o, f), yo.solve_dense(oc, f)
+    assert np.linalg.norm(r0["sigma"] - r1["sigma"]) > 0.1 * np.linalg.norm(r0["sigma"])
+    assert np.abs(r0["un"] - r1["un"]).max() < 2e-6 * np.abs(r0["un"]).max()
+    assert np.abs(r0["F"] - r1["F"]).max() < 1e-7 * np.abs(r0["F"]).max()
+    assert np.abs(r0["tau"] - r1["tau"]).max() < 1e-7 * np.abs(r0["F"]).max()
+    T = W.off_surface_targets(wl.particles, 12, wl.box, 0.5, seed=3)
+    u0, u1 = o.potential(r0["sigma"], T), oc.potential(r1["sigma"], T)
+    assert np.abs(u0 - u1).max() < 1e-8 * np.abs(u0).max()
+    # large rho: eigenvalues and GMRES iterations
+    rho = 16.0
+    wl = W.small_system(6, 13, shape=1, n_panels=16, A=1.0, B=0.5, rho=rho, gap=0.3)
+    f = yo.label(yo.make_geometry(wl.particles, 16, 16), 0, 10.0)
+    res = {}
+    for eta in (0.0, 0.25):
+        A = yo.Oracle(wl.particles, 16, 16, rho, yo.QBXParams(order=10), eta=eta).dense()
+        _, it, rel = yo.Oracle.gmres(lambda v: A @ v, f, tol=1e-12)
+        assert rel <= 1e-12
+        res[eta] = (np.abs(np.linalg.eigvals(A)).min(), it)
+    assert res[0.0][0] < 0.5 * res[0.25][0], res
+    assert res[0.25][1] < 0.75 * res[0.0][1], res
