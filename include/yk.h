@@ -60,6 +60,17 @@ extern "C" {
 #define YK_MIXED  1   /* FP32 far-field evaluation with FP64 accumulation inside
                          an FP64 iterative-refinement outer solve              */
 
+#define YK_REP_DOUBLE_LAYER 0 /* u = D[sigma] (Eq. intrep), equation Eq. bie    */
+#define YK_REP_COMBINED     1 /* u = D[sigma] + bw_eta S[sigma] (the combined
+                                 representation of the remark on Eq. bwform,
+                                 with a real coupling: S of Eq.
+                                 single-layer-def); the equation becomes
+                                 1/2 sigma + D sigma + bw_eta S sigma = f,
+                                 whose weak modes at large rho are lifted.
+                                 YK_FP64 precision, dense or cut-off far
+                                 field; yk_eval_potential_near is not
+                                 available with it                          */
+
 #define YK_PRECOND_NONE   0  /* plain GMRES                                   */
 #define YK_PRECOND_BLOCK  1  /* right preconditioning by the inverse of each
                                 particle's self-interaction block (the same
@@ -153,6 +164,12 @@ typedef struct {
     double fmm_leaf;       /* YK_FARFIELD_FMM: leaf box side; 0 (default)
                               chooses it by timing the admissible leaf sizes
                               on the first FMM operator application          */
+    int32_t representation;/* YK_REP_DOUBLE_LAYER (default) or YK_REP_COMBINED */
+    int32_t pad3_;
+    double bw_eta;         /* YK_REP_COMBINED: coupling eta > 0 of the single
+                              layer; default 0.25 (on six ellipses, plain GMRES
+                              to 1e-12 takes 25-26 iterations at rho = 4-16
+                              against 34-45 for the double layer alone)      */
 } yk_params;
 
 /* Constant-drag dynamics (Eq. euler) with the excluded-volume repulsion of

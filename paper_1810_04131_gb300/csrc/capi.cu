@@ -154,6 +154,12 @@ static int check_params(const yk_params* p) {
     if (p->precond != YK_PRECOND_NONE && p->precond != YK_PRECOND_BLOCK) return YK_ERR_ARG;
     if (p->precond == YK_PRECOND_BLOCK && (int64_t)p->n_panels * p->n_gl > 1024) return YK_ERR_ARG;
     if (!(p->split_tol > 0.0) || !(p->grad_split_tol > 0.0)) return YK_ERR_ARG;
+    if (p->representation != YK_REP_DOUBLE_LAYER && p->representation != YK_REP_COMBINED)
+        return YK_ERR_ARG;
+    if (p->representation == YK_REP_COMBINED &&
+        (p->precision != YK_FP64 || p->farfield == YK_FARFIELD_FMM || !(p->bw_eta > 0.0) ||
+         !isfinite(p->bw_eta)))
+        return YK_ERR_ARG;
     return YK_OK;
 }
 
@@ -224,6 +230,7 @@ yk::GeomView yk_geom::view() const {
     v.xi = d_xi;
     v.cval = d_cval;
     v.cgrad = d_cgrad;
+    v.eta = prm.representation == YK_REP_COMBINED ? prm.bw_eta : 0.0;
     return v;
 }
 
@@ -253,6 +260,8 @@ int yk_default_params(yk_params* p) {
     p->precond = YK_PRECOND_BLOCK;
     p->fmm_order = 12;
     p->fmm_leaf = 0.0;
+    p->representation = YK_REP_DOUBLE_LAYER;
+    p->bw_eta = 0.25;
     return YK_OK;
 }
 
@@ -741,6 +750,7 @@ int yk_eval_potential(yk_geom* g, const double* sigma, const double* targets, in
 int yk_eval_potential_near(yk_geom* g, const double* sigma, const double* targets, int64_t nt,
                            double* u) {
     if (!g || !sigma || nt < 0 || (nt > 0 && (!targets || !u))) return YK_ERR_ARG;
+    if (g->prm.representation != YK_REP_DOUBLE_LAYER) return YK_ERR_ARG;
     if (nt == 0) return YK_OK;
     YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
     Arg a, t, o;

@@ -120,17 +120,20 @@ __device__ __forceinline__ void contact_curve(const yk_particle& p, double t, do
 
 // The double-layer kernel (value: dG/dnu_y) or its normal derivative at the
 // target (nu_x . grad_x dG/dnu_y), times 2 pi (the caller divides).
+// (times 2 pi) the kernel of the operator (GRAD: its normal derivative at the
+// target): dG/dnu_y, plus eta G in the combined representation.
 template <bool GRAD>
 __device__ __forceinline__ double contact_kernel(double dx, double dy, double nxs, double nys,
-                                                 double nxt, double nyt, double rho) {
+                                                 double nxt, double nyt, double rho, double eta) {
     const double r = sqrt(dx * dx + dy * dy);
     double k0v, k1v;
     k01(r / rho, k0v, k1v);
     const double dn_s = dx * nxs + dy * nys;
-    if (!GRAD) return k1v * dn_s / (rho * r);
+    if (!GRAD) return k1v * dn_s / (rho * r) + eta * k0v;
     const double gg = k1v / (rho * r);
     const double gp = -(k0v / rho + 2.0 * k1v / r) / (rho * r);
-    return gg * (nxt * nxs + nyt * nys) + gp * dn_s * (dx * nxt + dy * nyt) / r;
+    const double dn_t = dx * nxt + dy * nyt;
+    return gg * (nxt * nxs + nyt * nys) + gp * dn_s * dn_t / r - eta * k1v * dn_t / (rho * r);
 }
 
 // One warp per flagged node: oversampled minus plain quadrature of each of
@@ -164,12 +167,12 @@ __global__ void __launch_bounds__(128) k_contact_apply(GeomView G,
             contact_curve(p, k * dt + 0.5 * dt * (fine_x[m] + 1.0), yx, yy, nx, ny, spd);
             double sf = 0.0;
             for (int j = 0; j < G.ngl; ++j) sf = fma(interp[m * G.ngl + j], sigma[base + j], sf);
-            acc += contact_kernel<GRAD>(xi - yx, yi - yy, nx, ny, nxt, nyt, rho) *
+            acc += contact_kernel<GRAD>(xi - yx, yi - yy, nx, ny, nxt, nyt, rho, G.eta) *
                    (0.5 * dt * fine_w[m] * spd) * sf;
         }
         for (int j = lane; j < G.ngl; j += 32)        // minus the plain nodes
             acc -= contact_kernel<GRAD>(xi - G.x[base + j], yi - G.y[base + j], G.nx[base + j],
-                                        G.ny[base + j], nxt, nyt, rho) *
+                                        G.ny[base + j], nxt, nyt, rho, G.eta) *
                    G.w[base + j] * sigma[base + j];
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

@@ -32,6 +32,7 @@ struct GeomView {
     int near_w;      // near panels on each side (cyclic); all panels when 2w+1 >= npan
     int n_near;      // near panels per target
     double rho;
+    double eta;      // coupling of the single layer (combined representation), else 0
     // per particle
     const yk::d4* part;   // (cx, cy, bounding radius, perimeter)
     const float4* c32;    // centre as FP32 hi/lo pairs (hx, hy, lx, ly)

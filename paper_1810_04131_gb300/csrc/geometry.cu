@@ -206,7 +206,7 @@ __global__ void k_label(int64_t n, int npp, const yk_particle* parts, const doub
 // on a canonical copy (centre 0, phi 0).
 // ---------------------------------------------------------------------------
 __global__ void k_qbx_rows(int npan, int ngl, int near_w, int n_near, int os, int order,
-                           double r_factor, double rho, const double2* shape_ab,
+                           double r_factor, double rho, double eta, const double2* shape_ab,
                            const double* glx, const double* glw, const double* fine_x,
                            const double* fine_w, const double* interp, double* cval,
                            double* cgrad) {
@@ -279,8 +279,9 @@ __global__ void k_qbx_rows(int npan, int ngl, int near_w, int n_near, int os, in
         double dlt = thx - phi;
         double c1, s1;
         sincos(dlt, &s1, &c1);
-        // n = 0 term: A_0 = a_s K_0'/rho = -a_s K_1 / rho
-        double A0 = -a_s * Kn[1] / rho;
+        // n = 0 term: A_0 = a_s K_0'/rho = -a_s K_1 / rho; the single layer's
+        // coefficient (combined representation) adds eta K_n(s/rho) e^{-in phi}
+        double A0 = -a_s * Kn[1] / rho + eta * Kn[0];
         double v = beta[0] * A0, vn = gam[0] * A0;
         double cn = 1.0, sn = 0.0;
         for (int n = 1; n <= order; ++n) {
@@ -290,7 +291,7 @@ __global__ void k_qbx_rows(int npan, int ngl, int near_w, int n_near, int os, in
             double kp = -0.5 * (Kn[n - 1] + Kn[n + 1]);
             double An = a_s * kp / rho;
             double Bn = a_p * Kn[n] / sd;
-            double term = An * cn + n * Bn * sn;
+            double term = An * cn + n * Bn * sn + eta * Kn[n] * cn;
             v += 2.0 * beta[n] * term;
             vn += 2.0 * gam[n] * term;
         }
@@ -323,7 +324,7 @@ __global__ void k_qbx_rows(int npan, int ngl, int near_w, int n_near, int os, in
 // its inverse serve every particle of that shape. GMRES is right
 // preconditioned by blockdiag(inverse blocks).
 // ---------------------------------------------------------------------------
-__global__ void k_self_block(int npan, int ngl, int near_w, int n_near, double rho,
+__global__ void k_self_block(int npan, int ngl, int near_w, int n_near, double rho, double eta,
                              const double2* shape_ab, const double* glx, const double* glw,
                              const double* cval, double* A) {
     const int npp = npan * ngl;
@@ -357,7 +358,7 @@ __global__ void k_self_block(int npan, int ngl, int near_w, int n_near, double r
             const double r = sqrt(ex * ex + ey * ey);
             double k0v, k1v;
             k01(r / rho, k0v, k1v);
-            v = k1v * (ex * nx + ey * ny) / (2.0 * PI * rho * r) * w;
+            v = (k1v * (ex * nx + ey * ny) / (rho * r) + eta * k0v) / (2.0 * PI) * w;
         }
         out[j] = v;
     }
@@ -511,7 +512,8 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restr
 // shape: the kernels involve only distances and dot products of normals,
 // which rigid motions keep, so the blocks are built once in the particle frame.
 template <bool GRAD>
-__global__ void k_self_far(int npan, int ngl, int near_w, double rho, const double2* shape_ab,
+__global__ void k_self_far(int npan, int ngl, int near_w, double rho, double eta,
+                           const double2* shape_ab,
                            const double* glx, const double* glw, double* S) {
     const int npp = npan * ngl;
     const int s = blockIdx.y, i = blockIdx.x;
@@ -542,13 +544,15 @@ __global__ void k_self_far(int npan, int ngl, int near_w, double rho, const doub
             k01(r / rho, k0v, k1v);
             const double dn_s = ex * nx + ey * ny;
             if (!GRAD) {
-                v = k1v * dn_s / (2.0 * PI * rho * r) * w;
+                v = (k1v * dn_s / (rho * r) + eta * k0v) / (2.0 * PI) * w;
             } else {
                 const double gg = k1v / (r * rho);
                 const double gp = -(k0v / rho + 2.0 * k1v / r) / (rho * r);
                 const double nn = nxi * nx + nyi * ny;
                 const double dn_t = ex * nxi + ey * nyi;
-                v = (gg * nn + gp * dn_s * dn_t / r) * w / (2.0 * PI);
+                // + eta nu_x . grad_x G = -eta K1(r/rho) (d . nu_x) / (rho r)
+                v = (gg * nn + gp * dn_s * dn_t / r - eta * k1v * dn_t / (rho * r)) * w /
+                    (2.0 * PI);
             }
         }
         out[(int64_t)j * npp + i] = v;
@@ -584,7 +588,8 @@ int build_preconditioner(yk_geom* g) {
     float* scale = W + 4 * nn * ns;
     unsigned* err_bits = reinterpret_cast<unsigned*>(scale + ns);
     YK_LAUNCH(k_self_block, dim3(n, ns), 128, 0, st, g->npan, g->ngl, g->prm.near_width,
-              g->n_near, g->prm.rho, g->d_shape_ab, g->d_glx, g->d_glw, g->d_cval, A);
+              g->n_near, g->prm.rho, g->view().eta, g->d_shape_ab, g->d_glx, g->d_glw, g->d_cval,
+              A);
     YK_LAUNCH(k_ns_setup, ns, 256, 0, st, n, A, A32, scale);
     const dim3 eg((unsigned)((nn + 255) / 256), ns);
     YK_LAUNCH(k_ns_init, eg, 256, 0, st, n, A32, scale, X);
@@ -674,11 +679,12 @@ constexpr size_t SHAPE_CACHE_BYTES = (size_t)4 << 30;
 
 struct ShapeKey {
     int device, npan, ngl, near_w, os, order, precond, use_self;
-    double A, B, r_factor, rho;
+    double A, B, r_factor, rho, eta;
     bool operator<(const ShapeKey& o) const {
         return std::tie(device, npan, ngl, near_w, os, order, precond, use_self, A, B, r_factor,
-                        rho) < std::tie(o.device, o.npan, o.ngl, o.near_w, o.os, o.order,
-                                        o.precond, o.use_self, o.A, o.B, o.r_factor, o.rho);
+                        rho, eta) < std::tie(o.device, o.npan, o.ngl, o.near_w, o.os, o.order,
+                                             o.precond, o.use_self, o.A, o.B, o.r_factor, o.rho,
+                                             o.eta);
     }
 };
 
@@ -725,6 +731,7 @@ static ShapeKey shape_key(const yk_geom* g, int s) {
     k.B = g->shape_ab[s].y;
     k.r_factor = g->prm.qbx_r_factor;
     k.rho = g->prm.rho;
+    k.eta = g->view().eta;
     return k;
 }
 
@@ -824,13 +831,13 @@ int build_geometry(yk_geom* g) {
                                          (int)smem));
     dim3 grid(g->npp, g->nshape);
     YK_LAUNCH(k_qbx_rows, grid, 128, smem, st, g->npan, g->ngl, P.near_width, g->n_near, os,
-              P.qbx_order, P.qbx_r_factor, P.rho, g->d_shape_ab, g->d_glx, g->d_glw,
+              P.qbx_order, P.qbx_r_factor, P.rho, g->view().eta, g->d_shape_ab, g->d_glx, g->d_glw,
               g->d_fine_x, g->d_fine_w, g->d_interp, g->d_cval, g->d_cgrad);
     if (g->use_self) {
         YK_LAUNCH(k_self_far<false>, grid, 128, 0, st, g->npan, g->ngl, P.near_width, P.rho,
-                  g->d_shape_ab, g->d_glx, g->d_glw, g->d_self);
+                  g->view().eta, g->d_shape_ab, g->d_glx, g->d_glw, g->d_self);
         YK_LAUNCH(k_self_far<true>, grid, 128, 0, st, g->npan, g->ngl, P.near_width, P.rho,
-                  g->d_shape_ab, g->d_glx, g->d_glw, g->d_self_grad);
+                  g->view().eta, g->d_shape_ab, g->d_glx, g->d_glw, g->d_self_grad);
         const int64_t cnt = (int64_t)g->nshape * g->npp * g->npp;
         YK_LAUNCH(k_to_f32, ceil_div(cnt, 256), 256, 0, st, cnt, g->d_self, g->d_self32);
     }

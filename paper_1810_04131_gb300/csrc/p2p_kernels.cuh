@@ -1153,10 +1153,10 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
                     const double ws = G.w[j] * sigma[j];
                     if (GRAD) {
                         srcQ[threadIdx.x] = make_d4(G.x[j], G.y[j], G.nx[j], G.ny[j]);
-                        wsQ[threadIdx.x] = ws;
                     } else {
                         srcQ[threadIdx.x] = make_d4(G.x[j], G.y[j], ws * G.nx[j], ws * G.ny[j]);
                     }
+                    wsQ[threadIdx.x] = ws;
                     ys[threadIdx.x] = 0.0;
                 }
                 __syncthreads();
@@ -1171,11 +1171,19 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
                         const double z = r2 * ri * kappa;
                         if (!GRAD) {
                             double k1v;
-                            if (z <= 2.0) k1v = k1_series(z);
-                            else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
+                            if (G.eta == 0.0) {
+                                if (z <= 2.0) k1v = k1_series(z);
+                                else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
+                            } else {   // combined representation: + eta K0 (w sigma)
+                                double k0v;
+                                k01(z, k0v, k1v);
+                                const double sl = G.eta * rho * k0v;   // in units of 1/(2 pi rho)
+                                ki = sl * wsQ[q];
+                                kj = sl * tws;
+                            }
                             const double k = k1v * ri;
-                            ki = k * fma(dx, S.z, dy * S.w);
-                            kj = -k * fma(dx, tnx * tws, dy * (tny * tws));
+                            ki += k * fma(dx, S.z, dy * S.w);
+                            kj -= k * fma(dx, tnx * tws, dy * (tny * tws));
                         } else {
                             double k0v, k1v;
                             k01(z, k0v, k1v);
@@ -1187,6 +1195,13 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
                             const double Gij = fma(gg, nn, gp * dn_s * dn_t * ri);
                             ki = Gij * wsQ[q];
                             kj = Gij * tws;
+                            if (G.eta != 0.0) {
+                                // + eta nu_t . grad G: -eta K1 (d . nu_i)/(rho r) for i <- j,
+                                // -eta K1 (-d . nu_j)/(rho r) for j <- i
+                                const double c = G.eta * k1v * kappa * ri;
+                                ki -= c * dn_t * wsQ[q];
+                                kj += c * dn_s * tws;
+                            }
                         }
                     }
                     acc += ki;
@@ -1270,6 +1285,7 @@ __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __r
                                                    const double* __restrict__ tgt, int64_t nt,
                                                    int ppc, double* __restrict__ partial) {
     __shared__ d4 src[STILE];
+    __shared__ double wss[STILE];
     const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
     const bool active = i < nt;
     const double tx = active ? tgt[2 * i] : 0.0, ty = active ? tgt[2 * i + 1] : 0.0;
@@ -1286,6 +1302,7 @@ __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __r
                 const int64_t j = base + jb + threadIdx.x;
                 const double ws = G.w[j] * sigma[j];
                 src[threadIdx.x] = make_d4(G.x[j], G.y[j], ws * G.nx[j], ws * G.ny[j]);
+                wss[threadIdx.x] = ws;
             }
             __syncthreads();
             if (!active) continue;
@@ -1296,8 +1313,14 @@ __global__ void __launch_bounds__(TPB) k_potential(GeomView G, const double* __r
                 const double ri = rsqrt(r2);
                 const double z = r2 * ri * kappa;
                 double k1v;
-                if (z <= 2.0) k1v = k1_series(z);
-                else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
+                if (G.eta == 0.0) {
+                    if (z <= 2.0) k1v = k1_series(z);
+                    else k1v = exp(-z) * p1_large(two_rho * ri) * rsqrt(z);
+                } else {   // combined representation: + eta K0 (w sigma), units 1/(2 pi rho)
+                    double k0v;
+                    k01(z, k0v, k1v);
+                    acc = fma(G.eta * rho * k0v, wss[q], acc);
+                }
                 acc = fma(k1v * ri, fma(dx, S.z, dy * S.w), acc);
             }
         }

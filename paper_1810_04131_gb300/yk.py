@@ -37,6 +37,8 @@ YK_SHAPE_DISK = 0
 YK_SHAPE_ELLIPSE = 1
 YK_FP64 = 0
 YK_MIXED = 1
+YK_REP_DOUBLE_LAYER = 0
+YK_REP_COMBINED = 1
 YK_PRECOND_NONE = 0
 YK_PRECOND_BLOCK = 1
 YK_FARFIELD_DENSE = 0
@@ -73,7 +75,8 @@ class yk_params(C.Structure):
                 ("max_refine", C.c_int32), ("farfield", C.c_int32), ("split_tol", C.c_double),
                 ("grad_split_tol", C.c_double), ("precond", C.c_int32), ("pad_", C.c_int32),
                 ("cutoff_tol", C.c_double), ("fmm_order", C.c_int32), ("pad2_", C.c_int32),
-                ("fmm_leaf", C.c_double)]
+                ("fmm_leaf", C.c_double), ("representation", C.c_int32), ("pad3_", C.c_int32),
+                ("bw_eta", C.c_double)]
 
 
 class yk_dynamics(C.Structure):
