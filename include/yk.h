@@ -100,6 +100,14 @@ extern "C" {
 #define YK_LABEL_CUSTOM  3   /* f supplied by the caller                       */
 
 /* serving request status */
+/* Stokes operators (yk_stokes_apply; Section 3). */
+#define YK_STOKES_TRACTION  0 /* (1/2 I + K*) sigma: traction of S[sigma] on the
+                                 inside of each boundary (Eq. stokesjump)     */
+#define YK_STOKES_COMPLETED 1 /* (1/2 I + K* + W) sigma: the operator of the
+                                 mobility equation (W: rigid-motion projector) */
+#define YK_STOKES_VELOCITY  2 /* S[sigma] on the boundary: the stokeslet single
+                                 layer of Eq. mobilityu                      */
+
 #define YK_REQ_QUEUED   0
 #define YK_REQ_RUNNING  1
 #define YK_REQ_DONE     2
@@ -170,6 +178,9 @@ typedef struct {
                               layer; default 0.25 (on six ellipses, plain GMRES
                               to 1e-12 takes 25-26 iterations at rho = 4-16
                               against 34-45 for the double layer alone)      */
+    double viscosity;      /* Stokes mobility: fluid viscosity mu of Eq. stokes;
+                              default 1 (the non-dimensional mu = 1 of the
+                              paper's time scale [T] = mu a / gamma)          */
 } yk_params;
 
 /* Constant-drag dynamics (Eq. euler) with the excluded-volume repulsion of
@@ -187,7 +198,10 @@ typedef struct {
     double label_param;    /* its parameter; default 10                      */
     int32_t warm_start;    /* 1 (default): the previous step's density is the
                               initial guess of the next solve                 */
-    int32_t pad_;
+    int32_t mobility;      /* 0 (default): constant drag, Eq. euler with xi_x,
+                              xi_theta; 1: the particle velocities from the
+                              Stokes mobility problem (yk_mobility), Eq.
+                              mob_vec by forward Euler                        */
 } yk_dynamics;
 
 /* Solve statistics (all host memory). */
@@ -316,11 +330,15 @@ int yk_repulsion(yk_geom* g, double c0, int q, double* F, double* tau, double* p
 
 int yk_default_dynamics(yk_dynamics* d);
 
-/* Algorithm 1 with constant drag: n_steps forward-Euler steps (Eq. euler),
- * each one Dirichlet label, GMRES (yk_solve, warm-started from the previous
- * step's density when d->warm_start), the hydrophobic force and torque
- * (yk_forces_torques), the repulsion (yk_repulsion), then
+/* Algorithm 1: n_steps forward-Euler steps, each one Dirichlet label, GMRES
+ * (yk_solve, warm-started from the previous step's density when
+ * d->warm_start), the hydrophobic force and torque (yk_forces_torques), the
+ * repulsion (yk_repulsion), then with constant drag (d->mobility = 0, Eq.
+ * euler)
  *   a_i += dt (F_i + F_rep_i) / xi_x,  theta_i += dt (tau_i + tau_rep_i) / xi_theta,
+ * or with the Stokes mobility (d->mobility = 1, Eq. mob_vec)
+ *   (v, omega) = yk_mobility(F + F_rep, tau + tau_rep),
+ *   a_i += dt v_i,  theta_i += dt omega_i,
  * and the re-discretisation at the new positions (yk_update_geometry).
  *   - particles (n_particles, nullable): the positions after the last step;
  *   - energy (n_steps, nullable): Phi of Eq. main plus the repulsion
@@ -404,6 +422,44 @@ int yk_poll(yk_ctx* ctx, uint64_t id, int* status, double* sigma, double* F,
 /* Run the serving loop until every queued request is done (or a request
  * failed). Returns the first error met, or YK_OK.                          */
 int yk_drain(yk_ctx* ctx);
+
+/* Stokes boundary operators of the mobility problem (Section 3), on a
+ * density sigma of 2 N values stored node by node (x and y component of node
+ * 0, then node 1, ...), with nu the normal out of each particle:
+ *   YK_STOKES_TRACTION:  out = 1/2 sigma + K* sigma, the traction of the
+ *     stokeslet single layer u = S[sigma] on the inside of each boundary,
+ *     K* sigma(x) = sum_y w_y T(x - y, nu(x)) sigma(y) with the stresslet
+ *     T(r, n) = -(1/pi) r r^T (r . n) / |r|^4 (Eq. stokesjump with the target
+ *     normal; the curvature limit -(kappa/(2 pi)) tau tau^T on the diagonal);
+ *   YK_STOKES_COMPLETED: out = that plus W sigma, W the orthogonal projector
+ *     on each boundary (weights w) onto the rigid motions (1, 0), (0, 1),
+ *     (x - a_i)^perp;
+ *   YK_STOKES_VELOCITY:  out = S[sigma] at the boundary nodes, the stokeslet
+ *     G = (1/(4 pi mu)) (-log r I + r r^T / r^2) integrated with the log's
+ *     singularity by product integration on each node's panel and its two
+ *     neighbours (needs n_panels >= 3).
+ * precision: YK_FP64, or YK_MIXED for the FP32 far field (YK_STOKES_COMPLETED
+ * only; the others are always FP64). sigma, out: host or device, 2 N.
+ * Needs n_panels >= 3 and n_panels * n_gl <= 512; YK_ERR_ARG otherwise.     */
+int yk_stokes_apply(yk_geom* g, int op, const double* sigma, double* out, int precision);
+
+/* The Stokes mobility problem (Section 3: Eqs. stokes, mobility_bc,
+ * stokesjump, mobilityu) of the geometry's particles under forces F
+ * (2 n_particles) and torques tau (n_particles, about each centre a_i): the
+ * density sigma = sigma_inc + mu, sigma_inc = F_i / |dP_i| + tau_i
+ * (x - a_i)^perp / J_i (J_i = int |x - a_i|^2 ds) carrying the loads, mu from
+ *   (1/2 I + K* + W) mu = -(1/2 I + K*) sigma_inc
+ * (zero interior traction, so S[sigma] moves every boundary rigidly; mu
+ * carries no force or torque), by GMRES (FP64) or mixed-precision GMRES with
+ * iterative refinement (YK_MIXED: FP32 far field in the inner solves) to
+ * gmres_tol; then the velocities of Eq. mobilityu,
+ *   v_i = int_{dP_i} S[sigma] ds / |dP_i|,
+ *   omega_i = int_{dP_i} (x - a_i) x S[sigma] ds / J_i.
+ * Outputs v (2 n_particles), omega (n_particles), sigma (2 N, nullable),
+ * info (nullable): host or device. Errors as yk_stokes_apply; outputs are
+ * written with YK_ERR_NOT_CONVERGED too.                                    */
+int yk_mobility(yk_geom* g, const double* F, const double* tau, double* v, double* omega,
+                double* sigma, yk_solve_info* info);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts), for accounting in benchmarks. Library-specific; the

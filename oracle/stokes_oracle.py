@@ -65,6 +65,7 @@ from __future__ import annotations
 
 import functools
 import math
+import warnings
 
 import numpy as np
 import scipy.integrate as si
@@ -132,6 +133,15 @@ def log_moments(n_gl):
     weights for xi0 inside the panel, adaptive quadrature outside."""
     xk, _ = np.polynomial.legendre.leggauss(n_gl)
     M = np.zeros((3, n_gl, n_gl))
+    with warnings.catch_warnings():
+        # QUADPACK notes round-off at 1e-15; the moments are checked against
+        # mpmath quadrature in the tests
+        warnings.simplefilter("ignore", si.IntegrationWarning)
+        _fill_moments(M, xk, n_gl)
+    return M
+
+
+def _fill_moments(M, xk, n_gl):
     for k in range(n_gl):
         L = _lagrange_basis(xk, k)
         for i in range(n_gl):
@@ -142,7 +152,6 @@ def log_moments(n_gl):
             for o, x1 in ((1, x0 + 2.0), (2, x0 - 2.0)):
                 M[o, i, k] = si.quad(lambda s: math.log(abs(x1 - s)) * L(s), -1.0, 1.0,
                                      epsabs=1e-16, epsrel=1e-15, limit=400)[0]
-    return M
 
 
 def curvature(particles, part, t):

@@ -156,6 +156,7 @@ static int check_params(const yk_params* p) {
     if (!(p->split_tol > 0.0) || !(p->grad_split_tol > 0.0)) return YK_ERR_ARG;
     if (p->representation != YK_REP_DOUBLE_LAYER && p->representation != YK_REP_COMBINED)
         return YK_ERR_ARG;
+    if (!(p->viscosity > 0.0) || !isfinite(p->viscosity)) return YK_ERR_ARG;
     if (p->representation == YK_REP_COMBINED &&
         (p->precision != YK_FP64 || p->farfield == YK_FARFIELD_FMM || !(p->bw_eta > 0.0) ||
          !isfinite(p->bw_eta)))
@@ -262,6 +263,7 @@ int yk_default_params(yk_params* p) {
     p->fmm_leaf = 0.0;
     p->representation = YK_REP_DOUBLE_LAYER;
     p->bw_eta = 0.25;
+    p->viscosity = 1.0;
     return YK_OK;
 }
 
@@ -321,6 +323,7 @@ int yk_destroy_geometry(yk_geom* g) {
     dev_free(g->nbr, st);
     fmm_free(g);
     dyn_free(g);
+    stokes_free(g);
     contact_free(g);
     for (auto& B : g->bands) {
         dev_free(B.off, st);
@@ -687,6 +690,7 @@ int yk_default_dynamics(yk_dynamics* d) {
     d->label_kind = YK_LABEL_TANH;
     d->label_param = 10.0;
     d->warm_start = 1;
+    d->mobility = 0;
     return YK_OK;
 }
 
@@ -699,6 +703,8 @@ int yk_step(yk_geom* g, const yk_dynamics* d, int n_steps, yk_particle* particle
     if (d->label_kind != YK_LABEL_TANH && d->label_kind != YK_LABEL_SINP &&
         d->label_kind != YK_LABEL_COS)
         return YK_ERR_ARG;
+    if (d->mobility != 0 && d->mobility != 1) return YK_ERR_ARG;
+    if (d->mobility && (g->npan < 3 || g->npp > 512)) return YK_ERR_ARG;
     YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
     for (int s = 0; s < n_steps; ++s)
         YK_TRY(step(g, *d, info ? info + s : nullptr, energy ? energy + s : nullptr));
@@ -710,6 +716,43 @@ int yk_step(yk_geom* g, const yk_dynamics* d, int n_steps, yk_particle* particle
             memcpy(particles, g->parts.data(), sizeof(yk_particle) * g->np);
     }
     return sync(g);
+}
+
+int yk_stokes_apply(yk_geom* g, int op, const double* sigma, double* out, int precision) {
+    if (!g || !sigma || !out) return YK_ERR_ARG;
+    if (op != YK_STOKES_TRACTION && op != YK_STOKES_COMPLETED && op != YK_STOKES_VELOCITY)
+        return YK_ERR_ARG;
+    if (precision != YK_FP64 && precision != YK_MIXED) return YK_ERR_ARG;
+    if (g->npan < 3 || g->npp > 512) return YK_ERR_ARG;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    const size_t bytes = 2 * (size_t)g->n * sizeof(double);
+    Arg a, o;
+    YK_TRY(a.init(g, sigma, bytes, false));
+    YK_TRY(o.init(g, out, bytes, true));
+    YK_TRY(stokes_apply(g, a.d(), o.d(), precision == YK_MIXED ? Prec::F32 : Prec::F64, op));
+    YK_TRY(o.finish());
+    return sync(g);
+}
+
+int yk_mobility(yk_geom* g, const double* F, const double* tau, double* v, double* omega,
+                double* sigma, yk_solve_info* info) {
+    if (!g || !F || !tau || !v || !omega) return YK_ERR_ARG;
+    if (g->npan < 3 || g->npp > 512) return YK_ERR_ARG;
+    YK_TRY_CUDA(cudaSetDevice(g->ctx->device));
+    const size_t np = (size_t)g->np;
+    Arg aF, at, ov, oo, os;
+    YK_TRY(aF.init(g, F, 2 * np * sizeof(double), false));
+    YK_TRY(at.init(g, tau, np * sizeof(double), false));
+    YK_TRY(ov.init(g, v, 2 * np * sizeof(double), true));
+    YK_TRY(oo.init(g, omega, np * sizeof(double), true));
+    YK_TRY(os.init(g, sigma, 2 * (size_t)g->n * sizeof(double), true));
+    const int rc = mobility(g, aF.d(), at.d(), ov.d(), oo.d(), sigma ? os.d() : nullptr, info);
+    if (rc != YK_OK && rc != YK_ERR_NOT_CONVERGED) return rc;
+    YK_TRY(ov.finish());
+    YK_TRY(oo.finish());
+    YK_TRY(os.finish());
+    YK_TRY(sync(g));
+    return rc;
 }
 
 int yk_energy(yk_geom* g, const double* sigma, const double* f, double* phi, double* phi_total) {

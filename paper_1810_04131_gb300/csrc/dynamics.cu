@@ -110,6 +110,26 @@ __global__ void k_euler(int np, yk_particle* __restrict__ parts, const double* _
     P.phi += dt * (tau[i] + taur[i]) / xi_theta;
 }
 
+// F += Fr, tau += taur (the loads of Eq. mobility_bc)
+__global__ void k_add_loads(int np, double* __restrict__ F, double* __restrict__ tau,
+                            const double* __restrict__ Fr, const double* __restrict__ taur) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    F[2 * i] += Fr[2 * i];
+    F[2 * i + 1] += Fr[2 * i + 1];
+    tau[i] += taur[i];
+}
+
+// Eq. mob_vec by forward Euler: a += dt v, theta += dt omega.
+__global__ void k_move(int np, yk_particle* __restrict__ parts, const double* __restrict__ v,
+                       const double* __restrict__ om, double dt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    parts[i].cx += dt * v[2 * i];
+    parts[i].cy += dt * v[2 * i + 1];
+    parts[i].phi += dt * om[i];
+}
+
 // Device copy of the particles and the step buffers, allocated on first use.
 static int dyn_buffers(yk_geom* g) {
     Dynamics& D = g->dyn;
@@ -119,7 +139,7 @@ static int dyn_buffers(yk_geom* g) {
     YK_TRY(dev_alloc((void**)&D.sigma, sizeof(double) * g->n, st));
     YK_TRY(dev_alloc((void**)&D.f, sizeof(double) * g->n, st));
     YK_TRY(dev_alloc((void**)&D.un, sizeof(double) * g->n, st));
-    YK_TRY(dev_alloc((void**)&D.work, sizeof(double) * (8 * (size_t)g->np + 8), st));
+    YK_TRY(dev_alloc((void**)&D.work, sizeof(double) * (9 * (size_t)g->np + 8), st));
     YK_TRY(dev_alloc((void**)&D.bad, sizeof(int), st));
     return YK_OK;
 }
@@ -191,8 +211,19 @@ int step(yk_geom* g, const yk_dynamics& d, yk_solve_info* info, double* energy_o
         for (double v : hp) e += v;
         *energy_out = e;
     }
-    YK_LAUNCH(k_euler, ceil_div(np, 128), 128, 0, st, np, D.parts, F, tau, Fr, taur, d.dt,
-              d.xi_x, d.xi_theta);
+    if (d.mobility) {
+        // Eq. mob_vec: the velocities of the Stokes mobility problem under the
+        // total loads (Eq. mobility_bc), then forward Euler
+        double* V = phi;            // 2 np (phi, phir are free after the energy)
+        double* Om = tot + 2;       // np
+        YK_LAUNCH(k_add_loads, ceil_div(np, 128), 128, 0, st, np, F, tau, Fr, taur);
+        const int rc = mobility(g, F, tau, V, Om, nullptr, nullptr);
+        YK_TRY(rc);
+        YK_LAUNCH(k_move, ceil_div(np, 128), 128, 0, st, np, D.parts, V, Om, d.dt);
+    } else {
+        YK_LAUNCH(k_euler, ceil_div(np, 128), 128, 0, st, np, D.parts, F, tau, Fr, taur, d.dt,
+                  d.xi_x, d.xi_theta);
+    }
     std::vector<yk_particle> moved(np);
     YK_TRY_CUDA(cudaMemcpyAsync(moved.data(), D.parts, sizeof(yk_particle) * np,
                                 cudaMemcpyDeviceToHost, st));

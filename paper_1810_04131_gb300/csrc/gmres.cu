@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <functional>
 
 #include "yk_internal.cuh"
 
@@ -159,19 +160,9 @@ __global__ void k_axpy1(double* __restrict__ x, const double* __restrict__ d, in
 
 // ---------------------------------------------------------------------------
 
-int alloc_workspace(yk_geom* g) {
-    Workspace& w = g->ws;
-    cudaStream_t st = g->ctx->stream;
-    const int64_t n = g->n;
-    const int m = g->prm.gmres_restart;
+int alloc_krylov(Workspace& w, int64_t n, int m, cudaStream_t st) {
     w.m = m;
-    const int nct = ceil_div(n, 256);
-    int nchunk = std::max(1, std::min(g->np, ceil_div(152 * 32, nct)));
-    const int ppc = ceil_div(g->np, nchunk);
-    w.nchunk = ceil_div(g->np, ppc);
     w.dot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(296, (n + 2047) / 2048));
-    YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n, st));
-    YK_TRY(dev_alloc((void**)&w.src4, sizeof(float4) * 2 * (size_t)g->np * ((g->npp + 1) / 2), st));
     YK_TRY(dev_alloc((void**)&w.V, sizeof(double) * (m + 1) * n, st));
     YK_TRY(dev_alloc((void**)&w.H, sizeof(double) * (m + 1) * m, st));
     YK_TRY(dev_alloc((void**)&w.gvec, sizeof(double) * (m + 1), st));
@@ -183,13 +174,25 @@ int alloc_workspace(yk_geom* g) {
     YK_TRY(dev_alloc((void**)&w.status, sizeof(double) * 8, st));
     YK_TRY(dev_alloc((void**)&w.hist, sizeof(double) * 2 * (m + 1), st));
     for (int k = 0; k < 8; ++k) YK_TRY(dev_alloc((void**)&w.vec[k], sizeof(double) * n, st));
+    return YK_OK;
+}
+
+int alloc_workspace(yk_geom* g) {
+    Workspace& w = g->ws;
+    cudaStream_t st = g->ctx->stream;
+    const int64_t n = g->n;
+    const int nct = ceil_div(n, 256);
+    int nchunk = std::max(1, std::min(g->np, ceil_div(152 * 32, nct)));
+    const int ppc = ceil_div(g->np, nchunk);
+    w.nchunk = ceil_div(g->np, ppc);
+    YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n, st));
+    YK_TRY(dev_alloc((void**)&w.src4, sizeof(float4) * 2 * (size_t)g->np * ((g->npp + 1) / 2), st));
+    YK_TRY(alloc_krylov(w, n, g->prm.gmres_restart, st));
     if (!host_status(g->ctx)) return YK_ERR_NO_MEMORY;
     return YK_OK;
 }
 
-void free_workspace(yk_geom* g) {
-    Workspace& w = g->ws;
-    cudaStream_t st = g->ctx->stream;
+void free_workspace(Workspace& w, cudaStream_t st) {
     dev_free(w.partial, st);
     dev_free(w.src4, st);
     dev_free(w.V, st);
@@ -206,18 +209,20 @@ void free_workspace(yk_geom* g) {
     w = Workspace{};
 }
 
+void free_workspace(yk_geom* g) { free_workspace(g->ws, g->ctx->stream); }
+
 // out[0..nvec) = V[0..nvec)^T w
-static void dots(yk_geom* g, const double* V, int nvec, const double* w, double* out) {
-    cudaStream_t st = g->ctx->stream;
-    dim3 grid(g->ws.dot_blocks, nvec);
-    YK_LAUNCH(k_dots, grid, DOT_TPB, 0, st, V, g->n, w, g->ws.dotpart);
-    YK_LAUNCH(k_reduce_parts, 1, 128, 0, st, nvec, g->ws.dot_blocks, g->ws.dotpart, out);
+static void dots(const KrylovOp& op, const double* V, int nvec, const double* w, double* out) {
+    cudaStream_t st = op.ctx->stream;
+    dim3 grid(op.ws->dot_blocks, nvec);
+    YK_LAUNCH(k_dots, grid, DOT_TPB, 0, st, V, op.n, w, op.ws->dotpart);
+    YK_LAUNCH(k_reduce_parts, 1, 128, 0, st, nvec, op.ws->dot_blocks, op.ws->dotpart, out);
 }
 
-static int read_status(yk_geom* g, double* s0, double* s1) {
-    cudaStream_t st = g->ctx->stream;
-    double* hs = g->ctx->h_status;
-    YK_TRY_CUDA(cudaMemcpyAsync(hs, g->ws.status, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+static int read_status(const KrylovOp& op, double* s0, double* s1) {
+    cudaStream_t st = op.ctx->stream;
+    double* hs = op.ctx->h_status;
+    YK_TRY_CUDA(cudaMemcpyAsync(hs, op.ws->status, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     *s0 = hs[0];
     *s1 = hs[1];
@@ -229,10 +234,10 @@ static int read_status(yk_geom* g, double* s0, double* s1) {
 constexpr int GMRES_BATCH = 4;
 
 // Reads the history of steps [j0, j0 + k) into res[], hn[].
-static int read_hist(yk_geom* g, int j0, int k, double* res, double* hn) {
-    cudaStream_t st = g->ctx->stream;
-    double* hs = g->ctx->h_status;
-    YK_TRY_CUDA(cudaMemcpyAsync(hs, g->ws.hist + 2 * j0, 2 * k * sizeof(double),
+static int read_hist(const KrylovOp& op, int j0, int k, double* res, double* hn) {
+    cudaStream_t st = op.ctx->stream;
+    double* hs = op.ctx->h_status;
+    YK_TRY_CUDA(cudaMemcpyAsync(hs, op.ws->hist + 2 * j0, 2 * k * sizeof(double),
                                 cudaMemcpyDeviceToHost, st));
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     for (int i = 0; i < k; ++i) {
@@ -253,15 +258,15 @@ static int next_batch(double res, double prev, double tol_abs) {
 
 // GMRES on A(prec) x = b with initial guess x (x_zero: x is taken as 0).
 // Stops when the residual estimate <= tol_abs. Returns iterations used.
-static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero, double tol_abs,
-                 int max_iter, int* iters_out, double* res_out, int* matvecs) {
-    Workspace& w = g->ws;
-    cudaStream_t st = g->ctx->stream;
-    const int64_t n = g->n;
+static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool x_zero,
+                 double tol_abs, int max_iter, int* iters_out, double* res_out, int* matvecs) {
+    Workspace& w = *op.ws;
+    cudaStream_t st = op.ctx->stream;
+    const int64_t n = op.n;
     const int m = w.m;
     const int ldh = m + 1;
     const int nb = ceil_div(n, 256);
-    const bool pc = g->prm.precond == YK_PRECOND_BLOCK;
+    const bool pc = (bool)op.precond;
     double* r = w.vec[0];
     double* h1 = w.hbuf;
     double* h2 = w.hbuf + (m + 2);
@@ -272,16 +277,16 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
     while (true) {
         // r = b - A x
         if (have_x) {
-            YK_TRY(matvec(g, x, r, prec));
+            YK_TRY(op.apply(x, r, prec));
             ++*matvecs;
             YK_LAUNCH(k_sub, nb, 256, 0, st, r, b, r, n);
         } else {
             YK_TRY_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         }
-        dots(g, r, 1, r, w.status + 2);
+        dots(op, r, 1, r, w.status + 2);
         YK_LAUNCH(k_init_cycle, 1, 32, 0, st, m, w.status + 2, w.gvec, w.status);
         double beta, dummy;
-        YK_TRY(read_status(g, &beta, &dummy));
+        YK_TRY(read_status(op, &beta, &dummy));
         res = beta;
         if (beta <= tol_abs || beta == 0.0 || total >= max_iter) break;
         YK_LAUNCH(k_scale, nb, 256, 0, st, w.V, r, n, w.status + 1, 0.0);
@@ -296,23 +301,23 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
                 double* vj = w.V + (int64_t)jj * n;
                 double* wv = w.V + (int64_t)(jj + 1) * n;
                 if (pc) {   // right preconditioning: w = A M^{-1} v_j
-                    YK_TRY(apply_preconditioner(g, vj, w.vec[6], prec == Prec::F32));
+                    YK_TRY(op.precond(vj, w.vec[6], prec == Prec::F32));
                     vj = w.vec[6];
                 }
-                YK_TRY(matvec(g, vj, wv, prec));
+                YK_TRY(op.apply(vj, wv, prec));
                 ++*matvecs;
                 // CGS2
-                dots(g, w.V, jj + 1, wv, h1);
+                dots(op, w.V, jj + 1, wv, h1);
                 YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, jj + 1, h1);
-                dots(g, w.V, jj + 1, wv, h2);
+                dots(op, w.V, jj + 1, wv, h2);
                 YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, jj + 1, h2);
-                dots(g, wv, 1, wv, w.status + 2);
+                dots(op, wv, 1, wv, w.status + 2);
                 YK_LAUNCH(k_arnoldi_col, 1, 32, 0, st, jj, ldh, w.H, h1, h2, w.status + 2, w.cs,
                           w.sn, w.gvec, w.status, w.hist);
                 YK_LAUNCH(k_scale, nb, 256, 0, st, wv, wv, n, w.status + 1, 0.0);
             }
             double rs[GMRES_BATCH], hs[GMRES_BATCH];
-            YK_TRY(read_hist(g, j, k, rs, hs));
+            YK_TRY(read_hist(op, j, k, rs, hs));
             int used = k;   // steps kept: up to the first that stops the cycle
             for (int b = 0; b < k; ++b) {
                 if (rs[b] <= tol_abs || hs[b] == 0.0 || !isfinite(rs[b])) {
@@ -334,7 +339,7 @@ static int gmres(yk_geom* g, Prec prec, const double* b, double* x, bool x_zero,
             double* t = w.vec[7];
             YK_TRY_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, st));
             YK_LAUNCH(k_add_basis, nb, 256, 0, st, t, w.V, n, j, w.ybuf);
-            YK_TRY(apply_preconditioner(g, t, w.vec[6], prec == Prec::F32));
+            YK_TRY(op.precond(t, w.vec[6], prec == Prec::F32));
             YK_LAUNCH(k_axpy1, nb, 256, 0, st, x, w.vec[6], n);
         } else {
             YK_LAUNCH(k_add_basis, nb, 256, 0, st, x, w.V, n, j, w.ybuf);
@@ -355,25 +360,37 @@ double inner_tolerance(const yk_params& P, double rel) {
     return std::max(P.inner_tol, std::min(0.1, 0.1 * P.gmres_tol / rel));
 }
 
-static double norm2(yk_geom* g, const double* v) {
-    dots(g, v, 1, v, g->ws.status + 2);
-    cudaStream_t st = g->ctx->stream;
-    double* hs = g->ctx->h_status;
-    cudaMemcpyAsync(hs + 2, g->ws.status + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
+static double norm2(const KrylovOp& op, const double* v) {
+    dots(op, v, 1, v, op.ws->status + 2);
+    cudaStream_t st = op.ctx->stream;
+    double* hs = op.ctx->h_status;
+    cudaMemcpyAsync(hs + 2, op.ws->status + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     return sqrt(hs[2]);
 }
 
-double device_norm2(yk_geom* g, const double* v) { return norm2(g, v); }
+KrylovOp yukawa_op(yk_geom* g) {
+    KrylovOp op;
+    op.ctx = g->ctx;
+    op.ws = &g->ws;
+    op.n = g->n;
+    op.apply = [g](const double* x, double* y, Prec p) { return matvec(g, x, y, p); };
+    if (g->prm.precond == YK_PRECOND_BLOCK)
+        op.precond = [g](const double* x, double* y, bool f32) {
+            return apply_preconditioner(g, x, y, f32);
+        };
+    return op;
+}
 
-int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
-          yk_solve_info* info) {
-    const yk_params& P = g->prm;
-    cudaStream_t st = g->ctx->stream;
-    const int64_t n = g->n;
+double device_norm2(yk_geom* g, const double* v) { return norm2(yukawa_op(g), v); }
+
+int solve_op(const KrylovOp& op, const yk_params& P, Prec residual, const double* f,
+             double* sigma, const double* sigma0, yk_solve_info* info) {
+    cudaStream_t st = op.ctx->stream;
+    const int64_t n = op.n;
     const int nb = ceil_div(n, 256);
     yk_solve_info inf{};
-    const double fn = norm2(g, f);
+    const double fn = norm2(op, f);
     if (fn == 0.0) {
         YK_TRY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * n, st));
         if (info) *info = inf;
@@ -385,25 +402,25 @@ int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
     if (P.precision == YK_FP64) {
         int it = 0, nmv = 0;
         double res = 0.0;
-        YK_TRY(gmres(g, Prec::F64, f, sigma, sigma0 == nullptr, P.gmres_tol * fn, P.max_iter, &it,
+        YK_TRY(gmres(op, Prec::F64, f, sigma, sigma0 == nullptr, P.gmres_tol * fn, P.max_iter, &it,
                      &res, &nmv));
         inf.iterations = it;
         inf.rel_residual = res / fn;
         inf.matvecs_fp64 = nmv;
         if (!(inf.rel_residual <= P.gmres_tol)) rc = YK_ERR_NOT_CONVERGED;
     } else {
-        double* r = g->ws.vec[1];
-        double* d = g->ws.vec[2];
-        double* ax = g->ws.vec[3];
+        double* r = op.ws->vec[1];
+        double* d = op.ws->vec[2];
+        double* ax = op.ws->vec[3];
         if (sigma0) {
-            YK_TRY(matvec(g, sigma, ax, Prec::SPLIT));
+            YK_TRY(op.apply(sigma, ax, residual));
             YK_LAUNCH(k_sub, nb, 256, 0, st, r, f, ax, n);
             inf.matvecs_fp64++;
         } else {
             YK_TRY_CUDA(cudaMemsetAsync(sigma, 0, sizeof(double) * n, st));
             YK_TRY_CUDA(cudaMemcpyAsync(r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         }
-        double rel = norm2(g, r) / fn;
+        double rel = norm2(op, r) / fn;
         int total = 0;
         int ref = 0;
         while (rel > P.gmres_tol && ref < P.max_refine && total < P.max_iter) {
@@ -411,15 +428,15 @@ int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
             const double itol = inner_tolerance(P, rel);
             int it = 0, nmv = 0;
             double res = 0.0;
-            YK_TRY(gmres(g, Prec::F32, r, d, true, itol * rn, P.max_iter - total, &it, &res,
+            YK_TRY(gmres(op, Prec::F32, r, d, true, itol * rn, P.max_iter - total, &it, &res,
                          &nmv));
             total += it;
             inf.matvecs_fp32 += nmv;
             YK_LAUNCH(k_axpy1, nb, 256, 0, st, sigma, d, n);
-            YK_TRY(matvec(g, sigma, ax, Prec::SPLIT));
+            YK_TRY(op.apply(sigma, ax, residual));
             YK_LAUNCH(k_sub, nb, 256, 0, st, r, f, ax, n);
             inf.matvecs_fp64++;
-            rel = norm2(g, r) / fn;
+            rel = norm2(op, r) / fn;
             ++ref;
         }
         inf.iterations = total;
@@ -430,6 +447,11 @@ int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
     YK_TRY_CUDA(cudaGetLastError());
     if (info) *info = inf;
     return rc;
+}
+
+int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
+          yk_solve_info* info) {
+    return solve_op(yukawa_op(g), g->prm, Prec::SPLIT, f, sigma, sigma0, info);
 }
 
 }  // namespace yk

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <functional>
 #include <set>
 #include <vector>
 
@@ -151,6 +152,25 @@ struct Dynamics {
 };
 }  // namespace yk
 
+namespace yk {
+// Stokes mobility state (stokes.cu), built on the first Stokes call.
+struct Stokes {
+    bool ready = false;
+    double* B0 = nullptr;       // per shape, body frame: 1/2 I + K* of the own particle
+    double* Bw = nullptr;       //   the same plus the rigid-motion projector W
+    float* Bw32 = nullptr;      //   Bw rounded to FP32 (inner operator)
+    double* S = nullptr;        //   on-surface single layer; all [shape][col][row], 2 npp square
+    double* moments = nullptr;  // log moments [3][ngl][ngl]
+    double* shapeLJ = nullptr;  // per shape: perimeter, int |y - a|^2 ds
+    double* LJ = nullptr;       // the same per particle
+    double4* s64 = nullptr;     // FP64 source records (x, y, w sigma)
+    float4* s32 = nullptr;      // FP32 source records (offset from the centre, w sigma)
+    double *sinc = nullptr, *mu = nullptr, *rhs = nullptr, *tmp = nullptr, *u = nullptr;  // 2n
+    double* vo = nullptr;       // 3 np scratch
+    Workspace ws;               // Krylov workspace on vectors of 2n
+};
+}  // namespace yk
+
 struct yk_geom {
     yk_ctx* ctx = nullptr;
     yk_params prm{};
@@ -176,6 +196,7 @@ struct yk_geom {
     bool nbr_valid = false;
     yk::FmmTree fmm;                       // FMM far field (YK_FARFIELD_FMM)
     yk::Dynamics dyn;                      // particle dynamics (yk_step)
+    yk::Stokes stokes;                     // Stokes mobility (yk_mobility)
     yk::Contact contact;                   // near-contact lists
     yk_particle* d_particles = nullptr;    // device copy of the particles
     // device allocations
@@ -259,6 +280,18 @@ int fmm_far(yk_geom* g, const double* sigma, double* out);
 void fmm_free(yk_geom* g);
 
 // gmres.cu
+// A linear operator for the device GMRES: y = A(prec) x on vectors of length
+// n, an optional right preconditioner, and the workspace (Krylov basis and
+// scratch vectors of length n) it runs in.
+struct KrylovOp {
+    yk_ctx* ctx = nullptr;
+    Workspace* ws = nullptr;
+    int64_t n = 0;
+    std::function<int(const double*, double*, Prec)> apply;
+    std::function<int(const double*, double*, bool)> precond;   // empty: none
+};
+int solve_op(const KrylovOp& op, const yk_params& P, Prec residual, const double* f,
+             double* sigma, const double* sigma0, yk_solve_info* info);
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0, yk_solve_info* info);
 double inner_tolerance(const yk_params& P, double rel);
 double device_norm2(yk_geom* g, const double* v);
@@ -266,7 +299,9 @@ double device_norm2(yk_geom* g, const double* v);
 int solve_batch(yk_geom* const* g, int count, const double* const* f, double* const* sigma,
                 yk_solve_info* info);
 int alloc_workspace(yk_geom* g);
+int alloc_krylov(Workspace& w, int64_t n, int m, cudaStream_t st);
 void free_workspace(yk_geom* g);
+void free_workspace(Workspace& w, cudaStream_t st);
 
 // forces.cu
 int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,
@@ -285,6 +320,15 @@ int repulsion(yk_geom* g, const yk_particle* d_parts, double c0, int q, double* 
 int repulsion_host(yk_geom* g, double c0, int q, double* F, double* tau, double* phi);
 int step(yk_geom* g, const yk_dynamics& d, yk_solve_info* info, double* energy_out);
 void dyn_free(yk_geom* g);
+
+// stokes.cu
+constexpr int STOKES_TRACTION = YK_STOKES_TRACTION;
+constexpr int STOKES_COMPLETED = YK_STOKES_COMPLETED;
+constexpr int STOKES_VELOCITY = YK_STOKES_VELOCITY;
+int stokes_apply(yk_geom* g, const double* sigma, double* out, Prec prec, int which);
+int mobility(yk_geom* g, const double* F, const double* tau, double* v, double* omega,
+             double* sigma_out, yk_solve_info* info);
+void stokes_free(yk_geom* g);
 
 // serve.cu
 int destroy_server(yk_ctx* ctx);

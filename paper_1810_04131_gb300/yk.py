@@ -48,6 +48,9 @@ YK_LABEL_TANH = 0
 YK_LABEL_SINP = 1
 YK_LABEL_COS = 2
 YK_LABEL_CUSTOM = 3
+YK_STOKES_TRACTION = 0
+YK_STOKES_COMPLETED = 1
+YK_STOKES_VELOCITY = 2
 YK_REQ_QUEUED, YK_REQ_RUNNING, YK_REQ_DONE, YK_REQ_FAILED = 0, 1, 2, 3
 
 # every entry point declared in include/yk.h
@@ -57,7 +60,7 @@ EXPORTS = [
     "yk_normal_derivative", "yk_solve", "yk_forces_torques", "yk_energy", "yk_eval_potential",
     "yk_eval_potential_noalloc", "yk_eval_potential_near", "yk_repulsion", "yk_default_dynamics", "yk_step",
     "yk_solve_forces", "yk_solve_batch", "yk_submit", "yk_poll", "yk_drain", "yk_fp32_fma_peak",
-    "yk_strerror",
+    "yk_stokes_apply", "yk_mobility", "yk_strerror",
 ]
 
 
@@ -76,13 +79,13 @@ class yk_params(C.Structure):
                 ("grad_split_tol", C.c_double), ("precond", C.c_int32), ("pad_", C.c_int32),
                 ("cutoff_tol", C.c_double), ("fmm_order", C.c_int32), ("pad2_", C.c_int32),
                 ("fmm_leaf", C.c_double), ("representation", C.c_int32), ("pad3_", C.c_int32),
-                ("bw_eta", C.c_double)]
+                ("bw_eta", C.c_double), ("viscosity", C.c_double)]
 
 
 class yk_dynamics(C.Structure):
     _fields_ = [("dt", C.c_double), ("xi_x", C.c_double), ("xi_theta", C.c_double),
                 ("c0", C.c_double), ("q", C.c_int32), ("label_kind", C.c_int32),
-                ("label_param", C.c_double), ("warm_start", C.c_int32), ("pad_", C.c_int32)]
+                ("label_param", C.c_double), ("warm_start", C.c_int32), ("mobility", C.c_int32)]
 
 
 class yk_solve_info(C.Structure):
@@ -154,6 +157,8 @@ def load(path=LIB_PATH):
         "yk_drain": [P],
         "yk_fp32_fma_peak": [I, C.POINTER(D)],
         "yk_solve_batch": [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), P],
+        "yk_stokes_apply": [P, I, P, P, I],
+        "yk_mobility": [P, P, P, P, P, P, C.POINTER(yk_solve_info)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -363,10 +368,40 @@ class Geometry:
                "yk_repulsion")
         return F, tau, phi
 
+    def yk_stokes_apply(self, sigma, op=YK_STOKES_COMPLETED, precision=YK_FP64, out=None):
+        """Stokes boundary operator on a density of 2 N values (node-major):
+        YK_STOKES_TRACTION (1/2 I + K*), YK_STOKES_COMPLETED (+ W) or
+        YK_STOKES_VELOCITY (S, the on-surface single layer)."""
+        _f64(sigma, 2 * self.n, "sigma")
+        out = np.zeros(2 * self.n) if out is None else _f64(out, 2 * self.n, "out")
+        _check(load().yk_stokes_apply(self.h, int(op), _ptr(sigma), _ptr(out), int(precision)),
+               "yk_stokes_apply")
+        return out
+
+    def yk_mobility(self, F, tau, want_sigma=False, allow_not_converged=False):
+        """Stokes mobility problem (Section 3): velocities v (Np, 2) and angular
+        velocities omega (Np,) under forces F (Np, 2) and torques tau (Np,);
+        also the density sigma (2 N) when want_sigma, and the solve statistics."""
+        F = np.ascontiguousarray(F, dtype=np.float64).reshape(self.n_particles, 2) \
+            if isinstance(F, (list, tuple, np.ndarray)) else F
+        tau = np.ascontiguousarray(tau, dtype=np.float64).reshape(self.n_particles) \
+            if isinstance(tau, (list, tuple, np.ndarray)) else tau
+        v = np.zeros((self.n_particles, 2))
+        om = np.zeros(self.n_particles)
+        sig = np.zeros(2 * self.n) if want_sigma else None
+        info = yk_solve_info()
+        ok = (YK_OK, YK_ERR_NOT_CONVERGED) if allow_not_converged else (YK_OK,)
+        rc = _check(load().yk_mobility(self.h, _ptr(F), _ptr(tau), _ptr(v), _ptr(om), _ptr(sig),
+                                       C.byref(info)), "yk_mobility", ok)
+        d = info.as_dict()
+        d["converged"] = rc == YK_OK
+        return v, om, sig, d
+
     def yk_step(self, n_steps=1, **kw):
-        """Constant-drag dynamics (Algorithm 1, Eq. euler): returns the particles
-        after n_steps (Np x 6 like the input), the energy and the solve
-        statistics of every step."""
+        """Particle dynamics (Algorithm 1): constant drag (Eq. euler) or, with
+        mobility=1, the Stokes mobility velocities (Eq. mob_vec). Returns the
+        particles after n_steps (Np x 6 like the input), the energy and the
+        solve statistics of every step."""
         d = default_dynamics(**kw)
         parts = (yk_particle * self.n_particles)()
         energy = np.zeros(max(n_steps, 1))
