@@ -25,6 +25,10 @@ Further legs, outside the timed steps (``--legs``; all by default):
   c4        8192 disks: mixed solves with the FMM and the cut-off far field,
             the FP64 cut-off solve, and a 256-disk (65,536-node) subset solved
             with the dense FP64 operator against the mixed FMM solve;
+  dynamics  Algorithm 1 on Table 2's collections (250 to 2000 disks, 70
+            boundary points each, rho = 4, tolerance 1e-5): seconds per time
+            step with constant drag and with the Stokes mobility, and the
+            mobility solve alone (mixed and FP64);
   batch     16 small requests solved one by one and as one batch
             (yk_solve_batch: inner GMRES in lock step);
   serving   the seeded request stream: saturation throughput, then Poisson
@@ -85,7 +89,12 @@ Z_SHORT = 10.0
 ZP_ZERO = 128.0
 LOG2E = 1.4426950408889634
 TARGETS_PER_BLOCK = 256
-ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "batch", "serving", "cpu")
+ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "dynamics", "batch", "serving",
+            "cpu")
+
+# Table 2 of the paper, context only: seconds per step of Algorithm 1
+# (T_total / T_ref with T_ref = 10 s) on an 8-core Xeon E5-2650 v4
+PAPER_TABLE2_S = {250: 97.0, 500: 144.0, 1000: 324.0, 2000: 553.0}
 # GMRES iterations of the FP64 path on the 512-disk system at tolerance 1e-12
 # (measured on the GPU; the CPU model of the reference arm, which has no GPU,
 # uses this count)
@@ -773,6 +782,50 @@ def main():
 
     if "c4" in legs:
         legt.done("c4")
+    # ---- Algorithm 1 on Table 2's collections --------------------------------
+    if "dynamics" in legs and rank == 0:
+        rows = []
+        for npart in sorted(PAPER_TABLE2_S):
+            wl = W.table2(npart)
+            row = {"n_particles": npart, "n_nodes": wl.n_nodes, "box": wl.box,
+                   "paper_s_per_step": PAPER_TABLE2_S[npart]}
+            for name, mob in (("constant_drag", 0), ("stokes_mobility", 1)):
+                gd = yk.Geometry(ctx, wl.particles, yk.params_for(wl, precision=yk.YK_MIXED))
+                gd.yk_step(1, dt=0.01, mobility=mob)           # first step: lists, blocks
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                parts_now, _, infos = gd.yk_step(2, dt=0.01, mobility=mob)
+                torch.cuda.synchronize()
+                row[name] = {"s_per_step": (time.perf_counter() - t0) / 2,
+                             "yukawa_iterations": [i["iterations"] for i in infos]}
+                if mob:
+                    f = gd.yk_label(yk.YK_LABEL_TANH, 10.0)
+                    _, Fh, th, _ = gd.yk_solve_forces(f)
+                    for pname, pr in (("mixed", yk.YK_MIXED), ("fp64", yk.YK_FP64)):
+                        gm = yk.Geometry(ctx, parts_now, yk.params_for(
+                            wl, precision=pr, gmres_tol=1e-12))
+                        gm.yk_mobility(Fh, th)                 # blocks built
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        _, _, _, minfo = gm.yk_mobility(Fh, th)
+                        torch.cuda.synchronize()
+                        row["mobility_solve_" + pname] = {
+                            "s": time.perf_counter() - t0, "tol": 1e-12,
+                            "iterations": minfo["iterations"],
+                            "refinements": minfo["refinements"],
+                            "rel_residual": minfo["rel_residual"]}
+                        gm.close()
+                gd.close()
+            rows.append(row)
+        extra["dynamics"] = {
+            "rows": rows,
+            "note": "Table 2's collections (unit disks, 10 panels x 7 nodes, rho = 4, gap >= "
+                    "0.5, QBX order 8): wall seconds per yk_step (label, mixed GMRES to 1e-5 "
+                    "warm-started, forces, repulsion, constant drag or Stokes mobility to 1e-5, "
+                    "Euler update, re-discretisation); the mobility solve of the step's loads "
+                    "alone to 1e-12; paper_s_per_step is the paper's 8-core CPU time, context"}
+    if "dynamics" in legs:
+        legt.done("dynamics")
     # ---- end to end through the C ABI with host buffers --------------------
     f_h = np.zeros(n)
     torch.cuda.synchronize()

@@ -657,6 +657,7 @@ int update_nodes(yk_geom* g) {
     g->fmm.valid = false;                       // the quadtree follows the particles
     for (auto& B : g->bands) B.valid = false;
     g->contact.valid = false;                   // so do the near-contact lists
+    g->stokes.lists_valid = false;              // and the Stokes pair lists
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     return YK_OK;

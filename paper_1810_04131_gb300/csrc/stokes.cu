@@ -47,6 +47,9 @@ constexpr int QGL = 16;           // graded quadrature rule of the log moments
 constexpr int MOMENT_LEVELS = 34; // geometric levels towards a singular point
 constexpr int FAR_TPB = 128;
 constexpr int FAR_TMAX = 4;       // targets per thread (npp <= FAR_TPB * FAR_TMAX)
+constexpr double FAR_FACTOR = 2.0; // particle expansions beyond 2 (r_P + r_Q) between centres
+constexpr int SP = 40;            // largest order of the particle expansions
+constexpr int SP1 = SP + 1;
 
 __device__ double lagrange(const double* xk, int ngl, int k, double x) {
     double v = 1.0;
@@ -341,22 +344,97 @@ __global__ void k_stokes_sources(int64_t n, const double* __restrict__ X,
     if (s32) s32[i] = make_float4(XI[i].x, XI[i].y, (float)qx, (float)qy);
 }
 
-// Pair sums over the nodes of other particles, FP64. KIND 0: traction
+// ---------------------------------------------------------------------------
+// Particle pairs. A pair whose centres are at least 2 (r_P + r_Q) apart (r
+// the bounding radius) is far: its interaction goes through the particle
+// expansions below; the others are summed node by node. The lists (near
+// partners and far pairs per target particle, CSR) are built once per
+// configuration, in FP64, so that both sides take the same decision.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool stokes_far_pair(const yk_particle& P, const yk_particle& Q,
+                                                double* dist) {
+    const double dx = P.cx - Q.cx, dy = P.cy - Q.cy;
+    *dist = sqrt(dx * dx + dy * dy);
+    return *dist >= FAR_FACTOR * (fmax(P.A, P.B) + fmax(Q.A, Q.B));
+}
+
+// smallest order with (max r / (|z0| - max r))^(p - 1) below eps = e^le
+__device__ __forceinline__ int stokes_order(double dist, double rm, double le) {
+    const double q = rm / (dist - rm);
+    return min(max((int)ceil(le / log(q)) + 1, 2), SP);
+}
+
+__global__ void k_stokes_count(int np, const yk_particle* __restrict__ parts,
+                               int* __restrict__ nnear, int* __restrict__ nfar) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= np) return;
+    const yk_particle pp = parts[P];
+    int cn = 0, cf = 0;
+    for (int Q = 0; Q < np; ++Q) {
+        if (Q == P) continue;
+        double d;
+        if (stokes_far_pair(pp, parts[Q], &d)) ++cf;
+        else ++cn;
+    }
+    nnear[P] = cn;
+    nfar[P] = cf;
+}
+
+__global__ void k_stokes_fill(int np, const yk_particle* __restrict__ parts,
+                              const int* __restrict__ near_off, int* __restrict__ near_idx,
+                              const int* __restrict__ far_off, StokesFar* __restrict__ far) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= np) return;
+    const yk_particle pp = parts[P];
+    int in = near_off[P], jf = far_off[P];
+    for (int Q = 0; Q < np; ++Q) {
+        if (Q == P) continue;
+        const yk_particle qq = parts[Q];
+        double d;
+        if (!stokes_far_pair(pp, qq, &d)) {
+            near_idx[in++] = Q;
+            continue;
+        }
+        StokesFar e;
+        e.z0 = make_double2(pp.cx - qq.cx, pp.cy - qq.cy);
+        const double id = 1.0 / (d * d);
+        e.zi = make_double2(e.z0.x * id, -e.z0.y * id);
+        e.logd = log(d);
+        e.q = Q;
+        const double rm = fmax(fmax(pp.A, pp.B), fmax(qq.A, qq.B));
+        e.p64 = (short)stokes_order(d, rm, -39.14);    // 1e-17
+        e.p32 = (short)stokes_order(d, rm, -18.42);    // 1e-8
+        far[jf++] = e;
+    }
+}
+
+// 1 / x for x > 0 in the float range: FP32 estimate and two Newton steps
+__device__ __forceinline__ double recip(double x) {
+    double r = (double)__frcp_rn((float)x);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// Node-by-node sums over the near particles, FP64. KIND 0: traction
 // -(1/pi) sum r (r . n_t)(r . q) / r^4; KIND 1: single layer
-// (1/(4 pi mu)) sum (-log r q + r (r . q) / r^2). Block (target particle,
-// source chunk); source particles c, c + nchunk, ...; out += (atomics).
+// (1/(4 pi mu)) sum (-log r q + r (r . q) / r^2). Block = target particle,
+// blockDim a multiple of 32 covering npp (up to FAR_TMAX targets a thread).
 template <int KIND>
 __global__ void __launch_bounds__(FAR_TPB)
-k_stokes_far64(int np, int npp, int nchunk, const double4* __restrict__ src,
-               const double* __restrict__ X, const double* __restrict__ Y,
-               const double* __restrict__ NX, const double* __restrict__ NY, double scale,
-               double* __restrict__ out) {
+k_stokes_near64(int npp, const int* __restrict__ near_off, const int* __restrict__ near_idx,
+                const double4* __restrict__ src, const double* __restrict__ X,
+                const double* __restrict__ Y, const double* __restrict__ NX,
+                const double* __restrict__ NY, double scale, double* __restrict__ out) {
     extern __shared__ double4 sf_src[];
     const int P = blockIdx.x;
+    const int e0 = near_off[P], e1 = near_off[P + 1];
+    if (e0 == e1) return;
+    const int tpb = blockDim.x;
     double tx[FAR_TMAX], ty[FAR_TMAX], nx[FAR_TMAX], ny[FAR_TMAX], ax[FAR_TMAX], ay[FAR_TMAX];
 #pragma unroll
     for (int k = 0; k < FAR_TMAX; ++k) {
-        const int t = threadIdx.x + k * FAR_TPB;
+        const int t = threadIdx.x + k * tpb;
         const int64_t gi = (int64_t)P * npp + (t < npp ? t : 0);
         tx[k] = X[gi];
         ty[k] = Y[gi];
@@ -364,19 +442,19 @@ k_stokes_far64(int np, int npp, int nchunk, const double4* __restrict__ src,
         ny[k] = KIND == 0 ? NY[gi] : 0.0;
         ax[k] = ay[k] = 0.0;
     }
-    for (int Q = blockIdx.y; Q < np; Q += nchunk) {
-        if (Q == P) continue;
+    for (int e = e0; e < e1; ++e) {
+        const int Q = near_idx[e];
         __syncthreads();
-        for (int s = threadIdx.x; s < npp; s += FAR_TPB) sf_src[s] = src[(int64_t)Q * npp + s];
+        for (int s = threadIdx.x; s < npp; s += tpb) sf_src[s] = src[(int64_t)Q * npp + s];
         __syncthreads();
         for (int s = 0; s < npp; ++s) {
             const double4 q = sf_src[s];
 #pragma unroll
             for (int k = 0; k < FAR_TMAX; ++k) {
-                if (k * FAR_TPB >= npp) break;
+                if (k * tpb >= npp) break;
                 const double rx = tx[k] - q.x, ry = ty[k] - q.y;
                 const double r2 = rx * rx + ry * ry;
-                const double inv = 1.0 / r2;
+                const double inv = recip(r2);
                 const double rq = rx * q.z + ry * q.w;
                 if (KIND == 0) {
                     const double c = (rx * nx[k] + ry * ny[k]) * rq * inv * inv;
@@ -393,30 +471,35 @@ k_stokes_far64(int np, int npp, int nchunk, const double4* __restrict__ src,
     }
 #pragma unroll
     for (int k = 0; k < FAR_TMAX; ++k) {
-        const int t = threadIdx.x + k * FAR_TPB;
+        const int t = threadIdx.x + k * tpb;
         if (t < npp) {
             const int64_t gi = (int64_t)P * npp + t;
-            atomicAdd(out + 2 * gi, scale * ax[k]);
-            atomicAdd(out + 2 * gi + 1, scale * ay[k]);
+            out[2 * gi] += scale * ax[k];
+            out[2 * gi + 1] += scale * ay[k];
         }
     }
 }
 
-// The traction pair sums in FP32 (inner operator): offsets from the particle
-// centres, the centre difference formed in FP64 once per particle pair, each
-// source particle's sum added to FP64 accumulators.
+// The traction node-by-node sums over the near particles in FP32 (inner
+// operator): offsets from the particle centres, the centre difference formed
+// in FP64 once per particle pair, each source particle's sum added to FP64
+// accumulators.
 __global__ void __launch_bounds__(FAR_TPB)
-k_stokes_far32(int np, int npp, int nchunk, const float4* __restrict__ src,
-               const float2* __restrict__ XI, const double* __restrict__ NX,
-               const double* __restrict__ NY, const yk_particle* __restrict__ parts,
-               double scale, double* __restrict__ out) {
+k_stokes_near32(int npp, const int* __restrict__ near_off, const int* __restrict__ near_idx,
+                const float4* __restrict__ src, const float2* __restrict__ XI,
+                const double* __restrict__ NX, const double* __restrict__ NY,
+                const yk_particle* __restrict__ parts, double scale, double* __restrict__ out) {
     extern __shared__ float4 sf_src32[];
+    __shared__ float2 dq;
     const int P = blockIdx.x;
+    const int e0 = near_off[P], e1 = near_off[P + 1];
+    if (e0 == e1) return;
+    const int tpb = blockDim.x;
     float tx[FAR_TMAX], ty[FAR_TMAX], nx[FAR_TMAX], ny[FAR_TMAX];
     double ax[FAR_TMAX], ay[FAR_TMAX];
 #pragma unroll
     for (int k = 0; k < FAR_TMAX; ++k) {
-        const int t = threadIdx.x + k * FAR_TPB;
+        const int t = threadIdx.x + k * tpb;
         const int64_t gi = (int64_t)P * npp + (t < npp ? t : 0);
         tx[k] = XI[gi].x;
         ty[k] = XI[gi].y;
@@ -424,25 +507,25 @@ k_stokes_far32(int np, int npp, int nchunk, const float4* __restrict__ src,
         ny[k] = (float)NY[gi];
         ax[k] = ay[k] = 0.0;
     }
-    const double pcx = parts[P].cx, pcy = parts[P].cy;
-    for (int Q = blockIdx.y; Q < np; Q += nchunk) {
-        if (Q == P) continue;
+    for (int e = e0; e < e1; ++e) {
+        const int Q = near_idx[e];
         __syncthreads();
-        for (int s = threadIdx.x; s < npp; s += FAR_TPB) sf_src32[s] = src[(int64_t)Q * npp + s];
+        for (int s = threadIdx.x; s < npp; s += tpb) sf_src32[s] = src[(int64_t)Q * npp + s];
+        if (threadIdx.x == 0)
+            dq = make_float2((float)(parts[P].cx - parts[Q].cx), (float)(parts[P].cy - parts[Q].cy));
         __syncthreads();
-        const float dx = (float)(pcx - parts[Q].cx), dy = (float)(pcy - parts[Q].cy);
         float ux[FAR_TMAX], uy[FAR_TMAX], bx[FAR_TMAX], by[FAR_TMAX];
 #pragma unroll
         for (int k = 0; k < FAR_TMAX; ++k) {
-            ux[k] = tx[k] + dx;
-            uy[k] = ty[k] + dy;
+            ux[k] = tx[k] + dq.x;
+            uy[k] = ty[k] + dq.y;
             bx[k] = by[k] = 0.0f;
         }
         for (int s = 0; s < npp; ++s) {
             const float4 q = sf_src32[s];
 #pragma unroll
             for (int k = 0; k < FAR_TMAX; ++k) {
-                if (k * FAR_TPB >= npp) break;
+                if (k * tpb >= npp) break;
                 const float rx = ux[k] - q.x, ry = uy[k] - q.y;
                 const float r2 = fmaf(rx, rx, ry * ry);
                 const float inv = __frcp_rn(r2);
@@ -459,12 +542,257 @@ k_stokes_far32(int np, int npp, int nchunk, const float4* __restrict__ src,
     }
 #pragma unroll
     for (int k = 0; k < FAR_TMAX; ++k) {
-        const int t = threadIdx.x + k * FAR_TPB;
+        const int t = threadIdx.x + k * tpb;
         if (t < npp) {
             const int64_t gi = (int64_t)P * npp + t;
-            atomicAdd(out + 2 * gi, scale * ax[k]);
-            atomicAdd(out + 2 * gi + 1, scale * ay[k]);
+            out[2 * gi] += scale * ax[k];
+            out[2 * gi + 1] += scale * ay[k];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Particle expansions of the far pairs (FP64 for the accurate operator, FP32
+// for the inner one). With z = x + i y, f = w (sigma_x + i sigma_y) at
+// s = y - c_Q and w = z - c_Q, the single layer and its traction summed over
+// the sources of Q are (complex forms of the stokeslet and of its stress)
+//   4 pi mu u = -(1/2) Phi_A(w) - (1/2) conj(Phi_Bc(w)) + (1/2) A_0
+//               + (1/2) w conj(Phi_A'(w)) - (1/2) conj(Psi_D'(w)),
+//   -4 pi t   = conj(nu) [conj(Phi_Bc'(w)) + conj(Psi_D''(w)) - w conj(Phi_A''(w))]
+//               + nu [conj(Phi_A'(w)) + Phi_A'(w)],
+// with the 2-D Laplace log-multipoles
+//   Phi_A  = A_0 log w - sum_k A_k w^-k / k,              A_k = sum f s^k,
+//   Phi_Bc = conj(A_0) log w - sum_k conj(B_k) w^-k / k,  B_k = sum f conj(s)^k,
+//   Psi_D  = conj(D_0) log w - sum_k conj(D_k) w^-k / k,  D_k = sum conj(f) s conj(s)^k.
+// Each is shifted to a local expansion about the target particle's centre
+// (the Laplace multipole-to-local translation). The factor w = omega + z0
+// (z0 = c_P - c_Q) is carried by a fourth local series conj(z0) Phi_A, so no
+// large absolute coordinate enters, and the constant (1/2) A_0 is folded into
+// the first. Only log|z0| enters the constant terms (their imaginary parts
+// cancel in u). The order per pair is the smallest that brings
+// (max r / (|z0| - max r))^p to 1e-17 (FP64) or 1e-8 (FP32).
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct cx {
+    T x, y;
+};
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T a, T b) {
+    cx<T> r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) {
+    return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) {
+    return mk<T>(a.x - b.x, a.y - b.y);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, T s) {
+    return mk<T>(a.x * s, a.y * s);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cj(cx<T> a) {
+    return mk<T>(a.x, -a.y);
+}
+template <typename T>
+__device__ cx<T> cpow(cx<T> a, int k) {
+    cx<T> r = mk<T>(1, 0);
+    while (k) {
+        if (k & 1) r = r * a;
+        a = a * a;
+        k >>= 1;
+    }
+    return r;
+}
+
+// Multipole coefficients coef[Q][set][k] (sets Phi_A, Phi_Bc, Psi_D) of every
+// particle, up to order kmax. Block Q, thread (set, k).
+template <typename T>
+__global__ void k_stokes_p2m(int npp, int kmax, const double4* __restrict__ s64,
+                             const float4* __restrict__ s32, const yk_particle* __restrict__ parts,
+                             cx<T>* __restrict__ coef) {
+    const int Q = blockIdx.x, t = threadIdx.x;
+    if (t >= 3 * SP1) return;
+    const int set = t / SP1, k = t % SP1;
+    cx<T> acc = mk<T>(0, 0);
+    if (k <= kmax) {
+        const double cxq = parts[Q].cx, cyq = parts[Q].cy;
+        for (int j = 0; j < npp; ++j) {
+            cx<T> sv, f;
+            if (sizeof(T) == 8) {
+                const double4 r = s64[(int64_t)Q * npp + j];
+                sv = mk<T>((T)(r.x - cxq), (T)(r.y - cyq));
+                f = mk<T>((T)r.z, (T)r.w);
+            } else {
+                const float4 r = s32[(int64_t)Q * npp + j];
+                sv = mk<T>((T)r.x, (T)r.y);
+                f = mk<T>((T)r.z, (T)r.w);
+            }
+            if (set == 0) acc = acc + f * cpow(sv, k);
+            else if (set == 1) acc = acc + f * cpow(cj(sv), k);
+            else acc = acc + cj(f) * sv * cpow(cj(sv), k);
+        }
+    }
+    cx<T> a = set == 0 ? acc : cj(acc);
+    if (k > 0) a = a * (T)(-1.0 / k);
+    coef[((int64_t)Q * 3 + set) * SP1 + k] = a;
+}
+
+// Local coefficients loc[P][set][l] (sets Phi_A, Phi_Bc, Psi_D, conj(z0)
+// Phi_A) of every particle from its far pairs; lmax[P] = the largest order
+// used (0: no far pair). Block P; warp w takes the pairs w, w + 8, ...; lane
+// l (and l + 32) the orders.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_stokes_m2l(const int* __restrict__ far_off, const StokesFar* __restrict__ far,
+             const cx<T>* __restrict__ coef, cx<T>* __restrict__ loc, int* __restrict__ lmax) {
+    __shared__ cx<T> red[8][4 * SP1];
+    __shared__ T invk[SP1 + 1];
+    __shared__ int wmax[8];
+    const int P = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k <= SP1; k += blockDim.x) invk[k] = k ? (T)(1.0 / k) : (T)0;
+    __syncthreads();
+    cx<T> acc[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc[h][s] = mk<T>(0, 0);
+    int pm = 0;
+    for (int e = far_off[P] + warp; e < far_off[P + 1]; e += 8) {
+        const StokesFar E = far[e];
+        const int p = sizeof(T) == 8 ? E.p64 : E.p32;
+        pm = max(pm, p);
+        const cx<T>* a = coef + (int64_t)E.q * 3 * SP1;
+        const cx<T> zi = mk<T>((T)E.zi.x, (T)E.zi.y);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = lane + 32 * h;
+            if (l > p) continue;
+            cx<T> v[3];
+            if (l == 0) {
+                const T lg = (T)E.logd;
+                cx<T> zk = zi;
+#pragma unroll
+                for (int s = 0; s < 3; ++s) v[s] = a[s * SP1] * lg;
+                for (int k = 1; k <= p; ++k) {
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) v[s] = v[s] + a[s * SP1 + k] * zk;
+                    zk = zk * zi;
+                }
+            } else {
+                const T il = invk[l];
+#pragma unroll
+                for (int s = 0; s < 3; ++s) v[s] = a[s * SP1] * (-il);
+                cx<T> zk = zi;
+                T c = 1;                                   // C(k + l - 1, l) at k = 1
+                for (int k = 1; k <= p; ++k) {
+                    const cx<T> w = zk * c;
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) v[s] = v[s] + a[s * SP1 + k] * w;
+                    zk = zk * zi;
+                    c = c * (T)(k + l) * invk[k];
+                }
+                const cx<T> zl = cpow(zi, l) * (T)((l & 1) ? -1 : 1);
+#pragma unroll
+                for (int s = 0; s < 3; ++s) v[s] = v[s] * zl;
+            }
+            const cx<T> z0c = mk<T>((T)E.z0.x, (T)(-E.z0.y));
+            acc[h][3] = acc[h][3] + z0c * v[0];
+            if (l == 0) v[0] = v[0] - a[0];
+#pragma unroll
+            for (int s = 0; s < 3; ++s) acc[h][s] = acc[h][s] + v[s];
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int l = lane + 32 * h;
+        if (l <= SP)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) red[warp][s * SP1 + l] = acc[h][s];
+    }
+    for (int o = 16; o > 0; o >>= 1) pm = max(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+    if (lane == 0) wmax[warp] = pm;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4 * SP1; e += blockDim.x) {
+        cx<T> t = red[0][e];
+        for (int w = 1; w < 8; ++w) t = t + red[w][e];
+        loc[(int64_t)P * 4 * SP1 + e] = t;
+    }
+    if (threadIdx.x == 0) {
+        int m = 0;
+        for (int w = 0; w < 8; ++w) m = max(m, wmax[w]);
+        lmax[P] = m;
+    }
+}
+
+// value, first and second derivative of sum_{l <= n} b_l w^l
+template <typename T>
+__device__ __forceinline__ void horner2(const cx<T>* b, int n, cx<T> w, cx<T>& f, cx<T>& f1,
+                                        cx<T>& f2) {
+    f = b[n];
+    f1 = mk<T>(0, 0);
+    f2 = mk<T>(0, 0);
+    for (int l = n - 1; l >= 0; --l) {
+        f2 = f2 * w + f1 * (T)2;
+        f1 = f1 * w + f;
+        f = f * w + b[l];
+    }
+}
+
+// out += the far field of the local expansions at every node (KIND 0:
+// traction with the node's normal, KIND 1: velocity). Block P.
+template <typename T, int KIND>
+__global__ void k_stokes_l2p(int npp, const double* __restrict__ X, const double* __restrict__ Y,
+                             const float2* __restrict__ XI, const double* __restrict__ NX,
+                             const double* __restrict__ NY, const yk_particle* __restrict__ parts,
+                             const cx<T>* __restrict__ loc, const int* __restrict__ lmax,
+                             double visc, double* __restrict__ out) {
+    __shared__ cx<T> b[4 * SP1];
+    const int P = blockIdx.x;
+    const int n = lmax[P];
+    if (n == 0) return;
+    for (int e = threadIdx.x; e < 4 * SP1; e += blockDim.x) b[e] = loc[(int64_t)P * 4 * SP1 + e];
+    __syncthreads();
+    const double pcx = parts[P].cx, pcy = parts[P].cy;
+    for (int t = threadIdx.x; t < npp; t += blockDim.x) {
+        const int64_t i = (int64_t)P * npp + t;
+        const cx<T> w = sizeof(T) == 8 ? mk<T>((T)(X[i] - pcx), (T)(Y[i] - pcy))
+                                       : mk<T>((T)XI[i].x, (T)XI[i].y);
+        cx<T> A, A1, A2, B, B1, B2, D, D1, D2, C, C1, C2;
+        horner2(b, n, w, A, A1, A2);
+        horner2(b + SP1, n, w, B, B1, B2);
+        horner2(b + 2 * SP1, n, w, D, D1, D2);
+        horner2(b + 3 * SP1, n, w, C, C1, C2);
+        double rx, ry;
+        if (KIND == 1) {
+            // 4 pi mu u = -(A + conj B)/2 + (w conj A' + conj C')/2 - conj D'/2
+            const cx<T> wa = w * cj(A1);
+            rx = 0.5 * (double)(-A.x - B.x + wa.x + C1.x - D1.x);
+            ry = 0.5 * (double)(-A.y + B.y + wa.y - C1.y + D1.y);
+            const double sc = 1.0 / (4.0 * S_PI * visc);
+            rx *= sc;
+            ry *= sc;
+        } else {
+            // -4 pi t = conj(nu) (conj B' + conj D'' - w conj A'' - conj C'') + nu (conj A' + A')
+            const cx<T> nu = mk<T>((T)NX[i], (T)NY[i]);
+            const cx<T> h = cj(B1 + D2 - C2) - w * cj(A2);
+            const cx<T> s1 = cj(nu) * h + nu * (A1.x * (T)2);
+            rx = -(double)s1.x / (4.0 * S_PI);
+            ry = -(double)s1.y / (4.0 * S_PI);
+        }
+        out[2 * i] += rx;
+        out[2 * i + 1] += ry;
     }
 }
 
@@ -564,7 +892,8 @@ void stokes_free(yk_geom* g) {
     Stokes& S = g->stokes;
     cudaStream_t st = g->ctx->stream;
     void* bufs[] = {S.B0, S.Bw, S.Bw32, S.S, S.moments, S.shapeLJ, S.LJ, S.s64, S.s32,
-                    S.sinc, S.mu, S.rhs, S.tmp, S.u, S.vo};
+                    S.sinc, S.mu, S.rhs, S.tmp, S.u, S.vo, S.coef64, S.loc64, S.coef32,
+                    S.loc32, S.lmax64, S.lmax32, S.near_off, S.near_idx, S.far_off, S.far};
     for (void* b : bufs) dev_free(b, st);
     free_workspace(S.ws, st);
     S = Stokes{};
@@ -577,7 +906,7 @@ static int stokes_ready(yk_geom* g) {
     if (S.ready) return YK_OK;
     if (g->npan < 3 || g->ngl > 64 || g->npp > FAR_TPB * FAR_TMAX) return YK_ERR_ARG;
     cudaStream_t st = g->ctx->stream;
-    const int npp = g->npp, ns = g->nshape;
+    const int npp = g->npp, ns = g->nshape, np = g->np;
     const int64_t ld = 2 * (int64_t)npp, blk = ld * ld;
     const int64_t n2 = 2 * g->n;
     YK_TRY(dev_alloc((void**)&S.B0, sizeof(double) * blk * ns, st));
@@ -586,12 +915,20 @@ static int stokes_ready(yk_geom* g) {
     YK_TRY(dev_alloc((void**)&S.S, sizeof(double) * blk * ns, st));
     YK_TRY(dev_alloc((void**)&S.moments, sizeof(double) * 3 * g->ngl * g->ngl, st));
     YK_TRY(dev_alloc((void**)&S.shapeLJ, sizeof(double) * 2 * ns, st));
-    YK_TRY(dev_alloc((void**)&S.LJ, sizeof(double) * 2 * g->np, st));
+    YK_TRY(dev_alloc((void**)&S.LJ, sizeof(double) * 2 * np, st));
     YK_TRY(dev_alloc((void**)&S.s64, sizeof(double4) * g->n, st));
     YK_TRY(dev_alloc((void**)&S.s32, sizeof(float4) * g->n, st));
     for (double** v : {&S.sinc, &S.mu, &S.rhs, &S.tmp, &S.u})
         YK_TRY(dev_alloc((void**)v, sizeof(double) * n2, st));
-    YK_TRY(dev_alloc((void**)&S.vo, sizeof(double) * 3 * g->np, st));
+    YK_TRY(dev_alloc((void**)&S.vo, sizeof(double) * 3 * np, st));
+    YK_TRY(dev_alloc((void**)&S.coef64, sizeof(double2) * 3 * SP1 * np, st));
+    YK_TRY(dev_alloc((void**)&S.loc64, sizeof(double2) * 4 * SP1 * np, st));
+    YK_TRY(dev_alloc((void**)&S.coef32, sizeof(float2) * 3 * SP1 * np, st));
+    YK_TRY(dev_alloc((void**)&S.loc32, sizeof(float2) * 4 * SP1 * np, st));
+    YK_TRY(dev_alloc((void**)&S.lmax64, sizeof(int) * np, st));
+    YK_TRY(dev_alloc((void**)&S.lmax32, sizeof(int) * np, st));
+    YK_TRY(dev_alloc((void**)&S.near_off, sizeof(int) * (np + 1), st));
+    YK_TRY(dev_alloc((void**)&S.far_off, sizeof(int) * (np + 1), st));
     YK_TRY(alloc_krylov(S.ws, n2, g->prm.gmres_restart, st));
     YK_LAUNCH(k_log_moments, 3 * g->ngl, 64, 0, st, g->ngl, g->d_glx, S.moments);
     YK_LAUNCH(k_shape_LJ, ns, 256, 0, st, g->npan, g->ngl, g->d_shape_ab, g->d_glx, g->d_glw,
@@ -605,12 +942,50 @@ static int stokes_ready(yk_geom* g) {
     return YK_OK;
 }
 
-static int far_chunks(const yk_geom* g) {
-    return std::max(1, std::min(g->np - 1, ceil_div(4 * 152, g->np)));
+// Near partners and far pairs of every particle (CSR), for the current
+// positions: counts, prefix sums on the host, fill.
+static int stokes_lists(yk_geom* g) {
+    Stokes& S = g->stokes;
+    if (S.lists_valid) return YK_OK;
+    cudaStream_t st = g->ctx->stream;
+    const int np = g->np;
+    std::vector<int> cn(np), cf(np);
+    YK_LAUNCH(k_stokes_count, ceil_div(np, 128), 128, 0, st, np, g->d_particles, S.near_off,
+              S.far_off);
+    YK_TRY_CUDA(cudaMemcpyAsync(cn.data(), S.near_off, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+    YK_TRY_CUDA(cudaMemcpyAsync(cf.data(), S.far_off, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+    YK_TRY_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> on(np + 1, 0), of(np + 1, 0);
+    for (int i = 0; i < np; ++i) {
+        on[i + 1] = on[i] + cn[i];
+        of[i + 1] = of[i] + cf[i];
+    }
+    if (on[np] > S.near_cap) {
+        dev_free(S.near_idx, st);
+        S.near_idx = nullptr;
+        YK_TRY(dev_alloc((void**)&S.near_idx, sizeof(int) * std::max(1, on[np]), st));
+        S.near_cap = on[np];
+    }
+    if (of[np] > S.far_cap) {
+        dev_free(S.far, st);
+        S.far = nullptr;
+        YK_TRY(dev_alloc((void**)&S.far, sizeof(StokesFar) * std::max(1, of[np]), st));
+        S.far_cap = of[np];
+    }
+    YK_TRY_CUDA(cudaMemcpyAsync(S.near_off, on.data(), sizeof(int) * (np + 1),
+                                cudaMemcpyHostToDevice, st));
+    YK_TRY_CUDA(cudaMemcpyAsync(S.far_off, of.data(), sizeof(int) * (np + 1),
+                                cudaMemcpyHostToDevice, st));
+    YK_LAUNCH(k_stokes_fill, ceil_div(np, 128), 128, 0, st, np, g->d_particles, S.near_off,
+              S.near_idx, S.far_off, S.far);
+    YK_TRY_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
+    S.lists_valid = true;
+    return YK_OK;
 }
 
 int stokes_apply(yk_geom* g, const double* sig, double* out, Prec prec, int which) {
     YK_TRY(stokes_ready(g));
+    YK_TRY(stokes_lists(g));
     Stokes& S = g->stokes;
     cudaStream_t st = g->ctx->stream;
     const int npp = g->npp, np = g->np;
@@ -630,18 +1005,40 @@ int stokes_apply(yk_geom* g, const double* sig, double* out, Prec prec, int whic
     if (np < 2) return YK_OK;
     YK_LAUNCH(k_stokes_sources, ceil_div(g->n, 256), 256, 0, st, g->n, g->d_x, g->d_y, g->d_w,
               g->d_xi, sig, f32 ? nullptr : S.s64, f32 ? S.s32 : nullptr);
-    const dim3 fgrid(np, far_chunks(g));
+    const int tpb = npp <= FAR_TPB ? 32 * ceil_div(npp, 32) : FAR_TPB;
     if (f32) {
-        YK_LAUNCH(k_stokes_far32, fgrid, FAR_TPB, sizeof(float4) * npp, st, np, npp, (int)fgrid.y,
-                  S.s32, g->d_xi, g->d_nx, g->d_ny, g->d_particles, -1.0 / S_PI, out);
-    } else if (which == STOKES_VELOCITY) {
-        YK_LAUNCH(k_stokes_far64<1>, fgrid, FAR_TPB, sizeof(double4) * npp, st, np, npp,
-                  (int)fgrid.y, S.s64, g->d_x, g->d_y, g->d_nx, g->d_ny,
-                  1.0 / (4.0 * S_PI * g->prm.viscosity), out);
-    } else {
-        YK_LAUNCH(k_stokes_far64<0>, fgrid, FAR_TPB, sizeof(double4) * npp, st, np, npp,
-                  (int)fgrid.y, S.s64, g->d_x, g->d_y, g->d_nx, g->d_ny, -1.0 / S_PI, out);
+        YK_LAUNCH(k_stokes_near32, np, tpb, sizeof(float4) * npp, st, npp, S.near_off,
+                  S.near_idx, S.s32, g->d_xi, g->d_nx, g->d_ny, g->d_particles, -1.0 / S_PI, out);
+        YK_LAUNCH(k_stokes_p2m<float>, np, 128, 0, st, npp, SP, S.s64, S.s32, g->d_particles,
+                  (cx<float>*)S.coef32);
+        YK_LAUNCH(k_stokes_m2l<float>, np, 256, 0, st, S.far_off, S.far,
+                  (const cx<float>*)S.coef32, (cx<float>*)S.loc32, S.lmax32);
+        YK_LAUNCH((k_stokes_l2p<float, 0>), np, 128, 0, st, npp, g->d_x, g->d_y, g->d_xi,
+                  g->d_nx, g->d_ny, g->d_particles, (const cx<float>*)S.loc32, S.lmax32,
+                  g->prm.viscosity, out);
+        YK_TRY_CUDA(cudaGetLastError());
+        return YK_OK;
     }
+    const bool vel = which == STOKES_VELOCITY;
+    if (vel)
+        YK_LAUNCH(k_stokes_near64<1>, np, tpb, sizeof(double4) * npp, st, npp, S.near_off,
+                  S.near_idx, S.s64, g->d_x, g->d_y, g->d_nx, g->d_ny,
+                  1.0 / (4.0 * S_PI * g->prm.viscosity), out);
+    else
+        YK_LAUNCH(k_stokes_near64<0>, np, tpb, sizeof(double4) * npp, st, npp, S.near_off,
+                  S.near_idx, S.s64, g->d_x, g->d_y, g->d_nx, g->d_ny, -1.0 / S_PI, out);
+    YK_LAUNCH(k_stokes_p2m<double>, np, 128, 0, st, npp, SP, S.s64, S.s32, g->d_particles,
+              (cx<double>*)S.coef64);
+    YK_LAUNCH(k_stokes_m2l<double>, np, 256, 0, st, S.far_off, S.far,
+              (const cx<double>*)S.coef64, (cx<double>*)S.loc64, S.lmax64);
+    if (vel)
+        YK_LAUNCH((k_stokes_l2p<double, 1>), np, 128, 0, st, npp, g->d_x, g->d_y, g->d_xi,
+                  g->d_nx, g->d_ny, g->d_particles, (const cx<double>*)S.loc64, S.lmax64,
+                  g->prm.viscosity, out);
+    else
+        YK_LAUNCH((k_stokes_l2p<double, 0>), np, 128, 0, st, npp, g->d_x, g->d_y, g->d_xi,
+                  g->d_nx, g->d_ny, g->d_particles, (const cx<double>*)S.loc64, S.lmax64,
+                  g->prm.viscosity, out);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

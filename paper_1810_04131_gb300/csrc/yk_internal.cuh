@@ -153,6 +153,15 @@ struct Dynamics {
 }  // namespace yk
 
 namespace yk {
+// A far particle pair of the Stokes far field (stokes.cu).
+struct StokesFar {
+    double2 z0;      // c_P - c_Q
+    double2 zi;      // 1 / z0
+    double logd;     // log |z0|
+    int q;           // source particle
+    short p64, p32;  // expansion orders for 1e-17 (FP64) and 1e-8 (FP32)
+};
+
 // Stokes mobility state (stokes.cu), built on the first Stokes call.
 struct Stokes {
     bool ready = false;
@@ -167,6 +176,19 @@ struct Stokes {
     float4* s32 = nullptr;      // FP32 source records (offset from the centre, w sigma)
     double *sinc = nullptr, *mu = nullptr, *rhs = nullptr, *tmp = nullptr, *u = nullptr;  // 2n
     double* vo = nullptr;       // 3 np scratch
+    double2* coef64 = nullptr;  // particle multipoles [np][3][41], FP64
+    double2* loc64 = nullptr;   // local expansions [np][4][41], FP64
+    float2* coef32 = nullptr;   // the same in FP32 (inner operator)
+    float2* loc32 = nullptr;
+    int* lmax64 = nullptr;      // [np] highest local order used (0: no far pair)
+    int* lmax32 = nullptr;
+    bool lists_valid = false;   // pair lists for the current positions
+    int* near_off = nullptr;    // [np + 1] near partners (CSR)
+    int* near_idx = nullptr;
+    int near_cap = 0;
+    int* far_off = nullptr;     // [np + 1] far pairs (CSR)
+    StokesFar* far = nullptr;
+    int far_cap = 0;
     Workspace ws;               // Krylov workspace on vectors of 2n
 };
 }  // namespace yk

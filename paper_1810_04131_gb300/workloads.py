@@ -225,6 +225,21 @@ def disks8192():
     return Workload("disks8192", p, rho=1.0, qbx_order=10, box=800.0)
 
 
+TABLE2_BOX = {250: 100.0, 500: 200.0, 1000: 200.0, 2000: 400.0}
+
+
+def table2(n_particles):
+    """The large collections of Table 2: n unit disks in the printed L x L box
+    (250: 100, 500 and 1000: 200, 2000: 400), 70 boundary points per particle
+    (10 panels x 7 nodes, the N_GL = 7 reading of Table 1), rho = 4, GMRES
+    tolerance 1e-5 as printed. Not printed, taken here: QBX order 8 (Table 1's
+    highest at 70 points) and a minimum gap of 0.5."""
+    box = TABLE2_BOX[n_particles]
+    p = make_particles(n_particles, box, 0.5, seed=20 + n_particles)
+    return Workload("table2_%d" % n_particles, p, rho=4.0, n_panels=10, n_gl=7, qbx_order=8,
+                    gmres_tol=1e-5, box=box)
+
+
 def small_system(n, seed, shape=SHAPE_DISK, n_panels=8, n_gl=16, rho=1.0,
                  qbx_order=10, gap=0.5, A=1.0, B=1.0):
     """A small seeded system for parity tests (box scaled to ~4% area fraction)."""

@@ -5,7 +5,10 @@
 
 Cases: p2p_f32 (mixed matvec: FP32 far field + near rows), p2p_f64 (FP64
 matvec), grad (precision-split normal derivative), qbx (geometry + QBX rows), solve (one mixed solve +
-forces). The geometry is built first; then the case runs --reps times. The case
+forces), stokes_f64 / stokes_f32 (the Stokes mobility operator, FP64 with
+particle expansions / FP32), mobility (one mixed Stokes mobility solve under
+unit loads). Workloads: the named ones and table2_<n> (n = 250, 500, 1000,
+2000). The geometry is built first; then the case runs --reps times. The case
 requests instead solves single requests of the seeded serving stream alone (one
 of about 4, 6, 13, 34, 68 and 156 particles), twice each, and prints the wall
 time of geometry creation and of the second solve.
@@ -23,7 +26,8 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="p2p_f32",
-                    choices=["p2p_f32", "p2p_f64", "grad", "qbx", "solve", "requests"])
+                    choices=["p2p_f32", "p2p_f64", "grad", "qbx", "solve", "requests",
+                             "stokes_f64", "stokes_f32", "mobility"])
     ap.add_argument("--workload", default="disks512")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--farfield", default="dense", choices=["dense", "cutoff", "fmm"])
@@ -34,7 +38,10 @@ def main():
     from paper_1810_04131_gb300 import yk
     if a.case == "requests":
         return requests(torch, W, yk)
-    wl = W.WORKLOADS[a.workload]()
+    if a.workload.startswith("table2_"):
+        wl = W.table2(int(a.workload[len("table2_"):]))
+    else:
+        wl = W.WORKLOADS[a.workload]()
     if a.particles > 0:
         wl.particles = wl.particles[:a.particles]
     ctx = yk.Context(0, torch.cuda.current_stream().cuda_stream)
@@ -56,6 +63,14 @@ def main():
         elif a.case == "qbx":
             g2 = yk.Geometry(ctx, wl.particles, prm)
             g2.close()
+        elif a.case in ("stokes_f64", "stokes_f32"):
+            s2 = torch.ones(2 * g.n, dtype=torch.float64, device=dev)
+            o2 = torch.zeros_like(s2)
+            g.yk_stokes_apply(s2, yk.YK_STOKES_COMPLETED,
+                              yk.YK_FP64 if a.case == "stokes_f64" else yk.YK_MIXED, out=o2)
+        elif a.case == "mobility":
+            n = g.n_particles
+            g.yk_mobility([[1.0, 0.0]] * n, [0.5] * n)
         elif a.case == "solve":
             s, info = g.yk_solve(f, out=y)
             g.yk_forces_torques(y, f, want_net=False)

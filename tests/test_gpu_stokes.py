@@ -4,8 +4,9 @@ mobilityu, mob_vec) against the FP64 oracle (oracle/stokes_oracle.py),
 through the C ABI:
   * the three boundary operators (interior traction 1/2 I + K*, the completed
     operator with the rigid-motion projector W, the on-surface single layer
-    S) on disks and turned ellipses, for two panel layouts: 1e-12 relative in
-    FP64, 1e-6 with the FP32 far field;
+    S) on disks and turned ellipses, for two panel layouts, close particles
+    (node-by-node sums) and spread ones (particle expansions for far pairs):
+    1e-12 relative in FP64, 1e-6 with the FP32 far field;
   * v, omega and the density of the mobility problem, FP64 and mixed
     precision, at the default tolerance: 1e-10;
   * a single disk under a torque turns at tau / (4 pi mu a^2);
@@ -59,9 +60,17 @@ def _geom(yk, ctx, parts, npan=16, ngl=16, **kw):
     return yk.Geometry(ctx, parts, yk.params_for(wl, **kw))
 
 
-@pytest.mark.parametrize("npan,ngl", [(16, 16), (12, 10)])
-def test_stokes_operators_match_oracle(yk, ctx, npan, ngl):
-    parts = _three()
+def _spread():
+    """12 ellipses over a 31 x 31 box: most particle pairs are far (centre
+    distance >= 2 (r_P + r_Q)) and go through the particle expansions."""
+    return W.small_system(12, 41, shape=W.SHAPE_ELLIPSE, n_panels=12, A=1.0, B=0.5,
+                          gap=0.3).particles
+
+
+@pytest.mark.parametrize("case,npan,ngl", [("three", 16, 16), ("three", 12, 10),
+                                           ("spread", 12, 16)])
+def test_stokes_operators_match_oracle(yk, ctx, case, npan, ngl):
+    parts = _three() if case == "three" else _spread()
     o = so.StokesOracle(parts, npan, ngl, viscosity=1.3)
     A0, A, S = o.operators
     g = _geom(yk, ctx, parts, npan, ngl, viscosity=1.3)
@@ -75,16 +84,18 @@ def test_stokes_operators_match_oracle(yk, ctx, npan, ngl):
     g.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_mobility_matches_oracle(yk, ctx, precision):
-    parts = _three()
+@pytest.mark.parametrize("case,precision", [("three", "fp64"), ("three", "mixed"),
+                                            ("spread", "fp64"), ("spread", "mixed")])
+def test_mobility_matches_oracle(yk, ctx, case, precision):
+    parts = _three() if case == "three" else _spread()
+    npan = 16 if case == "three" else 12
     rng = np.random.default_rng(7)
-    F = rng.standard_normal((3, 2))
-    tau = rng.standard_normal(3)
-    o = so.StokesOracle(parts, 16, 16, viscosity=0.8)
+    F = rng.standard_normal((len(parts), 2))
+    tau = rng.standard_normal(len(parts))
+    o = so.StokesOracle(parts, npan, 16, viscosity=0.8)
     ref = o.mobility(F, tau)
     prec = yk.YK_FP64 if precision == "fp64" else yk.YK_MIXED
-    g = _geom(yk, ctx, parts, precision=prec, viscosity=0.8)
+    g = _geom(yk, ctx, parts, npan, precision=prec, viscosity=0.8)
     v, om, sig, info = g.yk_mobility(F, tau, want_sigma=True)
     assert info["rel_residual"] <= 1e-12, info
     assert (info["refinements"] > 0) == (precision == "mixed")
