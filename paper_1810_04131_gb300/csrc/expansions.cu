@@ -81,24 +81,26 @@ __global__ void k_p2m(GeomView G, const double* __restrict__ sigma, int wpp,
 
 // M2L from the band neighbours of each target particle Q into its local
 // coefficients L[Q][m], m = 0..EXP_ORDER (written; zero without neighbours).
-// One block of four warps per target particle: warp w takes neighbours
-// w, w + 4, ... of the list, lane t handles m = t and m = t + 32, and the
-// four partial expansions are summed in a fixed order at the end.
-constexpr int M2L_WARPS = 4;
+// With D = c_Q - c_P = |D| e^{i psi}, Graf's theorem gives
+//   L_m = (-1)^m e^{i m psi} sum_{n=-p}^{p} M'_n K_{|n+m|}(|D|/rho),
+//   M'_n = M_n e^{i n psi}, M'_{-n} = conj(M'_n):
+// the multipole is turned once per pair so that the sum has real weights.
+// One block of eight warps per target particle: warp w takes neighbours
+// w, w + 8, ... of the list, lane t handles m = t and m = t + 32, and the
+// partial expansions are summed in a fixed order at the end.
+constexpr int M2L_WARPS = 8;
 __global__ void __launch_bounds__(32 * M2L_WARPS) k_band_m2l(GeomView G,
                                                              const double2* __restrict__ M,
                                                              const int* __restrict__ off,
                                                              const int* __restrict__ nbr,
                                                              double2* __restrict__ Lout) {
     __shared__ double Ksh[M2L_WARPS][2 * EXP_ORDER + 1];    // K_k(|D|/rho), k = 0..2p
-    __shared__ double2 Esh[M2L_WARPS][3 * EXP_ORDER + 1];   // e^{i k psi}, k = -p..2p
-    __shared__ double2 Msh[M2L_WARPS][EXP_N];
+    __shared__ double2 Msh[M2L_WARPS][EXP_N];               // M'_n, n = 0..p
     __shared__ double2 Lsh[M2L_WARPS][EXP_N];
     const int q = blockIdx.x;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (q >= G.np) return;                                // block-uniform
     double* Kr = Ksh[wib];
-    double2* eps = Esh[wib];
     double2* Ms = Msh[wib];
     const int k0 = off[q], k1 = off[q + 1];
     const double rho = G.rho;
@@ -119,28 +121,33 @@ __global__ void __launch_bounds__(32 * M2L_WARPS) k_band_m2l(GeomView G,
             const double zi2 = 2.0 / z;
             for (int n = 1; n < 2 * EXP_ORDER; ++n) Kr[n + 1] = fma(n * zi2, Kr[n], Kr[n - 1]);
         }
-        for (int t = lane; t < 3 * EXP_ORDER + 1; t += 32) {
+        double2 e[2];                                     // e^{i m psi}, m = lane, lane + 32
+        for (int h = 0; h < 2; ++h) {
+            const int t = lane + 32 * h;
+            if (t > EXP_ORDER) break;
             double s_, c_;
-            sincos((t - EXP_ORDER) * psi, &s_, &c_);
-            eps[t] = make_double2(c_, s_);
+            sincos(t * psi, &s_, &c_);
+            e[h] = make_double2(c_, s_);
+            const double2 m = M[(int64_t)p * EXP_N + t];
+            Ms[t] = make_double2(m.x * c_ - m.y * s_, m.x * s_ + m.y * c_);
         }
-        for (int t = lane; t < EXP_N; t += 32) Ms[t] = M[(int64_t)p * EXP_N + t];
         __syncwarp();
         for (int h = 0; h < 2; ++h) {
             const int m = lane + 32 * h;
             if (m > EXP_ORDER) break;
-            double lr = 0.0, li = 0.0;
-            for (int n = -EXP_ORDER; n <= EXP_ORDER; ++n) {
-                const double2 Mn = n >= 0 ? Ms[n] : make_double2(Ms[-n].x, -Ms[-n].y);
-                const int kk = n + m;                            // in [-p, 2p]
-                const double Kv = Kr[kk < 0 ? -kk : kk];
-                const double2 e = eps[kk + EXP_ORDER];
-                lr += Kv * (Mn.x * e.x - Mn.y * e.y);            // M_n K e^{i (n+m) psi}
-                li += Kv * (Mn.x * e.y + Mn.y * e.x);
+            double lr = Ms[0].x * Kr[m], li = Ms[0].y * Kr[m];
+            for (int n = 1; n <= EXP_ORDER; ++n) {
+                const double2 Mn = Ms[n];
+                const double kp = Kr[n + m], km = Kr[n > m ? n - m : m - n];
+                // M'_n K_{n+m} + conj(M'_n) K_{|m-n|}
+                lr = fma(Mn.x, kp + km, lr);
+                li = fma(Mn.y, kp - km, li);
             }
             const double sg = (m & 1) ? -1.0 : 1.0;
-            if (h == 0) lr0 += sg * lr, li0 += sg * li;
-            else lr1 += sg * lr, li1 += sg * li;
+            const double ur = sg * (lr * e[h].x - li * e[h].y);
+            const double ui = sg * (lr * e[h].y + li * e[h].x);
+            if (h == 0) lr0 += ur, li0 += ui;
+            else lr1 += ur, li1 += ui;
         }
     }
     Lsh[wib][lane] = make_double2(lr0, li0);
