@@ -187,6 +187,8 @@ int alloc_workspace(yk_geom* g) {
     w.nchunk = ceil_div(g->np, ppc);
     YK_TRY(dev_alloc((void**)&w.partial, sizeof(double) * w.nchunk * n, st));
     YK_TRY(dev_alloc((void**)&w.src4, sizeof(float4) * 2 * (size_t)g->np * ((g->npp + 1) / 2), st));
+    YK_TRY(dev_alloc((void**)&w.src4g, sizeof(float4) * 3 * (size_t)g->np * ((g->npp + 1) / 2),
+                     st));
     YK_TRY(alloc_krylov(w, n, g->prm.gmres_restart, st));
     if (!host_status(g->ctx)) return YK_ERR_NO_MEMORY;
     return YK_OK;
@@ -195,6 +197,7 @@ int alloc_workspace(yk_geom* g) {
 void free_workspace(Workspace& w, cudaStream_t st) {
     dev_free(w.partial, st);
     dev_free(w.src4, st);
+    dev_free(w.src4g, st);
     dev_free(w.V, st);
     dev_free(w.H, st);
     dev_free(w.gvec, st);

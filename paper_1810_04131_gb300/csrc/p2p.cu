@@ -58,8 +58,8 @@ static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
     if (!L.valid) {
         cudaStream_t st = g->ctx->stream;
         GeomView G = g->view();
-        const bool mask = kind == 1;
-        const double gap = mask ? g->split_gap : 0.0;
+        const bool mask = kind >= 1;   // 1: value split, 2: normal-derivative split
+        const double gap = kind == 1 ? g->split_gap : (kind == 2 ? g->split_gap_grad : 0.0);
         int* counts = (int*)g->ws.partial;   // 2 np + 1 ints of scratch (partial holds >= n doubles)
         int* off = counts + g->np;
         YK_LAUNCH(k_sym_count, ceil_div(g->np, 128), 128, 0, st, G, mask, gap, counts);
@@ -107,6 +107,22 @@ static int far_sym(yk_geom* g, int kind, double* out) {
     if (p.blocks == 0) return YK_OK;
     YK_LAUNCH(k_p2p_f32_sym, (unsigned)p.blocks, F32_TPB, 0, g->ctx->stream, g->view(),
               g->ws.src4, p.tasks, p.ntasks, p.qch, p.ipb, p.kscale, out);
+    return YK_OK;
+}
+
+// FP32 far field of the split normal derivative by the symmetric kernel
+// (pairs beyond the normal derivative's split distance), added to out.
+static int far_symg(yk_geom* g, const double* sigma, double* out) {
+    SymParams p;
+    YK_TRY(sym_params(g, 2, &p));
+    if (p.blocks == 0) return YK_OK;
+    const int64_t npairs = (int64_t)g->np * ((g->npp + 1) / 2);
+    cudaStream_t st = g->ctx->stream;
+    YK_LAUNCH(k_src_grad_pairs, (unsigned)((npairs + 255) / 256), 256, 0, st, g->view(), sigma,
+              (float)(LOG2E / g->prm.rho), g->ws.src4g);
+    const double kscale = sqrt(LOG2E) * (1.0 / g->prm.rho) * (LOG2E / g->prm.rho) / (2.0 * PI);
+    YK_LAUNCH(k_p2p_f32_symg, (unsigned)p.blocks, F32_TPB, 0, st, g->view(), g->ws.src4g, p.tasks,
+              p.ntasks, p.qch, p.ipb, kscale, out);
     return YK_OK;
 }
 
@@ -411,9 +427,6 @@ static int normal_derivative_body(yk_geom* g, const double* sigma, double* un, P
     if (g->prm.farfield != YK_FARFIELD_DENSE) return matvec_cutoff(g, sigma, un, prec, true);
     cudaStream_t st = g->ctx->stream;
     GeomView G = g->view();
-    const int nchunk = g->ws.nchunk;
-    const int ppc = ceil_div(g->np, nchunk);
-    dim3 grid(ceil_div(g->n, TPB), nchunk);
     const int kind = (prec == Prec::F64) ? 2 : 1;
     const int2* list;
     int ntiles;
@@ -421,13 +434,8 @@ static int normal_derivative_body(yk_geom* g, const double* sigma, double* un, P
     double* extra = g->ws.vec[5];
     YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
     YK_TRY(self_blocks(g, sigma, extra, true));
-    int used_chunks = 0;
-    if (prec != Prec::F64) {
-        YK_TRY(stage_sources(g, sigma));
-        YK_LAUNCH(k_p2p_f32_grad<true>, grid, F32_TPB, 0, st, G, g->ws.src4, ppc,
-                  g->split_gap_grad, g->ws.partial);
-        used_chunks = nchunk;
-    }
+    const int used_chunks = 0;
+    if (prec != Prec::F64) YK_TRY(far_symg(g, sigma, extra));   // pairs beyond the split distance
     YK_LAUNCH(k_tiles_f64<true>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
               tiles_qsplit(g, ntiles), extra);
     if (prec != Prec::F64) YK_TRY(band_expansions(g, sigma, extra, true));

@@ -16,14 +16,18 @@
 // The kernels:
 //  * k_src_pairs: the pair-packed FP32 source records of the density, once
 //    per operator application (read by every block of the FP32 kernels).
-//  * k_p2p_f32 / k_p2p_f32_grad: FP32 evaluation with FP64 accumulation per
-//    source particle; blockIdx.x = 256 consecutive targets (two per thread),
-//    blockIdx.y = a chunk of source particles, partial sums per chunk.
-//    With a skip distance they leave out the particle pairs that the FP64
-//    tiles handle (same FP64 predicate in both places). Per block and source
-//    particle, the range of node-pair distances picks the evaluation: none
-//    (every pair underflows to an exact FP32 zero), the full or the short K1
-//    fit, or (value kernels) an expansion about the particle's 1/z'.
+//  * k_p2p_f32: FP32 evaluation with FP64 accumulation per source particle
+//    (systems without self blocks); blockIdx.x = 256 consecutive targets (two
+//    per thread), blockIdx.y = a chunk of source particles, partial sums per
+//    chunk. Per block and source particle, the range of node-pair distances
+//    picks the evaluation: none (every pair underflows to an exact FP32
+//    zero), the full or the short K1 fit, or an expansion about the
+//    particle's 1/z'.
+//  * k_p2p_f32_sym / k_p2p_f32_symg: the symmetric FP32 far field over a list
+//    of particle pairs, value and normal derivative: one evaluation per node
+//    pair serves both directions. With a skip distance the lists leave out
+//    the particle pairs that the FP64 tiles handle (same FP64 predicate in
+//    both places).
 //  * k_p2p_f32_cut / k_p2p_f32_grad_cut: the same per target particle over
 //    a neighbour list (cut-off and FMM near fields).
 //  * k_tiles_f64<GRAD>: one block per listed particle pair (P, Q), P <= Q,
@@ -551,69 +555,6 @@ __global__ void __launch_bounds__(F32_TPB, 8) k_p2p_f32(GeomView G, const float4
 }
 #endif
 
-// FP32 normal derivative of the far field, two targets per thread, packed
-// pairs (same staging and masking as k_p2p_f32).
-#ifdef YK_DEFINE_P2P_KERNELS
-template <bool MASK>
-__global__ void __launch_bounds__(F32_TPB) k_p2p_f32_grad(GeomView G,
-                                                          const float4* __restrict__ rec,
-                                                          int ppc, double skip_gap,
-                                                          double* __restrict__ partial) {
-    __shared__ float4 srcA[STILE / 2], srcB[STILE / 2];
-    const int64_t i0 = blockIdx.x * (int64_t)TPB + threadIdx.x;
-    const int64_t i1 = i0 + F32_TPB;
-    const bool act0 = i0 < G.n, act1 = i1 < G.n;
-    const int64_t ii0 = act0 ? i0 : 0, ii1 = act1 ? i1 : 0;
-    const float2 xi0 = G.xi[ii0], xi1 = G.xi[ii1];
-    const float nx0 = (float)G.nx[ii0], ny0 = (float)G.ny[ii0];
-    const float nx1 = (float)G.nx[ii1], ny1 = (float)G.ny[ii1];
-    const int pt0 = (int)(ii0 / G.npp), pt1 = (int)(ii1 / G.npp);
-    const int pan0 = (int)(ii0 % G.npp) / G.ngl, pan1 = (int)(ii1 % G.npp) / G.ngl;
-    const float kappa = (float)(1.0 / G.rho), rho = (float)G.rho;
-    const float kpf = (float)(LOG2E / G.rho), inv_kp = (float)(G.rho / LOG2E);
-    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
-    const float short_gap = Z_SHORT * (float)G.rho, zero_gap = ZP_ZERO / kpf;
-    const int pa = (int)(blockIdx.x * (int64_t)TPB / G.npp);
-    const int pb = (int)((min((int64_t)G.n, (blockIdx.x + 1) * (int64_t)TPB) - 1) / G.npp);
-    const int s0 = blockIdx.y * ppc;
-    const int s1 = min(G.np, s0 + ppc);
-    double fast0 = 0.0, fast1 = 0.0, slow0 = 0.0, slow1 = 0.0;
-    for (int s = s0; s < s1; ++s) {
-        const float bg = block_range(G, pa, pb, s).gap;
-        if (bg >= zero_gap) continue;   // every pair adds +0 in FP32 (block-uniform)
-        const PolyRZ2 P(bg >= short_gap);
-        const bool short_fit = bg >= short_gap;
-        TargetF32 T0, T1;
-        target_setup(T0, G, pt0, s, xi0, kpf, near_gap, MASK, skip_gap, pan0);
-        target_setup(T1, G, pt1, s, xi1, kpf, near_gap, MASK, skip_gap, pan1);
-        const bool block_skip = MASK ? __syncthreads_and(T0.skip && T1.skip) : false;
-        if (block_skip) continue;
-        const bool use0 = !(MASK && T0.skip), use1 = !(MASK && T1.skip);
-        for (int jb = 0; jb < G.npp; jb += STILE) {
-            const int cnt = min(STILE, G.npp - jb);
-            __syncthreads();
-            stage_rec(rec, G.npp, s, jb, cnt, srcA, srcB);
-            __syncthreads();
-            float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-            if (short_fit)
-                grad_tile<FIT_SHORT>(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1,
-                             inv_kp, kappa, rho, P, a0, a1, b0, b1);
-            else
-                grad_tile<FIT_LONG>(srcA, srcB, jb, cnt, G, T0, T1, use0, use1, nx0, ny0, nx1, ny1,
-                             inv_kp, kappa, rho, P, a0, a1, b0, b1);
-            fast0 += (double)a0;
-            fast1 += (double)a1;
-            slow0 += (double)b0;
-            slow1 += (double)b1;
-        }
-    }
-    const double cf = sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho);
-    const double sc = 1.0 / (2.0 * PI);
-    if (act0) partial[blockIdx.y * G.n + i0] = (fast0 * cf + slow0) * sc;
-    if (act1) partial[blockIdx.y * G.n + i1] = (fast1 * cf + slow1) * sc;
-}
-#endif
-
 // ---------------------------------------------------------------------------
 // Symmetric FP32 far field of the dense operator (k_p2p_f32_sym).
 //
@@ -869,6 +810,257 @@ __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const fl
                                                            double kscale,
                                                            double* __restrict__ out) {
     sym_items(G, rec, tasks, ntasks, qch, ipb, kscale, out, blockIdx.x);
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// Symmetric FP32 far field of the normal derivative (k_p2p_f32_symg).
+//
+// For nodes i of P and j of Q, d = x_i - y_j, the normal-derivative kernel
+//   H(i, j) = g(r) (nu_i . nu_j) + g'(r) (d . nu_j)(d . nu_i) / r,
+//   g = K1(r/rho) / (rho r) (2 pi left out),
+// is symmetric: the term of node j at node i is H q_j and that of node i at
+// node j is H q_i (q = w sigma). One evaluation of H serves both directions.
+// The records carry the normals and q separately: per pair of nodes A =
+// scaled offsets (as for the value kernel), B = (nu0x, nu1x, nu0y, nu1y),
+// C = (q0, q1, 0, 0). The work items, the staging of Q, the rotation of the
+// reverse sums and the FP64 atomic outputs are those of k_p2p_f32_sym; the
+// fits are those of k_p2p_f32_grad (long or short in rz); close pairs
+// (z <= 2 possible) evaluate such node pairs by PairF32::grad.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void src_grad_pairs_at(const GeomView& G,
+                                                  const double* __restrict__ sigma, float kpf,
+                                                  float4* __restrict__ rec, int64_t idx) {
+    const int hp = (G.npp + 1) >> 1;
+    if (idx >= (int64_t)G.np * hp) return;
+    const int s = (int)(idx / hp), m = (int)(idx % hp);
+    float xs[2], ys[2], nx[2], ny[2], q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = 2 * m + h;
+        if (k < G.npp) {
+            const int64_t j = (int64_t)s * G.npp + k;
+            const float2 x = G.xi[j];
+            xs[h] = -kpf * x.x;
+            ys[h] = -kpf * x.y;
+            nx[h] = (float)G.nx[j];
+            ny[h] = (float)G.ny[j];
+            q[h] = (float)(G.w[j] * sigma[j]);
+        } else {
+            xs[h] = 1.0e6f;
+            ys[h] = 0.0f;
+            nx[h] = ny[h] = q[h] = 0.0f;
+        }
+    }
+    rec[3 * idx] = make_float4(xs[0], xs[1], ys[0], ys[1]);
+    rec[3 * idx + 1] = make_float4(nx[0], nx[1], ny[0], ny[1]);
+    rec[3 * idx + 2] = make_float4(q[0], q[1], 0.0f, 0.0f);
+}
+
+#ifdef YK_DEFINE_P2P_KERNELS
+__global__ void k_src_grad_pairs(GeomView G, const double* __restrict__ sigma, float kpf,
+                                 float4* __restrict__ rec) {
+    src_grad_pairs_at(G, sigma, kpf, rec, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+#endif
+
+// Constants of the symmetric normal derivative: the scaled units of the fit
+// path times cf = sqrt(log2 e) kappa kappa' are physical (2 pi left out).
+struct SymGradC {
+    float inv_kp, kappa, rho, icf;   // 1/kappa', 1/rho, rho, 1/cf
+};
+
+// H of one node pair in the fit path's units, any z: the long fit for
+// z > 2, else PairF32::grad (physical units) times 1/cf.
+__device__ __forceinline__ float hsym_any(float dX, float dY, float ntx, float nty, float nsx,
+                                          float nsy, const SymGradC& K) {
+    const float z2 = fmaf(dX, dX, dY * dY);
+    if (z2 > ZCUT2) {
+        const float rz = rsqrt_fast(z2);
+        const float zp = z2 * rz;
+        float p0 = YK_P0_F32_RZ[FIT_LONG - 1], p1 = YK_P1_F32_RZ[FIT_LONG - 1];
+#pragma unroll
+        for (int k = FIT_LONG - 2; k >= 0; --k) {
+            p0 = fmaf(p0, rz, YK_P0_F32_RZ[k]);
+            p1 = fmaf(p1, rz, YK_P1_F32_RZ[k]);
+        }
+        const float E = ex2_fast(-zp) * rsqrt_fast(zp);
+        const float nn = fmaf(ntx, nsx, nty * nsy);
+        const float ds = fmaf(dX, nsx, dY * nsy), dt = fmaf(dX, ntx, dY * nty);
+        const float a = fmaf(-0.69314718f, p0, -2.0f * rz * p1);
+        return E * rz * fmaf(p1, nn, a * ds * dt * rz);
+    }
+    return PairF32::grad(dX * K.inv_kp, dY * K.inv_kp, ntx, nty, nsx, nsy, K.kappa, K.rho) * K.icf;
+}
+
+template <int NC>
+__device__ __forceinline__ void symg_pair(float2 TX, float2 TY, float2 NX, float2 NY, float2 QT,
+                                          const float4& A, const float4& B, const float4& C,
+                                          const PolyRZ2& P, const SymGradC& K, float2& fw,
+                                          float2& rv) {
+    const float2 dX = __fadd2_rn(TX, make_float2(A.x, A.y));
+    const float2 dY = __fadd2_rn(TY, make_float2(A.z, A.w));
+    const float2 Bx = make_float2(B.x, B.y), By = make_float2(B.z, B.w);
+    float2 H;
+    if constexpr (NC == CLOSE) {
+        H.x = hsym_any(dX.x, dY.x, NX.x, NY.x, B.x, B.z, K);
+        H.y = hsym_any(dX.y, dY.y, NX.y, NY.y, B.y, B.w, K);
+    } else {
+        const float2 z2 = __ffma2_rn(dX, dX, __fmul2_rn(dY, dY));
+        const float2 rz = make_float2(rsqrt_fast(z2.x), rsqrt_fast(z2.y));
+        const float2 zp = __fmul2_rn(z2, rz);
+        float2 p0 = P.c0[NC - 1], p1 = P.c1[NC - 1];
+#pragma unroll
+        for (int k = NC - 2; k >= 0; --k) {
+            p0 = __ffma2_rn(p0, rz, P.c0[k]);
+            p1 = __ffma2_rn(p1, rz, P.c1[k]);
+        }
+        const float2 E = make_float2(ex2_fast(-zp.x) * rsqrt_fast(zp.x),
+                                     ex2_fast(-zp.y) * rsqrt_fast(zp.y));
+        const float2 nn = __ffma2_rn(NX, Bx, __fmul2_rn(NY, By));
+        const float2 ds = __ffma2_rn(dX, Bx, __fmul2_rn(dY, By));
+        const float2 dt = __ffma2_rn(dX, NX, __fmul2_rn(dY, NY));
+        const float2 a = __ffma2_rn(make_float2(-0.69314718f, -0.69314718f), p0,
+                                    __fmul2_rn(__fmul2_rn(make_float2(-2.0f, -2.0f), rz), p1));
+        const float2 br = __ffma2_rn(p1, nn, __fmul2_rn(__fmul2_rn(a, ds), __fmul2_rn(dt, rz)));
+        H = __fmul2_rn(__fmul2_rn(E, rz), br);
+    }
+    fw = __ffma2_rn(H, make_float2(C.x, C.y), fw);
+    rv = __ffma2_rn(H, QT, rv);
+}
+
+template <int NC>
+__device__ __forceinline__ void symg_chunk(const float4* qA, const float4* qB, const float4* qC,
+                                           int ngrp, int lane, const float* TX, const float* TY,
+                                           const float* NX, const float* NY, const float* QT,
+                                           const PolyRZ2& P, const SymGradC& K, float2& fw0,
+                                           float2& fw1, float* rsum_w) {
+    const float2 tx0 = make_float2(TX[0], TX[0]), ty0 = make_float2(TY[0], TY[0]);
+    const float2 tx1 = make_float2(TX[1], TX[1]), ty1 = make_float2(TY[1], TY[1]);
+    const float2 nx0 = make_float2(NX[0], NX[0]), ny0 = make_float2(NY[0], NY[0]);
+    const float2 nx1 = make_float2(NX[1], NX[1]), ny1 = make_float2(NY[1], NY[1]);
+    const float2 q0 = make_float2(QT[0], QT[0]), q1 = make_float2(QT[1], QT[1]);
+    const int next = (lane + 1) & 31;
+    for (int b = 0; b < ngrp; ++b) {
+        float2 rv = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+            const int m = 32 * b + ((lane + k) & 31);
+            const float4 A = qA[m], B = qB[m], C = qC[m];
+            symg_pair<NC>(tx0, ty0, nx0, ny0, q0, A, B, C, P, K, fw0, rv);
+            symg_pair<NC>(tx1, ty1, nx1, ny1, q1, A, B, C, P, K, fw1, rv);
+            rv.x = __shfl_sync(0xffffffffu, rv.x, next);
+            rv.y = __shfl_sync(0xffffffffu, rv.y, next);
+        }
+        rsum_w[64 * b + 2 * lane] = rv.x;
+        rsum_w[64 * b + 2 * lane + 1] = rv.y;
+    }
+}
+
+#ifdef YK_DEFINE_P2P_KERNELS
+__global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
+                                                            const float4* __restrict__ rec,
+                                                            const int2* __restrict__ tasks,
+                                                            int ntasks, int qch, int ipb,
+                                                            double kscale,
+                                                            double* __restrict__ out) {
+    __shared__ float4 qA[STILE / 2], qB[STILE / 2], qC[STILE / 2];
+    __shared__ float rsum[F32_TPB / 32][STILE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float kpf = (float)(LOG2E / G.rho);
+    const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
+    const float short_gap = Z_SHORT * (float)G.rho;
+    SymGradC K;
+    K.inv_kp = (float)(G.rho / LOG2E);
+    K.kappa = (float)(1.0 / G.rho);
+    K.rho = (float)G.rho;
+    K.icf = (float)(1.0 / (sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho)));
+    const int hp = (G.npp + 1) >> 1;
+    const int npc = (G.npp + STILE - 1) / STILE, nqc = (G.npp + qch - 1) / qch;
+    const int64_t items = (int64_t)ntasks * npc * nqc;
+    const int64_t w0 = (int64_t)blockIdx.x * ipb, w1 = min(items, w0 + ipb);
+    const int lt0 = 64 * warp + lane, lt1 = lt0 + 32;
+    int curP = -1, curC = 0;
+    double f0 = 0.0, f1 = 0.0;
+    for (int64_t w = w0; w < w1; ++w) {
+        const int t = (int)(w / ((int64_t)npc * nqc));
+        const int pc = (int)((w / nqc) % npc) * STILE;
+        const int qc = (int)(w % nqc) * qch;
+        const int2 pq = tasks[t];
+        const int P = pq.x, Q = pq.y;
+        const PairRange rg = block_range(G, P, P, Q);   // block-uniform
+        const int mode = (rg.gap <= near_gap) ? CLOSE : (rg.gap >= short_gap ? FIT_SHORT : FIT_LONG);
+        const PolyRZ2 Pz(mode == FIT_SHORT);
+        const float4 cp = G.c32[P], cq = G.c32[Q];
+        const float oX = kpf * ((cp.x - cq.x) + (cp.z - cq.z));
+        const float oY = kpf * ((cp.y - cq.y) + (cp.w - cq.w));
+        if (P != curP || pc != curC) {
+            if (curP >= 0) {
+                const int64_t b = (int64_t)curP * G.npp + curC;
+                if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+                if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+            }
+            curP = P;
+            curC = pc;
+            f0 = f1 = 0.0;
+        }
+        float TX[2], TY[2], NX[2], NY[2], QT[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int li = pc + (h ? lt1 : lt0);
+            if (li < G.npp) {
+                const int64_t r = 3 * ((int64_t)P * hp + (li >> 1));
+                const float4 A = rec[r], B = rec[r + 1], C = rec[r + 2];
+                const bool odd = li & 1;
+                TX[h] = oX - (odd ? A.y : A.x);
+                TY[h] = oY - (odd ? A.w : A.z);
+                NX[h] = odd ? B.y : B.x;
+                NY[h] = odd ? B.w : B.z;
+                QT[h] = odd ? C.y : C.x;
+            } else {   // no node: far away and weightless
+                TX[h] = 3.0e6f;
+                TY[h] = 0.0f;
+                NX[h] = NY[h] = QT[h] = 0.0f;
+            }
+        }
+        const int cnt = min(qch, G.npp - qc);
+        const int npair = (cnt + 1) >> 1;
+        const int ngrp = (npair + 31) >> 5;
+        __syncthreads();   // previous chunk's shared data fully used
+        const float4* rq = rec + 3 * ((int64_t)Q * hp + (qc >> 1));
+        for (int m = threadIdx.x; m < 32 * ngrp; m += blockDim.x) {
+            if (m < npair) {
+                qA[m] = rq[3 * m];
+                qB[m] = rq[3 * m + 1];
+                qC[m] = rq[3 * m + 2];
+            } else {       // padding records: far away and weightless
+                qA[m] = make_float4(1.0e6f, 1.0e6f, 0.0f, 0.0f);
+                qB[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                qC[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
+        __syncthreads();
+        float2 fw0 = make_float2(0.0f, 0.0f), fw1 = fw0;
+        float* rw = rsum[warp];
+        if (mode == CLOSE)
+            symg_chunk<CLOSE>(qA, qB, qC, ngrp, lane, TX, TY, NX, NY, QT, Pz, K, fw0, fw1, rw);
+        else if (mode == FIT_SHORT)
+            symg_chunk<FIT_SHORT>(qA, qB, qC, ngrp, lane, TX, TY, NX, NY, QT, Pz, K, fw0, fw1, rw);
+        else
+            symg_chunk<FIT_LONG>(qA, qB, qC, ngrp, lane, TX, TY, NX, NY, QT, Pz, K, fw0, fw1, rw);
+        f0 += (double)(fw0.x + fw0.y);
+        f1 += (double)(fw1.x + fw1.y);
+        __syncthreads();   // every warp's reverse sums are in rsum
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const float v = (rsum[0][j] + rsum[1][j]) + (rsum[2][j] + rsum[3][j]);
+            atomicAdd(&out[(int64_t)Q * G.npp + qc + j], (double)v * kscale);
+        }
+    }
+    if (curP >= 0) {
+        const int64_t b = (int64_t)curP * G.npp + curC;
+        if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+        if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+    }
 }
 #endif
 

@@ -43,6 +43,7 @@ struct Workspace {
     double* partial = nullptr;   // [nchunk][n]
     int nchunk = 0;
     float4* src4 = nullptr;      // pair-packed FP32 source records [np][ceil(npp/2)][2]
+    float4* src4g = nullptr;     // the same for the normal derivative [np][ceil(npp/2)][3]
     double* V = nullptr;         // Krylov basis [(m+1)][n]
     double* H = nullptr;         // Hessenberg (m+1) x m, column-major
     double* gvec = nullptr;      // rotated rhs, m+1
@@ -227,7 +228,8 @@ struct yk_geom {
     float* d_r32 = nullptr;
     int* d_counter = nullptr;
     yk::PairList lists[4];                 // residual split, gradient split, all, cut-off
-    yk::PairList sym[2];                   // symmetric FP32 far field: inner operator, split
+    yk::PairList sym[3];                   // symmetric FP32 far field: inner operator, split,
+                                           //   normal-derivative split
     int* d_shape_of = nullptr;
     double2* d_shape_ab = nullptr;
     double* d_x = nullptr;
