@@ -41,27 +41,38 @@ __global__ void k_contact_hmax(GeomView G, unsigned long long* __restrict__ hbit
 // Partners of each particle: the others whose bounding circles are closer
 // than thr (at most CONTACT_MAX_PARTNERS; flag[0] = 1 beyond); flag[1]
 // counts them all.
+// One warp per particle Q, lanes over P; partners kept in order of P.
 __global__ void k_contact_partners(int np, const d4* __restrict__ part, double thr,
                                    int* __restrict__ partners, int* __restrict__ npartners,
                                    int* __restrict__ flag) {
-    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (Q >= np) return;
+    const int Q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (Q >= np) return;   // warp-uniform
     const d4 a = part[Q];
     int c = 0;
-    for (int P = 0; P < np; ++P) {
-        if (P == Q) continue;
-        const d4 b = part[P];
-        const double dx = a.x - b.x, dy = a.y - b.y;
-        if (sqrt(dx * dx + dy * dy) - a.z - b.z < thr) {
-            if (c == CONTACT_MAX_PARTNERS) {
-                atomicExch(&flag[0], 1);
-                break;
-            }
-            partners[Q * CONTACT_MAX_PARTNERS + c++] = P;
+    bool full = false;
+    for (int P0 = 0; P0 < np && !full; P0 += 32) {
+        const int P = P0 + lane;
+        bool hit = false;
+        if (P < np && P != Q) {
+            const d4 b = part[P];
+            const double dx = a.x - b.x, dy = a.y - b.y;
+            hit = sqrt(dx * dx + dy * dy) - a.z - b.z < thr;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const int k = c + __popc(m & ((1u << lane) - 1u));
+        if (hit && k < CONTACT_MAX_PARTNERS) partners[Q * CONTACT_MAX_PARTNERS + k] = P;
+        c += __popc(m);
+        if (c > CONTACT_MAX_PARTNERS) {
+            full = true;
+            c = CONTACT_MAX_PARTNERS;
+            if (lane == 0) atomicExch(&flag[0], 1);
         }
     }
-    npartners[Q] = c;
-    if (c > 0) atomicAdd(&flag[1], c);
+    if (lane == 0) {
+        npartners[Q] = c;
+        if (c > 0) atomicAdd(&flag[1], c);
+    }
 }
 
 // Entries of node i: (P, k) for the partners' panels closer than
@@ -207,7 +218,7 @@ static int contact_build(yk_geom* g) {
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     double hmax;
     memcpy(&hmax, &hb, sizeof(double));
-    YK_LAUNCH(k_contact_partners, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part,
+    YK_LAUNCH(k_contact_partners, ceil_div(g->np, 4), 128, 0, st, g->np, g->d_part,
               CONTACT_FACTOR * hmax, C.partners, C.npartners, C.flag);
     int hf[2] = {0, 0};
     YK_TRY_CUDA(cudaMemcpyAsync(hf, C.flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));

@@ -219,24 +219,35 @@ __device__ __forceinline__ bool gap_below(const d4& a, const d4& b, double thr) 
     return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < __dmul_rn(s, s);
 }
 
+// One warp per target particle Q, lanes over P; the fill writes in order of P.
 __global__ void k_band_count(int np, const d4* __restrict__ part, double lo, double hi, int* counts) {
-    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (Q >= np) return;
+    const int Q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (Q >= np) return;   // warp-uniform
     const d4 a = part[Q];
     int c = 0;
-    for (int P = 0; P < np; ++P)
-        c += (P != Q && !gap_below(a, part[P], lo) && gap_below(a, part[P], hi)) ? 1 : 0;
-    counts[Q] = c;
+    for (int P0 = 0; P0 < np; P0 += 32) {
+        const int P = P0 + lane;
+        const bool hit = P < np && P != Q && !gap_below(a, part[P], lo) && gap_below(a, part[P], hi);
+        c += __popc(__ballot_sync(0xffffffffu, hit));
+    }
+    if (lane == 0) counts[Q] = c;
 }
 
 __global__ void k_band_fill(int np, const d4* __restrict__ part, double lo, double hi,
                             const int* __restrict__ off, int* __restrict__ nbr) {
-    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (Q >= np) return;
+    const int Q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (Q >= np) return;   // warp-uniform
     const d4 a = part[Q];
     int k = off[Q];
-    for (int P = 0; P < np; ++P)
-        if (P != Q && !gap_below(a, part[P], lo) && gap_below(a, part[P], hi)) nbr[k++] = P;
+    for (int P0 = 0; P0 < np; P0 += 32) {
+        const int P = P0 + lane;
+        const bool hit = P < np && P != Q && !gap_below(a, part[P], lo) && gap_below(a, part[P], hi);
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) nbr[k + __popc(m & ((1u << lane) - 1u))] = P;
+        k += __popc(m);
+    }
 }
 
 __global__ void k_scan_counts(int np, const int* __restrict__ counts, int* __restrict__ off) {
@@ -268,7 +279,7 @@ static int band_list(yk_geom* g, int kind, double lo, double hi) {
     cudaStream_t st = g->ctx->stream;
     if (!B.off) YK_TRY(dev_alloc((void**)&B.off, sizeof(int) * (g->np + 1), st));
     int* counts = g->d_counts;
-    YK_LAUNCH(k_band_count, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, lo, hi, counts);
+    YK_LAUNCH(k_band_count, ceil_div(g->np, 4), 128, 0, st, g->np, g->d_part, lo, hi, counts);
     YK_LAUNCH(k_scan_counts, 1, 1024, 0, st, g->np, counts, B.off);
     int total = 0;
     YK_TRY_CUDA(cudaMemcpyAsync(&total, B.off + g->np, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -281,7 +292,7 @@ static int band_list(yk_geom* g, int kind, double lo, double hi) {
         B.cap = std::max(total, 1);
     }
     if (total > 0)
-        YK_LAUNCH(k_band_fill, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, lo, hi, B.off,
+        YK_LAUNCH(k_band_fill, ceil_div(g->np, 4), 128, 0, st, g->np, g->d_part, lo, hi, B.off,
                   B.idx);
     YK_TRY_CUDA(cudaGetLastError());
     B.n = total;

@@ -25,7 +25,7 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
                            : kind == 2 ? INFINITY : g->cutoff_gap;
         int* d_count = g->d_counter;
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
-        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr,
+        YK_LAUNCH(k_pair_list, ceil_div(g->np, 4), 128, 0, st, g->np, g->d_part, thr,
                   !g->use_self, d_count, (int2*)nullptr, 0);
         int n = 0;
         YK_TRY_CUDA(cudaMemcpyAsync(&n, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -38,7 +38,7 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
             L.cap = n;
         }
         YK_TRY_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), st));
-        YK_LAUNCH(k_pair_list, ceil_div(g->np, 128), 128, 0, st, g->np, g->d_part, thr,
+        YK_LAUNCH(k_pair_list, ceil_div(g->np, 4), 128, 0, st, g->np, g->d_part, thr,
                   !g->use_self, d_count, L.d, L.cap);
         YK_TRY_CUDA(cudaGetLastError());
         L.n = n;
@@ -62,7 +62,7 @@ static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
         const double gap = kind == 1 ? g->split_gap : (kind == 2 ? g->split_gap_grad : 0.0);
         int* counts = (int*)g->ws.partial;   // 2 np + 1 ints of scratch (partial holds >= n doubles)
         int* off = counts + g->np;
-        YK_LAUNCH(k_sym_count, ceil_div(g->np, 128), 128, 0, st, G, mask, gap, counts);
+        YK_LAUNCH(k_sym_count, ceil_div(g->np, 4), 128, 0, st, G, mask, gap, counts);
         YK_LAUNCH(k_scan_offsets, 1, 1024, 0, st, g->np, counts, off);
         int n = 0;
         YK_TRY_CUDA(cudaMemcpyAsync(&n, off + g->np, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -74,7 +74,7 @@ static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
             YK_TRY(dev_alloc((void**)&L.d, sizeof(int2) * (size_t)n, st));
             L.cap = n;
         }
-        if (n > 0) YK_LAUNCH(k_sym_fill, ceil_div(g->np, 128), 128, 0, st, G, mask, gap, off, L.d);
+        if (n > 0) YK_LAUNCH(k_sym_fill, ceil_div(g->np, 4), 128, 0, st, G, mask, gap, off, L.d);
         YK_TRY_CUDA(cudaGetLastError());
         L.n = n;
         L.valid = true;

@@ -1073,26 +1073,39 @@ __device__ __forceinline__ bool sym_pair_listed(const GeomView& G, int P, int Q,
     return !(mask && pair_in_tiles(G.part[P], G.part[Q], skip_gap));
 }
 
+// One warp per particle P (lanes over Q, 32 at a time); the fill writes each
+// P's pairs in order of Q from the ballot of the lanes.
 #ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_sym_count(GeomView G, bool mask, double skip_gap, int* __restrict__ counts) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= G.np) return;
+    const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (P >= G.np) return;   // warp-uniform
     const float zero_gap = ZP_ZERO / (float)(LOG2E / G.rho);
     int c = 0;
-    for (int Q = P + 1; Q < G.np; ++Q) c += sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap);
-    counts[P] = c;
+    for (int Q0 = P + 1; Q0 < G.np; Q0 += 32) {
+        const int Q = Q0 + lane;
+        const bool hit = Q < G.np && sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap);
+        c += __popc(__ballot_sync(0xffffffffu, hit));
+    }
+    if (lane == 0) counts[P] = c;
 }
 #endif
 
 #ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __restrict__ off,
                            int2* __restrict__ tasks) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= G.np) return;
+    const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (P >= G.np) return;   // warp-uniform
     const float zero_gap = ZP_ZERO / (float)(LOG2E / G.rho);
     int k = off[P];
-    for (int Q = P + 1; Q < G.np; ++Q)
-        if (sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap)) tasks[k++] = make_int2(P, Q);
+    for (int Q0 = P + 1; Q0 < G.np; Q0 += 32) {
+        const int Q = Q0 + lane;
+        const bool hit = Q < G.np && sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap);
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) tasks[k + __popc(m & ((1u << lane) - 1u))] = make_int2(P, Q);
+        k += __popc(m);
+    }
 }
 #endif
 
@@ -1420,14 +1433,21 @@ __global__ void __launch_bounds__(TILE_TPB, 2) k_tiles_f64(GeomView G, const dou
 #ifdef YK_DEFINE_P2P_KERNELS
 __global__ void k_pair_list(int np, const d4* __restrict__ part, double thr, bool self_pairs,
                             int* count, int2* __restrict__ out, int cap) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= np) return;
+    // one warp per particle P, lanes over Q; slots reserved once per 32 Q
+    const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (P >= np) return;   // warp-uniform
     const d4 a = part[P];
-    for (int Q = self_pairs ? P : P + 1; Q < np; ++Q) {
-        if (Q == P || pair_in_tiles(a, part[Q], thr)) {
-            const int k = atomicAdd(count, 1);
-            if (k < cap) out[k] = make_int2(P, Q);
-        }
+    for (int Q0 = self_pairs ? P : P + 1; Q0 < np; Q0 += 32) {
+        const int Q = Q0 + lane;
+        const bool hit = Q < np && (Q == P || pair_in_tiles(a, part[Q], thr));
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int k = base + __popc(m & ((1u << lane) - 1u));
+        if (hit && k < cap) out[k] = make_int2(P, Q);
     }
 }
 #endif

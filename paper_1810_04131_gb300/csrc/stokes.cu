@@ -365,47 +365,67 @@ __device__ __forceinline__ int stokes_order(double dist, double rm, double le) {
     return min(max((int)ceil(le / log(q)) + 1, 2), SP);
 }
 
+// One warp per particle P, lanes over Q; entries in order of Q.
 __global__ void k_stokes_count(int np, const yk_particle* __restrict__ parts,
                                int* __restrict__ nnear, int* __restrict__ nfar) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= np) return;
+    const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (P >= np) return;   // warp-uniform
     const yk_particle pp = parts[P];
     int cn = 0, cf = 0;
-    for (int Q = 0; Q < np; ++Q) {
-        if (Q == P) continue;
-        double d;
-        if (stokes_far_pair(pp, parts[Q], &d)) ++cf;
-        else ++cn;
+    for (int Q0 = 0; Q0 < np; Q0 += 32) {
+        const int Q = Q0 + lane;
+        bool isn = false, isf = false;
+        if (Q < np && Q != P) {
+            double d;
+            isf = stokes_far_pair(pp, parts[Q], &d);
+            isn = !isf;
+        }
+        cn += __popc(__ballot_sync(0xffffffffu, isn));
+        cf += __popc(__ballot_sync(0xffffffffu, isf));
     }
-    nnear[P] = cn;
-    nfar[P] = cf;
+    if (lane == 0) {
+        nnear[P] = cn;
+        nfar[P] = cf;
+    }
 }
 
 __global__ void k_stokes_fill(int np, const yk_particle* __restrict__ parts,
                               const int* __restrict__ near_off, int* __restrict__ near_idx,
                               const int* __restrict__ far_off, StokesFar* __restrict__ far) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= np) return;
+    const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (P >= np) return;   // warp-uniform
     const yk_particle pp = parts[P];
     int in = near_off[P], jf = far_off[P];
-    for (int Q = 0; Q < np; ++Q) {
-        if (Q == P) continue;
-        const yk_particle qq = parts[Q];
-        double d;
-        if (!stokes_far_pair(pp, qq, &d)) {
-            near_idx[in++] = Q;
-            continue;
+    for (int Q0 = 0; Q0 < np; Q0 += 32) {
+        const int Q = Q0 + lane;
+        bool isn = false, isf = false;
+        double d = 0.0;
+        yk_particle qq;
+        if (Q < np && Q != P) {
+            qq = parts[Q];
+            isf = stokes_far_pair(pp, qq, &d);
+            isn = !isf;
         }
-        StokesFar e;
-        e.z0 = make_double2(pp.cx - qq.cx, pp.cy - qq.cy);
-        const double id = 1.0 / (d * d);
-        e.zi = make_double2(e.z0.x * id, -e.z0.y * id);
-        e.logd = log(d);
-        e.q = Q;
-        const double rm = fmax(fmax(pp.A, pp.B), fmax(qq.A, qq.B));
-        e.p64 = (short)stokes_order(d, rm, -39.14);    // 1e-17
-        e.p32 = (short)stokes_order(d, rm, -18.42);    // 1e-8
-        far[jf++] = e;
+        const unsigned lt = (1u << lane) - 1u;
+        const unsigned mn = __ballot_sync(0xffffffffu, isn);
+        const unsigned mf = __ballot_sync(0xffffffffu, isf);
+        if (isn) near_idx[in + __popc(mn & lt)] = Q;
+        if (isf) {
+            StokesFar e;
+            e.z0 = make_double2(pp.cx - qq.cx, pp.cy - qq.cy);
+            const double id = 1.0 / (d * d);
+            e.zi = make_double2(e.z0.x * id, -e.z0.y * id);
+            e.logd = log(d);
+            e.q = Q;
+            const double rm = fmax(fmax(pp.A, pp.B), fmax(qq.A, qq.B));
+            e.p64 = (short)stokes_order(d, rm, -39.14);    // 1e-17
+            e.p32 = (short)stokes_order(d, rm, -18.42);    // 1e-8
+            far[jf + __popc(mf & lt)] = e;
+        }
+        in += __popc(mn);
+        jf += __popc(mf);
     }
 }
 
@@ -950,7 +970,7 @@ static int stokes_lists(yk_geom* g) {
     cudaStream_t st = g->ctx->stream;
     const int np = g->np;
     std::vector<int> cn(np), cf(np);
-    YK_LAUNCH(k_stokes_count, ceil_div(np, 128), 128, 0, st, np, g->d_particles, S.near_off,
+    YK_LAUNCH(k_stokes_count, ceil_div(np, 4), 128, 0, st, np, g->d_particles, S.near_off,
               S.far_off);
     YK_TRY_CUDA(cudaMemcpyAsync(cn.data(), S.near_off, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
     YK_TRY_CUDA(cudaMemcpyAsync(cf.data(), S.far_off, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
@@ -976,7 +996,7 @@ static int stokes_lists(yk_geom* g) {
                                 cudaMemcpyHostToDevice, st));
     YK_TRY_CUDA(cudaMemcpyAsync(S.far_off, of.data(), sizeof(int) * (np + 1),
                                 cudaMemcpyHostToDevice, st));
-    YK_LAUNCH(k_stokes_fill, ceil_div(np, 128), 128, 0, st, np, g->d_particles, S.near_off,
+    YK_LAUNCH(k_stokes_fill, ceil_div(np, 4), 128, 0, st, np, g->d_particles, S.near_off,
               S.near_idx, S.far_off, S.far);
     YK_TRY_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
     S.lists_valid = true;
