@@ -670,8 +670,10 @@ __global__ void k_stokes_p2m(int npp, int kmax, const double4* __restrict__ s64,
 
 // Local coefficients loc[P][set][l] (sets Phi_A, Phi_Bc, Psi_D, conj(z0)
 // Phi_A) of every particle from its far pairs; lmax[P] = the largest order
-// used (0: no far pair). Block P; warp w takes the pairs w, w + 8, ...; lane
-// l (and l + 32) the orders.
+// used (0: no far pair). Block P; each half-warp takes a far pair (the 16
+// half-warps of the block take pairs h, h + 16, ...), lane l of the half
+// the orders l, l + 16, l + 32 up to the pair's order, so that two pairs of
+// order below 16 share a warp instruction on the FP64 pipe.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_stokes_m2l(const int* __restrict__ far_off, const StokesFar* __restrict__ far,
@@ -681,24 +683,27 @@ k_stokes_m2l(const int* __restrict__ far_off, const StokesFar* __restrict__ far,
     __shared__ int wmax[8];
     const int P = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hl = lane & 15, half = lane >> 4;
     for (int k = threadIdx.x; k <= SP1; k += blockDim.x) invk[k] = k ? (T)(1.0 / k) : (T)0;
     __syncthreads();
-    cx<T> acc[2][4];
+    constexpr int R = (SP + 16) / 16;                // rounds of 16 orders
+    cx<T> acc[R][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int s = 0; s < 4; ++s) acc[h][s] = mk<T>(0, 0);
+        for (int s = 0; s < 4; ++s) acc[r][s] = mk<T>(0, 0);
     int pm = 0;
-    for (int e = far_off[P] + warp; e < far_off[P + 1]; e += 8) {
+    for (int e = far_off[P] + 2 * warp + half; e < far_off[P + 1]; e += 16) {
         const StokesFar E = far[e];
         const int p = sizeof(T) == 8 ? E.p64 : E.p32;
         pm = max(pm, p);
         const cx<T>* a = coef + (int64_t)E.q * 3 * SP1;
         const cx<T> zi = mk<T>((T)E.zi.x, (T)E.zi.y);
+        const cx<T> z0c = mk<T>((T)E.z0.x, (T)(-E.z0.y));
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int l = lane + 32 * h;
-            if (l > p) continue;
+        for (int r = 0; r < R; ++r) {
+            const int l = hl + 16 * r;
+            if (l > p) break;
             cx<T> v[3];
             if (l == 0) {
                 const T lg = (T)E.logd;
@@ -727,20 +732,28 @@ k_stokes_m2l(const int* __restrict__ far_off, const StokesFar* __restrict__ far,
 #pragma unroll
                 for (int s = 0; s < 3; ++s) v[s] = v[s] * zl;
             }
-            const cx<T> z0c = mk<T>((T)E.z0.x, (T)(-E.z0.y));
-            acc[h][3] = acc[h][3] + z0c * v[0];
+            acc[r][3] = acc[r][3] + z0c * v[0];
             if (l == 0) v[0] = v[0] - a[0];
 #pragma unroll
-            for (int s = 0; s < 3; ++s) acc[h][s] = acc[h][s] + v[s];
+            for (int s = 0; s < 3; ++s) acc[r][s] = acc[r][s] + v[s];
         }
     }
+    // the two halves hold the same orders: add them, then the warps in smem
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int l = lane + 32 * h;
-        if (l <= SP)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int s = 0; s < 4; ++s) red[warp][s * SP1 + l] = acc[h][s];
-    }
+        for (int s = 0; s < 4; ++s) {
+            acc[r][s].x += __shfl_xor_sync(0xffffffffu, acc[r][s].x, 16);
+            acc[r][s].y += __shfl_xor_sync(0xffffffffu, acc[r][s].y, 16);
+        }
+    if (half == 0)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int l = hl + 16 * r;
+            if (l <= SP)
+#pragma unroll
+                for (int s = 0; s < 4; ++s) red[warp][s * SP1 + l] = acc[r][s];
+        }
     for (int o = 16; o > 0; o >>= 1) pm = max(pm, __shfl_xor_sync(0xffffffffu, pm, o));
     if (lane == 0) wmax[warp] = pm;
     __syncthreads();
