@@ -420,7 +420,8 @@ int yk_poll(yk_ctx* ctx, uint64_t id, int* status, double* sigma, double* F,
             double* tau, yk_solve_info* info, double* latency_ms);
 
 /* Run the serving loop until every queued request is done (or a request
- * failed). Returns the first error met, or YK_OK.                          */
+ * failed). Returns the first error met, or YK_OK; YK_ERR_TIMEOUT when no
+ * request has completed for five minutes.                                  */
 int yk_drain(yk_ctx* ctx);
 
 /* Stokes boundary operators of the mobility problem (Section 3), on a

@@ -16,7 +16,7 @@
 // soon as a slot and memory free up, and their kernels overlap on the
 // device (one stream per slot). Results are copied to host memory and kept
 // until yk_poll collects them. Host waits are bounded: yk_drain gives up
-// after a time limit and reports YK_ERR_TIMEOUT.
+// when no request has completed for five minutes and reports YK_ERR_TIMEOUT.
 #include <string.h>
 
 #include <atomic>
@@ -58,6 +58,7 @@ struct Server {
     size_t max_queue = 1 << 16;
     size_t mem_budget = 0, mem_in_flight = 0;
     int running = 0;
+    uint64_t finished = 0;                           // requests completed so far
     bool stop = false;
     std::vector<std::thread> workers;
     int device = 0;
@@ -268,6 +269,7 @@ static void worker_main(Server* s) {
             q->t_done = Clock::now();
             s->mem_in_flight -= q->mem_bytes;
             s->running--;
+            s->finished++;
             if (rcs[b] != YK_OK) {
                 q->status = YK_REQ_FAILED;
                 q->error = rcs[b];
@@ -382,16 +384,23 @@ int yk_poll(yk_ctx* ctx, uint64_t id, int* status, double* sigma, double* F, dou
     return YK_OK;
 }
 
+constexpr auto DRAIN_STALL = std::chrono::minutes(5);
+
 int yk_drain(yk_ctx* ctx) {
     if (!ctx) return YK_ERR_ARG;
     if (!ctx->server) return YK_OK;
     Server* s = (Server*)ctx->server;
     std::unique_lock<std::mutex> lk(s->mu);
-    const auto deadline = Clock::now() + std::chrono::hours(2);
-    const bool ok = s->cv_done.wait_until(lk, deadline, [&] {
-        return s->queue.empty() && s->running == 0;
-    });
-    if (!ok) return YK_ERR_TIMEOUT;
+    // bounded by progress: give up when no request has completed for
+    // DRAIN_STALL (a request larger than the serving stream's largest takes
+    // a few seconds), however long the whole queue takes
+    while (!(s->queue.empty() && s->running == 0)) {
+        const uint64_t seen = s->finished;
+        const bool moved = s->cv_done.wait_for(lk, DRAIN_STALL, [&] {
+            return s->finished != seen || (s->queue.empty() && s->running == 0);
+        });
+        if (!moved) return YK_ERR_TIMEOUT;
+    }
     for (auto& kv : s->reqs)
         if (kv.second->status == YK_REQ_FAILED) return kv.second->error;
     return YK_OK;
