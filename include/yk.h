@@ -441,7 +441,9 @@ int yk_drain(yk_ctx* ctx);
  *     neighbours (needs n_panels >= 3).
  * precision: YK_FP64, or YK_MIXED for the FP32 far field (YK_STOKES_COMPLETED
  * only; the others are always FP64). sigma, out: host or device, 2 N.
- * Needs n_panels >= 3 and n_panels * n_gl <= 512; YK_ERR_ARG otherwise.     */
+ * Needs n_panels >= 3 and n_panels * n_gl <= 512 (YK_ERR_ARG otherwise) and
+ * at most 16384 particles (the particle-pair lists hold every pair;
+ * YK_ERR_TOO_LARGE beyond).                                                 */
 int yk_stokes_apply(yk_geom* g, int op, const double* sigma, double* out, int precision);
 
 /* The Stokes mobility problem (Section 3: Eqs. stokes, mobility_bc,

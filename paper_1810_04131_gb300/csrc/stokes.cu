@@ -48,6 +48,7 @@ constexpr int MOMENT_LEVELS = 34; // geometric levels towards a singular point
 constexpr int FAR_TPB = 128;
 constexpr int FAR_TMAX = 4;       // targets per thread (npp <= FAR_TPB * FAR_TMAX)
 constexpr double FAR_FACTOR = 2.0; // particle expansions beyond 2 (r_P + r_Q) between centres
+constexpr int STOKES_MAX_PARTICLES = 16384;   // the pair lists hold every particle pair
 constexpr int SP = 40;            // largest order of the particle expansions
 constexpr int SP1 = SP + 1;
 
@@ -980,6 +981,7 @@ static int stokes_ready(yk_geom* g) {
 static int stokes_lists(yk_geom* g) {
     Stokes& S = g->stokes;
     if (S.lists_valid) return YK_OK;
+    if (g->np > STOKES_MAX_PARTICLES) return YK_ERR_TOO_LARGE;   // pair lists ~ 48 np^2 bytes
     cudaStream_t st = g->ctx->stream;
     const int np = g->np;
     std::vector<int> cn(np), cf(np);
