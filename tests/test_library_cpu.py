@@ -122,3 +122,19 @@ def test_workloads_are_seeded_and_separated():
     s = W.request_stream(50, seed=6)
     assert len(s) == 50 and all(4 <= r["n_particles"] <= 2048 for r in s)
     assert all(8 <= r["n_panels"] <= 32 for r in s)
+
+
+def test_table2_collections_as_printed():
+    """Table 2: 250 / 500 / 1000 / 2000 unit disks in 100 / 200 / 200 / 400
+    square boxes, N_bdy = 70 boundary points each, tolerance 1e-5; seeded,
+    inside the box and at least 0.5 apart (centre distance >= 2.5)."""
+    for n, box in ((250, 100.0), (500, 200.0), (1000, 200.0), (2000, 400.0)):
+        wl = W.table2(n)
+        assert wl.n_particles == n and wl.box == box and wl.n_panels * wl.n_gl == 70
+        assert wl.n_nodes == 70 * n and wl.rho == 4.0 and wl.gmres_tol == 1e-5
+        assert np.array_equal(wl.particles, W.table2(n).particles)
+        c = wl.particles[:, 1:3]
+        assert (c >= 1.0).all() and (c <= box - 1.0).all()
+        d = np.hypot(c[:, None, 0] - c[None, :, 0], c[:, None, 1] - c[None, :, 1])
+        d[np.arange(n), np.arange(n)] = np.inf
+        assert d.min() >= 2.5
