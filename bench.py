@@ -29,6 +29,10 @@ Further legs, outside the timed steps (``--legs``; all by default):
             boundary points each, rho = 4, tolerance 1e-5): seconds per time
             step with constant drag and with the Stokes mobility, and the
             mobility solve alone (mixed and FP64);
+  table1    Table 1's single Janus disk (rho = 4, 7 nodes per panel, 10 to 80
+            panels, QBX orders 4, 6, 8): GMRES iterations and the l_inf field
+            error on the 200 x 200 grid against Eq. true_soln, next to the
+            printed values;
   batch     16 small requests solved one by one and as one batch
             (yk_solve_batch: inner GMRES in lock step);
   serving   the seeded request stream: saturation throughput, then Poisson
@@ -89,8 +93,8 @@ Z_SHORT = 10.0
 ZP_ZERO = 128.0
 LOG2E = 1.4426950408889634
 TARGETS_PER_BLOCK = 256
-ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "dynamics", "batch", "serving",
-            "cpu")
+ALL_LEGS = ("fp64", "samefar", "cold", "accuracy", "c3", "c4", "dynamics", "table1", "batch",
+            "serving", "cpu")
 
 # Table 2 of the paper, context only: seconds per step of Algorithm 1
 # (T_total / T_ref with T_ref = 10 s) on an 8-core Xeon E5-2650 v4
@@ -826,6 +830,50 @@ def main():
                     "alone to 1e-12; paper_s_per_step is the paper's 8-core CPU time, context"}
     if "dynamics" in legs:
         legt.done("dynamics")
+    # ---- Table 1: the single Janus disk against Eq. true_soln ----------------
+    if "table1" in legs and rank == 0:
+        import scipy.special as sps
+        gold = json.load(open(os.path.join(GOLDEN, "table1_single_disk.json")))
+        rho, ngl = gold["rho"], gold["n_gl"]
+        xs = np.linspace(-2.5, 2.5, 200)
+        X, Y = np.meshgrid(xs, xs)
+        T = np.stack([X.ravel(), Y.ravel()], 1)
+        rr = np.hypot(T[:, 0], T[:, 1])
+        T, rr = np.ascontiguousarray(T[rr > 1.0]), rr[rr > 1.0]
+        th = np.arctan2(T[:, 1], T[:, 0])
+        # data (1 + cos theta)/2 on the unit disk: u = (1/2) K0(r/rho)/K0(1/rho)
+        # + (1/2) K1(r/rho)/K1(1/rho) cos theta (Eq. true_soln)
+        ue = 0.5 * sps.kv(0, rr / rho) / sps.kv(0, 1.0 / rho) + \
+            0.5 * sps.kv(1, rr / rho) / sps.kv(1, 1.0 / rho) * np.cos(th)
+        far = rr > 1.5
+        rows = []
+        for p in (4, 6, 8):
+            for k, npan in enumerate(gold["n_panels"]):
+                wl1 = W.Workload("table1_disk", np.array([[W.SHAPE_DISK, 0.0, 0.0, 0.0, 1.0, 1.0]]),
+                                 rho=rho, n_panels=npan, n_gl=ngl, qbx_order=p)
+                g1 = yk.Geometry(ctx, wl1.particles, yk.params_for(
+                    wl1, precision=yk.YK_FP64, gmres_tol=1e-13, qbx_r_factor=0.25,
+                    precond=yk.YK_PRECOND_NONE))
+                f1 = g1.yk_label(yk.YK_LABEL_COS)
+                s1, i1 = g1.yk_solve(f1)
+                u1 = g1.yk_eval_potential_near(s1, T)
+                rows.append({"qbx_order": p, "n_panels": npan, "n_bdy": npan * ngl,
+                             "iterations": i1["iterations"],
+                             "linf_error_far": float(np.abs(u1[far] - ue[far]).max()),
+                             "linf_error_grid": float(np.nanmax(np.abs(u1 - ue))),
+                             "paper_linf_error": gold["linf_error"][str(p)][k],
+                             "paper_iterations": gold["gmres_iters"][str(p)][k]})
+                g1.close()
+        extra["table1"] = {
+            "rows": rows,
+            "note": "single unit disk, rho = 4, data (1 + cos theta)/2, 7 Gauss-Legendre nodes per "
+                    "panel, plain FP64 GMRES to 1e-13, QBX radius h/4 (as the oracle's printed-"
+                    "value pin); l_inf error against Eq. true_soln over the 200 x 200 grid of the "
+                    "5 x 5 box outside the disk (grid) and over its points more than 0.5 from the "
+                    "boundary (far); paper_* are Table 1's printed values (GIGAQBX with an FMM, "
+                    "another method near the boundary)"}
+    if "table1" in legs:
+        legt.done("table1")
     # ---- end to end through the C ABI with host buffers --------------------
     f_h = np.zeros(n)
     torch.cuda.synchronize()
