@@ -8,7 +8,8 @@ through the C ABI:
     (node-by-node sums) and spread ones (particle expansions for far pairs):
     1e-12 relative in FP64, 1e-6 with the FP32 far field;
   * v, omega and the density of the mobility problem, FP64 and mixed
-    precision, at the default tolerance: 1e-10;
+    precision, at the default tolerance: 1e-10 (close particles, spread ones,
+    and 30 disks at Table 2's density and 10 x 7 nodes);
   * a single disk under a torque turns at tau / (4 pi mu a^2);
   * one step of Algorithm 1 with the mobility velocities against the oracle's
     Yukawa solve, forces, repulsion, mobility and Euler update;
@@ -84,18 +85,25 @@ def test_stokes_operators_match_oracle(yk, ctx, case, npan, ngl):
     g.close()
 
 
+def _table2_like():
+    """30 unit disks at Table 2's density and discretisation (10 panels x 7
+    nodes, gap >= 0.5): near and far pairs, 70 nodes per particle."""
+    return W.small_system(30, 43, n_panels=10, n_gl=7, rho=4.0, gap=0.5).particles
+
+
 @pytest.mark.parametrize("case,precision", [("three", "fp64"), ("three", "mixed"),
-                                            ("spread", "fp64"), ("spread", "mixed")])
+                                            ("spread", "fp64"), ("spread", "mixed"),
+                                            ("table2", "fp64"), ("table2", "mixed")])
 def test_mobility_matches_oracle(yk, ctx, case, precision):
-    parts = _three() if case == "three" else _spread()
-    npan = 16 if case == "three" else 12
+    parts = {"three": _three, "spread": _spread, "table2": _table2_like}[case]()
+    npan, ngl = {"three": (16, 16), "spread": (12, 16), "table2": (10, 7)}[case]
     rng = np.random.default_rng(7)
     F = rng.standard_normal((len(parts), 2))
     tau = rng.standard_normal(len(parts))
-    o = so.StokesOracle(parts, npan, 16, viscosity=0.8)
+    o = so.StokesOracle(parts, npan, ngl, viscosity=0.8)
     ref = o.mobility(F, tau)
     prec = yk.YK_FP64 if precision == "fp64" else yk.YK_MIXED
-    g = _geom(yk, ctx, parts, npan, precision=prec, viscosity=0.8)
+    g = _geom(yk, ctx, parts, npan, ngl, precision=prec, viscosity=0.8)
     v, om, sig, info = g.yk_mobility(F, tau, want_sigma=True)
     assert info["rel_residual"] <= 1e-12, info
     assert (info["refinements"] > 0) == (precision == "mixed")
