@@ -589,6 +589,7 @@ int fmm_build(yk_geom* g, int L) {
     FmmTree& F = g->fmm;
     cudaStream_t st = g->ctx->stream;
     if (L < 0 || L > FMM_LMAX) return YK_ERR_ARG;
+    g->sym[3].valid = false;   // the near lists change with the tree
     fmm_root_box(g, &F.x0, &F.y0, &F.side);
     F.L = L;
     F.p = g->prm.fmm_order;

@@ -55,6 +55,31 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
 // the particles move.
 static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
     PairList& L = g->sym[kind];
+    if (!L.valid && kind == 3) {   // the FMM near field's particle pairs
+        cudaStream_t st = g->ctx->stream;
+        GeomView G = g->view();
+        int* counts = (int*)g->ws.partial;
+        int* off = counts + g->np;
+        YK_LAUNCH(k_sym_near<false>, ceil_div(g->np, 4), 128, 0, st, G, g->fmm.near_off,
+                  g->fmm.near, counts, (const int*)nullptr, (int2*)nullptr);
+        YK_LAUNCH(k_scan_offsets, 1, 1024, 0, st, g->np, counts, off);
+        int n = 0;
+        YK_TRY_CUDA(cudaMemcpyAsync(&n, off + g->np, sizeof(int), cudaMemcpyDeviceToHost, st));
+        YK_TRY_CUDA(cudaStreamSynchronize(st));
+        if (n > L.cap) {
+            dev_free(L.d, st);
+            L.d = nullptr;
+            L.cap = 0;
+            YK_TRY(dev_alloc((void**)&L.d, sizeof(int2) * (size_t)n, st));
+            L.cap = n;
+        }
+        if (n > 0)
+            YK_LAUNCH(k_sym_near<true>, ceil_div(g->np, 4), 128, 0, st, G, g->fmm.near_off,
+                      g->fmm.near, (int*)nullptr, off, L.d);
+        YK_TRY_CUDA(cudaGetLastError());
+        L.n = n;
+        L.valid = true;
+    }
     if (!L.valid) {
         cudaStream_t st = g->ctx->stream;
         GeomView G = g->view();
@@ -262,12 +287,24 @@ static int fmm_apply(yk_geom* g, const double* sigma, double* y) {
     double* extra = g->ws.vec[5];
     YK_TRY(fmm_far(g, sigma, extra));
     YK_TRY(self_blocks_f32(g, sigma, extra, true));
-    const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
     YK_TRY(stage_sources(g, sigma));
-    YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,
-              g->use_self, g->fmm.near_off, g->fmm.near, g->ws.partial);
-    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, 1, g->ws.partial, extra, G.cval,
-              sigma, y);
+    int chunks = 0;
+    if (g->use_self) {
+        // near field by the symmetric kernel over the near lists' pairs P < Q
+        // (the own particle's pairs come from the self block)
+        SymParams p;
+        YK_TRY(sym_params(g, 3, &p));
+        if (p.blocks > 0)
+            YK_LAUNCH(k_p2p_f32_sym, (unsigned)p.blocks, F32_TPB, 0, st, G, g->ws.src4, p.tasks,
+                      p.ntasks, p.qch, p.ipb, p.kscale, extra);
+    } else {
+        const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
+        YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,
+                  g->use_self, g->fmm.near_off, g->fmm.near, g->ws.partial);
+        chunks = 1;
+    }
+    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, st, G, chunks, g->ws.partial, extra,
+              G.cval, sigma, y);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

@@ -1109,6 +1109,32 @@ __global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __
 }
 #endif
 
+// Pairs of the symmetric kernel from the FMM near lists (kind 3): Q in
+// near(P), Q > P, not every term an exact FP32 zero; one warp per P, in the
+// order of P's near list.
+#ifdef YK_DEFINE_P2P_KERNELS
+template <bool FILL>
+__global__ void k_sym_near(GeomView G, const int* __restrict__ near_off,
+                           const int* __restrict__ near, int* __restrict__ counts,
+                           const int* __restrict__ off, int2* __restrict__ tasks) {
+    const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (P >= G.np) return;   // warp-uniform
+    const float zero_gap = ZP_ZERO / (float)(LOG2E / G.rho);
+    const int e0 = near_off[P], e1 = near_off[P + 1];
+    int k = FILL ? off[P] : 0;
+    for (int b = e0; b < e1; b += 32) {
+        const int e = b + lane;
+        const int Q = e < e1 ? near[e] : -1;
+        const bool hit = Q > P && block_range(G, P, P, Q).gap < zero_gap;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (FILL && hit) tasks[k + __popc(m & ((1u << lane) - 1u))] = make_int2(P, Q);
+        k += __popc(m);
+    }
+    if (!FILL && lane == 0) counts[P] = k;
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Cut-off far field: one block per target particle, sweeping only the source
 // particles in its neighbour list (bounding-circle gap below the cut-off);

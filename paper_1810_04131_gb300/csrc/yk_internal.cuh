@@ -228,8 +228,8 @@ struct yk_geom {
     float* d_r32 = nullptr;
     int* d_counter = nullptr;
     yk::PairList lists[4];                 // residual split, gradient split, all, cut-off
-    yk::PairList sym[3];                   // symmetric FP32 far field: inner operator, split,
-                                           //   normal-derivative split
+    yk::PairList sym[4];                   // symmetric FP32 far field: inner operator, split,
+                                           //   normal-derivative split, FMM near field
     int* d_shape_of = nullptr;
     double2* d_shape_ab = nullptr;
     double* d_x = nullptr;

@@ -324,7 +324,9 @@ def test_fmm_operator_and_solve(yk, ctx):
                                                    fmm_leaf=leaf))
         y32 = g.yk_matvec(sig, yk.YK_MIXED)
         assert rel(y32, A @ sig) < 1e-6
-        assert rel(g.yk_matvec(sig, yk.YK_MIXED), y32) == 0.0      # deterministic
+        # repeatable up to the order of the near field's FP64 atomic adds
+        # (the symmetric kernel over the near lists' particle pairs)
+        assert rel(g.yk_matvec(sig, yk.YK_MIXED), y32) < 1e-15
         y64 = g.yk_matvec(sig, yk.YK_FP64)
         assert np.abs(y64 - A @ sig).max() <= 20 * 1e-15 * np.abs(sig).max() + 1e-13
         g.close()
