@@ -55,13 +55,19 @@ static int tile_list(yk_geom* g, int kind, const int2** list, int* count) {
 // the particles move.
 static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
     PairList& L = g->sym[kind];
-    if (!L.valid && kind == 3) {   // the FMM near field's particle pairs
+    if (!L.valid && kind >= 3) {
+        // from neighbour lists: 3 the FMM near field; the cut-off neighbours
+        // 4 beyond the value split, 5 beyond the normal-derivative split, 6 all
         cudaStream_t st = g->ctx->stream;
         GeomView G = g->view();
+        const int* noff = kind == 3 ? g->fmm.near_off : g->nbr_off;
+        const int* nlst = kind == 3 ? g->fmm.near : g->nbr;
+        const bool mask = kind == 4 || kind == 5;
+        const double gap = kind == 4 ? g->split_gap : (kind == 5 ? g->split_gap_grad : 0.0);
         int* counts = (int*)g->ws.partial;
         int* off = counts + g->np;
-        YK_LAUNCH(k_sym_near<false>, ceil_div(g->np, 4), 128, 0, st, G, g->fmm.near_off,
-                  g->fmm.near, counts, (const int*)nullptr, (int2*)nullptr);
+        YK_LAUNCH(k_sym_near<false>, ceil_div(g->np, 4), 128, 0, st, G, noff, nlst, mask, gap,
+                  counts, (const int*)nullptr, (int2*)nullptr);
         YK_LAUNCH(k_scan_offsets, 1, 1024, 0, st, g->np, counts, off);
         int n = 0;
         YK_TRY_CUDA(cudaMemcpyAsync(&n, off + g->np, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -74,8 +80,8 @@ static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
             L.cap = n;
         }
         if (n > 0)
-            YK_LAUNCH(k_sym_near<true>, ceil_div(g->np, 4), 128, 0, st, G, g->fmm.near_off,
-                      g->fmm.near, (int*)nullptr, off, L.d);
+            YK_LAUNCH(k_sym_near<true>, ceil_div(g->np, 4), 128, 0, st, G, noff, nlst, mask, gap,
+                      (int*)nullptr, off, L.d);
         YK_TRY_CUDA(cudaGetLastError());
         L.n = n;
         L.valid = true;
@@ -137,9 +143,9 @@ static int far_sym(yk_geom* g, int kind, double* out) {
 
 // FP32 far field of the split normal derivative by the symmetric kernel
 // (pairs beyond the normal derivative's split distance), added to out.
-static int far_symg(yk_geom* g, const double* sigma, double* out) {
+static int far_symg(yk_geom* g, int kind, const double* sigma, double* out) {
     SymParams p;
-    YK_TRY(sym_params(g, 2, &p));
+    YK_TRY(sym_params(g, kind, &p));
     if (p.blocks == 0) return YK_OK;
     const int64_t npairs = (int64_t)g->np * ((g->npp + 1) / 2);
     cudaStream_t st = g->ctx->stream;
@@ -235,15 +241,19 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
     int used = 1;
     if (prec == Prec::F32) {
         YK_TRY(stage_sources(g, sigma));
-        if (grad)
-            YK_LAUNCH(k_p2p_f32_grad_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, 0.0,
-                      g->nbr_off, g->nbr, g->ws.partial);
-        else
-            YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,
-                      g->use_self, g->nbr_off, g->nbr, g->ws.partial);
         if (!grad && g->use_self) {
+            // own particle by the FP32 self block, neighbour pairs P < Q by the
+            // symmetric kernel
             extra = g->ws.vec[5];
             YK_TRY(self_blocks_f32(g, sigma, extra, false));
+            YK_TRY(far_sym(g, 6, extra));
+            used = 0;
+        } else if (grad) {
+            YK_LAUNCH(k_p2p_f32_grad_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, 0.0,
+                      g->nbr_off, g->nbr, g->ws.partial);
+        } else {
+            YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,
+                      g->use_self, g->nbr_off, g->nbr, g->ws.partial);
         }
     } else {
         const int kind = (prec == Prec::F64) ? 3 : (grad ? 1 : 0);
@@ -253,17 +263,14 @@ static int matvec_cutoff(yk_geom* g, const double* sigma, double* y, Prec prec, 
         extra = g->ws.vec[5];
         YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
         YK_TRY(self_blocks(g, sigma, extra, grad));
-        if (prec == Prec::SPLIT) {
-            const double gap = grad ? g->split_gap_grad : g->split_gap;
-            YK_TRY(stage_sources(g, sigma));
-            if (grad)
-                YK_LAUNCH(k_p2p_f32_grad_cut<true>, g->np, F32_TPB, 0, st, G, g->ws.src4, gap,
-                          g->nbr_off, g->nbr, g->ws.partial);
-            else
-                YK_LAUNCH(k_p2p_f32_cut<true>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks,
-                          gap, false, g->nbr_off, g->nbr, g->ws.partial);
-        } else {
-            used = 0;
+        used = 0;
+        if (prec == Prec::SPLIT) {   // neighbour pairs beyond the split distance, symmetric FP32
+            if (grad) {
+                YK_TRY(far_symg(g, 5, sigma, extra));
+            } else {
+                YK_TRY(stage_sources(g, sigma));
+                YK_TRY(far_sym(g, 4, extra));
+            }
         }
         if (grad)
             YK_LAUNCH(k_tiles_f64<true>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list,
@@ -472,7 +479,7 @@ static int normal_derivative_body(yk_geom* g, const double* sigma, double* un, P
     YK_TRY_CUDA(cudaMemsetAsync(extra, 0, sizeof(double) * g->n, st));
     YK_TRY(self_blocks(g, sigma, extra, true));
     const int used_chunks = 0;
-    if (prec != Prec::F64) YK_TRY(far_symg(g, sigma, extra));   // pairs beyond the split distance
+    if (prec != Prec::F64) YK_TRY(far_symg(g, 2, sigma, extra));   // pairs beyond the split distance
     YK_LAUNCH(k_tiles_f64<true>, tiles_grid(g, ntiles), TILE_TPB, 0, st, G, sigma, list, ntiles,
               tiles_qsplit(g, ntiles), extra);
     if (prec != Prec::F64) YK_TRY(band_expansions(g, sigma, extra, true));

@@ -1109,14 +1109,16 @@ __global__ void k_sym_fill(GeomView G, bool mask, double skip_gap, const int* __
 }
 #endif
 
-// Pairs of the symmetric kernel from the FMM near lists (kind 3): Q in
-// near(P), Q > P, not every term an exact FP32 zero; one warp per P, in the
-// order of P's near list.
+// Pairs of the symmetric kernel from per-particle neighbour lists (the FMM
+// near lists, the cut-off neighbour lists): Q in near(P), Q > P, not every
+// term an exact FP32 zero, and with a skip distance not a pair of the FP64
+// tiles; one warp per P, in the order of P's list.
 #ifdef YK_DEFINE_P2P_KERNELS
 template <bool FILL>
 __global__ void k_sym_near(GeomView G, const int* __restrict__ near_off,
-                           const int* __restrict__ near, int* __restrict__ counts,
-                           const int* __restrict__ off, int2* __restrict__ tasks) {
+                           const int* __restrict__ near, bool mask, double skip_gap,
+                           int* __restrict__ counts, const int* __restrict__ off,
+                           int2* __restrict__ tasks) {
     const int P = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (P >= G.np) return;   // warp-uniform
@@ -1126,7 +1128,7 @@ __global__ void k_sym_near(GeomView G, const int* __restrict__ near_off,
     for (int b = e0; b < e1; b += 32) {
         const int e = b + lane;
         const int Q = e < e1 ? near[e] : -1;
-        const bool hit = Q > P && block_range(G, P, P, Q).gap < zero_gap;
+        const bool hit = Q > P && sym_pair_listed(G, P, Q, zero_gap, mask, skip_gap);
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (FILL && hit) tasks[k + __popc(m & ((1u << lane) - 1u))] = make_int2(P, Q);
         k += __popc(m);

@@ -228,8 +228,9 @@ struct yk_geom {
     float* d_r32 = nullptr;
     int* d_counter = nullptr;
     yk::PairList lists[4];                 // residual split, gradient split, all, cut-off
-    yk::PairList sym[4];                   // symmetric FP32 far field: inner operator, split,
-                                           //   normal-derivative split, FMM near field
+    yk::PairList sym[7];                   // symmetric FP32 far field: inner operator, split,
+                                           //   normal-derivative split, FMM near field,
+                                           //   cut-off: value split, derivative split, all
     int* d_shape_of = nullptr;
     double2* d_shape_ab = nullptr;
     double* d_x = nullptr;

@@ -362,7 +362,9 @@ def test_fmm_without_admissible_leaf_falls_back_to_cutoff(yk, ctx):
     sig = rng.standard_normal(24 * 128)
     g = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_FMM, fmm_order=4))
     gc = yk.Geometry(ctx, wl.particles, _params(yk, wl, farfield=yk.YK_FARFIELD_CUTOFF))
-    assert np.array_equal(g.yk_matvec(sig, yk.YK_MIXED), gc.yk_matvec(sig, yk.YK_MIXED))
+    # the same operator, up to the order of the symmetric kernel's FP64 atomic adds
+    y, yc = g.yk_matvec(sig, yk.YK_MIXED), gc.yk_matvec(sig, yk.YK_MIXED)
+    assert rel(y, yc) < 1e-15
 
 
 def test_repulsion_matches_oracle(yk, ctx):
