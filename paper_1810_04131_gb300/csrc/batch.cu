@@ -52,7 +52,7 @@ struct SysDesc {
     double* x;         // its solution
     double kscale;
     float kpf;
-    int ntasks, qch, ipb, sym_blocks, dot_blocks, m, k1, active;
+    int ntasks, qch, ipb, nw, sym_blocks, dot_blocks, m, k1, active;
 };
 
 // part[k][blk] of the dot products: src 0: V_k . V_{j+1}; 1: V_{j+1} . V_{j+1}; 2: b . b
@@ -193,7 +193,8 @@ __global__ void kb_src(const SysDesc* __restrict__ D) {
 __global__ void __launch_bounds__(F32_TPB, 6) kb_sym(const SysDesc* __restrict__ D) {
     const SysDesc& S = D[blockIdx.y];
     if (!S.active || (int)blockIdx.x >= S.sym_blocks) return;
-    sym_items(S.G, S.rec, S.tasks, S.ntasks, S.qch, S.ipb, S.kscale, S.extra, blockIdx.x);
+    sym_items<false>(S.G, S.rec, S.tasks, S.ntasks, S.qch, S.ipb, S.nw, S.kscale, S.extra,
+                     blockIdx.x);
 }
 
 // V_{j+1} = extra + near QBX rows x t6
@@ -345,6 +346,7 @@ static int batched_gmres(std::vector<Inner>& sys, const std::vector<const double
         d.ntasks = p.ntasks;
         d.qch = p.qch;
         d.ipb = p.ipb;
+        d.nw = p.nw;
         d.sym_blocks = p.blocks;
         d.dot_blocks = w.dot_blocks;
         d.m = w.m;

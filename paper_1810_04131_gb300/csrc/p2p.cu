@@ -120,7 +120,10 @@ static int sym_list(yk_geom* g, int kind, const int2** list, int* count) {
 // blocks per SM (small systems), up to SYM_TASKS items per block beyond.
 int sym_params(yk_geom* g, int kind, SymParams* p) {
     YK_TRY(sym_list(g, kind, &p->tasks, &p->ntasks));
-    const int64_t npc = ceil_div(g->npp, STILE);
+    // 64 of P's nodes per warp, as few warps as cover a particle (up to 4):
+    // particles of few nodes leave no warp idle
+    p->nw = std::min(F32_TPB / 32, ceil_div(g->npp, 64));
+    const int64_t npc = ceil_div(g->npp, 64 * p->nw);
     int qch = STILE;
     while (qch > 64 && (int64_t)p->ntasks * npc * ceil_div(g->npp, qch) < 152 * 8) qch /= 2;
     const int64_t items = (int64_t)p->ntasks * npc * ceil_div(g->npp, qch);
@@ -136,8 +139,12 @@ static int far_sym(yk_geom* g, int kind, double* out) {
     SymParams p;
     YK_TRY(sym_params(g, kind, &p));
     if (p.blocks == 0) return YK_OK;
-    YK_LAUNCH(k_p2p_f32_sym, (unsigned)p.blocks, F32_TPB, 0, g->ctx->stream, g->view(),
-              g->ws.src4, p.tasks, p.ntasks, p.qch, p.ipb, p.kscale, out);
+    if (p.nw == F32_TPB / 32)
+        YK_LAUNCH(k_p2p_f32_sym<true>, (unsigned)p.blocks, F32_TPB, 0, g->ctx->stream, g->view(),
+                  g->ws.src4, p.tasks, p.ntasks, p.qch, p.ipb, p.nw, p.kscale, out);
+    else
+        YK_LAUNCH(k_p2p_f32_sym<false>, (unsigned)p.blocks, 32 * p.nw, 0, g->ctx->stream,
+                  g->view(), g->ws.src4, p.tasks, p.ntasks, p.qch, p.ipb, p.nw, p.kscale, out);
     return YK_OK;
 }
 
@@ -152,8 +159,12 @@ static int far_symg(yk_geom* g, int kind, const double* sigma, double* out) {
     YK_LAUNCH(k_src_grad_pairs, (unsigned)((npairs + 255) / 256), 256, 0, st, g->view(), sigma,
               (float)(LOG2E / g->prm.rho), g->ws.src4g);
     const double kscale = sqrt(LOG2E) * (1.0 / g->prm.rho) * (LOG2E / g->prm.rho) / (2.0 * PI);
-    YK_LAUNCH(k_p2p_f32_symg, (unsigned)p.blocks, F32_TPB, 0, st, g->view(), g->ws.src4g, p.tasks,
-              p.ntasks, p.qch, p.ipb, kscale, out);
+    if (p.nw == F32_TPB / 32)
+        YK_LAUNCH(k_p2p_f32_symg<true>, (unsigned)p.blocks, F32_TPB, 0, st, g->view(), g->ws.src4g,
+                  p.tasks, p.ntasks, p.qch, p.ipb, p.nw, kscale, out);
+    else
+        YK_LAUNCH(k_p2p_f32_symg<false>, (unsigned)p.blocks, 32 * p.nw, 0, st, g->view(),
+                  g->ws.src4g, p.tasks, p.ntasks, p.qch, p.ipb, p.nw, kscale, out);
     return YK_OK;
 }
 
@@ -299,11 +310,7 @@ static int fmm_apply(yk_geom* g, const double* sigma, double* y) {
     if (g->use_self) {
         // near field by the symmetric kernel over the near lists' pairs P < Q
         // (the own particle's pairs come from the self block)
-        SymParams p;
-        YK_TRY(sym_params(g, 3, &p));
-        if (p.blocks > 0)
-            YK_LAUNCH(k_p2p_f32_sym, (unsigned)p.blocks, F32_TPB, 0, st, G, g->ws.src4, p.tasks,
-                      p.ntasks, p.qch, p.ipb, p.kscale, extra);
+        YK_TRY(far_sym(g, 3, extra));
     } else {
         const double ks = sqrt(LOG2E) / (2.0 * PI * g->prm.rho);
         YK_LAUNCH(k_p2p_f32_cut<false>, g->np, F32_TPB, 0, st, G, g->ws.src4, (float)ks, 0.0,

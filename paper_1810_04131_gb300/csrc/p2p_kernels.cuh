@@ -687,18 +687,21 @@ __device__ __forceinline__ void sym_chunk(const float4* qA, const float4* qB, in
 // nodes, and range w mod nqc of qch of Q's nodes (qch a multiple of 64, at
 // most 256; smaller ranges give small systems enough blocks). A block takes
 // ipb consecutive items.
+template <bool ALL>   // ALL: every warp of the block holds targets (nw = F32_TPB / 32)
 __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __restrict__ rec,
                                           const int2* __restrict__ tasks, int ntasks, int qch,
-                                          int ipb, double kscale, double* __restrict__ out,
-                                          int block) {
+                                          int ipb, int nw, double kscale,
+                                          double* __restrict__ out, int block) {
     __shared__ float4 qA[STILE / 2], qB[STILE / 2];
     __shared__ float rsum[F32_TPB / 32][STILE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool wact = ALL || warp < nw;   // nw warps hold a chunk of 64 nw of P's nodes
     const float kpf = (float)(LOG2E / G.rho);
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
     const float short_gap = Z_SHORT * (float)G.rho;
     const int hp = (G.npp + 1) >> 1;
-    const int npc = (G.npp + STILE - 1) / STILE, nqc = (G.npp + qch - 1) / qch;
+    const int csz = ALL ? STILE : 64 * nw;
+    const int npc = (G.npp + csz - 1) / csz, nqc = (G.npp + qch - 1) / qch;
     const int64_t items = (int64_t)ntasks * npc * nqc;
     const int64_t w0 = (int64_t)block * ipb, w1 = min(items, w0 + ipb);
     const int lt0 = 64 * warp + lane, lt1 = lt0 + 32;   // the lane's targets in a chunk
@@ -706,7 +709,7 @@ __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __res
     double f0 = 0.0, f1 = 0.0;
     for (int64_t w = w0; w < w1; ++w) {
         const int t = (int)(w / ((int64_t)npc * nqc));
-        const int pc = (int)((w / nqc) % npc) * STILE;
+        const int pc = (int)((w / nqc) % npc) * csz;
         const int qc = (int)(w % nqc) * qch;
         const int2 pq = tasks[t];
         const int P = pq.x, Q = pq.y;
@@ -721,8 +724,8 @@ __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __res
             if (P != curP || pc != curC) {
                 if (curP >= 0) {
                     const int64_t b = (int64_t)curP * G.npp + curC;
-                    if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
-                    if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+                    if (wact && curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+                    if (wact && curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
                 }
                 curP = P;
                 curC = pc;
@@ -733,7 +736,7 @@ __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __res
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int li = pc + (h ? lt1 : lt0);
-                if (li < G.npp) {
+                if (wact && li < G.npp) {
                     const int64_t r = 2 * ((int64_t)P * hp + (li >> 1));
                     const float4 A = rec[r], B = rec[r + 1];
                     const bool odd = li & 1;
@@ -765,7 +768,7 @@ __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __res
                 __syncthreads();
                 float2 fw0 = make_float2(0.0f, 0.0f), fw1 = fw0;
                 float* rw = rsum[warp];
-                switch (mode) {
+                if (wact) switch (mode) {
                     case NARROW3:
                         sym_chunk<NARROW3>(qA, qB, ngrp, lane, TX[0], TY[0], TX[1], TY[1], NGX[0],
                                            NGY[0], NGX[1], NGY[1], Pz, fw0, fw1, rw);
@@ -790,7 +793,13 @@ __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __res
                 f1 += (double)(fw1.x + fw1.y);
                 __syncthreads();   // every warp's reverse sums are in rsum
                 for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-                    const float v = (rsum[0][j] + rsum[1][j]) + (rsum[2][j] + rsum[3][j]);
+                    float v;
+                    if (ALL) {
+                        v = (rsum[0][j] + rsum[1][j]) + (rsum[2][j] + rsum[3][j]);
+                    } else {
+                        v = rsum[0][j];
+                        for (int q = 1; q < nw; ++q) v += rsum[q][j];
+                    }
                     atomicAdd(&out[(int64_t)Q * G.npp + qc + j], (double)v * kscale);
                 }
             }
@@ -798,18 +807,21 @@ __device__ __forceinline__ void sym_items(const GeomView& G, const float4* __res
     }
     if (curP >= 0) {
         const int64_t b = (int64_t)curP * G.npp + curC;
-        if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
-        if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+        if (wact && curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+        if (wact && curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
     }
 }
 
 #ifdef YK_DEFINE_P2P_KERNELS
+// ALL: blocks of F32_TPB threads, every warp with targets; otherwise nw
+// warps (particles of at most 64 nw nodes)
+template <bool ALL>
 __global__ void __launch_bounds__(F32_TPB, 6) k_p2p_f32_sym(GeomView G, const float4* __restrict__ rec,
                                                            const int2* __restrict__ tasks,
-                                                           int ntasks, int qch, int ipb,
+                                                           int ntasks, int qch, int ipb, int nw,
                                                            double kscale,
                                                            double* __restrict__ out) {
-    sym_items(G, rec, tasks, ntasks, qch, ipb, kscale, out, blockIdx.x);
+    sym_items<ALL>(G, rec, tasks, ntasks, qch, ipb, nw, kscale, out, blockIdx.x);
 }
 #endif
 
@@ -958,15 +970,17 @@ __device__ __forceinline__ void symg_chunk(const float4* qA, const float4* qB, c
 }
 
 #ifdef YK_DEFINE_P2P_KERNELS
+template <bool ALL>   // as k_p2p_f32_sym
 __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
                                                             const float4* __restrict__ rec,
                                                             const int2* __restrict__ tasks,
-                                                            int ntasks, int qch, int ipb,
+                                                            int ntasks, int qch, int ipb, int nw,
                                                             double kscale,
                                                             double* __restrict__ out) {
     __shared__ float4 qA[STILE / 2], qB[STILE / 2], qC[STILE / 2];
     __shared__ float rsum[F32_TPB / 32][STILE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool wact = ALL || warp < nw;   // nw warps hold a chunk of 64 nw of P's nodes
     const float kpf = (float)(LOG2E / G.rho);
     const float near_gap = 2.0f * (float)G.rho * 1.0001f + 1e-4f;
     const float short_gap = Z_SHORT * (float)G.rho;
@@ -976,7 +990,8 @@ __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
     K.rho = (float)G.rho;
     K.icf = (float)(1.0 / (sqrt(LOG2E) * (1.0 / G.rho) * (LOG2E / G.rho)));
     const int hp = (G.npp + 1) >> 1;
-    const int npc = (G.npp + STILE - 1) / STILE, nqc = (G.npp + qch - 1) / qch;
+    const int csz = ALL ? STILE : 64 * nw;
+    const int npc = (G.npp + csz - 1) / csz, nqc = (G.npp + qch - 1) / qch;
     const int64_t items = (int64_t)ntasks * npc * nqc;
     const int64_t w0 = (int64_t)blockIdx.x * ipb, w1 = min(items, w0 + ipb);
     const int lt0 = 64 * warp + lane, lt1 = lt0 + 32;
@@ -984,7 +999,7 @@ __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
     double f0 = 0.0, f1 = 0.0;
     for (int64_t w = w0; w < w1; ++w) {
         const int t = (int)(w / ((int64_t)npc * nqc));
-        const int pc = (int)((w / nqc) % npc) * STILE;
+        const int pc = (int)((w / nqc) % npc) * csz;
         const int qc = (int)(w % nqc) * qch;
         const int2 pq = tasks[t];
         const int P = pq.x, Q = pq.y;
@@ -997,8 +1012,8 @@ __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
         if (P != curP || pc != curC) {
             if (curP >= 0) {
                 const int64_t b = (int64_t)curP * G.npp + curC;
-                if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
-                if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+                if (wact && curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+                if (wact && curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
             }
             curP = P;
             curC = pc;
@@ -1008,7 +1023,7 @@ __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int li = pc + (h ? lt1 : lt0);
-            if (li < G.npp) {
+            if (wact && li < G.npp) {
                 const int64_t r = 3 * ((int64_t)P * hp + (li >> 1));
                 const float4 A = rec[r], B = rec[r + 1], C = rec[r + 2];
                 const bool odd = li & 1;
@@ -1042,7 +1057,8 @@ __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
         __syncthreads();
         float2 fw0 = make_float2(0.0f, 0.0f), fw1 = fw0;
         float* rw = rsum[warp];
-        if (mode == CLOSE)
+        if (!wact) {
+        } else if (mode == CLOSE)
             symg_chunk<CLOSE>(qA, qB, qC, ngrp, lane, TX, TY, NX, NY, QT, Pz, K, fw0, fw1, rw);
         else if (mode == FIT_SHORT)
             symg_chunk<FIT_SHORT>(qA, qB, qC, ngrp, lane, TX, TY, NX, NY, QT, Pz, K, fw0, fw1, rw);
@@ -1052,14 +1068,20 @@ __global__ void __launch_bounds__(F32_TPB, 5) k_p2p_f32_symg(GeomView G,
         f1 += (double)(fw1.x + fw1.y);
         __syncthreads();   // every warp's reverse sums are in rsum
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            const float v = (rsum[0][j] + rsum[1][j]) + (rsum[2][j] + rsum[3][j]);
+            float v;
+            if (ALL) {
+                v = (rsum[0][j] + rsum[1][j]) + (rsum[2][j] + rsum[3][j]);
+            } else {
+                v = rsum[0][j];
+                for (int q = 1; q < nw; ++q) v += rsum[q][j];
+            }
             atomicAdd(&out[(int64_t)Q * G.npp + qc + j], (double)v * kscale);
         }
     }
     if (curP >= 0) {
         const int64_t b = (int64_t)curP * G.npp + curC;
-        if (curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
-        if (curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
+        if (wact && curC + lt0 < G.npp) atomicAdd(&out[b + lt0], f0 * kscale);
+        if (wact && curC + lt1 < G.npp) atomicAdd(&out[b + lt1], f1 * kscale);
     }
 }
 #endif

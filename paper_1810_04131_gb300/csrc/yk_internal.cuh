@@ -276,6 +276,7 @@ int matvec(yk_geom* g, const double* sigma, double* y, Prec prec);
 struct SymParams {
     const int2* tasks = nullptr;
     int ntasks = 0, qch = 0, ipb = 1, blocks = 0;
+    int nw = 4;            // warps holding a chunk of P's nodes (64 per warp)
     double kscale = 0.0;
 };
 int sym_params(yk_geom* g, int kind, SymParams* p);
