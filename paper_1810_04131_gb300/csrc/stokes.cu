@@ -26,10 +26,12 @@
 //     basis, by graded Gauss-Legendre quadrature on the device). A particle
 //     turned by phi applies R B R^T: its density is turned into the body
 //     frame as it is loaded and the result turned back as it is stored;
-//   * other particles: dense pair sums, FP64 (x, y, w sigma) records, or FP32
-//     offsets from each particle's centre with the centre difference formed
-//     in FP64 (inner operator); targets of one particle per block, source
-//     particles split over grid.y and added with FP64 atomics;
+//   * other particles: node-by-node sums for near particle pairs (FP64
+//     (x, y, w sigma) records, or FP32 offsets from each particle's centre with
+//     the centre difference formed in FP64 for the inner operator; one block
+//     per target particle), complex-variable particle expansions for far pairs
+//     (multipoles, translation to local expansions, evaluation; FP64, or FP32
+//     for the inner operator), over pair lists built once per configuration;
 //   * vectors are node-major (x and y component of node 0, then node 1, ...).
 #include <math.h>
 
