@@ -76,6 +76,20 @@ extern "C" {
                                 particle's self-interaction block (the same
                                 block for all particles of one shape)        */
 
+#define YK_COARSE_NONE    0  /* the inner GMRES sees block Jacobi alone       */
+#define YK_COARSE_MODES   1  /* YK_MIXED with YK_PRECOND_BLOCK: the inner
+                                (FP32) GMRES is deflated by a coarse space of
+                                three density modes per particle (1, cos and
+                                sin of the polar angle about its centre): the
+                                coupling of every particle's lowest modes to
+                                its neighbours is stored (B Z, per target
+                                particle, for source particles whose coupling
+                                exceeds 1e-9 x max|sigma|) and Z^T B Z
+                                (3 np square) is inverted once per
+                                configuration. Used for 2..2048 particles
+                                without near-contact panels; otherwise the
+                                solve runs with block Jacobi alone          */
+
 #define YK_FARFIELD_DENSE  0  /* every far source pair evaluated              */
 #define YK_FARFIELD_CUTOFF 1  /* source particles whose whole contribution is
                                  bounded below cutoff_tol * max|sigma| are
@@ -181,6 +195,8 @@ typedef struct {
     double viscosity;      /* Stokes mobility: fluid viscosity mu of Eq. stokes;
                               default 1 (the non-dimensional mu = 1 of the
                               paper's time scale [T] = mu a / gamma)          */
+    int32_t coarse;        /* YK_COARSE_NONE or YK_COARSE_MODES; default MODES */
+    int32_t pad4_;
 } yk_params;
 
 /* Constant-drag dynamics (Eq. euler) with the excluded-volume repulsion of
@@ -211,6 +227,9 @@ typedef struct {
     double rel_residual;     /* final ||f - A sigma|| / ||f|| in FP64         */
     int32_t matvecs_fp64;    /* FP64-accurate operator applications           */
     int32_t matvecs_fp32;    /* FP32 far-field operator applications          */
+    int32_t coarse_dim;      /* columns of the coarse space that deflated the
+                                inner GMRES (3 per particle, YK_COARSE_MODES),
+                                0 when the solve ran without one              */
 } yk_solve_info;
 
 /* ---- context -------------------------------------------------------------- */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libyk.so")
-SOURCES = ["geometry.cu", "p2p.cu", "expansions.cu", "fmm.cu", "near.cu", "contact.cu", "gmres.cu", "forces.cu", "dynamics.cu", "capi.cu", "serve.cu", "peaks.cu", "batch.cu", "stokes.cu"]
+SOURCES = ["geometry.cu", "p2p.cu", "expansions.cu", "fmm.cu", "near.cu", "contact.cu", "gmres.cu", "forces.cu", "dynamics.cu", "capi.cu", "serve.cu", "peaks.cu", "batch.cu", "stokes.cu", "coarse.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 

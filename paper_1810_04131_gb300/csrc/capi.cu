@@ -157,6 +157,7 @@ static int check_params(const yk_params* p) {
     if (p->representation != YK_REP_DOUBLE_LAYER && p->representation != YK_REP_COMBINED)
         return YK_ERR_ARG;
     if (!(p->viscosity > 0.0) || !isfinite(p->viscosity)) return YK_ERR_ARG;
+    if (p->coarse != YK_COARSE_NONE && p->coarse != YK_COARSE_MODES) return YK_ERR_ARG;
     if (p->representation == YK_REP_COMBINED &&
         (p->precision != YK_FP64 || p->farfield == YK_FARFIELD_FMM || !(p->bw_eta > 0.0) ||
          !isfinite(p->bw_eta)))
@@ -173,7 +174,7 @@ static int check_params(const yk_params* p) {
 // Smallest surface gap beyond which a whole source particle's contribution
 // (value or normal derivative) is below tol * max|sigma|:
 // L/(2 pi rho) K1(z) (1 + 2/z) * 2 with the same K1 bound, z = gap/rho.
-static double cutoff_gap(double rho, double perim, double tol) {
+double cutoff_gap(double rho, double perim, double tol) {
     auto bound = [&](double z) {
         const double k1ub = sqrt(PI / (2.0 * z)) * exp(-z) * (1.0 + 1.0 / z);
         return perim / (2.0 * PI * rho) * k1ub * (1.0 + 2.0 / z) * 2.0;
@@ -264,6 +265,7 @@ int yk_default_params(yk_params* p) {
     p->representation = YK_REP_DOUBLE_LAYER;
     p->bw_eta = 0.25;
     p->viscosity = 1.0;
+    p->coarse = YK_COARSE_MODES;
     return YK_OK;
 }
 
@@ -325,6 +327,7 @@ int yk_destroy_geometry(yk_geom* g) {
     dyn_free(g);
     stokes_free(g);
     contact_free(g);
+    coarse_free(g);
     for (auto& B : g->bands) {
         dev_free(B.off, st);
         dev_free(B.idx, st);

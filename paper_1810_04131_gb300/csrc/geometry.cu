@@ -658,6 +658,7 @@ int update_nodes(yk_geom* g) {
     for (auto& B : g->bands) B.valid = false;
     g->contact.valid = false;                   // so do the near-contact lists
     g->stokes.lists_valid = false;              // and the Stokes pair lists
+    g->coarse.valid = false;                    // and the coarse space's couplings
     YK_TRY_CUDA(cudaGetLastError());
     YK_TRY_CUDA(cudaStreamSynchronize(st));
     return YK_OK;

@@ -15,6 +15,9 @@
 // Mixed: sigma <- sigma + GMRES_32(r), r = f - A_64 sigma, where A_32 is
 // the FP32-far-field operator (accurate to about 1e-6) and A_64 the
 // FP64-accurate precision-split operator; stops when ||r|| <= tol ||f||.
+// The FP32 GMRES may be deflated by a coarse space (coarse.cu): each
+// Arnoldi column A M v_j is then corrected to the deflated operator's, and
+// the cycle's correction V y to P V y before M is applied.
 #include <math.h>
 
 #include <algorithm>
@@ -270,6 +273,7 @@ static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool
     const int ldh = m + 1;
     const int nb = ceil_div(n, 256);
     const bool pc = (bool)op.precond;
+    const bool defl = pc && prec == Prec::F32 && (bool)op.deflate;
     double* r = w.vec[0];
     double* h1 = w.hbuf;
     double* h2 = w.hbuf + (m + 2);
@@ -301,14 +305,16 @@ static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool
             const int k = std::min(batch, std::min(m - j, max_iter - total));
             for (int b = 0; b < k; ++b) {
                 const int jj = j + b;
-                double* vj = w.V + (int64_t)jj * n;
+                const double* vj = w.V + (int64_t)jj * n;
                 double* wv = w.V + (int64_t)(jj + 1) * n;
                 if (pc) {   // right preconditioning: w = A M^{-1} v_j
                     YK_TRY(op.precond(vj, w.vec[6], prec == Prec::F32));
-                    vj = w.vec[6];
+                    YK_TRY(op.apply(w.vec[6], wv, prec));
+                } else {
+                    YK_TRY(op.apply(vj, wv, prec));
                 }
-                YK_TRY(op.apply(vj, wv, prec));
                 ++*matvecs;
+                if (defl) YK_TRY(op.deflate(vj, wv, jj));
                 // CGS2
                 dots(op, w.V, jj + 1, wv, h1);
                 YK_LAUNCH(k_sub_proj, nb, 256, 0, st, wv, w.V, n, jj + 1, h1);
@@ -342,6 +348,7 @@ static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool
             double* t = w.vec[7];
             YK_TRY_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, st));
             YK_LAUNCH(k_add_basis, nb, 256, 0, st, t, w.V, n, j, w.ybuf);
+            if (defl) YK_TRY(op.deflate_end(j, w.ybuf, t));   // t = P V y
             YK_TRY(op.precond(t, w.vec[6], prec == Prec::F32));
             YK_LAUNCH(k_axpy1, nb, 256, 0, st, x, w.vec[6], n);
         } else {
@@ -382,6 +389,12 @@ KrylovOp yukawa_op(yk_geom* g) {
         op.precond = [g](const double* x, double* y, bool f32) {
             return apply_preconditioner(g, x, y, f32);
         };
+    if (g->coarse.on) {
+        op.deflate = [g](const double* v, double* w, int j) { return coarse_deflate(g, v, w, j); };
+        op.deflate_end = [g](int k, const double* y, double* t) {
+            return coarse_correct(g, k, y, t);
+        };
+    }
     return op;
 }
 
@@ -454,7 +467,10 @@ int solve_op(const KrylovOp& op, const yk_params& P, Prec residual, const double
 
 int solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
           yk_solve_info* info) {
-    return solve_op(yukawa_op(g), g->prm, Prec::SPLIT, f, sigma, sigma0, info);
+    YK_TRY(coarse_prepare(g));
+    const int rc = solve_op(yukawa_op(g), g->prm, Prec::SPLIT, f, sigma, sigma0, info);
+    if (info) info->coarse_dim = g->coarse.on ? g->coarse.nc : 0;
+    return rc;
 }
 
 }  // namespace yk

@@ -206,6 +206,19 @@ static int self_blocks(yk_geom* g, const double* sigma, double* extra, bool grad
     return YK_OK;
 }
 
+// The own-particle part of the FP32 inner operator, y_P = A_PP x_P for
+// every particle P: the FP32 self block and the QBX near rows.
+int own_apply_f32(yk_geom* g, const double* x, double* y) {
+    if (!g->use_self) return YK_ERR_ARG;
+    double* extra = g->ws.vec[5];
+    YK_TRY(self_blocks_f32(g, x, extra, false));
+    GeomView G = g->view();
+    YK_LAUNCH(k_assemble, ceil_div(g->n, 256), 256, 0, g->ctx->stream, G, 0, g->ws.partial, extra,
+              G.cval, x, y);
+    YK_TRY_CUDA(cudaGetLastError());
+    return YK_OK;
+}
+
 // The FP32 source records of sigma (k_src_pairs), before any FP32 far-field kernel.
 static int stage_sources(yk_geom* g, const double* sigma) {
     const int64_t npairs = (int64_t)g->np * ((g->npp + 1) / 2);

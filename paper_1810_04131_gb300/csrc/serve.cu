@@ -65,8 +65,9 @@ struct Server {
 };
 
 // Device memory of one request: node arrays, Krylov basis, chunk partials,
-// scratch vectors, QBX rows, and per shape (at most two) the two self blocks
-// and the FP64 + FP32 preconditioner inverse (an estimate with a safety factor).
+// scratch vectors, QBX rows, per shape (at most two) the two self blocks and
+// the FP64 + FP32 preconditioner inverse and the inner GMRES's coarse space
+// (an estimate with a safety factor).
 static size_t request_bytes(const Request& r) {
     const size_t npp = (size_t)r.prm.n_panels * r.prm.n_gl;
     const size_t n = (size_t)r.parts.size() * npp;
@@ -74,7 +75,9 @@ static size_t request_bytes(const Request& r) {
     const size_t nchunk = 32;
     const size_t rows = npp * 9 * r.prm.n_gl * 2;
     const size_t blocks = 2 * npp * npp * (8 * 2 + 8 + 4);
-    return (size_t)(1.25 * (8.0 * (double)(n * (m + 1 + nchunk + 16) + rows) + (double)blocks)) +
+    const size_t coarse = coarse_bytes(r.parts.data(), (int)r.parts.size(), r.prm);
+    return (size_t)(1.25 * (8.0 * (double)(n * (m + 1 + nchunk + 16) + rows) + (double)blocks +
+                            (double)coarse)) +
            (8u << 20);
 }
 

@@ -194,6 +194,29 @@ struct Stokes {
 };
 }  // namespace yk
 
+namespace yk {
+// Coarse space of the inner GMRES (coarse.cu): three density modes per
+// particle, B Z per coupled particle pair and (Z^T B Z)^{-1}.
+struct Coarse {
+    bool valid = false;         // built (or found unusable) for the current positions
+    bool on = false;            // deflation in use for these positions
+    int nc = 0;                 // 3 np
+    int* off = nullptr;         // [np + 1] coupled source particles of each target (CSR)
+    int2* ent = nullptr;        // (target, source) of every entry, in CSR order
+    int cap = 0;
+    double* Z = nullptr;        // [3][n] modes, orthonormal over each particle's nodes
+    double* Y = nullptr;        // [3][n] M Z (M: the FP32 block preconditioner)
+    double* O = nullptr;        // [3][n] own-particle part of A M Z
+    float* W = nullptr;         // [entry][3][npp] B Z on the target's nodes
+    size_t wcap = 0;            // floats
+    float* C = nullptr;         // [nc][nc] Z^T B Z, then its inverse
+    float* piv = nullptr;       // Gauss-Jordan panel: D^{-1}, M_:K copy, D^{-1} M_K:
+    double* U = nullptr;        // [m][nc] Z^T (B v_j - v_j) of the Arnoldi steps
+    double* cv = nullptr;       // [2][nc] scratch
+    int* flag = nullptr;        // [1] failed pivot
+};
+}  // namespace yk
+
 struct yk_geom {
     yk_ctx* ctx = nullptr;
     yk_params prm{};
@@ -221,6 +244,7 @@ struct yk_geom {
     yk::Dynamics dyn;                      // particle dynamics (yk_step)
     yk::Stokes stokes;                     // Stokes mobility (yk_mobility)
     yk::Contact contact;                   // near-contact lists
+    yk::Coarse coarse;                     // coarse space of the inner GMRES
     yk_particle* d_particles = nullptr;    // device copy of the particles
     // device allocations
     yk::d4* d_part = nullptr;
@@ -280,6 +304,7 @@ struct SymParams {
     double kscale = 0.0;
 };
 int sym_params(yk_geom* g, int kind, SymParams* p);
+int own_apply_f32(yk_geom* g, const double* x, double* y);   // own-particle part, FP32 operator
 int normal_derivative(yk_geom* g, const double* sigma, double* un, Prec prec);
 int potential(yk_geom* g, const double* sigma, const double* targets, int64_t nt, double* u);
 // near.cu
@@ -315,6 +340,11 @@ struct KrylovOp {
     int64_t n = 0;
     std::function<int(const double*, double*, Prec)> apply;
     std::function<int(const double*, double*, bool)> precond;   // empty: none
+    // Optional deflation of the FP32 inner solve (with precond): deflate(v_j,
+    // w, j) turns w = A M v_j into the deflated operator's column, and
+    // deflate_end(k, y, t) turns t = V y (k basis vectors) into P V y.
+    std::function<int(const double*, double*, int)> deflate;
+    std::function<int(int, const double*, double*)> deflate_end;
 };
 int solve_op(const KrylovOp& op, const yk_params& P, Prec residual, const double* f,
              double* sigma, const double* sigma0, yk_solve_info* info);
@@ -328,6 +358,15 @@ int alloc_workspace(yk_geom* g);
 int alloc_krylov(Workspace& w, int64_t n, int m, cudaStream_t st);
 void free_workspace(yk_geom* g);
 void free_workspace(Workspace& w, cudaStream_t st);
+
+// coarse.cu
+constexpr int COARSE_MAX_PARTICLES = 2048;
+constexpr double COARSE_TOL = 1e-9;   // couplings bounded below this x max|sigma| are left out
+int coarse_prepare(yk_geom* g);
+size_t coarse_bytes(const yk_particle* parts, int np, const yk_params& P);   // device memory
+int coarse_deflate(yk_geom* g, const double* v, double* w, int j);
+int coarse_correct(yk_geom* g, int k, const double* y, double* t);
+void coarse_free(yk_geom* g);
 
 // forces.cu
 int forces_torques(yk_geom* g, const double* sigma, const double* f, const double* un,
@@ -360,6 +399,7 @@ void stokes_free(yk_geom* g);
 int destroy_server(yk_ctx* ctx);
 
 // capi.cu helpers
+double cutoff_gap(double rho, double perim, double tol);
 bool is_device_ptr(const void* p);
 // stream-ordered device allocations (no device-wide synchronisation)
 int dev_alloc(void** p, size_t bytes, cudaStream_t st);

@@ -41,6 +41,8 @@ YK_REP_DOUBLE_LAYER = 0
 YK_REP_COMBINED = 1
 YK_PRECOND_NONE = 0
 YK_PRECOND_BLOCK = 1
+YK_COARSE_NONE = 0
+YK_COARSE_MODES = 1
 YK_FARFIELD_DENSE = 0
 YK_FARFIELD_CUTOFF = 1
 YK_FARFIELD_FMM = 2
@@ -79,7 +81,8 @@ class yk_params(C.Structure):
                 ("grad_split_tol", C.c_double), ("precond", C.c_int32), ("pad_", C.c_int32),
                 ("cutoff_tol", C.c_double), ("fmm_order", C.c_int32), ("pad2_", C.c_int32),
                 ("fmm_leaf", C.c_double), ("representation", C.c_int32), ("pad3_", C.c_int32),
-                ("bw_eta", C.c_double), ("viscosity", C.c_double)]
+                ("bw_eta", C.c_double), ("viscosity", C.c_double),
+                ("coarse", C.c_int32), ("pad4_", C.c_int32)]
 
 
 class yk_dynamics(C.Structure):
@@ -91,7 +94,7 @@ class yk_dynamics(C.Structure):
 class yk_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32),
                 ("rel_residual", C.c_double), ("matvecs_fp64", C.c_int32),
-                ("matvecs_fp32", C.c_int32)]
+                ("matvecs_fp32", C.c_int32), ("coarse_dim", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -77,6 +77,7 @@ def test_defaults_and_errors_without_gpu(lib):
     assert p.qbx_r_factor == 0.125 and p.oversample == 8 and p.near_width == 1
     assert p.precision == yk.YK_MIXED and p.gmres_tol == 1e-12
     assert p.farfield == yk.YK_FARFIELD_DENSE and p.fmm_order == 12 and p.fmm_leaf == 0.0
+    assert p.coarse == yk.YK_COARSE_MODES
     assert lib.yk_default_params(None) == yk.YK_ERR_ARG
     assert lib.yk_strerror(yk.YK_ERR_BAD_GEOMETRY) == b"particles overlap"
     assert lib.yk_create(None, 0, None) == yk.YK_ERR_ARG
