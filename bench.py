@@ -13,7 +13,8 @@ between steps (a 256 MiB write) outside the timed events.
 Further legs, outside the timed steps (``--legs``; all by default):
   fp64      the same system with every step in FP64 (dense far field);
   samefar   both precisions on the cut-off far field, so that the ratio
-            measures precision alone (at the library's 1e-12 and at 1e-10);
+            measures precision alone (at the library's 1e-12 and at 1e-10;
+            the mixed solve with and without the coarse space);
   cold      a first solve from scratch: geometry, QBX rows, self blocks,
             preconditioner, label, solve, forces;
   accuracy  the headline density, forces and torques against the FP64
@@ -675,15 +676,20 @@ def main():
         out = {}
         for tol in (1e-12, 1e-10):
             rec = {}
-            for name, pr in (("mixed", yk.YK_MIXED), ("fp64", yk.YK_FP64)):
+            for name, pr, co in (("mixed", yk.YK_MIXED, yk.YK_COARSE_MODES),
+                                 ("mixed_no_coarse", yk.YK_MIXED, yk.YK_COARSE_NONE),
+                                 ("fp64", yk.YK_FP64, yk.YK_COARSE_NONE)):
                 rec[name], _ = solve_leg(yk, ctx, dev, parts, yk.params_for(
-                    wl, precision=pr, farfield=yk.YK_FARFIELD_CUTOFF, gmres_tol=tol),
+                    wl, precision=pr, farfield=yk.YK_FARFIELD_CUTOFF, gmres_tol=tol, coarse=co),
                     reps=2 if pr else 1)
             rec["mixed_speedup"] = rec["fp64"]["solve_s"] / rec["mixed"]["solve_s"]
+            rec["precision_speedup"] = rec["fp64"]["solve_s"] / rec["mixed_no_coarse"]["solve_s"]
             out["tol_%g" % tol] = rec
         out["note"] = ("disks512, both precisions with the cut-off far field (source particles "
-                       "bounded below 1e-15 max|sigma| left out): the ratio comes from precision; "
-                       "at the library's default tolerance 1e-12 and at 1e-10")
+                       "bounded below 1e-15 max|sigma| left out), at the library's default "
+                       "tolerance 1e-12 and at 1e-10. precision_speedup: both with block Jacobi "
+                       "alone, the ratio from precision; mixed_speedup: the mixed solve as it "
+                       "runs by default, its inner GMRES also deflated by the coarse space")
         extra["same_farfield"] = out
 
     if "samefar" in legs:
