@@ -87,7 +87,8 @@ extern "C" {
                                 exceeds 1e-9 x max|sigma|) and Z^T B Z
                                 (3 np square) is inverted once per
                                 configuration. Used for 2..2048 particles
-                                without near-contact panels; otherwise the
+                                without near-contact panels and with at most
+                                2 GiB of stored couplings; otherwise the
                                 solve runs with block Jacobi alone          */
 
 #define YK_FARFIELD_DENSE  0  /* every far source pair evaluated              */

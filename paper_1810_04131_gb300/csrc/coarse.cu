@@ -499,21 +499,28 @@ static bool coarse_eligible(const yk_geom* g) {
            g->use_self && g->np >= 2 && g->np <= COARSE_MAX_PARTICLES;
 }
 
+// Device memory of the coarse space for a request (serving admission): the
+// coupled pairs are estimated from the particle density over the centres'
+// bounding box (twice the uniform-density count, at most np per particle).
 size_t coarse_bytes(const yk_particle* parts, int np, const yk_params& P) {
     if (P.coarse != YK_COARSE_MODES || P.precision != YK_MIXED || P.precond != YK_PRECOND_BLOCK ||
         np < 2 || np > COARSE_MAX_PARTICLES)
         return 0;
-    double perim = 0.0;
-    for (int i = 0; i < np; ++i) perim = std::max(perim, 2.0 * PI * std::max(parts[i].A, parts[i].B));
-    const double gap = cutoff_gap(P.rho, perim, COARSE_TOL);
-    size_t nent = 0;
-    for (int i = 0; i < np; ++i)
-        for (int j = 0; j < np; ++j) {
-            const double dx = parts[i].cx - parts[j].cx, dy = parts[i].cy - parts[j].cy;
-            const double ri = std::max(parts[i].A, parts[i].B), rj = std::max(parts[j].A, parts[j].B);
-            nent += (i == j || sqrt(dx * dx + dy * dy) - ri - rj < gap) ? 1 : 0;
-        }
+    double rmax = 0.0, x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int i = 0; i < np; ++i) {
+        rmax = std::max(rmax, std::max(parts[i].A, parts[i].B));
+        x0 = std::min(x0, parts[i].cx);
+        x1 = std::max(x1, parts[i].cx);
+        y0 = std::min(y0, parts[i].cy);
+        y1 = std::max(y1, parts[i].cy);
+    }
+    const double gap = cutoff_gap(P.rho, 2.0 * PI * rmax, COARSE_TOL);
+    const double area = (x1 - x0 + 2.0 * rmax) * (y1 - y0 + 2.0 * rmax);
+    const double reach = gap + 2.0 * rmax;
+    const double per = isfinite(reach) ? 1.0 + 2.0 * np * PI * reach * reach / area : (double)np;
+    const size_t nent = (size_t)np * (size_t)std::min((double)np, per);
     const size_t npp = (size_t)P.n_panels * P.n_gl, nc = 3 * (size_t)np;
+    if (nent * 3 * npp > COARSE_MAX_W_FLOATS) return 0;
     return nent * (3 * npp * sizeof(float) + sizeof(int2)) + nc * nc * sizeof(float) +
            9 * np * npp * sizeof(double) + ((size_t)P.gmres_restart + 2) * nc * sizeof(double) +
            (GJ_W * GJ_W + 2 * GJ_W * nc) * sizeof(float);
@@ -576,6 +583,10 @@ int coarse_prepare(yk_geom* g) {
         K.cap = nent;
     }
     const size_t wneed = (size_t)nent * 3 * npp;
+    if (wneed > COARSE_MAX_W_FLOATS) {   // couplings too wide-reaching to store: no deflation
+        K.valid = true;
+        return YK_OK;
+    }
     if (wneed > K.wcap) {
         dev_free(K.W, st);
         K.W = nullptr;

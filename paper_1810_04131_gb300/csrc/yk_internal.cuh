@@ -362,6 +362,7 @@ void free_workspace(Workspace& w, cudaStream_t st);
 // coarse.cu
 constexpr int COARSE_MAX_PARTICLES = 2048;
 constexpr double COARSE_TOL = 1e-9;   // couplings bounded below this x max|sigma| are left out
+constexpr size_t COARSE_MAX_W_FLOATS = (size_t)1 << 29;   // 2 GiB of stored couplings at most
 int coarse_prepare(yk_geom* g);
 size_t coarse_bytes(const yk_particle* parts, int np, const yk_params& P);   // device memory
 int coarse_deflate(yk_geom* g, const double* v, double* w, int j);
