@@ -13,7 +13,8 @@
 // (Z^T B P = Z^T); a cycle's correction is x += M P y with
 // P y = y - Z C Z^T (B y - y), and Z^T (B y - y) is the combination of the
 // Z^T (B v_j - v_j) kept from the Arnoldi steps, so B P costs one operator
-// application, like B.
+// application, like B. With the kept z_j = M v_j of the GMRES, M P y is
+// Z_kept y - (M Z) C sum_j y_j Z^T (B v_j - v_j).
 //
 // B Z is stored. Its column for mode c of particle Q is A (M Z_Q): on Q's
 // own nodes the own-particle part of the FP32 operator (self block and QBX
@@ -29,7 +30,7 @@
 //
 // Per Arnoldi step: u_j = Z^T (w - v_j) (one block per particle),
 // c = C u_j (one warp per row), w -= (B Z) c (one block per target
-// particle over its entries).
+// particle over its entries); per cycle x -= (M Z) C sum_j y_j u_j.
 #include <math.h>
 
 #include <algorithm>
@@ -480,7 +481,7 @@ __global__ void k_coarse_combine(int nc, int k1, const double* __restrict__ U,
     s[r] = a;
 }
 
-// t -= Z c.
+// t -= Z c (Z: three vectors of length n, one column per particle each).
 __global__ void k_coarse_prolong_z(int npp, int64_t n, const double* __restrict__ Z,
                                    const float* __restrict__ c, double* __restrict__ t) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -644,15 +645,16 @@ int coarse_deflate(yk_geom* g, const double* v, double* w, int j) {
     return YK_OK;
 }
 
-// t = V y  ->  P V y = t - Z C sum_k y_k Z^T (B v_k - v_k).
-int coarse_correct(yk_geom* g, int k, const double* y, double* t) {
+// The coarse term of a cycle's correction: M P V y = Z_kept y - (M Z) C
+// sum_k y_k Z^T (B v_k - v_k); x -= Y C sum_k y_k u_k (Y = M Z).
+int coarse_correct(yk_geom* g, int k, const double* y, double* x) {
     Coarse& K = g->coarse;
     cudaStream_t st = g->ctx->stream;
     double* s = K.cv;
     float* c = (float*)(K.cv + K.nc);
     YK_LAUNCH(k_coarse_combine, ceil_div(K.nc, 256), 256, 0, st, K.nc, k, K.U, y, s);
     YK_LAUNCH(k_coarse_gemv, ceil_div((int64_t)K.nc * 32, 256), 256, 0, st, K.nc, K.C, s, c);
-    YK_LAUNCH(k_coarse_prolong_z, ceil_div(g->n, 256), 256, 0, st, g->npp, g->n, K.Z, c, t);
+    YK_LAUNCH(k_coarse_prolong_z, ceil_div(g->n, 256), 256, 0, st, g->npp, g->n, K.Y, c, x);
     YK_TRY_CUDA(cudaGetLastError());
     return YK_OK;
 }

@@ -15,9 +15,11 @@
 // Mixed: sigma <- sigma + GMRES_32(r), r = f - A_64 sigma, where A_32 is
 // the FP32-far-field operator (accurate to about 1e-6) and A_64 the
 // FP64-accurate precision-split operator; stops when ||r|| <= tol ||f||.
-// The FP32 GMRES may be deflated by a coarse space (coarse.cu): each
-// Arnoldi column A M v_j is then corrected to the deflated operator's, and
-// the cycle's correction V y to P V y before M is applied.
+// With a right preconditioner the z_j = M^{-1} v_j are kept and a cycle's
+// correction is Z y (the form of flexible GMRES), so an FP32 M adds no
+// rounding of its own to the correction. The FP32 GMRES may be deflated by
+// a coarse space (coarse.cu): each Arnoldi column A z_j is then corrected to
+// the deflated operator's, and the correction by the coarse term.
 #include <math.h>
 
 #include <algorithm>
@@ -202,6 +204,7 @@ void free_workspace(Workspace& w, cudaStream_t st) {
     dev_free(w.src4, st);
     dev_free(w.src4g, st);
     dev_free(w.V, st);
+    dev_free(w.Zp, st);
     dev_free(w.H, st);
     dev_free(w.gvec, st);
     dev_free(w.cs, st);
@@ -277,6 +280,7 @@ static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool
     double* r = w.vec[0];
     double* h1 = w.hbuf;
     double* h2 = w.hbuf + (m + 2);
+    if (pc && !w.Zp) YK_TRY(dev_alloc((void**)&w.Zp, sizeof(double) * (size_t)m * n, st));
     int total = 0;
     double res = INFINITY;
     bool have_x = !x_zero;
@@ -307,9 +311,10 @@ static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool
                 const int jj = j + b;
                 const double* vj = w.V + (int64_t)jj * n;
                 double* wv = w.V + (int64_t)(jj + 1) * n;
-                if (pc) {   // right preconditioning: w = A M^{-1} v_j
-                    YK_TRY(op.precond(vj, w.vec[6], prec == Prec::F32));
-                    YK_TRY(op.apply(w.vec[6], wv, prec));
+                if (pc) {   // right preconditioning: w = A z_j, z_j = M^{-1} v_j kept
+                    double* zj = w.Zp + (int64_t)jj * n;
+                    YK_TRY(op.precond(vj, zj, prec == Prec::F32));
+                    YK_TRY(op.apply(zj, wv, prec));
                 } else {
                     YK_TRY(op.apply(vj, wv, prec));
                 }
@@ -344,13 +349,12 @@ static int gmres(const KrylovOp& op, Prec prec, const double* b, double* x, bool
         }
         // x += V y
         YK_LAUNCH(k_tri_solve, 1, 32, 0, st, j, ldh, w.H, w.gvec, w.ybuf);
-        if (pc) {   // x += M^{-1} (V y)
-            double* t = w.vec[7];
-            YK_TRY_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, st));
-            YK_LAUNCH(k_add_basis, nb, 256, 0, st, t, w.V, n, j, w.ybuf);
-            if (defl) YK_TRY(op.deflate_end(j, w.ybuf, t));   // t = P V y
-            YK_TRY(op.precond(t, w.vec[6], prec == Prec::F32));
-            YK_LAUNCH(k_axpy1, nb, 256, 0, st, x, w.vec[6], n);
+        if (pc) {
+            // x += M^{-1} V y = Z y from the kept z_j (a fresh application of an
+            // FP32 M would add its own rounding to the correction); deflated:
+            // x += M^{-1} P V y = Z y - (M^{-1} Z_c) C sum_k y_k u_k
+            YK_LAUNCH(k_add_basis, nb, 256, 0, st, x, w.Zp, n, j, w.ybuf);
+            if (defl) YK_TRY(op.deflate_end(j, w.ybuf, x));
         } else {
             YK_LAUNCH(k_add_basis, nb, 256, 0, st, x, w.V, n, j, w.ybuf);
         }

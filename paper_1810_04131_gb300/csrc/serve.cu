@@ -64,7 +64,8 @@ struct Server {
     int device = 0;
 };
 
-// Device memory of one request: node arrays, Krylov basis, chunk partials,
+// Device memory of one request: node arrays, Krylov basis (and its
+// preconditioned copy), chunk partials,
 // scratch vectors, QBX rows, per shape (at most two) the two self blocks and
 // the FP64 + FP32 preconditioner inverse and the inner GMRES's coarse space
 // (an estimate with a safety factor).
@@ -76,7 +77,7 @@ static size_t request_bytes(const Request& r) {
     const size_t rows = npp * 9 * r.prm.n_gl * 2;
     const size_t blocks = 2 * npp * npp * (8 * 2 + 8 + 4);
     const size_t coarse = coarse_bytes(r.parts.data(), (int)r.parts.size(), r.prm);
-    return (size_t)(1.25 * (8.0 * (double)(n * (m + 1 + nchunk + 16) + rows) + (double)blocks +
+    return (size_t)(1.25 * (8.0 * (double)(n * (2 * m + 1 + nchunk + 16) + rows) + (double)blocks +
                             (double)coarse)) +
            (8u << 20);
 }

@@ -45,6 +45,7 @@ struct Workspace {
     float4* src4 = nullptr;      // pair-packed FP32 source records [np][ceil(npp/2)][2]
     float4* src4g = nullptr;     // the same for the normal derivative [np][ceil(npp/2)][3]
     double* V = nullptr;         // Krylov basis [(m+1)][n]
+    double* Zp = nullptr;        // preconditioned basis z_j = M^{-1} v_j [m][n] (on first use)
     double* H = nullptr;         // Hessenberg (m+1) x m, column-major
     double* gvec = nullptr;      // rotated rhs, m+1
     double* cs = nullptr;        // Givens cosines, m
@@ -342,7 +343,8 @@ struct KrylovOp {
     std::function<int(const double*, double*, bool)> precond;   // empty: none
     // Optional deflation of the FP32 inner solve (with precond): deflate(v_j,
     // w, j) turns w = A M v_j into the deflated operator's column, and
-    // deflate_end(k, y, t) turns t = V y (k basis vectors) into P V y.
+    // deflate_end(k, y, x) adds the coarse term of the cycle's correction
+    // (k basis vectors) to x.
     std::function<int(const double*, double*, int)> deflate;
     std::function<int(int, const double*, double*)> deflate_end;
 };
