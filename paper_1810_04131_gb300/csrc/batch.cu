@@ -8,8 +8,8 @@
 // the inner FP32 GMRES, which holds nearly all of the steps: the systems'
 // inner solves advance in lock step, and each step of the Arnoldi process
 // is ONE launch per kernel for all of them:
-//   M^-1 v_j (block preconditioner), the FP32 source records of that
-//   vector, the FP32 self block, the symmetric FP32 far field, the near
+//   z_j = M^-1 v_j (block preconditioner, kept: the solution is Z y), the
+//   FP32 source records of z_j, the FP32 self block, the symmetric FP32 far field, the near
 //   QBX rows (the operator of Eq. bie), the CGS2 dot products and
 //   projections, the Givens update and the normalisation.
 // A launch's grid covers the largest system; the blocks of smaller systems
@@ -43,7 +43,7 @@ constexpr int BATCH_STEPS = 4;   // Arnoldi steps per host look at most
 struct SysDesc {
     GeomView G;
     double *V, *H, *gv, *cs, *sn, *h1, *h2, *ybuf, *dotpart, *status, *hist;
-    double *t6, *t7, *extra;
+    double *Zp, *extra;   // Zp: kept z_j = M^-1 v_j [m][n]
     float4* rec;
     const float* minv32;
     const float* self32;
@@ -162,31 +162,33 @@ __global__ void kb_scale(const SysDesc* __restrict__ D, int j, int mode) {
     else S.V[(int64_t)(j + 1) * n + i] *= f;
 }
 
-// t6 = M^-1 (src 0: V_j, src 1: t7), FP32 block preconditioner
+// z_j = M^-1 V_j (FP32 block preconditioner), kept for the solution
 __global__ void __launch_bounds__(BAPPLY_ROWS * BAPPLY_SLICES)
-kb_precond(const SysDesc* __restrict__ D, int j, int src) {
+kb_precond(const SysDesc* __restrict__ D, int j) {
     extern __shared__ unsigned char kb_smem[];
     const SysDesc& S = D[blockIdx.z];
     if (!S.active || (int)blockIdx.x >= S.G.np || (int)blockIdx.y * BAPPLY_ROWS >= S.G.npp) return;
-    const double* x = src == 0 ? S.V + (int64_t)j * S.G.n : S.t7;
-    blocks_apply_tile<float, false>(S.G.npp, S.G.shape_of, S.minv32, x, S.t6, blockIdx.x,
+    blocks_apply_tile<float, false>(S.G.npp, S.G.shape_of, S.minv32, S.V + (int64_t)j * S.G.n,
+                                    S.Zp + (int64_t)j * S.G.n, blockIdx.x,
                                     blockIdx.y * BAPPLY_ROWS, kb_smem);
 }
 
-// extra = FP32 self block x t6 (own-particle far pairs)
-__global__ void __launch_bounds__(BAPPLY_ROWS * BAPPLY_SLICES) kb_self(const SysDesc* __restrict__ D) {
+// extra = FP32 self block x z_j (own-particle far pairs)
+__global__ void __launch_bounds__(BAPPLY_ROWS * BAPPLY_SLICES)
+kb_self(const SysDesc* __restrict__ D, int j) {
     extern __shared__ unsigned char kb_smem[];
     const SysDesc& S = D[blockIdx.z];
     if (!S.active || (int)blockIdx.x >= S.G.np || (int)blockIdx.y * BAPPLY_ROWS >= S.G.npp) return;
-    blocks_apply_tile<float, false>(S.G.npp, S.G.shape_of, S.self32, S.t6, S.extra, blockIdx.x,
-                                    blockIdx.y * BAPPLY_ROWS, kb_smem);
+    blocks_apply_tile<float, false>(S.G.npp, S.G.shape_of, S.self32, S.Zp + (int64_t)j * S.G.n,
+                                    S.extra, blockIdx.x, blockIdx.y * BAPPLY_ROWS, kb_smem);
 }
 
-// FP32 source records of t6
-__global__ void kb_src(const SysDesc* __restrict__ D) {
+// FP32 source records of z_j
+__global__ void kb_src(const SysDesc* __restrict__ D, int j) {
     const SysDesc& S = D[blockIdx.y];
     if (!S.active) return;
-    src_pairs_at(S.G, S.t6, S.kpf, S.rec, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    src_pairs_at(S.G, S.Zp + (int64_t)j * S.G.n, S.kpf, S.rec,
+                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // extra += symmetric FP32 far field of the records
@@ -197,12 +199,12 @@ __global__ void __launch_bounds__(F32_TPB, 6) kb_sym(const SysDesc* __restrict__
                      blockIdx.x);
 }
 
-// V_{j+1} = extra + near QBX rows x t6
+// V_{j+1} = extra + near QBX rows x z_j
 __global__ void kb_assemble(const SysDesc* __restrict__ D, int j) {
     const SysDesc& S = D[blockIdx.y];
     if (!S.active) return;
-    assemble_at(S.G, 0, nullptr, S.extra, S.G.cval, S.t6, S.V + (int64_t)(j + 1) * S.G.n,
-                blockIdx.x * (int64_t)BT + threadIdx.x);
+    assemble_at(S.G, 0, nullptr, S.extra, S.G.cval, S.Zp + (int64_t)j * S.G.n,
+                S.V + (int64_t)(j + 1) * S.G.n, blockIdx.x * (int64_t)BT + threadIdx.x);
 }
 
 // y = H(0:k1,0:k1)^-1 g(0:k1)
@@ -217,7 +219,8 @@ __global__ void kb_tri_solve(const SysDesc* __restrict__ D) {
     }
 }
 
-// t7 = sum_{k < k1} V_k y[k]
+// x = sum_{k < k1} z_k y[k] (the solution M^-1 V y from a zero start, from the
+// kept z_k, so that the FP32 preconditioner adds no rounding of its own)
 __global__ void kb_add_basis(const SysDesc* __restrict__ D) {
     const SysDesc& S = D[blockIdx.y];
     if (!S.active) return;
@@ -229,16 +232,8 @@ __global__ void kb_add_basis(const SysDesc* __restrict__ D) {
     const int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x;
     if (i >= n) return;
     double acc = 0.0;
-    for (int k = 0; k < S.k1; ++k) acc = fma(S.V[(int64_t)k * n + i], ys[k], acc);
-    S.t7[i] = acc;
-}
-
-// x = t6 (the solution M^-1 V y from a zero start)
-__global__ void kb_finish(const SysDesc* __restrict__ D) {
-    const SysDesc& S = D[blockIdx.y];
-    if (!S.active) return;
-    const int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x;
-    if (i < S.G.n) S.x[i] = S.t6[i];
+    for (int k = 0; k < S.k1; ++k) acc = fma(S.Zp[(int64_t)k * n + i], ys[k], acc);
+    S.x[i] = acc;
 }
 
 // out[s][0] = status[1] (mode 0), or out[s][2 b + {0,1}] = hist[2 (j0 + b) + {0,1}], b < k
@@ -332,8 +327,8 @@ static int batched_gmres(std::vector<Inner>& sys, const std::vector<const double
         d.dotpart = w.dotpart;
         d.status = w.status;
         d.hist = w.hist;
-        d.t6 = w.vec[6];
-        d.t7 = w.vec[7];
+        if (!w.Zp) YK_TRY(dev_alloc((void**)&w.Zp, sizeof(double) * (size_t)w.m * g->n, st));
+        d.Zp = w.Zp;
         d.extra = w.vec[5];
         d.rec = w.src4;
         d.minv32 = g->d_minv32;
@@ -411,9 +406,9 @@ static int batched_gmres(std::vector<Inner>& sys, const std::vector<const double
         const int k = std::min(batch, room);
         for (int q = 0; q < k && rc == YK_OK; ++q) {
             const int jj = j + q;
-            YK_LAUNCH(kb_precond, gblk, BAPPLY_ROWS * BAPPLY_SLICES, smem, st, D, jj, 0);
-            YK_LAUNCH(kb_src, dim3(npairs, ns), BT, 0, st, D);
-            YK_LAUNCH(kb_self, gblk, BAPPLY_ROWS * BAPPLY_SLICES, smem, st, D);
+            YK_LAUNCH(kb_precond, gblk, BAPPLY_ROWS * BAPPLY_SLICES, smem, st, D, jj);
+            YK_LAUNCH(kb_src, dim3(npairs, ns), BT, 0, st, D, jj);
+            YK_LAUNCH(kb_self, gblk, BAPPLY_ROWS * BAPPLY_SLICES, smem, st, D, jj);
             if (max_sym > 0) YK_LAUNCH(kb_sym, dim3(max_sym, ns), F32_TPB, 0, st, D);
             YK_LAUNCH(kb_assemble, dim3(nb, ns), BT, 0, st, D, jj);
             for (int pass = 0; pass < 2; ++pass) {   // CGS2
@@ -456,7 +451,7 @@ static int batched_gmres(std::vector<Inner>& sys, const std::vector<const double
         }
         j += k;
     }
-    // x = M^-1 V y for every system with steps (x = 0 for the others)
+    // x = M^-1 V y = Z y for every system with steps (x = 0 for the others)
     if (rc == YK_OK) {
         for (int s = 0; s < ns; ++s) {
             if (sys[s].steps > 0) YK_LAUNCH(kb_set, 1, 32, 0, st, D, s, 1, sys[s].steps);
@@ -465,8 +460,6 @@ static int batched_gmres(std::vector<Inner>& sys, const std::vector<const double
         }
         YK_LAUNCH(kb_tri_solve, ns, 32, 0, st, D);
         YK_LAUNCH(kb_add_basis, dim3(nb, ns), BT, 0, st, D);
-        YK_LAUNCH(kb_precond, gblk, BAPPLY_ROWS * BAPPLY_SLICES, smem, st, D, 0, 1);
-        YK_LAUNCH(kb_finish, dim3(nb, ns), BT, 0, st, D);
         if (cudaGetLastError() != cudaSuccess) rc = YK_ERR_CUDA;
     }
     dev_free(D, st);
