@@ -962,7 +962,10 @@ def main():
                "solve": {"iterations": info["iterations"], "refinements": info["refinements"],
                          "rel_residual": info["rel_residual"],
                          "matvecs_fp32": info["matvecs_fp32"],
-                         "matvecs_fp64": info["matvecs_fp64"]},
+                         "matvecs_fp64": info["matvecs_fp64"],
+                         "coarse_dim": info["coarse_dim"],
+                         "preconditioner": "block Jacobi (inverse self blocks), inner GMRES "
+                                           "deflated by 3 density modes per particle"},
                "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
                "gpu_launches": int(launches), "clocks": clk, "leg_seconds": legt.t}
         out.update(extra)
