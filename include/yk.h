@@ -294,10 +294,15 @@ int yk_normal_derivative(yk_geom* g, const double* sigma, double* u_nu, int prec
 
 /* Solve 1/2 sigma + D sigma = f (Eq. bie) by restarted GMRES (YK_FP64) or
  * FP64 iterative refinement over FP32-operator GMRES (YK_MIXED), as set in
- * the geometry's parameters. sigma0 (N, nullable) is an initial guess
- * (warm start); sigma (N) receives the solution; info (host, nullable)
- * receives statistics. Returns YK_ERR_NOT_CONVERGED if the tolerance was
- * not reached (sigma then holds the last iterate).                        */
+ * the geometry's parameters: right block preconditioner (precond), and for
+ * YK_MIXED the inner GMRES deflated by the coarse space (coarse). The
+ * stopping test is on the FP64 residual ||f - A sigma|| / ||f|| of the
+ * plain operator, whatever preconditions the inner solve. sigma0 (N,
+ * nullable) is an initial guess (warm start); sigma (N) receives the
+ * solution; info (host, nullable) receives statistics. Returns
+ * YK_ERR_NOT_CONVERGED if the tolerance was not reached (sigma then holds
+ * the last iterate). The first solve on a geometry allocates its Krylov
+ * bases; a solve after the particles moved rebuilds the coarse space.     */
 int yk_solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
              yk_solve_info* info);
 
