@@ -301,8 +301,9 @@ int yk_normal_derivative(yk_geom* g, const double* sigma, double* u_nu, int prec
  * nullable) is an initial guess (warm start); sigma (N) receives the
  * solution; info (host, nullable) receives statistics. Returns
  * YK_ERR_NOT_CONVERGED if the tolerance was not reached (sigma then holds
- * the last iterate). The first solve on a geometry allocates its Krylov
- * bases; a solve after the particles moved rebuilds the coarse space.     */
+ * the last iterate). The first preconditioned solve on a geometry
+ * allocates the preconditioned Krylov basis (gmres_restart x N doubles) and
+ * the coarse space; a solve after the particles moved rebuilds the latter. */
 int yk_solve(yk_geom* g, const double* f, double* sigma, const double* sigma0,
              yk_solve_info* info);
 
